@@ -1,0 +1,206 @@
+"""Seeded synthetic workloads shaped like the paper's particle problems.
+
+This module only *generates inputs*: voxel phase maps, the influx source field, the
+initial concentration and optional per-voxel log-scale fields, plus the material
+constants and solver tolerances of each workload.  It holds none of the method's
+arithmetic, so both the CUDA path and the CPU oracle can be fed from it.
+
+Geometry follows the paper's set-up: one active particle embedded in a compliant,
+almost non-diffusive buffer phase that emulates the surrounding electrolyte
+(Sec. 4.3, Sec. 5.1), with the ion influx imposed as a volume source in a band of
+width dL just inside the particle surface (Eqs. neumann1, neumann2).  All random
+numbers come from ``numpy.random.Generator(PCG64(seed))``.
+
+Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
+
+* ``disc2d``    64x64x1 plane strain, disc radius 20, band 6 voxels, 10 steps.
+* ``ellipsoid`` 128^3, semi-axes 50/40/35 with a Gaussian-filtered rough surface
+  (std 1.5 voxels, correlation length 4 voxels), band 8 voxels, 50 steps.
+* ``ellipsoid`` at 256^3 scaled x2 (semi-axes 100/80/70, roughness std 3,
+  correlation 8) plus a Gaussian concentration perturbation of std 0.02, 100 steps.
+* ``spheres``   64 RVEs with edge N in {48, 64, 80, 96} and sphere radius
+  U(0.30, 0.45) N.
+* ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LAW_SVK = 0
+LAW_NEOHOOKE = 1
+PARTICLE = 0
+BUFFER = 1
+
+
+@dataclass
+class PhaseSpec:
+    law: int = LAW_NEOHOOKE
+    E: float = 10e9
+    nu: float = 0.3
+    Omega: float = 0.0
+    c0: float = 0.01
+    D: float = 1e-14
+    sigma_max: float = 100e6
+
+
+@dataclass
+class Workload:
+    name: str
+    shape: tuple                 # (nz, ny, nx)
+    h: tuple                     # (hx, hy, hz) in m
+    phases: list                 # [PhaseSpec(particle), PhaseSpec(buffer)]
+    phase_id: np.ndarray         # uint8 (nz, ny, nx)
+    cdot_B: np.ndarray           # float64 (nz, ny, nx), 1/s
+    c_init: np.ndarray           # float64 (nz, ny, nx)
+    gc: float                    # J/m^2
+    lc: float                    # m
+    dt: float                    # s
+    nsteps: int
+    log_E: np.ndarray | None = None
+    log_gc: np.ndarray | None = None
+    log_D: np.ndarray | None = None
+    RT: float = 8.314462618 * 298.15
+    cmax: float = 3.0e4
+    tol: dict = field(default_factory=lambda: dict(
+        tol_newton=1e-9, tol_cg=1e-10, tol_chem=1e-9, tol_chem_cg=1e-10, tol_pff_cg=1e-10,
+        tol_stag=1e-9, max_newton=30, max_cg=5000, max_chem_newton=50, max_stag=50))
+
+    @property
+    def nvox(self):
+        return int(np.prod(self.shape))
+
+
+def default_phases(E=10e9, nu=0.3, c0=0.01, D=1e-14, sigma_max=100e6, vol_change=0.10,
+                   buffer_E=1e-3, buffer_D=1e-5, law=LAW_NEOHOOKE):
+    """Particle and buffer constants.  The swelling coefficient gives ``vol_change`` of
+    volume change at c = 1 relative to the stress-free c0: Omega = vol_change/(1-c0)."""
+    omega = vol_change / (1.0 - c0)
+    particle = PhaseSpec(law=law, E=E, nu=nu, Omega=omega, c0=c0, D=D, sigma_max=sigma_max)
+    buffer = PhaseSpec(law=law, E=E * buffer_E, nu=nu, Omega=0.0, c0=c0, D=D * buffer_D,
+                       sigma_max=sigma_max)
+    return [particle, buffer]
+
+
+def _grid_coords(shape):
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cz, cy, cx = (nz - 1) / 2.0, (ny - 1) / 2.0, (nx - 1) / 2.0
+    return x - cx, y - cy, z - cz
+
+
+def influx_band(particle, width):
+    """Particle voxels whose Euclidean distance to the nearest buffer voxel is <= width."""
+    from scipy import ndimage
+    if particle.shape[0] == 1:
+        dist = ndimage.distance_transform_edt(particle[0])[None]
+    else:
+        dist = ndimage.distance_transform_edt(particle)
+    return particle & (dist <= width)
+
+
+def _rough_field(rng, shape, std, corr):
+    from scipy import ndimage
+    noise = rng.standard_normal(shape)
+    sm = ndimage.gaussian_filter(noise, sigma=corr, mode="wrap")
+    sd = sm.std()
+    return sm * (std / sd) if sd > 0 else sm
+
+
+def _finish(name, shape, h, particle, band_width, nsteps, dt, rng, phases=None, c_perturb=0.0,
+            target_c=0.5, gc=1.0, lc_vox=2.0):
+    phases = phases or default_phases()
+    phase_id = np.where(particle, PARTICLE, BUFFER).astype(np.uint8)
+    band = influx_band(particle, band_width)
+    c0 = phases[PARTICLE].c0
+    # influx rate: the band alone would reach target_c at the last step without diffusion
+    rate = (target_c - c0) / (dt * nsteps)
+    cdot_B = np.where(band, rate, 0.0)
+    c_init = np.full(shape, c0)
+    if c_perturb > 0.0:
+        pert = rng.normal(0.0, c_perturb, size=shape)
+        c_init = np.where(particle, np.clip(c0 + pert, 0.005, 0.995), c0)
+    return Workload(name=name, shape=shape, h=h, phases=phases, phase_id=phase_id,
+                    cdot_B=cdot_B, c_init=c_init, gc=gc, lc=lc_vox * h[0], dt=dt, nsteps=nsteps)
+
+
+def disc2d(n=64, radius=20.0, band=6, nsteps=10, seed=0, h=0.1e-6, **kw):
+    """2D plane-strain disc particle in a buffer matrix (configuration of Sec. 5.1 type)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (1, n, n)
+    x, y, _ = _grid_coords(shape)
+    particle = (x * x + y * y) <= radius * radius
+    return _finish("disc2d", shape, (h, h, h), particle, band, nsteps, 1.0, rng, **kw)
+
+
+def ellipsoid(n=128, axes=(50.0, 40.0, 35.0), rough_std=1.5, rough_corr=4.0, band=8,
+              nsteps=50, seed=0, h=0.1e-6, c_perturb=0.0, shape=None, **kw):
+    """3D ellipsoidal particle with a seeded rough surface: voxel x is particle when
+    (rho(x) - 1) R_min <= eta(x), rho the ellipsoidal radius and eta the roughness."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = shape or (n, n, n)
+    x, y, z = _grid_coords(shape)
+    a, b, c = axes
+    rho = np.sqrt((x / a) ** 2 + (y / b) ** 2 + (z / c) ** 2)
+    eta = _rough_field(rng, shape, rough_std, rough_corr) if rough_std > 0 else 0.0
+    particle = (rho - 1.0) * min(axes) <= eta
+    return _finish("ellipsoid", shape, (h, h, h), particle, band, nsteps, 1.0, rng,
+                   c_perturb=c_perturb, **kw)
+
+
+def ellipsoid256(seed=0, nsteps=100, **kw):
+    return ellipsoid(n=256, axes=(100.0, 80.0, 70.0), rough_std=3.0, rough_corr=8.0, band=8,
+                     nsteps=nsteps, seed=seed, c_perturb=0.02, **kw)
+
+
+def sphere(n, radius_frac, band=4, nsteps=20, seed=0, h=0.1e-6, **kw):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (n, n, n)
+    x, y, z = _grid_coords(shape)
+    particle = (x * x + y * y + z * z) <= (radius_frac * n) ** 2
+    return _finish("sphere", shape, (h, h, h), particle, band, nsteps, 1.0, rng, **kw)
+
+
+def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=20, seed=0):
+    """Independent particle RVEs of uneven size (one persistent batch)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.choice(np.array(sizes), size=count)
+    rs = rng.uniform(rmin, rmax, size=count)
+    return [sphere(int(n), float(r), nsteps=nsteps, seed=seed + 1 + i)
+            for i, (n, r) in enumerate(zip(ns, rs))]
+
+
+def with_log_fields(w, std=0.1, seed=0):
+    """Attach per-voxel log-stiffness, log-toughness and log-diffusivity ~ N(0, std^2)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    w.log_E = rng.normal(0.0, std, size=w.shape)
+    w.log_gc = rng.normal(0.0, std, size=w.shape)
+    w.log_D = rng.normal(0.0, std, size=w.shape)
+    return w
+
+
+def random_state(shape, seed=0, f_amp=0.03, c_lo=0.05, c_hi=0.6, d_hi=0.5):
+    """Random but physical fields for operator tests: F = I + small perturbation,
+    c in (c_lo, c_hi), d in [0, d_hi)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    F = np.zeros((3, 3) + tuple(shape))
+    for i in range(3):
+        F[i, i] = 1.0
+    F = F + f_amp * rng.standard_normal(F.shape)
+    if shape[0] == 1:  # plane strain: no out-of-plane shear
+        F[0, 2] = F[1, 2] = F[2, 0] = F[2, 1] = 0.0
+    c = rng.uniform(c_lo, c_hi, size=shape)
+    d = rng.uniform(0.0, d_hi, size=shape)
+    return F, c, d
+
+
+def random_tensor_field(shape, seed=0, ncomp=9):
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    return rng.standard_normal((ncomp,) + tuple(shape))
+
+
+def random_phase_map(shape, seed=0, frac=0.5):
+    rng = np.random.Generator(np.random.PCG64(seed + 15485863))
+    return (rng.uniform(size=shape) > frac).astype(np.uint8)

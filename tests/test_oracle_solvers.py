@@ -1,0 +1,262 @@
+"""Pins of the oracle's solvers (Alg. 1-4) against closed forms, brute force and
+invariants that the paper's set-up fixes."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fg_oracle as O
+
+RNG = np.random.default_rng(7)
+H = (1e-7, 1e-7, 1e-7)
+
+
+def two_phase(shape, pid, law=O.LAW_NEOHOOKE, E=(10e9, 2e9), omega=(0.2, 0.0)):
+    phases = [O.Phase(law=law, E=E[0], nu=0.3, Omega=omega[0], c0=0.01, D=1e-14),
+              O.Phase(law=law, E=E[1], nu=0.25, Omega=omega[1], c0=0.01, D=1e-16)]
+    return O.make_params(phases, pid, H, gc=1.0, lc=2e-7)
+
+
+def identity(shape):
+    F = np.zeros((3, 3) + shape)
+    for i in range(3):
+        F[i, i] = 1.0
+    return F
+
+
+# ---------------------------------------------------------------- mechanics (Alg. 1)
+
+def test_homogeneous_medium_is_uniform_in_one_iteration():
+    shape = (4, 4, 4)
+    prm = two_phase(shape, np.zeros(shape, dtype=int))
+    c = np.full(shape, 0.3)
+    d = np.full(shape, 0.2)
+    Fbar = np.array([[1.02, 0.01, 0.0], [0.0, 0.99, 0.005], [0.0, 0.0, 1.01]])
+    F0 = np.broadcast_to(Fbar.reshape(3, 3, 1, 1, 1), (3, 3) + shape).copy()
+    stats = {}
+    F, err = O.mech_newton(F0, c, d, prm, Fbar, 1e-9, 1e-10, 5, 100, stats)
+    assert err <= 1e-9 and stats.get("newton_mech", 0) == 0
+    np.testing.assert_array_equal(F, F0)
+
+
+@pytest.mark.parametrize("law", [O.LAW_NEOHOOKE, O.LAW_SVK])
+def test_laminate_closed_form(law):
+    """Phases alternate along x: the exact discrete solution is F = diag(l(x), 1, 1) with
+    P_xx equal in both layers and the mean stretch prescribed.  The layer stretches are
+    found here by bisection on the scalar uniaxial stress of each law."""
+    shape = (2, 3, 8)
+    pid = np.zeros(shape, dtype=int)
+    pid[:, :, 3:] = 1  # f1 = 3/8, f2 = 5/8
+    prm = two_phase(shape, pid, law=law)
+    c = np.where(pid == 0, 0.4, 0.01)  # swelling mismatch in layer 1
+    d = np.where(pid == 0, 0.1, 0.0)
+    Fbar = np.diag([1.01, 1.0, 1.0])
+
+    def pxx(lmb, ph, cc, dd):
+        E, nu, om = [(10e9, 0.3, 0.2), (2e9, 0.25, 0.0)][ph]
+        lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+        mu = E / (2 * (1 + nu))
+        a = (1 + om * (cc - 0.01)) ** (-1 / 3)
+        le = a * lmb
+        if law == O.LAW_NEOHOOKE:
+            p0 = mu * (le - 1 / le) + lam * math.log(a ** 3 * lmb) / le
+        else:
+            exx, eyy = 0.5 * (le * le - 1), 0.5 * (a * a - 1)
+            p0 = le * (lam * (exx + 2 * eyy) + 2 * mu * exx)
+        return (1 - dd) ** 2 * a * p0
+
+    f1, f2 = 3 / 8, 5 / 8
+    g = lambda l1: pxx(l1, 0, 0.4, 0.1) - pxx((1.01 - f1 * l1) / f2, 1, 0.01, 0.0)
+    lo, hi = 0.9, 1.1
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(lo) * g(mid) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    l1 = 0.5 * (lo + hi)
+    l2 = (1.01 - f1 * l1) / f2
+    F0 = identity(shape)
+    F0[0, 0] = 1.01
+    F, err = O.mech_newton(F0, c, d, prm, Fbar, 1e-12, 1e-13, 20, 500)
+    ref = np.where(pid == 0, l1, l2)
+    np.testing.assert_allclose(F[0, 0], ref, rtol=1e-10)
+    np.testing.assert_allclose(F[1, 1], 1.0, atol=1e-12)
+    np.testing.assert_allclose(F[2, 2], 1.0, atol=1e-12)
+    P = O.stress(F, c, d, prm)
+    np.testing.assert_allclose(P[0, 0], P[0, 0].mean(), rtol=1e-9)
+
+
+def test_cg_matches_dense_solve():
+    """Assemble G K G on a 4x4x2 grid column by column and solve it densely (minimum
+    norm least squares: the operator is singular on incompatible fields)."""
+    shape = (2, 4, 4)
+    pid = RNG.integers(0, 2, size=shape)
+    prm = two_phase(shape, pid)
+    F = identity(shape) + 0.03 * RNG.standard_normal((3, 3) + shape)
+    c = RNG.uniform(0.05, 0.5, shape)
+    d = RNG.uniform(0.0, 0.4, shape)
+    n = 9 * int(np.prod(shape))
+    op = lambda x: O.apply_G(O.tangent_apply(F, c, d, prm, O.apply_G(x, H)), H)
+    M = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        M[:, k] = op(e.reshape((3, 3) + shape)).ravel()
+    assert np.allclose(M, M.T, atol=1e-6 * np.abs(M).max())
+    b = -O.apply_G(O.stress(F, c, d, prm), H)
+    x_dense = np.linalg.lstsq(M, b.ravel(), rcond=1e-10)[0]
+    x_cg, _ = O.cg(lambda x: O.mech_apply(F, c, d, prm, x), b, 1e-13, 2000)
+    np.testing.assert_allclose(x_cg.ravel(), x_dense, atol=1e-9 * np.abs(x_dense).max())
+
+
+# ---------------------------------------------------------------- phase field (Alg. 2)
+
+def pff_params(shape, lc=2e-7, gc=1.0):
+    phases = [O.Phase()]
+    return O.make_params(phases, np.zeros(shape, dtype=int), H, gc=gc, lc=lc)
+
+
+def test_pff_uniform_history_closed_form_one_iteration():
+    shape = (4, 6, 8)
+    prm = pff_params(shape)
+    Hh = np.full(shape, 3.7e6)
+    stats = {}
+    d = O.pff_solve(Hh, np.zeros(shape), prm, 1e-12, 50, stats)
+    ref = 2 * 3.7e6 / (prm.gc / prm.lc + 2 * 3.7e6)
+    np.testing.assert_allclose(d, ref, rtol=1e-12)
+    assert stats["cg_pff"] == 1
+
+
+def test_pff_1d_crack_discrete_closed_form():
+    """History on the plane x = 0 only: off the plane the discrete equation is
+    d_{j+1} + d_{j-1} = (2 + h^2/l^2) d_j, so d_j = A (r^j + r^{N-j}) with
+    r + 1/r = 2 + h^2/l^2; A follows from the equation on the plane."""
+    N = 32
+    shape = (1, 2, N)
+    lc = 2e-7
+    prm = pff_params(shape, lc=lc)
+    h = H[0]
+    Hh = np.zeros(shape)
+    H0 = 5e7
+    Hh[..., 0] = H0
+    d = O.pff_solve(Hh, np.zeros(shape), prm, 1e-14, 500)
+    t = 2 + h * h / (lc * lc)
+    r = (t - math.sqrt(t * t - 4)) / 2
+    j = np.arange(N)
+    prof = r ** j + r ** (N - j)
+    # plane equation: (gc/lc + 2H0) d0 - gc lc (d1 - 2 d0 + d_{N-1}) / h^2 = 2 H0
+    coef = (prm.gc / prm.lc + 2 * H0) * prof[0] - prm.gc * prm.lc * (prof[1] - 2 * prof[0] + prof[N - 1]) / h ** 2
+    A = 2 * H0 / coef
+    np.testing.assert_allclose(d[0, 0], A * prof, rtol=1e-10)
+    np.testing.assert_allclose(d[0, 1], A * prof, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- chemistry (Alg. 3)
+
+def shift(u, axis_xyz, s):
+    return np.roll(u, -s, axis=-1 - axis_xyz)
+
+
+def test_chem_operator_is_divergence_stencil():
+    """L u = -sum_j [flux_j(x) - flux_j(x - e_j)] / h_j with flux = K grad_f u,
+    grad_f the forward difference, for a random symmetric K field."""
+    shape = (3, 4, 6)
+    h = (0.9e-7, 1.1e-7, 1.0e-7)
+    prm = O.make_params([O.Phase()], np.zeros(shape, dtype=int), h, gc=1.0, lc=2e-7)
+    A = RNG.standard_normal((3, 3) + shape)
+    K = np.einsum("ik...,jk...->ij...", A, A) * 1e-14
+    u = RNG.standard_normal(shape)
+    g = np.stack([(shift(u, j, 1) - u) / h[j] for j in range(3)])
+    flux = np.einsum("jl...,l...->j...", K, g)
+    ref = -sum((flux[j] - shift(flux[j], j, -1)) / h[j] for j in range(3))
+    np.testing.assert_allclose(O.chem_L(u, K, prm), ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+def _chem_mode_setup(n, amp, kx=1):
+    shape = (1, 1, n)
+    L = 1.0e-6
+    h = (L / n, L / n, L / n)
+    phases = [O.Phase(Omega=0.0, D=1e-14)]
+    prm = O.make_params(phases, np.zeros(shape, dtype=int), h, gc=1.0, lc=2e-7)
+    x = np.arange(n) * h[0]
+    k = 2 * np.pi * kx / L
+    c_t = 0.3 + amp * np.cos(k * x)
+    return prm, c_t.reshape(shape), k, h
+
+
+def test_chem_single_mode_decay():
+    """Small-amplitude Fourier mode, no swelling, F = I, d = 0: each backward-Euler step
+    multiplies the amplitude by 1/(1 + 0.9 D dt |xi|^2) (0.9 = phi(0) of Eq. mobility),
+    to first order in the amplitude."""
+    n, amp = 16, 1e-6
+    prm, c_t, k, h = _chem_mode_setup(n, amp)
+    F = identity(c_t.shape)
+    dt = 0.5
+    c = O.chem_solve(c_t, F, np.zeros_like(c_t), dt, np.zeros_like(c_t), prm, 1e-13, 1e-14, 30, 200)
+    xi2 = 4 * math.sin(math.pi / n) ** 2 / h[0] ** 2
+    fac = 1.0 / (1.0 + 0.9 * 1e-14 * dt * xi2)
+    amp_new = 2 * np.abs(np.fft.rfft(c.ravel())[1]) / n
+    assert abs(amp_new / amp - fac) < 1e-5
+    np.testing.assert_allclose(c.mean(), c_t.mean(), rtol=1e-14)
+
+
+def test_chem_mode_converges_to_continuum_decay():
+    """Refining h and dt together, the decay approaches exp(-0.9 D k^2 t) (first order
+    in dt)."""
+    errs = []
+    for n, steps in [(16, 4), (32, 8), (64, 16)]:
+        prm, c, k, h = _chem_mode_setup(n, 1e-6)
+        T = 0.2 / (0.9 * 1e-14 * k * k)
+        dt = T / steps
+        F = identity(c.shape)
+        z = np.zeros_like(c)
+        for _ in range(steps):
+            c = O.chem_solve(c, F, z, dt, z, prm, 1e-13, 1e-14, 30, 400)
+        amp = 2 * np.abs(np.fft.rfft(c.ravel())[1]) / n / 1e-6
+        errs.append(abs(amp - math.exp(-0.2)))
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1]
+    assert errs[2] < 5e-3
+
+
+def test_chem_mass_balance_with_source():
+    shape = (2, 6, 8)
+    pid = RNG.integers(0, 2, size=shape)
+    phases = [O.Phase(Omega=0.15, D=1e-14), O.Phase(E=1e7, Omega=0.0, D=1e-19)]
+    prm = O.make_params(phases, pid, H, gc=1.0, lc=2e-7)
+    c_t = RNG.uniform(0.02, 0.3, shape)
+    F = identity(shape) + 0.01 * RNG.standard_normal((3, 3) + shape)
+    d_t = RNG.uniform(0, 0.3, shape)
+    src = np.where(RNG.uniform(size=shape) < 0.3, 0.05, 0.0)
+    dt = 1.0
+    c = O.chem_solve(c_t, F, d_t, dt, src, prm, 1e-12, 1e-13, 50, 500)
+    assert abs(c.mean() - (c_t.mean() + dt * src.mean())) < 1e-12
+    Kc = O.chem_conductivity(F, c_t, d_t, prm)
+    f = O.chem_residual(c, c_t, F, d_t, Kc, dt, src, prm)
+    assert np.abs(f).max() < 1e-10
+
+
+# ---------------------------------------------------------------- coupled step (Alg. 4)
+
+@pytest.mark.slow
+def test_coupled_steps_invariants():
+    shape = (1, 16, 16)
+    y, x = np.meshgrid(np.arange(16) - 7.5, np.arange(16) - 7.5, indexing="ij")
+    part = (x * x + y * y <= 36.0)[None]
+    pid = np.where(part, 0, 1)
+    phases = [O.Phase(E=10e9, Omega=0.1 / 0.99, D=1e-14, sigma_max=25e6),
+              O.Phase(E=10e6, Omega=0.0, D=1e-19, sigma_max=25e6)]
+    prm = O.make_params(phases, pid, H, gc=1.0, lc=2e-7)
+    src = np.where(part & ~((x * x + y * y) <= 9.0)[None], 0.05, 0.0)
+    st = O.CoupledState(prm, np.full(shape, 0.01), src)
+    Hprev = st.H.copy()
+    for _ in range(3):
+        m0 = st.c.mean()
+        stats = st.step(1.0, np.eye(3))
+        assert abs(st.c.mean() - (m0 + src.mean())) < 1e-11
+        assert np.all(st.H >= Hprev)
+        assert st.d.min() >= -1e-12 and st.d.max() < 1.0
+        _, err = O.mech_residual(st.F, st.c, st.d, prm, np.eye(3))
+        assert err <= 1e-9
+        Hprev = st.H.copy()
+    assert st.H.max() > 0.0  # the band's swelling mismatch reaches the damage threshold
