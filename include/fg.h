@@ -1,0 +1,179 @@
+/*
+ * fg.h -- C ABI of the GB300 FFT chemo-mechanical fracture solver.
+ *
+ * The library advances the three coupled fields of the paper "An FFT based
+ * chemo-mechanical framework with fracture" (arXiv 2411.16583): the deformation
+ * gradient F, the ion concentration c and the phase field d, on a periodic
+ * nx x ny x nz voxel grid (Sec. 3.1, Eq. Fsplit).  Each time step is the paper's
+ * global staggered scheme (Alg. 4): one backward-Euler Newton-CG solve of the Fick
+ * problem (Alg. 3), then mechanical Newton-CG (Alg. 1) and phase-field PCG (Alg. 2)
+ * repeated until the equilibrium residual (Eq. mechresiduum) is below tolerance.
+ * Every Krylov iteration applies a matrix-free Fourier operator (Eqs. mechanicalsolve,
+ * PFFA, PFFprecond, ChemresidualFourier_A) built from the library's own CUDA FFT.
+ *
+ * Conventions
+ *   - Voxel arrays are x-fastest: index (z * ny + y) * nx + x.  A tensor field is
+ *     9 such arrays back to back, component (i, j) at offset (3 i + j) * V.
+ *   - nz = 1 is plane strain.  nx must be even; nx, ny, nz must be among the
+ *     transform lengths the library was built for (fg_supported_size).
+ *   - Host arrays passed to fg_setup are copied; the caller keeps ownership.
+ *   - Device pointers passed to fg_apply / fg_get_field(on_device=1) belong to the
+ *     caller and must hold the stated number of elements.
+ *   - All GPU work is enqueued on opts.cuda_stream (NULL: the legacy default stream);
+ *     calls return after that work has completed unless stated otherwise.
+ *   - Functions return FG_OK (0) or a negative FG_ERR_* code, and never throw;
+ *     fg_last_error() gives the calling thread's last message.
+ */
+#ifndef FG_H
+#define FG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FG_OK 0
+#define FG_ERR_INVALID (-1) /* bad argument, size or unsupported option */
+#define FG_ERR_OOM (-2)     /* device allocation failed */
+#define FG_ERR_CUDA (-3)    /* a CUDA call failed */
+#define FG_ERR_NOCONV (-4)  /* a Newton, Krylov or staggered loop hit its cap */
+#define FG_ERR_DOMAIN (-5)  /* c left (0, 1) or det F / J_c <= 0 */
+#define FG_ERR_NUMERIC (-6) /* NaN or Inf met, or a Krylov operator was not positive */
+
+#define FG_SVK 0       /* Saint-Venant-Kirchhoff (Eqs. Ee, psie0) */
+#define FG_NEOHOOKE 1  /* compressible Neo-Hookean */
+
+#define FG_FP64 0      /* every operator and solve in FP64 */
+#define FG_MIXED 1     /* FP32 Krylov operators, FP64 residuals and updates */
+
+/* operators of fg_apply */
+#define FG_OP_MECH 0     /* y = F^-1[G : F[K : x]]          (9 comps, Eq. mechanicalsolve) */
+#define FG_OP_PFF 1      /* y = A(x) of Eq. PFFA            (1 comp) */
+#define FG_OP_PFF_PREC 2 /* y = P(x) of Eq. PFFprecond      (1 comp) */
+#define FG_OP_CHEM 3     /* y = x c(1-c) + dt L x, the Newton operator of Eq. Chemderfc
+                            in the variable x = dc / (c (1-c))   (1 comp) */
+#define FG_OP_GRES 4     /* y = F^-1[G : F[x]], FP64 only   (9 comps, Eq. mechresiduum) */
+
+/* fields of fg_get_field / fg_set_field */
+#define FG_FIELD_C 0  /* concentration, V doubles */
+#define FG_FIELD_F 1  /* deformation gradient, 9 V doubles */
+#define FG_FIELD_D 2  /* phase field, V doubles */
+#define FG_FIELD_H 3  /* history H, V doubles */
+#define FG_FIELD_P 4  /* first Piola stress of the current (F, c, d), 9 V doubles (get) */
+
+typedef struct {
+  int nx, ny, nz;        /* voxels per axis */
+  double hx, hy, hz;     /* voxel size per axis (m) */
+} fg_grid;
+
+typedef struct {
+  int law;           /* FG_NEOHOOKE (GPU path); FG_SVK is rejected with FG_ERR_INVALID */
+  double E, nu;      /* Young's modulus (Pa), Poisson ratio */
+  double Omega;      /* swelling: J_c = 1 + Omega (c - c0) (Eq. Fc) */
+  double c0;         /* stress-free concentration */
+  double D;          /* diffusivity (m^2/s) (Eq. mobility) */
+  double sigma_max;  /* damage threshold stress (Pa) (Eq. SigDrivingForce) */
+} fg_phase;
+
+typedef struct {
+  int precision;      /* FG_FP64 or FG_MIXED */
+  double gc, lc;      /* fracture toughness (J/m^2), length scale (m) (Eq. PFF) */
+  double RT;          /* gas constant x temperature (J/mol) */
+  double cmax;        /* molar density scaling mu_e (mol/m^3) */
+  double tol_newton;  /* mechanical Newton tolerance on err_res */
+  double tol_cg;      /* relative Krylov tolerance (FP64 mode; mixed mode: floor) */
+  double tol_chem;    /* ||dc|| / ||c_t|| (Eq. Chemerror) */
+  double tol_chem_cg; /* relative Krylov tolerance of the chemistry solve */
+  double tol_pff_cg;  /* relative tolerance of the phase-field solve */
+  double tol_stag;    /* staggered loop: err_res threshold */
+  double cg_forcing;  /* mixed mode: relative tolerance of each FP32 inner solve */
+  int max_newton, max_cg, max_chem_newton, max_stag;
+  void* cuda_stream;  /* cudaStream_t, NULL for the legacy default stream */
+} fg_opts;
+
+typedef struct {
+  int newton_chem, newton_mech, cg_chem, cg_mech, cg_pff, stag;
+  int inner_refine;   /* FP64 residual refinements of mixed-mode phase-field solves */
+  double err_mech;    /* final err_res */
+  double err_chem;    /* final ||dc|| / ||c_t|| */
+  double mass;        /* sum of c after the step */
+  double mass_err;    /* sum c - (sum c_t + dt sum cdot_B), relative to sum c */
+  int status;         /* FG_OK or the error code of the step */
+} fg_stats;
+
+typedef struct fg_ctx fg_ctx;
+
+/* Default options: FP64, gc = 1, lc = 2e-7, RT = 8.314462618 * 298.15, cmax = 3e4,
+ * tolerances 1e-9 (Newton, chem, staggered) and 1e-10 (Krylov), cg_forcing 1e-5,
+ * caps 30 / 5000 / 50 / 50. */
+void fg_default_opts(fg_opts* o);
+
+/* 1 when the transform length n is compiled in, else 0. */
+int fg_supported_size(int n);
+
+/*
+ * Creates a solver context (Sec. 3.1 problem statement; Alg. 4 initial state).
+ *   grid, phases[nphases]   geometry and per-phase constants; every phase uses one law
+ *   phase_id[V]             phase of each voxel (< nphases); the paper's compliant
+ *                           buffer material around the particle is one of the phases
+ *   cdot_B[V]               influx volume source (1/s), nonzero only in the band of
+ *                           width dL inside the particle surface (Eqs. neumann1-2)
+ *   c_init[V]               initial concentration, or NULL for phases[id].c0
+ *   log_E[V], log_D[V]      optional per-voxel log-scale of E and D (NULL: none)
+ * Initial state F = I, d = 0, H = 0 (Alg. 4).  Allocates all device memory.
+ * Errors: FG_ERR_INVALID (sizes, ids, law), FG_ERR_OOM, FG_ERR_CUDA.
+ */
+int fg_setup(fg_ctx** out, const fg_grid* grid, const fg_phase* phases, int nphases,
+             const uint8_t* phase_id, const double* cdot_B, const double* c_init,
+             const double* log_E, const double* log_D, const fg_opts* opts);
+
+/*
+ * One time step of Alg. 4 from the stored state (F_t, c_t, d_t, H_t) to t + dt with the
+ * macroscopic deformation gradient Fbar[9] (row-major) at t + dt.  On success the new
+ * state is stored.  On FG_ERR_NOCONV / FG_ERR_DOMAIN / FG_ERR_NUMERIC the stored state
+ * is left at the start of the step.  st may be NULL.
+ */
+int fg_step(fg_ctx* ctx, double dt, const double Fbar[9], fg_stats* st);
+
+/*
+ * Residuals of the stored state: err_mech = ||G*P(F)|| / ||G*P(Fbar)|| (Eq. mechresiduum,
+ * with the fallbacks ||P(Fbar)|| then 1 when the comparison stress has no incompatible
+ * part), err_chem = ||f(c)|| of Eq. Chemresidualfc for the last step's data (0 before
+ * the first step), mass_sum = sum of c.  Any output pointer may be NULL.
+ */
+int fg_residual(fg_ctx* ctx, double* err_mech, double* err_chem, double* mass_sum);
+
+/*
+ * One operator application y = op(x) at the stored state, for tests and benchmarks.
+ *   op         FG_OP_*;  prec: 0 = FP64 (x, y double), 1 = FP32 (x, y float)
+ *   x, y       device pointers, 9 V (MECH, GRES) or V (others) elements
+ *   dt         time step of FG_OP_CHEM (ignored otherwise)
+ *   dot        if not NULL receives <x, y> accumulated in FP64
+ * MECH uses the tangent at the stored (F, c, d); CHEM uses c_t = c, d_t = d, F_t = F;
+ * PFF and PFF_PREC use the stored H.  Enqueued on the context stream; returns when done.
+ */
+int fg_apply(fg_ctx* ctx, int op, int prec, const void* x, void* y, double dt, double* dot);
+
+/* Copies a field out (host or device destination, see FG_FIELD_*). */
+int fg_get_field(fg_ctx* ctx, int field, void* dst, int on_device);
+
+/* Overwrites a stored field (C, F, D or H) from host or device memory, for tests and
+ * restarts.  The step's t-state is the stored state. */
+int fg_set_field(fg_ctx* ctx, int field, const void* src, int on_device);
+
+/* Runs n applications of op back to back on the stream between two CUDA events and
+ * reports the mean time per application in ms (no synchronisation inside). */
+int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
+
+/* Releases the context and its device memory.  NULL is ignored. */
+void fg_destroy(fg_ctx* ctx);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* fg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FG_H */

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of the C ABI in ``include/fg.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/libfg.so``; this module only
+converts arguments.  Loading fails loudly when the library has not been built: there is
+no Python or CPU fallback.  PyTorch is used for device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libfg.so")
+
+FG_OK = 0
+ERRORS = {-1: "FG_ERR_INVALID", -2: "FG_ERR_OOM", -3: "FG_ERR_CUDA", -4: "FG_ERR_NOCONV",
+          -5: "FG_ERR_DOMAIN", -6: "FG_ERR_NUMERIC"}
+FG_SVK, FG_NEOHOOKE = 0, 1
+FG_FP64, FG_MIXED = 0, 1
+OP_MECH, OP_PFF, OP_PFF_PREC, OP_CHEM, OP_GRES = 0, 1, 2, 3, 4
+FIELD_C, FIELD_F, FIELD_D, FIELD_H, FIELD_P = 0, 1, 2, 3, 4
+
+
+class FgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double)]
+
+
+class Phase(C.Structure):
+    _fields_ = [("law", C.c_int), ("E", C.c_double), ("nu", C.c_double), ("Omega", C.c_double),
+                ("c0", C.c_double), ("D", C.c_double), ("sigma_max", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("gc", C.c_double), ("lc", C.c_double),
+                ("RT", C.c_double), ("cmax", C.c_double), ("tol_newton", C.c_double),
+                ("tol_cg", C.c_double), ("tol_chem", C.c_double), ("tol_chem_cg", C.c_double),
+                ("tol_pff_cg", C.c_double), ("tol_stag", C.c_double), ("cg_forcing", C.c_double),
+                ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
+                ("max_stag", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_chem", C.c_int), ("newton_mech", C.c_int), ("cg_chem", C.c_int),
+                ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
+                ("inner_refine", C.c_int), ("err_mech", C.c_double), ("err_chem", C.c_double),
+                ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
+           "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_destroy",
+           "fg_last_error"]
+
+_libs = {}
+
+
+def load_library(path=LIB_PATH):
+    """Loads a build of the C ABI and declares its signatures."""
+    path = os.path.abspath(path)
+    if path in _libs:
+        return _libs[path]
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    lib.fg_default_opts.argtypes = [C.POINTER(Opts)]
+    lib.fg_default_opts.restype = None
+    lib.fg_supported_size.argtypes = [C.c_int]
+    lib.fg_setup.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(Phase), C.c_int,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.POINTER(Opts)]
+    lib.fg_step.argtypes = [C.c_void_p, C.c_double, dp, C.POINTER(Stats)]
+    lib.fg_residual.argtypes = [C.c_void_p, dp, dp, dp]
+    lib.fg_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, dp]
+    lib.fg_get_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    lib.fg_set_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    lib.fg_time_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
+    lib.fg_destroy.argtypes = [C.c_void_p]
+    lib.fg_destroy.restype = None
+    lib.fg_last_error.restype = C.c_char_p
+    _libs[path] = lib
+    return lib
+
+
+def default_opts(lib=None):
+    lib = lib or load_library()
+    o = Opts()
+    lib.fg_default_opts(C.byref(o))
+    return o
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+class Solver:
+    """One periodic RVE: owns an ``fg_ctx``.  Host arrays are numpy, (nz, ny, nx)."""
+
+    def __init__(self, shape, h, phases, phase_id, cdot_B, c_init=None, log_E=None, log_D=None,
+                 opts=None, precision=FG_FP64, stream=None, lib=None, **opt_kw):
+        self.lib = lib or load_library()
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.V = nx * ny * nz
+        g = Grid(nx, ny, nz, *[float(x) for x in h])
+        ph = (Phase * len(phases))()
+        for k, p in enumerate(phases):
+            ph[k] = Phase(int(p.law), p.E, p.nu, p.Omega, p.c0, p.D, p.sigma_max)
+        o = opts or default_opts(self.lib)
+        o.precision = precision
+        for k, v in opt_kw.items():
+            setattr(o, k, v)
+        if stream is not None:
+            o.cuda_stream = C.c_void_p(stream)
+        self.opts = o
+        self._keep = [np.ascontiguousarray(phase_id, dtype=np.uint8).ravel(), _f64(cdot_B).ravel()]
+        opt_arrays = []
+        for a in (c_init, log_E, log_D):
+            opt_arrays.append(None if a is None else _f64(a).ravel())
+        self._keep += opt_arrays
+        ctx = C.c_void_p()
+        rc = self.lib.fg_setup(C.byref(ctx), C.byref(g), ph, len(phases), _ptr(self._keep[0]),
+                               _ptr(self._keep[1]),
+                               *[None if a is None else _ptr(a) for a in opt_arrays],
+                               C.byref(o))
+        self._check(rc)
+        self.ctx = ctx
+
+    def _check(self, rc):
+        if rc != FG_OK:
+            raise FgError(rc, self.lib.fg_last_error().decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, dt, Fbar=None, check=True):
+        Fb = _f64(np.eye(3) if Fbar is None else Fbar).ravel()
+        st = Stats()
+        rc = self.lib.fg_step(self.ctx, dt, Fb.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st))
+        if check:
+            self._check(rc)
+        return st.as_dict()
+
+    def residual(self):
+        em, ec, ms = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.fg_residual(self.ctx, C.byref(em), C.byref(ec), C.byref(ms)))
+        return em.value, ec.value, ms.value
+
+    def get(self, field):
+        n = 9 if field in (FIELD_F, FIELD_P) else 1
+        out = np.empty((n,) + self.shape if n == 9 else self.shape)
+        self._check(self.lib.fg_get_field(self.ctx, field, _ptr(out), 0))
+        return out.reshape((3, 3) + self.shape) if n == 9 else out
+
+    def set(self, field, value):
+        v = _f64(value).ravel()
+        self._check(self.lib.fg_set_field(self.ctx, field, _ptr(v), 0))
+
+    def apply(self, op, x, y, prec=0, dt=1.0):
+        """y = op(x) on device buffers (torch tensors); returns <x, y>."""
+        dot = C.c_double()
+        self._check(self.lib.fg_apply(self.ctx, op, prec, _ptr(x), _ptr(y), dt, C.byref(dot)))
+        return dot.value
+
+    def time_apply(self, op, prec, n):
+        ms = C.c_double()
+        self._check(self.lib.fg_time_apply(self.ctx, op, prec, n, C.byref(ms)))
+        return ms.value
+
+
+def from_workload(w, precision=FG_FP64, lib=None, stream=None, **opt_kw):
+    """Solver for a ``synth.Workload``."""
+    kw = dict(w.tol)
+    kw.update(opt_kw)
+    return Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=w.c_init, log_E=w.log_E,
+                  log_D=w.log_D, precision=precision, lib=lib, stream=stream, gc=w.gc, lc=w.lc,
+                  RT=w.RT, cmax=w.cmax, **kw)

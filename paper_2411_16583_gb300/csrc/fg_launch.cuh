@@ -1,0 +1,107 @@
+// Launch of the FFT pass kernels, and the per-size table of launchers that the runtime
+// dispatches through (one table per transform length N and precision).
+#pragma once
+#include <vector>
+#include <cstring>
+#include "fg_ops.cuh"
+
+namespace fg {
+
+#ifndef FG_EMU
+template <class K, class A>
+__global__ void __launch_bounds__(K::NT) pass_kernel(A a) {
+  extern __shared__ __align__(16) char smem[];
+  typename K::Locals L;
+  K::body(a, Dim3{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z},
+          Dim3{(int)gridDim.x, (int)gridDim.y, (int)gridDim.z}, smem, &L);
+}
+#endif
+
+// Launches kernel K with arguments A on `grid` blocks of K::NT threads.  Returns the
+// number of blocks launched (the number of partial sums a reducing kernel writes).
+template <class K, class A>
+int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
+  const size_t sm = K::smem_bytes();
+#ifdef FG_EMU
+  (void)st;
+  std::vector<char> smem(sm);
+  std::vector<typename K::Locals> Ls(K::NT);
+  for (int z = 0; z < grid.z; ++z)
+    for (int y = 0; y < grid.y; ++y)
+      for (int x = 0; x < grid.x; ++x) {
+        std::memset(smem.data(), 0, sm);
+        K::body(a, Dim3{x, y, z}, grid, smem.data(), Ls.data());
+      }
+#else
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    configured = true;
+  }
+  pass_kernel<K, A><<<dim3(grid.x, grid.y, grid.z), K::NT, sm, st>>>(a);
+#endif
+  return grid.x * grid.y * grid.z;
+}
+
+template <typename R>
+using PassFn = int (*)(const PassArgs<R>&, cudaStream_t);
+
+// Launchers of one transform length.  x* use N = nx, y* use N = ny, z* use N = nz.
+template <typename R>
+struct SizeOps {
+  int N;
+  PassFn<R> xf_tangent, xf_copy1, xf_copy3, xf_copy9;
+  PassFn<R> xi_store1, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
+      xi_chemrhs;
+  PassFn<R> yf, yi;
+  PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
+};
+
+template <class K, typename R>
+int run_x(const PassArgs<R>& a, cudaStream_t st) {
+  return launch_pass<K>(a, Dim3{K::grid_x(a.ny, a.nz), 1, 1}, st);
+}
+template <class K, typename R>
+int run_y(const PassArgs<R>& a, cudaStream_t st) {
+  return launch_pass<K>(a, Dim3{K::grid_x(a.hx, a.nz), a.ncomp, 1}, st);
+}
+template <class K, typename R>
+int run_z(const PassArgs<R>& a, cudaStream_t st) {
+  return launch_pass<K>(a, Dim3{K::grid_x(a.hx, a.ny), 1, 1}, st);
+}
+
+template <typename R, int N>
+SizeOps<R> make_size_ops() {
+  SizeOps<R> s{};
+  s.N = N;
+  if constexpr (N % 2 == 0) {
+    s.xf_tangent = run_x<XFwd<R, N, PTangentNH<R>>, R>;
+    s.xf_copy1 = run_x<XFwd<R, N, PCopy<R, 1>>, R>;
+    s.xf_copy3 = run_x<XFwd<R, N, PCopy<R, 3>>, R>;
+    s.xf_copy9 = run_x<XFwd<R, N, PCopy<R, 9>>, R>;
+    s.xi_store1 = run_x<XInv<R, N, EStore<R, 1>>, R>;
+    s.xi_storedot1 = run_x<XInv<R, N, EStoreDot<R, 1>>, R>;
+    s.xi_storedot9 = run_x<XInv<R, N, EStoreDot<R, 9>>, R>;
+    s.xi_norm9 = run_x<XInv<R, N, ENorm<R, 9>>, R>;
+    s.xi_pff = run_x<XInv<R, N, EPff<R>>, R>;
+    s.xi_chemflux = run_x<XInv<R, N, EChemFlux<R>>, R>;
+    s.xi_chemop = run_x<XInv<R, N, EChemOp<R>>, R>;
+    s.xi_chemrhs = run_x<XInv<R, N, EChemRhs<R>>, R>;
+  }
+  s.yf = run_y<YPass<R, N, false>, R>;
+  s.yi = run_y<YPass<R, N, true>, R>;
+  s.z_proj = run_z<ZPass<R, N, ZProject<R>>, R>;
+  s.z_lap = run_z<ZPass<R, N, ZLaplace<R>>, R>;
+  s.z_prec = run_z<ZPass<R, N, ZPrecond<R>>, R>;
+  s.z_grad = run_z<ZPass<R, N, ZGrad<R>>, R>;
+  s.z_div = run_z<ZPass<R, N, ZDiv<R>>, R>;
+  return s;
+}
+
+// Registry: each instantiation unit registers the sizes it compiles.
+template <typename R>
+const SizeOps<R>* size_ops(int N);
+void register_size_ops_f(const SizeOps<float>& s);
+void register_size_ops_d(const SizeOps<double>& s);
+
+}  // namespace fg

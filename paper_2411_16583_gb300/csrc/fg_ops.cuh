@@ -1,0 +1,229 @@
+// Pointwise parts fused into the FFT passes: the real-space prologues of X-fwd, the
+// frequency-space operators of the Z pass and the real-space epilogues of X-inv.
+#pragma once
+#include "fg_passes.cuh"
+
+namespace fg {
+
+// ================================================================== Z-pass operators
+
+// Compatibility projection (Eqs. mapping G, mechanicalsolve): A'_ij = n_j (A_im n_m)/|n|^2
+// with the rotated-scheme vector n_j = (2/h_j) sin(q_j/2) prod_{m!=j} cos(q_m/2); zero
+// where |n| = 0.  coef[0] = 1/V (inverse DFT scaling).
+template <typename R>
+struct ZProject {
+  using C = cplx<R>;
+  static constexpr int CIN = 9, COUT = 9;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+    const R n0 = a.rs[0][kx] * a.rc[1][ky] * a.rc[2][kz];
+    const R n1 = a.rs[1][ky] * a.rc[0][kx] * a.rc[2][kz];
+    const R n2 = a.rs[2][kz] * a.rc[0][kx] * a.rc[1][ky];
+    const R nn = n0 * n0 + n1 * n1 + n2 * n2;
+    const R s = nn > (R)0 ? a.coef[0] / nn : (R)0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      C t = cadd(cadd(cscale(v[3 * i], n0), cscale(v[3 * i + 1], n1)), cscale(v[3 * i + 2], n2));
+      t = cscale(t, s);
+      v[3 * i] = cscale(t, n0);
+      v[3 * i + 1] = cscale(t, n1);
+      v[3 * i + 2] = cscale(t, n2);
+    }
+  }
+};
+
+// Phase-field spectral term (Eq. PFFA): g_c l_c |xi|^2 d^, coef[0] = g_c l_c / V.
+template <typename R>
+struct ZLaplace {
+  using C = cplx<R>;
+  static constexpr int CIN = 1, COUT = 1;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+    const R l = a.lap[0][kx] + a.lap[1][ky] + a.lap[2][kz];
+    v[0] = cscale(v[0], a.coef[0] * l);
+  }
+};
+
+// Phase-field preconditioner (Eq. PFFprecond): r^ / (g_c/l_c + 2 Hbar + g_c l_c |xi|^2).
+// coef[0] = 1/V, coef[1] = g_c/l_c, coef[2] = g_c l_c, dscal[0] = Hbar.
+template <typename R>
+struct ZPrecond {
+  using C = cplx<R>;
+  static constexpr int CIN = 1, COUT = 1;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+    const R l = a.lap[0][kx] + a.lap[1][ky] + a.lap[2][kz];
+    const R den = a.coef[1] + (R)(2.0 * a.dscal[0]) + a.coef[2] * l;
+    v[0] = cscale(v[0], a.coef[0] / den);
+  }
+};
+
+// Forward-difference gradient (chemistry, Eq. ChemresidualFourier_A): g_j^ = xi_j u^ / V.
+template <typename R>
+struct ZGrad {
+  using C = cplx<R>;
+  static constexpr int CIN = 1, COUT = 3;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+    const C u = cscale(v[0], a.coef[0]);
+    v[0] = cmul(a.xi[0][kx], u);
+    v[1] = cmul(a.xi[1][ky], u);
+    v[2] = cmul(a.xi[2][kz], u);
+  }
+};
+
+// Adjoint of the forward difference: sum_j conj(xi_j) f_j^ / V (minus the divergence).
+template <typename R>
+struct ZDiv {
+  using C = cplx<R>;
+  static constexpr int CIN = 3, COUT = 1;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+    C s = cadd(cadd(cmulc(v[0], a.xi[0][kx]), cmulc(v[1], a.xi[1][ky])), cmulc(v[2], a.xi[2][kz]));
+    v[0] = cscale(s, a.coef[0]);
+  }
+};
+
+// ================================================================== X-fwd prologues
+
+template <typename R, int NC>
+struct PCopy {
+  static constexpr int COUT = NC;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = a.rin[c * a.V + v];
+  }
+};
+
+// Neo-Hookean tangent K : dF from the packed per-voxel state
+// (B = F^-T, s1 = g a^2 G, s2 = g (G - lam ln J_e), s3 = g lam; g = (1-d)^2):
+//   K : dF = s1 dF + s2 B dF^T B + s3 (B : dF) B.
+template <typename R>
+FG_DEV void tangent_nh(const R* B, R s1, R s2, R s3, const R* p, R* t) {
+  R m[9];  // M = B p^T : M_il = sum_k B_ik p_lk
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      m[3 * i + l] = B[3 * i] * p[3 * l] + B[3 * i + 1] * p[3 * l + 1] + B[3 * i + 2] * p[3 * l + 2];
+  R bp = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) bp += B[k] * p[k];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const R mb = m[3 * i] * B[j] + m[3 * i + 1] * B[3 + j] + m[3 * i + 2] * B[6 + j];
+      t[3 * i + j] = s1 * p[3 * i + j] + s2 * mb + s3 * bp * B[3 * i + j];
+    }
+}
+
+template <typename R>
+struct PTangentNH {
+  static constexpr int COUT = 9;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+    R p[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) p[c] = a.rin[c * a.V + v];
+    const R* st = a.aux[0];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) B[c] = st[c * a.V + v];
+    tangent_nh(B, st[9 * a.V + v], st[10 * a.V + v], st[11 * a.V + v], p, out);
+  }
+};
+
+// ================================================================== X-inv epilogues
+
+template <typename R, int NC>
+struct EStore {
+  static constexpr int CIN = NC;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double&) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a.rout[c * a.V + v] = val[c];
+  }
+};
+
+// store and accumulate <aux0, y>
+template <typename R, int NC>
+struct EStoreDot {
+  static constexpr int CIN = NC;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      a.rout[c * a.V + v] = val[c];
+      acc += (double)val[c] * (double)a.aux[0][c * a.V + v];
+    }
+  }
+};
+
+// store and accumulate |y|^2
+template <typename R, int NC>
+struct ENorm {
+  static constexpr int CIN = NC;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      a.rout[c * a.V + v] = val[c];
+      acc += (double)val[c] * (double)val[c];
+    }
+  }
+};
+
+// A(p) = [g_c/l_c + 2H] p + (spectral part); aux0 = p, aux1 = H, coef[0] = g_c/l_c.
+template <typename R>
+struct EPff {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+    const R p = a.aux[0][v];
+    const R y = (a.coef[0] + (R)2 * a.aux[1][v]) * p + val[0];
+    a.rout[v] = y;
+    acc += (double)p * (double)y;
+  }
+};
+
+// chemistry flux K_c g, K_c symmetric stored as (xx, yy, zz, xy, xz, yz) in aux0
+template <typename R>
+struct EChemFlux {
+  static constexpr int CIN = 3;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* g, double&) {
+    const R* K = a.aux[0];
+    const long long V = a.V;
+    const R kxx = K[v], kyy = K[V + v], kzz = K[2 * V + v];
+    const R kxy = K[3 * V + v], kxz = K[4 * V + v], kyz = K[5 * V + v];
+    a.rout[v] = kxx * g[0] + kxy * g[1] + kxz * g[2];
+    a.rout[V + v] = kxy * g[0] + kyy * g[1] + kyz * g[2];
+    a.rout[2 * V + v] = kxz * g[0] + kyz * g[1] + kzz * g[2];
+  }
+};
+
+// chemistry Newton operator in y = m dc: y/m + dt L y; aux0 = y, aux1 = 1/m = c(1-c),
+// coef[0] = dt; accumulates <y, A y>.
+template <typename R>
+struct EChemOp {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+    const R y = a.aux[0][v];
+    const R o = a.aux[1][v] * y + a.coef[0] * val[0];
+    a.rout[v] = o;
+    acc += (double)y * (double)o;
+  }
+};
+
+// chemistry residual, stored negated as the Newton right-hand side:
+// out = -(base + dt L mu~), base = c - c_t - dt cdot_B in aux0, coef[0] = dt;
+// accumulates |out|^2.
+template <typename R>
+struct EChemRhs {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+    const R o = -(a.aux[0][v] + a.coef[0] * val[0]);
+    a.rout[v] = o;
+    acc += (double)o * (double)o;
+  }
+};
+
+}  // namespace fg

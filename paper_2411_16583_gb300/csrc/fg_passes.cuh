@@ -1,0 +1,371 @@
+// The five passes of one operator application y = F^-1[ Op_k . F[ Op_x(x) ] ] on an
+// Nx x Ny x Nz periodic grid (Sec. 3.2; Eqs. mechanicalsolve, PFFA, PFFprecond,
+// ChemresidualFourier_A).
+//
+//   X-fwd  real rows along x  -> fused pointwise prologue, R2C along x    -> S1 [c][kx][z][y]
+//   Y-fwd  S1 rows along y    -> complex FFT along y, transposed store    -> S2 [c][kx][ky][z]
+//   Z      S2 rows along z    -> FFT z, frequency-space operator, IFFT z  -> S2 (in place)
+//   Y-inv  S2 (transposed)    -> inverse FFT along y                      -> S1
+//   X-inv  S1 (transposed)    -> C2R along x, fused pointwise epilogue    -> real fields
+//
+// Every pass reads one side as whole contiguous rows and the other as runs of consecutive
+// rows, so each global access is a contiguous segment.  Two real rows are transformed as
+// one complex row (a + i b) and separated with the Hermitian symmetry of real data.
+// The forward transform is unnormalised; the 1/V of the inverse is applied in the Z pass.
+#pragma once
+#include "fg_fft.cuh"
+
+namespace fg {
+
+template <typename R>
+struct PassArgs {
+  using C = cplx<R>;
+  int nx, ny, nz, hx;   // hx = nx/2 + 1
+  long long V, VH;      // voxels, half-spectrum points per component
+  const R* rin;         // real input fields (X-fwd prologue)
+  R* rout;              // real output fields (X-inv epilogue)
+  const C* cin;         // complex input
+  C* cout;              // complex output
+  const C* tw;          // exp(-2 pi i m / N), m < N, for this pass's axis
+  // per-axis frequency tables (Z pass), index k in [0, n_j) ([0, hx) for x)
+  const R* rs[3];       // rotated scheme: (2/h_j) sin(pi k / n_j)
+  const R* rc[3];       // rotated scheme: cos(pi k / n_j), exactly 0 at Nyquist
+  const C* xi[3];       // forward difference: (exp(2 pi i k / n_j) - 1) / h_j
+  const R* lap[3];      // 4 sin^2(pi k / n_j) / h_j^2
+  const R* aux[4];      // operator inputs (state, p, H, ...)
+  R coef[4];            // operator constants
+  const double* dscal;  // device scalars read by operators
+  double* partials;     // one partial sum per block (reducing epilogues)
+  const int* done;      // early exit when *done != 0 (converged Krylov loop)
+  int ncomp;            // components (Y passes)
+};
+
+// ------------------------------------------------------------------ tile sizing
+
+constexpr int tpr(int N) { return N / make_plan(N).rmax; }
+constexpr int round32(int n) { return (n + 31) / 32 * 32; }
+
+constexpr int rows_x(int N, int ncomp, int csize) {
+  int rows = 64;
+  while (rows > 2 && (ncomp * (rows / 2) * row_pitch(N) * csize > 80 * 1024 ||
+                      ncomp * (rows / 2) * tpr(N) > 1024 || ncomp * (rows / 2) > 64))
+    rows /= 2;
+  return rows;
+}
+constexpr int rows_y(int N, int csize) {
+  int rows = 64;
+  while (rows > 1 && (rows * row_pitch(N) * csize > 40 * 1024 || rows * tpr(N) > 512)) rows /= 2;
+  return rows;
+}
+constexpr int rows_z(int N, int ncomp, int csize) {
+  int rows = 16;
+  while (rows > 1 && (ncomp * rows * row_pitch(N) * csize > 48 * 1024 ||
+                      ncomp * rows * tpr(N) > 1024))
+    rows /= 2;
+  return rows;
+}
+
+// ------------------------------------------------------------------ block reduction
+// Sums L.acc over the block into a.partials[block]; uses the `red` scratch (NT doubles).
+
+#ifdef FG_EMU
+#define FG_BLOCK_REDUCE(NT_, red, out)                     \
+  {                                                        \
+    double s_ = 0.0;                                       \
+    for (int t_ = 0; t_ < (NT_); ++t_) s_ += Ls[t_].acc;   \
+    out = s_;                                              \
+  }
+#else
+#define FG_BLOCK_REDUCE(NT_, red, out)                                      \
+  {                                                                         \
+    double v_ = Ls[0].acc;                                                  \
+    for (int o_ = 16; o_ > 0; o_ >>= 1) v_ += __shfl_down_sync(0xffffffffu, v_, o_); \
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v_;                \
+    __syncthreads();                                                        \
+    if (threadIdx.x == 0) {                                                 \
+      double s_ = 0.0;                                                      \
+      for (int w_ = 0; w_ < (NT_) / 32; ++w_) s_ += red[w_];                \
+      out = s_;                                                             \
+    }                                                                       \
+  }
+#endif
+
+FG_DEV long long block_linear(Dim3 b, int gx, int gy) {
+  return ((long long)b.z * gy + b.y) * gx + b.x;
+}
+
+// ------------------------------------------------------------------ X-fwd
+
+template <typename R, int N, class Op>
+struct XFwd {
+  using C = cplx<R>;
+  static constexpr int CO = Op::COUT;
+  static constexpr int ROWS = rows_x(N, CO, sizeof(C));
+  static constexpr int CR = ROWS / 2;
+  static constexpr int NROWS = CO * CR;
+  static constexpr int NT = round32(NROWS * tpr(N));
+  using TF = TileFFT<R, N, NROWS, NT, false>;
+  static constexpr int PITCH = TF::PITCH;
+  struct Locals {
+    C v[TF::VMAX];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
+  static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + NROWS * PITCH;
+    double* red = (double*)(tw + N);
+    (void)red;
+    const int nrows = a.ny * a.nz;
+    const int row0 = bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    FG_PHASE(NT)
+    L.acc = 0.0;
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    for (int e = tid; e < ROWS * N; e += NT) {
+      const int r = e / N, x = e - r * N;
+      R out[CO];
+      if (r < nr) {
+        Op::apply(a, (long long)(row0 + r) * N + x, out, L.acc);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CO; ++c) out[c] = (R)0;
+      }
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        C& z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+        if (r & 1) z.y = out[c]; else z.x = out[c];
+      }
+    }
+    FG_END_PHASE
+    tile_fft<TF, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    constexpr int H = N / 2 + 1;
+    for (int e = tid; e < CO * nr * H; e += NT) {
+      const int r = e % nr, t = e / nr;
+      const int kx = t % H, c = t / H;
+      const C* row = tile + (c * CR + (r >> 1)) * PITCH;
+      const C zk = row[pad16(kx)];
+      const C zn = row[pad16((N - kx) % N)];
+      C val;
+      if (!(r & 1)) {
+        val = cmk<C>((zk.x + zn.x) * (R)0.5, (zk.y - zn.y) * (R)0.5);
+      } else {
+        const R dx = zk.x - zn.x, dy = zk.y + zn.y;
+        val = cmk<C>(dy * (R)0.5, -dx * (R)0.5);
+      }
+      a.cout[c * a.VH + (long long)kx * nrows + row0 + r] = val;
+    }
+    FG_END_PHASE
+    if constexpr (Op::RED) {
+      double s = 0.0;
+      FG_BLOCK_REDUCE(NT, red, s)
+#ifdef FG_EMU
+      a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#else
+      if (threadIdx.x == 0) a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#endif
+    }
+  }
+};
+
+// ------------------------------------------------------------------ X-inv
+
+template <typename R, int N, class Op>
+struct XInv {
+  using C = cplx<R>;
+  static constexpr int CI = Op::CIN;
+  static constexpr int ROWS = rows_x(N, CI, sizeof(C));
+  static constexpr int CR = ROWS / 2;
+  static constexpr int NROWS = CI * CR;
+  static constexpr int NT = round32(NROWS * tpr(N));
+  using TF = TileFFT<R, N, NROWS, NT, true>;
+  static constexpr int PITCH = TF::PITCH;
+  struct Locals {
+    C v[TF::VMAX];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
+  static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + NROWS * PITCH;
+    double* red = (double*)(tw + N);
+    (void)red;
+    const int nrows = a.ny * a.nz;
+    const int row0 = bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    FG_PHASE(NT)
+    L.acc = 0.0;
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    constexpr int H = N / 2 + 1;
+    for (int e = tid; e < CI * CR * H; e += NT) {
+      const int q = e % CR, t = e / CR;
+      const int kx = t % H, c = t / H;
+      const int r0 = 2 * q;
+      if (r0 < nr) {
+        const long long base = c * a.VH + (long long)kx * nrows + row0 + r0;
+        const C A = a.cin[base];
+        const C B = (r0 + 1 < nr) ? a.cin[base + 1] : cmk<C>((R)0, (R)0);
+        C* row = tile + (c * CR + q) * PITCH;
+        if (kx == 0 || 2 * kx == N) {
+          row[pad16(kx)] = cmk<C>(A.x, B.x);
+        } else {
+          row[pad16(kx)] = cmk<C>(A.x - B.y, A.y + B.x);
+          row[pad16(N - kx)] = cmk<C>(A.x + B.y, B.x - A.y);
+        }
+      }
+    }
+    FG_END_PHASE
+    tile_fft<TF, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    for (int e = tid; e < nr * N; e += NT) {
+      const int r = e / N, x = e - r * N;
+      R val[CI];
+#pragma unroll
+      for (int c = 0; c < CI; ++c) {
+        const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+        val[c] = (r & 1) ? z.y : z.x;
+      }
+      Op::apply(a, (long long)(row0 + r) * N + x, val, L.acc);
+    }
+    FG_END_PHASE
+    if constexpr (Op::RED) {
+      double s = 0.0;
+      FG_BLOCK_REDUCE(NT, red, s)
+#ifdef FG_EMU
+      a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#else
+      if (threadIdx.x == 0) a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#endif
+    }
+  }
+};
+
+// ------------------------------------------------------------------ Y passes
+
+template <typename R, int N, bool INV>
+struct YPass {
+  using C = cplx<R>;
+  static constexpr int ROWS = rows_y(N, sizeof(C));
+  static constexpr int NT = round32(ROWS * tpr(N));
+  using TF = TileFFT<R, N, ROWS, NT, INV>;
+  static constexpr int PITCH = TF::PITCH;
+  struct Locals {
+    C v[TF::VMAX];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(ROWS * PITCH + N) * sizeof(C); }
+  static int grid_x(int hx, int nz) { return (hx * nz + ROWS - 1) / ROWS; }
+
+  // element (row s of the (kx, z) rows, index n along y) in the [c][kx][ky][z] layout
+  FG_DEV static long long tpos(int s, int n, int nz) {
+    const int kx = s / nz, z = s - kx * nz;
+    return ((long long)kx * N + n) * nz + z;
+  }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + ROWS * PITCH;
+    const int c = bid.y;
+    const int nrows = a.hx * a.nz;
+    const int row0 = bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    const C* in = a.cin + c * a.VH;
+    C* out = a.cout + c * a.VH;
+    const bool rfast = a.nz >= 4;  // runs of consecutive rows are long enough to coalesce
+    FG_PHASE(NT)
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    for (int e = tid; e < nr * N; e += NT) {
+      int r, n;
+      if (!INV || !rfast) { r = e / N; n = e - r * N; }
+      else { n = e / nr; r = e - n * nr; }
+      const long long g = INV ? tpos(row0 + r, n, a.nz) : (long long)(row0 + r) * N + n;
+      tile[r * PITCH + pad16(n)] = in[g];
+    }
+    FG_END_PHASE
+    tile_fft<TF, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    for (int e = tid; e < nr * N; e += NT) {
+      int r, n;
+      if (INV || !rfast) { r = e / N; n = e - r * N; }
+      else { n = e / nr; r = e - n * nr; }
+      const long long g = INV ? (long long)(row0 + r) * N + n : tpos(row0 + r, n, a.nz);
+      out[g] = tile[r * PITCH + pad16(n)];
+    }
+    FG_END_PHASE
+  }
+};
+
+// ------------------------------------------------------------------ Z pass
+
+template <typename R, int N, class Op>
+struct ZPass {
+  using C = cplx<R>;
+  static constexpr int CI = Op::CIN;
+  static constexpr int CO = Op::COUT;
+  static constexpr int CM = CI > CO ? CI : CO;
+  static constexpr int ROWS = rows_z(N, CM, sizeof(C));
+  static constexpr int NT = round32(CM * ROWS * tpr(N));
+  using TFf = TileFFT<R, N, CI * ROWS, NT, false>;
+  using TFi = TileFFT<R, N, CO * ROWS, NT, true>;
+  static constexpr int PITCH = TFf::PITCH;
+  static constexpr int VMAX = TFf::VMAX > TFi::VMAX ? TFf::VMAX : TFi::VMAX;
+  struct Locals {
+    C v[VMAX];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(CM * ROWS * PITCH + N) * sizeof(C); }
+  static int grid_x(int hx, int ny) { return (hx * ny + ROWS - 1) / ROWS; }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + CM * ROWS * PITCH;
+    const int nrows = a.hx * a.ny;
+    const int row0 = bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    FG_PHASE(NT)
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    for (int e = tid; e < CI * nr * N; e += NT) {
+      const int c = e / (nr * N), rem = e - c * (nr * N);
+      const int r = rem / N, n = rem - r * N;
+      tile[(c * ROWS + r) * PITCH + pad16(n)] = a.cin[c * a.VH + (long long)(row0 + r) * N + n];
+    }
+    FG_END_PHASE
+    tile_fft<TFf, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    for (int e = tid; e < nr * N; e += NT) {
+      const int r = e / N, n = e - r * N;
+      const int s = row0 + r;
+      const int kx = s / a.ny, ky = s - kx * a.ny;
+      C v[CM];
+#pragma unroll
+      for (int c = 0; c < CI; ++c) v[c] = tile[(c * ROWS + r) * PITCH + pad16(n)];
+      Op::apply(a, kx, ky, n, v);
+#pragma unroll
+      for (int c = 0; c < CO; ++c) tile[(c * ROWS + r) * PITCH + pad16(n)] = v[c];
+    }
+    FG_END_PHASE
+    tile_fft<TFi, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    for (int e = tid; e < CO * nr * N; e += NT) {
+      const int c = e / (nr * N), rem = e - c * (nr * N);
+      const int r = rem / N, n = rem - r * N;
+      a.cout[c * a.VH + (long long)(row0 + r) * N + n] = tile[(c * ROWS + r) * PITCH + pad16(n)];
+    }
+    FG_END_PHASE
+  }
+};
+
+}  // namespace fg

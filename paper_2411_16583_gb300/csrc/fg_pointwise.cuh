@@ -1,0 +1,574 @@
+// Voxel-wise kernels: constitutive state and stress, damage driving force and history,
+// chemistry coefficients, Krylov vector updates and the single-block finalisers that
+// turn partial sums into the Krylov scalars.  All are grid-stride loops over voxels.
+#pragma once
+#include "fg_launch.cuh"
+
+namespace fg {
+
+constexpr int VEC_NT = 256;
+constexpr int VEC_BLOCKS = 1216;  // 8 x 152 SMs
+
+// Krylov scalars kept on the device (one block per solve).
+struct KScal {
+  double rz;     // <r, z> (z = r without preconditioner)
+  double pq;     // <p, A p>
+  double rr;     // <r, r>
+  double bb;     // <b, b>
+  double tol2;   // tol^2 <b, b>
+  double alpha, beta;
+  double aux;    // spare sum (mass, norms)
+  int done, iters, maxit, status;
+};
+
+enum : int { ST_OK = 0, ST_INDEFINITE = 1, ST_DOMAIN = 2, ST_NUMERIC = 4 };
+
+struct VArgs {
+  long long n;          // elements processed
+  long long V;          // voxels
+  const void* in[10];   // inputs (meaning per kernel)
+  void* out[6];         // outputs
+  double s[10];         // scalars
+  double* partials;     // per-block partial sums
+  KScal* ks;            // Krylov scalars (may be null)
+  const int* done;      // early exit
+  int* flags;           // error flags (domain / numeric)
+};
+
+// Generic grid-stride kernel: F::apply(a, i, acc) for every element i.
+template <class F>
+struct VecKernel {
+  static constexpr int NT = VEC_NT;
+  struct Locals {
+    double acc;
+  };
+  static size_t smem_bytes() { return NT * sizeof(double); }
+  template <class Loc>
+  FG_DEV static void body(const VArgs& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    double* red = (double*)smem;
+    (void)red;
+    FG_PHASE(NT)
+    L.acc = 0.0;
+    for (long long i = (long long)bid.x * NT + tid; i < a.n; i += (long long)grid.x * NT)
+      F::apply(a, i, L.acc);
+    FG_END_PHASE
+    if constexpr (F::RED) {
+      double s = 0.0;
+      FG_BLOCK_REDUCE(NT, red, s)
+#ifdef FG_EMU
+      a.partials[bid.x] = s;
+#else
+      if (threadIdx.x == 0) a.partials[bid.x] = s;
+#endif
+    }
+  }
+};
+
+template <class F>
+int launch_vec(const VArgs& a, cudaStream_t st) {
+  long long nb = (a.n + VEC_NT - 1) / VEC_NT;
+  int g = (int)(nb < VEC_BLOCKS ? (nb < 1 ? 1 : nb) : VEC_BLOCKS);
+  if (F::RED) g = VEC_BLOCKS;  // fixed count of partial sums
+  return launch_pass<VecKernel<F>>(a, Dim3{g, 1, 1}, st);
+}
+
+// Single-block finaliser: sums `npart` partials (in a fixed order) and calls F::fin.
+template <class F>
+struct FinKernel {
+  static constexpr int NT = 256;
+  struct Locals {
+    double acc;
+  };
+  static size_t smem_bytes() { return NT * sizeof(double); }
+  template <class Loc>
+  FG_DEV static void body(const VArgs& a, Dim3, Dim3, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    double* red = (double*)smem;
+    FG_PHASE(NT)
+    double s = 0.0;
+    for (long long i = tid; i < a.n; i += NT) s += a.partials[i];
+    red[tid] = s;
+    FG_END_PHASE
+    FG_PHASE(NT)
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < NT; ++i) t += red[i];
+      F::fin(a, t);
+    }
+    FG_END_PHASE
+  }
+};
+
+template <class F>
+void launch_fin(const VArgs& a, cudaStream_t st) {
+  launch_pass<FinKernel<F>>(a, Dim3{1, 1, 1}, st);
+}
+
+// ================================================================== 3x3 helpers
+
+FG_DEV double det3(const double* A) {
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+// cofactor matrix: cof(A) = det(A) A^-T
+FG_DEV void cof3(const double* A, double* C) {
+  C[0] = A[4] * A[8] - A[5] * A[7];
+  C[1] = A[5] * A[6] - A[3] * A[8];
+  C[2] = A[3] * A[7] - A[4] * A[6];
+  C[3] = A[2] * A[7] - A[1] * A[8];
+  C[4] = A[0] * A[8] - A[2] * A[6];
+  C[5] = A[1] * A[6] - A[0] * A[7];
+  C[6] = A[1] * A[5] - A[2] * A[4];
+  C[7] = A[2] * A[3] - A[0] * A[5];
+  C[8] = A[0] * A[4] - A[1] * A[3];
+}
+
+// Eigenvalues of a symmetric 3x3 matrix by the trigonometric closed form of
+// O. K. Smith, "Eigenvalues of a symmetric 3x3 matrix", Comm. ACM 4 (1961) 168.
+FG_DEV void sym_eig3(double a00, double a11, double a22, double a01, double a02, double a12,
+                    double* e) {
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const double q = (a00 + a11 + a22) / 3.0;
+  const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+  if (p2 <= 0.0) {
+    e[0] = e[1] = e[2] = q;
+    return;
+  }
+  const double p = sqrt(p2 / 6.0);
+  const double ip = 1.0 / p;
+  const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip;
+  const double c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+  double r = 0.5 * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) +
+                    c02 * (c01 * c12 - c11 * c02));
+  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+  const double phi = acos(r) / 3.0;
+  const double two_pi_3 = 2.0943951023931954923;
+  e[0] = q + 2.0 * p * cos(phi);
+  e[2] = q + 2.0 * p * cos(phi + two_pi_3);
+  e[1] = 3.0 * q - e[0] - e[2];
+}
+
+// Per-voxel material (FP64 arrays, one per quantity).
+struct MatPtrs {
+  const double* lam;
+  const double* mu;
+  const double* Om;
+  const double* c0;
+};
+
+// Neo-Hookean pieces at voxel v: a = J_c^{-1/3}, F_e = a F.
+struct NHPoint {
+  double a, g, lam, mu, lnJe, B[9];  // B = F^-T
+  double Fe[9];
+};
+
+FG_DEV bool nh_point(const double* F, double c, double d, double lam, double mu, double Om,
+                    double c0, NHPoint& P) {
+  const double Jc = 1.0 + Om * (c - c0);
+  const double J = det3(F);
+  if (!(Jc > 0.0) || !(J > 0.0)) return false;
+  P.a = 1.0 / cbrt(Jc);
+  P.g = (1.0 - d) * (1.0 - d);
+  P.lam = lam;
+  P.mu = mu;
+  P.lnJe = log(P.a * P.a * P.a * J);
+  double C[9];
+  cof3(F, C);
+  const double iJ = 1.0 / J;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    P.B[k] = C[k] * iJ;
+    P.Fe[k] = P.a * F[k];
+  }
+  return true;
+}
+
+// P0(F_e) of the compressible Neo-Hookean law: G (F_e - F_e^-T) + lam ln J_e F_e^-T.
+FG_DEV void nh_P0(const NHPoint& P, double* P0) {
+  const double ia = 1.0 / P.a;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double FeiT = P.B[k] * ia;
+    P0[k] = P.mu * (P.Fe[k] - FeiT) + P.lam * P.lnJe * FeiT;
+  }
+}
+
+// ---------------------------------------------------------------- mechanics state
+// in: F (9 V) or uniform Fbar (s[0..8], when in[0] == null), c, d, material
+// out0: P (9 V, FP64, may be null), out1: packed tangent state (12 V, precision R)
+
+template <typename R>
+struct KMechState {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+    const long long V = a.V;
+    const double* Fp = (const double*)a.in[0];
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = Fp ? Fp[k * V + v] : a.s[k];
+    const double c = ((const double*)a.in[1])[v];
+    const double d = ((const double*)a.in[2])[v];
+    const double lam = ((const double*)a.in[3])[v], mu = ((const double*)a.in[4])[v];
+    const double Om = ((const double*)a.in[5])[v], c0 = ((const double*)a.in[6])[v];
+    NHPoint P;
+    if (!nh_point(F, c, d, lam, mu, Om, c0, P)) {
+      atomicOr(a.flags, ST_DOMAIN);
+      return;
+    }
+    if (a.out[0]) {
+      double P0[9];
+      nh_P0(P, P0);
+      double* Po = (double*)a.out[0];
+      const double ga = P.g * P.a;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Po[k * V + v] = ga * P0[k];
+    }
+    if (a.out[1]) {
+      R* st = (R*)a.out[1];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) st[k * V + v] = (R)P.B[k];
+      st[9 * V + v] = (R)(P.g * P.a * P.a * P.mu);
+      st[10 * V + v] = (R)(P.g * (P.mu - P.lam * P.lnJe));
+      st[11 * V + v] = (R)(P.g * P.lam);
+    }
+  }
+};
+
+// ---------------------------------------------------------------- damage history
+// H = max(H_t, g_c/(2 l_c) D_f), D_f from the principal values of the undegraded Cauchy
+// stress sigma = J^-1 a P0(a F) F^T (Eqs. Hist, SigDrivingForce).  Accumulates sum H.
+// in: F, c, H_t, lam, mu, Om, c0, smax ; out0: H ; s0 = g_c/(2 l_c)
+struct KHistory {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long v, double& acc) {
+    const long long V = a.V;
+    const double* Fp = (const double*)a.in[0];
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = Fp[k * V + v];
+    const double c = ((const double*)a.in[1])[v];
+    const double Ht = ((const double*)a.in[2])[v];
+    NHPoint P;
+    double Hn = Ht;
+    if (nh_point(F, c, 0.0, ((const double*)a.in[3])[v], ((const double*)a.in[4])[v],
+                 ((const double*)a.in[5])[v], ((const double*)a.in[6])[v], P)) {
+      double P0[9];
+      nh_P0(P, P0);
+      const double J = det3(F);
+      const double s = P.a / J;
+      double sg[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          sg[3 * i + j] = s * (P0[3 * i] * F[3 * j] + P0[3 * i + 1] * F[3 * j + 1] +
+                               P0[3 * i + 2] * F[3 * j + 2]);
+      double e[3];
+      sym_eig3(sg[0], sg[4], sg[8], 0.5 * (sg[1] + sg[3]), 0.5 * (sg[2] + sg[6]),
+               0.5 * (sg[5] + sg[7]), e);
+      const double smax = ((const double*)a.in[7])[v];
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double u = e[i] > 0.0 ? e[i] / smax : 0.0;
+        t += u * u;
+      }
+      const double Df = t - 1.0 > 0.0 ? t - 1.0 : 0.0;
+      const double Hc = a.s[0] * Df;
+      Hn = Hc > Ht ? Hc : Ht;
+    } else {
+      atomicOr(a.flags, ST_DOMAIN);
+    }
+    ((double*)a.out[0])[v] = Hn;
+    acc += Hn;
+  }
+};
+
+// ---------------------------------------------------------------- chemistry
+// K_c = D phi(d_t) c_t (1-c_t) C^-1, C = F^T F, stored (xx, yy, zz, xy, xz, yz) in R.
+// in: F, c_t, d_t, D ; out0: K (6 V)
+template <typename R>
+struct KChemCond {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+    const long long V = a.V;
+    const double* Fp = (const double*)a.in[0];
+    double F[9], C[9], Ci[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = Fp[k * V + v];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        C[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+    cof3(C, Ci);
+    const double ct = ((const double*)a.in[1])[v];
+    const double dt_ = ((const double*)a.in[2])[v];
+    const double D = ((const double*)a.in[3])[v];
+    const double phi = 0.9 * (1.0 - dt_) * (1.0 - dt_) + 0.1 * dt_ * dt_;
+    const double s = D * phi * ct * (1.0 - ct) / det3(C);
+    R* K = (R*)a.out[0];
+    K[v] = (R)(s * Ci[0]);
+    K[V + v] = (R)(s * Ci[4]);
+    K[2 * V + v] = (R)(s * Ci[8]);
+    K[3 * V + v] = (R)(s * Ci[1]);
+    K[4 * V + v] = (R)(s * Ci[2]);
+    K[5 * V + v] = (R)(s * Ci[5]);
+  }
+};
+
+// Newton quantities at the iterate c (FP64):
+//   out0 = mu~(c) = log(c/(1-c)) + mu_e / RT        (Eqs. muc, mue)
+//   out1 = c - c_t - dt cdot_B                     (residual without the flux term)
+//   out2 = c (1 - c) in precision R                (1/m of the Jacobian)
+// mu_e = -(1-d)^2 Omega / (3 J_c) P0(F_e) : F_e / c_max.
+// in: c, c_t, cdot_B, F, d_t, lam, mu, Om, c0 ; s0 = dt, s1 = 1/RT, s2 = 1/c_max
+template <typename R>
+struct KChemPrep {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+    const long long V = a.V;
+    const double c = ((const double*)a.in[0])[v];
+    const double ct = ((const double*)a.in[1])[v];
+    const double cb = ((const double*)a.in[2])[v];
+    if (!(c > 0.0 && c < 1.0)) {
+      atomicOr(a.flags, ST_DOMAIN);
+      return;
+    }
+    const double* Fp = (const double*)a.in[3];
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = Fp[k * V + v];
+    const double d = ((const double*)a.in[4])[v];
+    const double lam = ((const double*)a.in[5])[v], mu = ((const double*)a.in[6])[v];
+    const double Om = ((const double*)a.in[7])[v], c0 = ((const double*)a.in[8])[v];
+    double mue = 0.0;
+    if (Om != 0.0) {
+      NHPoint P;
+      if (nh_point(F, c, d, lam, mu, Om, c0, P)) {
+        double trC = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) trC += P.Fe[k] * P.Fe[k];
+        const double P0Fe = mu * (trC - 3.0) + 3.0 * lam * P.lnJe;
+        const double Jc = 1.0 + Om * (c - c0);
+        mue = -P.g * Om / (3.0 * Jc) * P0Fe * a.s[2];
+      } else {
+        atomicOr(a.flags, ST_DOMAIN);
+      }
+    }
+    ((double*)a.out[0])[v] = log(c / (1.0 - c)) + mue * a.s[1];
+    ((double*)a.out[1])[v] = c - ct - a.s[0] * cb;
+    ((R*)a.out[2])[v] = (R)(c * (1.0 - c));
+  }
+};
+
+// c += dc with dc = y c (1 - c) (y = m dc); accumulates |dc|^2.  in0 = y (R); out0 = c
+template <typename R>
+struct KChemUpdate {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long v, double& acc) {
+    double* c = (double*)a.out[0];
+    const double ci = c[v];
+    const double dc = (double)((const R*)a.in[0])[v] * ci * (1.0 - ci);
+    const double cn = ci + dc;
+    c[v] = cn;
+    if (!(cn > 0.0 && cn < 1.0)) atomicOr(a.flags, ST_DOMAIN);
+    acc += dc * dc;
+  }
+};
+
+// ---------------------------------------------------------------- conversions / sums
+
+// out0 (R) = s0 * in0 (FP64); accumulates |out|^2
+template <typename R>
+struct KScaleTo {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const R o = (R)(a.s[0] * ((const double*)a.in[0])[i]);
+    ((R*)a.out[0])[i] = o;
+    acc += (double)o * (double)o;
+  }
+};
+
+// out0 (FP64) += in0 (R)
+template <typename R>
+struct KAddTo {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    ((double*)a.out[0])[i] += (double)((const R*)a.in[0])[i];
+  }
+};
+
+// sum of in0 (FP64) and of in0^2 into (partials, partials + VEC_BLOCKS)
+struct KSum {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    acc += ((const double*)a.in[0])[i];
+  }
+};
+struct KSumSq {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const double x = ((const double*)a.in[0])[i];
+    acc += x * x;
+  }
+};
+// out0 (FP64) = in0 (FP64) + s0..s8 pattern: F = F_t + dFbar (component = i / V)
+struct KShiftF {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    ((double*)a.out[0])[i] = ((const double*)a.in[0])[i] + a.s[i / a.V];
+  }
+};
+
+// ---------------------------------------------------------------- Krylov vectors
+
+// CG start from x = 0: x = 0, r = b, p = b (in0 = b, out0 = x, out1 = r, out2 = p); sum b^2
+template <typename R>
+struct KCgInit {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const R b = ((const R*)a.in[0])[i];
+    ((R*)a.out[0])[i] = (R)0;
+    ((R*)a.out[1])[i] = b;
+    if (a.out[2]) ((R*)a.out[2])[i] = b;
+    acc += (double)b * (double)b;
+  }
+};
+
+// x += alpha p, r -= alpha q; sum r^2 (in0 = p, in1 = q, out0 = x, out1 = r)
+template <typename R>
+struct KCgXR {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const R al = (R)a.ks->alpha;
+    R* x = (R*)a.out[0];
+    R* r = (R*)a.out[1];
+    x[i] += al * ((const R*)a.in[0])[i];
+    const R rn = r[i] - al * ((const R*)a.in[1])[i];
+    r[i] = rn;
+    acc += (double)rn * (double)rn;
+  }
+};
+
+// p = z + beta p (in0 = z, out0 = p)
+template <typename R>
+struct KCgP {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    R* p = (R*)a.out[0];
+    p[i] = ((const R*)a.in[0])[i] + (R)a.ks->beta * p[i];
+  }
+};
+
+// r = b - q (in0 = b, in1 = q, out0 = r); sum r^2 and b^2 (two passes of partials)
+template <typename R>
+struct KResid {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const R rv = ((const R*)a.in[0])[i] - ((const R*)a.in[1])[i];
+    ((R*)a.out[0])[i] = rv;
+    acc += (double)rv * (double)rv;
+  }
+};
+template <typename R>
+struct KSumSqR {
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+    const double x = (double)((const R*)a.in[0])[i];
+    acc += x * x;
+  }
+};
+template <typename R>
+struct KCopy {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    ((R*)a.out[0])[i] = ((const R*)a.in[0])[i];
+  }
+};
+
+// ---------------------------------------------------------------- finalisers
+
+// CG start: bb = rr = rz = t; tol2 = s0^2 bb; maxit = s1; done when bb == 0
+struct FCgStart {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->bb = t;
+    k->rr = t;
+    k->rz = t;
+    k->tol2 = a.s[0] * a.s[0] * t;
+    k->iters = 0;
+    k->maxit = (int)a.s[1];
+    k->status = 0;
+    k->done = (t == 0.0 || t <= k->tol2) ? 1 : 0;
+  }
+};
+// alpha = rz / <p, Ap>
+struct FAlpha {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->pq = t;
+    if (!(t > 0.0)) {
+      k->status |= ST_INDEFINITE;
+      k->done = 1;
+      k->alpha = 0.0;
+      return;
+    }
+    k->alpha = k->rz / t;
+  }
+};
+// unpreconditioned CG: rr = t; beta = rr / rz; rz = rr; convergence
+struct FBetaCg {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->iters += 1;
+    k->rr = t;
+    k->beta = t / k->rz;
+    k->rz = t;
+    if (!(t == t)) k->status |= ST_NUMERIC;
+    if (t <= k->tol2 || k->iters >= k->maxit || !(t == t)) k->done = 1;
+  }
+};
+// preconditioned CG, after the r update: rr = t; convergence
+struct FResPcg {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->iters += 1;
+    k->rr = t;
+    if (!(t == t)) k->status |= ST_NUMERIC;
+    if (t <= k->tol2 || k->iters >= k->maxit || !(t == t)) k->done = 1;
+  }
+};
+// preconditioned CG, after z = P r: beta = <r,z>_new / <r,z>_old
+struct FBetaPcg {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->beta = t / k->rz;
+    k->rz = t;
+  }
+};
+// PCG start: rr = t (s0 = tol, s1 = bb, s2 = maxit); done test
+struct FPcgStart {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    KScal* k = a.ks;
+    k->rr = t;
+    k->bb = a.s[1];
+    k->tol2 = a.s[0] * a.s[0] * a.s[1];
+    k->iters = 0;
+    k->maxit = (int)a.s[2];
+    k->status = 0;
+    k->done = (a.s[1] == 0.0 || t <= k->tol2) ? 1 : 0;
+  }
+};
+// PCG start, after z0 = P r0: rz = t
+struct FPcgRz {
+  FG_DEV static void fin(const VArgs& a, double t) { a.ks->rz = t; }
+};
+// store a plain sum into ks->aux
+struct FStore {
+  FG_DEV static void fin(const VArgs& a, double t) { a.ks->aux = t; }
+};
+
+}  // namespace fg

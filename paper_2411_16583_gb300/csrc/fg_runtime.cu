@@ -1,0 +1,1219 @@
+// Host runtime of the solver: context and device memory, the operator pipelines, the
+// Krylov / Newton / staggered drivers (Alg. 1-4) and the C ABI of include/fg.h.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fg_pointwise.cuh"
+#include "../../include/fg.h"
+
+namespace fg {
+
+// ------------------------------------------------------------------ size registry
+
+template <typename R>
+static std::map<int, SizeOps<R>>& registry() {
+  static std::map<int, SizeOps<R>> m;
+  return m;
+}
+void register_size_ops_f(const SizeOps<float>& s) { registry<float>()[s.N] = s; }
+void register_size_ops_d(const SizeOps<double>& s) { registry<double>()[s.N] = s; }
+template <typename R>
+const SizeOps<R>* size_ops(int N) {
+  auto& m = registry<R>();
+  auto it = m.find(N);
+  return it == m.end() ? nullptr : &it->second;
+}
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+struct Fail {
+  int code;
+};
+
+static void fail(int code, const std::string& msg) {
+  g_err = msg;
+  throw Fail{code};
+}
+
+// ------------------------------------------------------------------ device memory
+
+#ifdef FG_EMU
+static void* dalloc(size_t n) {
+  void* p = calloc(n ? n : 1, 1);
+  if (!p) fail(FG_ERR_OOM, "host allocation failed");
+  return p;
+}
+static void dfree(void* p) { free(p); }
+static void dcopy(void* d, const void* s, size_t n, cudaStream_t) { memcpy(d, s, n); }
+static void dzero(void* d, size_t n, cudaStream_t) { memset(d, 0, n); }
+static void dsync(cudaStream_t) {}
+static void ccheck(const char*) {}
+static void* hpinned(size_t n) { return dalloc(n); }
+static void hfree(void* p) { free(p); }
+#else
+static void ccheck(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(FG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+static void* dalloc(size_t n) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, n ? n : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(FG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return p;
+}
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+static void dcopy(void* d, const void* s, size_t n, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(d, s, n, cudaMemcpyDefault, st);
+  if (e != cudaSuccess) fail(FG_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+}
+static void dzero(void* d, size_t n, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d, 0, n, st);
+  if (e != cudaSuccess) fail(FG_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+}
+static void dsync(cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) fail(FG_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  ccheck("kernel");
+}
+static void* hpinned(size_t n) {
+  void* p = nullptr;
+  if (cudaMallocHost(&p, n) != cudaSuccess) fail(FG_ERR_OOM, "cudaMallocHost failed");
+  return p;
+}
+static void hfree(void* p) {
+  if (p) cudaFreeHost(p);
+}
+#endif
+
+// ------------------------------------------------------------------ context
+
+enum { KS_MECH = 0, KS_PFF = 1, KS_CHEM = 2, KS_MISC = 3, KS_HBAR = 4, KS_N = 5 };
+
+template <typename R>
+struct Prec {
+  using C = cplx<R>;
+  bool on = false;
+  C *S1 = nullptr, *S2 = nullptr;
+  C *twx = nullptr, *twy = nullptr, *twz = nullptr;
+  R *rs[3] = {}, *rc[3] = {}, *lap[3] = {};
+  C* xi[3] = {};
+  R *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *z = nullptr;
+  R *state = nullptr, *kc = nullptr, *w = nullptr, *Hr = nullptr, *tmp3 = nullptr;
+  const SizeOps<R>*ox = nullptr, *oy = nullptr, *oz = nullptr;
+};
+
+}  // namespace fg
+
+struct fg_ctx {
+  int nx = 0, ny = 0, nz = 0, hx = 0;
+  long long V = 0, VH = 0;
+  double h[3] = {0, 0, 0};
+  fg_opts o{};
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+  // FP64 fields
+  double *F = nullptr, *Ft = nullptr, *c = nullptr, *ct = nullptr, *d = nullptr, *dt = nullptr;
+  double *H = nullptr, *Ht = nullptr, *cdotB = nullptr, *P = nullptr, *GP = nullptr;
+  double *mu = nullptr, *base = nullptr;
+  double *lam = nullptr, *mu_ = nullptr, *Om = nullptr, *c0 = nullptr, *D = nullptr, *smax = nullptr;
+  double* partials = nullptr;
+  long long npartials = 0;
+  fg::KScal* ks = nullptr;
+  fg::KScal* ks_host = nullptr;
+  int* flags = nullptr;
+  int* flags_host = nullptr;
+  fg::Prec<double> pd;
+  fg::Prec<float> pf;
+  double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double last_dt = 0.0;
+  bool stepped = false;
+  int last_inner_refine = 0;
+};
+
+namespace fg {
+
+template <typename T>
+static T* alloc_n(fg_ctx& c, long long n) {
+  void* p = dalloc((size_t)n * sizeof(T));
+  c.allocs.push_back(p);
+  return (T*)p;
+}
+
+static void free_all(fg_ctx& c) {
+  for (void* p : c.allocs) dfree(p);
+  c.allocs.clear();
+  hfree(c.ks_host);
+  hfree(c.flags_host);
+  c.ks_host = nullptr;
+  c.flags_host = nullptr;
+}
+
+static bool is_mixed(const fg_ctx& c) { return c.o.precision == FG_MIXED; }
+
+// per-axis frequency tables of one precision (host FP64, then rounded)
+template <typename R>
+static void build_tables(fg_ctx& c, Prec<R>& P) {
+  using C = cplx<R>;
+  const int n[3] = {c.nx, c.ny, c.nz};
+  const int len[3] = {c.hx, c.ny, c.nz};
+  for (int j = 0; j < 3; ++j) {
+    std::vector<R> rs(len[j]), rc(len[j]), lap(len[j]);
+    std::vector<C> xi(len[j]);
+    for (int k = 0; k < len[j]; ++k) {
+      const int ks = (j > 0 && 2 * k > n[j]) ? k - n[j] : k;  // signed index
+      const double th = M_PI * (double)ks / (double)n[j];
+      const double s = sin(th);
+      double co = cos(th);
+      if (2 * std::abs(ks) == n[j]) co = 0.0;
+      rs[k] = (R)(2.0 / c.h[j] * s);
+      rc[k] = (R)co;
+      lap[k] = (R)(4.0 * s * s / (c.h[j] * c.h[j]));
+      const double q = 2.0 * th;
+      xi[k] = cmk<C>((R)((cos(q) - 1.0) / c.h[j]), (R)(sin(q) / c.h[j]));
+    }
+    P.rs[j] = alloc_n<R>(c, len[j]);
+    P.rc[j] = alloc_n<R>(c, len[j]);
+    P.lap[j] = alloc_n<R>(c, len[j]);
+    P.xi[j] = alloc_n<C>(c, len[j]);
+    dcopy(P.rs[j], rs.data(), len[j] * sizeof(R), c.st);
+    dcopy(P.rc[j], rc.data(), len[j] * sizeof(R), c.st);
+    dcopy(P.lap[j], lap.data(), len[j] * sizeof(R), c.st);
+    dcopy(P.xi[j], xi.data(), len[j] * sizeof(C), c.st);
+  }
+  auto tw = [&](int N) {
+    std::vector<C> t(N);
+    for (int m = 0; m < N; ++m) {
+      const double a = 2.0 * M_PI * (double)m / (double)N;
+      t[m] = cmk<C>((R)cos(a), (R)(-sin(a)));
+    }
+    C* d = alloc_n<C>(c, N);
+    dcopy(d, t.data(), N * sizeof(C), c.st);
+    return d;
+  };
+  P.twx = tw(c.nx);
+  P.twy = tw(c.ny);
+  P.twz = tw(c.nz);
+  dsync(c.st);
+}
+
+template <typename R>
+static void setup_prec(fg_ctx& c, Prec<R>& P, int krylov_comps) {
+  P.on = true;
+  P.ox = size_ops<R>(c.nx);
+  P.oy = size_ops<R>(c.ny);
+  P.oz = size_ops<R>(c.nz);
+  if (!P.ox || !P.oy || !P.oz || !P.ox->xf_tangent)
+    fail(FG_ERR_INVALID, "grid size not compiled in (nx, ny, nz)");
+  P.S1 = alloc_n<cplx<R>>(c, 9 * c.VH);
+  P.S2 = alloc_n<cplx<R>>(c, 9 * c.VH);
+  build_tables(c, P);
+  const long long n = (long long)krylov_comps * c.V;
+  P.x = alloc_n<R>(c, n);
+  P.r = alloc_n<R>(c, n);
+  P.p = alloc_n<R>(c, n);
+  P.q = alloc_n<R>(c, n);
+  P.b = alloc_n<R>(c, n);
+  P.z = alloc_n<R>(c, c.V);
+  P.kc = alloc_n<R>(c, 6 * c.V);
+  P.w = alloc_n<R>(c, c.V);
+  P.Hr = alloc_n<R>(c, c.V);
+  P.tmp3 = alloc_n<R>(c, 3 * c.V);
+  if (krylov_comps == 9) P.state = alloc_n<R>(c, 12 * c.V);
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+static VArgs vbase(fg_ctx& c, long long n) {
+  VArgs v{};
+  v.n = n;
+  v.V = c.V;
+  v.partials = c.partials;
+  v.flags = c.flags;
+  return v;
+}
+
+template <class F>
+static void fin(fg_ctx& c, int slot, long long nparts, const int* done, double s0 = 0, double s1 = 0,
+                double s2 = 0) {
+  VArgs v = vbase(c, nparts);
+  v.ks = c.ks + slot;
+  v.done = done;
+  v.s[0] = s0;
+  v.s[1] = s1;
+  v.s[2] = s2;
+  launch_fin<F>(v, c.st);
+}
+
+static void read_ks(fg_ctx& c) {
+  dcopy(c.ks_host, c.ks, KS_N * sizeof(KScal), c.st);
+  dcopy(c.flags_host, c.flags, sizeof(int), c.st);
+  dsync(c.st);
+}
+
+static double reduce_sum(fg_ctx& c, const double* x, long long n, bool sq) {
+  VArgs v = vbase(c, n);
+  v.in[0] = x;
+  if (sq) launch_vec<KSumSq>(v, c.st);
+  else launch_vec<KSum>(v, c.st);
+  fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+  read_ks(c);
+  return c.ks_host[KS_MISC].aux;
+}
+
+template <typename R>
+static PassArgs<R> pbase(fg_ctx& c, Prec<R>& P, const int* done) {
+  PassArgs<R> a{};
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.nz = c.nz;
+  a.hx = c.hx;
+  a.V = c.V;
+  a.VH = c.VH;
+  for (int j = 0; j < 3; ++j) {
+    a.rs[j] = P.rs[j];
+    a.rc[j] = P.rc[j];
+    a.xi[j] = P.xi[j];
+    a.lap[j] = P.lap[j];
+  }
+  a.partials = c.partials;
+  a.done = done;
+  return a;
+}
+
+// Y-fwd, Z op, Y-inv on the spectrum in S1 (ncomp_in comps) -> S1 (ncomp_out comps)
+template <typename R>
+static void yzy(fg_ctx& c, Prec<R>& P, const int* done, int cin, PassFn<R> zop, int cout,
+                const R* zcoef, const double* dscal) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twy;
+  a.cin = P.S1;
+  a.cout = P.S2;
+  a.ncomp = cin;
+  P.oy->yf(a, c.st);
+  a = pbase(c, P, done);
+  a.tw = P.twz;
+  a.cin = P.S2;
+  a.cout = P.S2;
+  for (int k = 0; k < 4; ++k) a.coef[k] = zcoef[k];
+  a.dscal = dscal;
+  zop(a, c.st);
+  a = pbase(c, P, done);
+  a.tw = P.twy;
+  a.cin = P.S2;
+  a.cout = P.S1;
+  a.ncomp = cout;
+  P.oy->yi(a, c.st);
+}
+
+// y = G : F^-1[ F[K : x] ] ; accumulates <x, y>; returns partial count
+template <typename R>
+static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = x;
+  a.aux[0] = P.state;
+  a.cout = P.S1;
+  P.ox->xf_tangent(a, c.st);
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = y;
+  a.aux[0] = x;
+  return P.ox->xi_storedot9(a, c.st);
+}
+
+// y = G * x (projection of a tensor field), accumulates |y|^2
+template <typename R>
+static int op_gres(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = x;
+  a.cout = P.S1;
+  P.ox->xf_copy9(a, c.st);
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = y;
+  return P.ox->xi_norm9(a, c.st);
+}
+
+// y = [g_c/l_c + 2H] x + F^-1{ g_c l_c |xi|^2 x^ } ; accumulates <x, y>
+template <typename R>
+static int op_pff(fg_ctx& c, Prec<R>& P, const R* x, R* y, const R* H, const int* done) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = x;
+  a.cout = P.S1;
+  P.ox->xf_copy1(a, c.st);
+  const R zc[4] = {(R)(c.o.gc * c.o.lc / (double)c.V), 0, 0, 0};
+  yzy(c, P, done, 1, P.oz->z_lap, 1, zc, nullptr);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = y;
+  a.aux[0] = x;
+  a.aux[1] = H;
+  a.coef[0] = (R)(c.o.gc / c.o.lc);
+  return P.ox->xi_pff(a, c.st);
+}
+
+// z = F^-1{ r^ / (g_c/l_c + 2 Hbar + g_c l_c |xi|^2) } ; accumulates <r, z>
+template <typename R>
+static int op_prec(fg_ctx& c, Prec<R>& P, const R* r, R* z, const int* done) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = r;
+  a.cout = P.S1;
+  P.ox->xf_copy1(a, c.st);
+  const R zc[4] = {(R)(1.0 / (double)c.V), (R)(c.o.gc / c.o.lc), (R)(c.o.gc * c.o.lc), 0};
+  yzy(c, P, done, 1, P.oz->z_prec, 1, zc, &c.ks[KS_HBAR].aux);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = z;
+  a.aux[0] = r;
+  return P.ox->xi_storedot1(a, c.st);
+}
+
+// L u = grad_f^H (K_c grad_f u) into S1 (1 comp), K_c from P.kc
+template <typename R>
+static void op_chem_L(fg_ctx& c, Prec<R>& P, const R* u, const int* done) {
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = u;
+  a.cout = P.S1;
+  P.ox->xf_copy1(a, c.st);
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  yzy(c, P, done, 1, P.oz->z_grad, 3, zc, nullptr);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = P.tmp3;
+  a.aux[0] = P.kc;
+  P.ox->xi_chemflux(a, c.st);
+  a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.rin = P.tmp3;
+  a.cout = P.S1;
+  P.ox->xf_copy3(a, c.st);
+  yzy(c, P, done, 3, P.oz->z_div, 1, zc, nullptr);
+}
+
+// y = x c(1-c) + dt L x ; accumulates <x, y>
+template <typename R>
+static int op_chem(fg_ctx& c, Prec<R>& P, const R* x, R* y, double dt, const int* done) {
+  op_chem_L(c, P, x, done);
+  PassArgs<R> a = pbase(c, P, done);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = y;
+  a.aux[0] = x;
+  a.aux[1] = P.w;
+  a.coef[0] = (R)dt;
+  return P.ox->xi_chemop(a, c.st);
+}
+
+// b = -(base + dt L mu) in FP64 ; returns |b|^2 partial count
+static int op_chem_rhs(fg_ctx& c, double* b, double dt) {
+  Prec<double>& P = c.pd;
+  op_chem_L(c, P, c.mu, nullptr);
+  PassArgs<double> a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = b;
+  a.aux[0] = c.base;
+  a.coef[0] = dt;
+  return P.ox->xi_chemrhs(a, c.st);
+}
+
+// ------------------------------------------------------------------ state kernels
+
+template <typename R>
+static void mech_state(fg_ctx& c, const double* F, const double* Fbar, double* Pout, R* state) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = F;
+  if (!F)
+    for (int k = 0; k < 9; ++k) v.s[k] = Fbar[k];
+  v.in[1] = c.c;
+  v.in[2] = c.d;
+  v.in[3] = c.lam;
+  v.in[4] = c.mu_;
+  v.in[5] = c.Om;
+  v.in[6] = c.c0;
+  v.out[0] = Pout;
+  v.out[1] = state;
+  launch_vec<KMechState<R>>(v, c.st);
+}
+
+template <typename R>
+static void to_prec(fg_ctx& c, const double* x, R* y, long long n, double s) {
+  VArgs v = vbase(c, n);
+  v.in[0] = x;
+  v.out[0] = y;
+  v.s[0] = s;
+  launch_vec<KScaleTo<R>>(v, c.st);
+}
+
+static void check_flags(fg_ctx& c, const char* where) {
+  if (*c.flags_host & ST_DOMAIN) {
+    dzero(c.flags, sizeof(int), c.st);
+    fail(FG_ERR_DOMAIN, std::string(where) + ": c left (0,1) or det F <= 0");
+  }
+  if (*c.flags_host & ST_NUMERIC) {
+    dzero(c.flags, sizeof(int), c.st);
+    fail(FG_ERR_NUMERIC, std::string(where) + ": non-finite value");
+  }
+}
+
+// ------------------------------------------------------------------ Krylov drivers
+
+// Conjugate gradients on P.b (n elements) from x = 0; result in P.x.  apply(p, q, done)
+// computes q = A p and the partial sums of <p, q>, returning their count.
+template <typename R, class Apply>
+static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, int maxit, Apply apply) {
+  KScal* ks = c.ks + slot;
+  VArgs v = vbase(c, n);
+  v.in[0] = P.b;
+  v.out[0] = P.x;
+  v.out[1] = P.r;
+  v.out[2] = P.p;
+  launch_vec<KCgInit<R>>(v, c.st);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit);
+  const int* done = &ks->done;
+  int chunk = 4;
+  while (true) {
+    for (int j = 0; j < chunk; ++j) {
+      const int nb = apply(P.p, P.q, done);
+      fin<FAlpha>(c, slot, nb, done);
+      VArgs u = vbase(c, n);
+      u.ks = ks;
+      u.done = done;
+      u.in[0] = P.p;
+      u.in[1] = P.q;
+      u.out[0] = P.x;
+      u.out[1] = P.r;
+      launch_vec<KCgXR<R>>(u, c.st);
+      fin<FBetaCg>(c, slot, VEC_BLOCKS, done);
+      VArgs w = vbase(c, n);
+      w.ks = ks;
+      w.done = done;
+      w.in[0] = P.r;
+      w.out[0] = P.p;
+      launch_vec<KCgP<R>>(w, c.st);
+    }
+    read_ks(c);
+    if (c.ks_host[slot].done) break;
+    if (chunk < 16) chunk *= 2;
+  }
+  const KScal& k = c.ks_host[slot];
+  if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
+  if (k.status & ST_INDEFINITE) fail(FG_ERR_NUMERIC, "Krylov operator not positive definite");
+  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+  return k.iters;
+}
+
+// Preconditioned CG for the phase field (Alg. 2) on P.b from x0 = P.x (V elements).
+template <typename R>
+static int pcg_pff(fg_ctx& c, Prec<R>& P, const R* H, double tol, int maxit) {
+  const long long n = c.V;
+  const int slot = KS_PFF;
+  KScal* ks = c.ks + slot;
+  // bb
+  {
+    VArgs v = vbase(c, n);
+    v.in[0] = P.b;
+    launch_vec<KSumSqR<R>>(v, c.st);
+    fin<FStore>(c, slot, VEC_BLOCKS, nullptr);
+  }
+  read_ks(c);
+  const double bb = c.ks_host[slot].aux;
+  // r = b - A x0
+  op_pff(c, P, P.x, P.q, H, nullptr);
+  {
+    VArgs v = vbase(c, n);
+    v.in[0] = P.b;
+    v.in[1] = P.q;
+    v.out[0] = P.r;
+    launch_vec<KResid<R>>(v, c.st);
+    fin<FPcgStart>(c, slot, VEC_BLOCKS, nullptr, tol, bb, (double)maxit);
+  }
+  const int* done = &ks->done;
+  {
+    const int nb = op_prec(c, P, P.r, P.z, done);
+    fin<FPcgRz>(c, slot, nb, done);
+    VArgs v = vbase(c, n);
+    v.done = done;
+    v.in[0] = P.z;
+    v.out[0] = P.p;
+    launch_vec<KCopy<R>>(v, c.st);
+  }
+  int chunk = 4;
+  while (true) {
+    for (int j = 0; j < chunk; ++j) {
+      int nb = op_pff(c, P, P.p, P.q, H, done);
+      fin<FAlpha>(c, slot, nb, done);
+      VArgs u = vbase(c, n);
+      u.ks = ks;
+      u.done = done;
+      u.in[0] = P.p;
+      u.in[1] = P.q;
+      u.out[0] = P.x;
+      u.out[1] = P.r;
+      launch_vec<KCgXR<R>>(u, c.st);
+      fin<FResPcg>(c, slot, VEC_BLOCKS, done);
+      nb = op_prec(c, P, P.r, P.z, done);
+      fin<FBetaPcg>(c, slot, nb, done);
+      VArgs w = vbase(c, n);
+      w.ks = ks;
+      w.done = done;
+      w.in[0] = P.z;
+      w.out[0] = P.p;
+      launch_vec<KCgP<R>>(w, c.st);
+    }
+    read_ks(c);
+    if (c.ks_host[slot].done) break;
+    if (chunk < 16) chunk *= 2;
+  }
+  const KScal& k = c.ks_host[slot];
+  if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "phase-field solve produced a non-finite value");
+  if (k.status & ST_INDEFINITE) fail(FG_ERR_NUMERIC, "phase-field operator not positive definite");
+  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "phase-field PCG hit max_cg");
+  return k.iters;
+}
+
+// ------------------------------------------------------------------ solves
+
+static double mixed_tol(const fg_ctx& c, double tol) {
+  return is_mixed(c) ? std::max(tol, c.o.cg_forcing) : tol;
+}
+
+// ||G*P(Fbar)|| with the fallbacks ||P(Fbar)||, then 1
+static double residual_den(fg_ctx& c) {
+  mech_state<double>(c, nullptr, c.Fbar, c.P, nullptr);
+  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
+  fin<FStore>(c, KS_MISC, nb, nullptr);
+  read_ks(c);
+  check_flags(c, "residual");
+  const double g = sqrt(c.ks_host[KS_MISC].aux);
+  const double p = sqrt(reduce_sum(c, c.P, 9 * c.V, true));
+  double den = g;
+  if (den <= 1e-12 * p) den = p;
+  if (den == 0.0) den = 1.0;
+  return den;
+}
+
+// err_res of the current (F, c, d); leaves G*P in c.GP and the tangent state of
+// precision R in P.state when state != null
+template <typename R>
+static double residual_mech(fg_ctx& c, double den, R* state) {
+  mech_state<R>(c, c.F, nullptr, c.P, state);
+  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
+  fin<FStore>(c, KS_MISC, nb, nullptr);
+  read_ks(c);
+  check_flags(c, "residual");
+  return sqrt(c.ks_host[KS_MISC].aux) / den;
+}
+
+template <typename R>
+static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
+  for (int it = 0;; ++it) {
+    const double err = residual_mech<R>(c, den, P.state);
+    s.err_mech = err;
+    if (!(err == err)) fail(FG_ERR_NUMERIC, "mechanical residual is not finite");
+    if (err <= c.o.tol_newton) return;
+    if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
+    to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
+    const int n = cg_solve<R>(c, P, 9 * c.V, KS_MECH, mixed_tol(c, c.o.tol_cg), c.o.max_cg,
+                              [&](const R* p, R* q, const int* done) { return op_mech(c, P, p, q, done); });
+    s.cg_mech += n;
+    s.newton_mech += 1;
+    VArgs v = vbase(c, 9 * c.V);
+    v.in[0] = P.x;
+    v.out[0] = c.F;
+    launch_vec<KAddTo<R>>(v, c.st);
+  }
+}
+
+struct FScaleAux {
+  FG_DEV static void fin(const VArgs& a, double t) { a.ks->aux = t * a.s[0]; }
+};
+
+// H = max(H_t, g_c/(2 l_c) D_f(F, c)); Hbar = mean H to the device scalar
+static void history(fg_ctx& c) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = c.F;
+  v.in[1] = c.c;
+  v.in[2] = c.Ht;
+  v.in[3] = c.lam;
+  v.in[4] = c.mu_;
+  v.in[5] = c.Om;
+  v.in[6] = c.c0;
+  v.in[7] = c.smax;
+  v.out[0] = c.H;
+  v.s[0] = c.o.gc / (2.0 * c.o.lc);
+  launch_vec<KHistory>(v, c.st);
+  fin<FScaleAux>(c, KS_HBAR, VEC_BLOCKS, nullptr, 1.0 / (double)c.V);
+}
+
+// Hbar = mean H of the stored H
+static void hbar_from_sum(fg_ctx& c) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = c.H;
+  launch_vec<KSum>(v, c.st);
+  fin<FScaleAux>(c, KS_HBAR, VEC_BLOCKS, nullptr, 1.0 / (double)c.V);
+}
+
+template <typename R>
+static void pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
+  if (!is_mixed(c)) {
+    to_prec<double>(c, c.H, c.pd.b, c.V, 2.0);
+    dcopy(c.pd.x, c.d, c.V * sizeof(double), c.st);
+    s.cg_pff += pcg_pff<double>(c, c.pd, c.H, c.o.tol_pff_cg, c.o.max_cg);
+    dcopy(c.d, c.pd.x, c.V * sizeof(double), c.st);
+    return;
+  }
+  // mixed: FP64 residual b - A d, FP32 PCG corrections
+  to_prec<R>(c, c.H, P.Hr, c.V, 1.0);
+  const double bb = 4.0 * reduce_sum(c, c.H, c.V, true);
+  if (bb == 0.0) {
+    dzero(c.d, c.V * sizeof(double), c.st);
+    return;
+  }
+  Prec<double>& D = c.pd;
+  for (int it = 0;; ++it) {
+    op_pff(c, D, c.d, D.q, c.H, nullptr);  // q = A d in FP64
+    {
+      VArgs t = vbase(c, c.V);  // b = 2H
+      t.in[0] = c.H;
+      t.out[0] = D.b;
+      t.s[0] = 2.0;
+      launch_vec<KScaleTo<double>>(t, c.st);
+    }
+    {
+      VArgs v = vbase(c, c.V);  // r = b - A d
+      v.in[0] = D.b;
+      v.in[1] = D.q;
+      v.out[0] = D.r;
+      launch_vec<KResid<double>>(v, c.st);
+      fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+    }
+    read_ks(c);
+    const double rr = c.ks_host[KS_MISC].aux;
+    if (rr <= c.o.tol_pff_cg * c.o.tol_pff_cg * bb) break;
+    if (it >= 50) fail(FG_ERR_NOCONV, "phase-field refinement did not converge");
+    to_prec<R>(c, D.r, P.b, c.V, 1.0);
+    dzero(P.x, c.V * sizeof(R), c.st);
+    s.cg_pff += pcg_pff<R>(c, P, P.Hr, std::max(c.o.tol_pff_cg, c.o.cg_forcing), c.o.max_cg);
+    s.inner_refine += 1;
+    VArgs u = vbase(c, c.V);
+    u.in[0] = P.x;
+    u.out[0] = c.d;
+    launch_vec<KAddTo<R>>(u, c.st);
+  }
+}
+
+template <typename R>
+static void chem_cond(fg_ctx& c, Prec<R>& P, const double* F, const double* ct, const double* dt) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = F;
+  v.in[1] = ct;
+  v.in[2] = dt;
+  v.in[3] = c.D;
+  v.out[0] = P.kc;
+  launch_vec<KChemCond<R>>(v, c.st);
+}
+
+template <typename R>
+static void chem_prep(fg_ctx& c, Prec<R>& P, double dt) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = c.c;
+  v.in[1] = c.ct;
+  v.in[2] = c.cdotB;
+  v.in[3] = c.F;
+  v.in[4] = c.dt;
+  v.in[5] = c.lam;
+  v.in[6] = c.mu_;
+  v.in[7] = c.Om;
+  v.in[8] = c.c0;
+  v.out[0] = c.mu;
+  v.out[1] = c.base;
+  v.out[2] = P.w;
+  v.s[0] = dt;
+  v.s[1] = 1.0 / c.o.RT;
+  v.s[2] = 1.0 / c.o.cmax;
+  launch_vec<KChemPrep<R>>(v, c.st);
+}
+
+template <typename R>
+static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
+  chem_cond<R>(c, P, c.F, c.ct, c.dt);
+  if (is_mixed(c)) chem_cond<double>(c, c.pd, c.F, c.ct, c.dt);
+  dcopy(c.c, c.ct, c.V * sizeof(double), c.st);
+  const double nct = sqrt(reduce_sum(c, c.ct, c.V, true));
+  for (int it = 0;; ++it) {
+    if (it >= c.o.max_chem_newton) fail(FG_ERR_NOCONV, "chemical Newton hit max_chem_newton");
+    chem_prep<R>(c, P, dt);
+    read_ks(c);
+    check_flags(c, "chemistry");
+    double* b64 = is_mixed(c) ? c.pd.b : (double*)P.b;
+    op_chem_rhs(c, b64, dt);
+    if (is_mixed(c)) to_prec<R>(c, b64, P.b, c.V, 1.0);
+    const int n = cg_solve<R>(c, P, c.V, KS_CHEM, mixed_tol(c, c.o.tol_chem_cg), c.o.max_cg,
+                              [&](const R* p, R* q, const int* done) { return op_chem(c, P, p, q, dt, done); });
+    s.cg_chem += n;
+    s.newton_chem += 1;
+    VArgs v = vbase(c, c.V);
+    v.in[0] = P.x;
+    v.out[0] = c.c;
+    launch_vec<KChemUpdate<R>>(v, c.st);
+    fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+    read_ks(c);
+    check_flags(c, "chemistry");
+    const double rel = sqrt(c.ks_host[KS_MISC].aux) / nct;
+    s.err_chem = rel;
+    if (rel < c.o.tol_chem) return;
+  }
+}
+
+template <typename R>
+static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_stats& s) {
+  const long long V = c.V;
+  // t-state
+  dcopy(c.Ft, c.F, 9 * V * sizeof(double), c.st);
+  dcopy(c.ct, c.c, V * sizeof(double), c.st);
+  dcopy(c.dt, c.d, V * sizeof(double), c.st);
+  dcopy(c.Ht, c.H, V * sizeof(double), c.st);
+  const double mass_t = reduce_sum(c, c.ct, V, false);
+  const double src = reduce_sum(c, c.cdotB, V, false);
+  // F = F_t + (Fbar_{t+dt} - Fbar_t)
+  {
+    VArgs v = vbase(c, 9 * V);
+    v.in[0] = c.Ft;
+    v.out[0] = c.F;
+    for (int k = 0; k < 9; ++k) v.s[k] = Fbar[k] - c.Fbar[k];
+    launch_vec<KShiftF>(v, c.st);
+  }
+  double Fbar_old[9];
+  memcpy(Fbar_old, c.Fbar, sizeof(Fbar_old));
+  memcpy(c.Fbar, Fbar, sizeof(c.Fbar));
+  try {
+    chem_solve<R>(c, P, dt, s);
+    const double mass = reduce_sum(c, c.c, V, false);
+    s.mass = mass;
+    s.mass_err = (mass - (mass_t + dt * src)) / (mass != 0.0 ? mass : 1.0);
+    for (int k = 0;; ++k) {
+      const double den = residual_den(c);
+      const double err = residual_mech<double>(c, den, nullptr);
+      s.err_mech = err;
+      if (err <= c.o.tol_stag) break;
+      if (k >= c.o.max_stag) fail(FG_ERR_NOCONV, "staggered scheme hit max_stag");
+      mech_newton<R>(c, P, den, s);
+      history(c);
+      pff_solve<R>(c, P, s);
+      s.stag += 1;
+    }
+  } catch (Fail&) {
+    // restore the t-state
+    dcopy(c.F, c.Ft, 9 * V * sizeof(double), c.st);
+    dcopy(c.c, c.ct, V * sizeof(double), c.st);
+    dcopy(c.d, c.dt, V * sizeof(double), c.st);
+    dcopy(c.H, c.Ht, V * sizeof(double), c.st);
+    memcpy(c.Fbar, Fbar_old, sizeof(c.Fbar));
+    dsync(c.st);
+    throw;
+  }
+  c.last_dt = dt;
+  c.stepped = true;
+  dsync(c.st);
+}
+
+}  // namespace fg
+
+using namespace fg;
+
+template <typename R>
+static double do_apply(fg_ctx& c, Prec<R>& P, int op, const R* x, R* y, double dt) {
+  int nb = 0;
+  switch (op) {
+    case FG_OP_MECH:
+      if (!P.state) fail(FG_ERR_INVALID, "fg_apply: no tangent state in this precision");
+      mech_state<R>(c, c.F, nullptr, nullptr, P.state);
+      nb = op_mech(c, P, x, y, nullptr);
+      break;
+    case FG_OP_GRES:
+      nb = op_gres(c, P, x, y, nullptr);
+      break;
+    case FG_OP_PFF: {
+      const R* H;
+      if constexpr (sizeof(R) == 8) H = (const R*)c.H;
+      else {
+        to_prec<R>(c, c.H, P.Hr, c.V, 1.0);
+        H = P.Hr;
+      }
+      nb = op_pff(c, P, x, y, H, nullptr);
+      break;
+    }
+    case FG_OP_PFF_PREC:
+      hbar_from_sum(c);
+      nb = op_prec(c, P, x, y, nullptr);
+      break;
+    case FG_OP_CHEM:
+      dcopy(c.ct, c.c, c.V * sizeof(double), c.st);
+      dcopy(c.dt, c.d, c.V * sizeof(double), c.st);
+      chem_cond<R>(c, P, c.F, c.c, c.d);
+      chem_prep<R>(c, P, dt);
+      nb = op_chem(c, P, x, y, dt, nullptr);
+      break;
+    default:
+      fail(FG_ERR_INVALID, "fg_apply: unknown operator");
+  }
+  fin<FStore>(c, KS_MISC, nb, nullptr);
+  read_ks(c);
+  check_flags(c, "apply");
+  return c.ks_host[KS_MISC].aux;
+}
+
+// ================================================================== C ABI
+
+#define FG_API_BEGIN \
+  g_err.clear();     \
+  try {
+#define FG_API_END                                     \
+  }                                                    \
+  catch (Fail & f) {                                   \
+    return f.code;                                     \
+  }                                                    \
+  catch (std::exception & e) {                         \
+    g_err = e.what();                                  \
+    return FG_ERR_INVALID;                             \
+  }                                                    \
+  return FG_OK;
+
+extern "C" {
+
+void fg_default_opts(fg_opts* o) {
+  memset(o, 0, sizeof(*o));
+  o->precision = FG_FP64;
+  o->gc = 1.0;
+  o->lc = 2e-7;
+  o->RT = 8.314462618 * 298.15;
+  o->cmax = 3.0e4;
+  o->tol_newton = 1e-9;
+  o->tol_cg = 1e-10;
+  o->tol_chem = 1e-9;
+  o->tol_chem_cg = 1e-10;
+  o->tol_pff_cg = 1e-10;
+  o->tol_stag = 1e-9;
+  o->cg_forcing = 1e-5;
+  o->max_newton = 30;
+  o->max_cg = 5000;
+  o->max_chem_newton = 50;
+  o->max_stag = 50;
+  o->cuda_stream = nullptr;
+}
+
+int fg_supported_size(int n) {
+  const SizeOps<double>* s = size_ops<double>(n);
+  return s != nullptr && size_ops<float>(n) != nullptr;
+}
+
+const char* fg_last_error(void) { return g_err.c_str(); }
+
+void fg_destroy(fg_ctx* ctx) {
+  if (!ctx) return;
+#ifndef FG_EMU
+  cudaStreamSynchronize(ctx->st);
+#endif
+  free_all(*ctx);
+  delete ctx;
+}
+
+int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases,
+             const uint8_t* phase_id, const double* cdot_B, const double* c_init,
+             const double* log_E, const double* log_D, const fg_opts* opts) {
+  FG_API_BEGIN
+  if (!out || !g || !phases || nphases <= 0 || nphases > 255 || !phase_id || !cdot_B)
+    fail(FG_ERR_INVALID, "fg_setup: null argument or bad phase count");
+  *out = nullptr;
+  if (g->nx < 2 || g->ny < 1 || g->nz < 1 || g->nx % 2)
+    fail(FG_ERR_INVALID, "fg_setup: nx must be even and >= 2, ny, nz >= 1");
+  if (!(g->hx > 0 && g->hy > 0 && g->hz > 0)) fail(FG_ERR_INVALID, "fg_setup: voxel size <= 0");
+  if (!fg_supported_size(g->nx) || !fg_supported_size(g->ny) || !fg_supported_size(g->nz))
+    fail(FG_ERR_INVALID, "fg_setup: transform length not compiled in");
+  for (int k = 0; k < nphases; ++k) {
+    if (phases[k].law != FG_NEOHOOKE)
+      fail(FG_ERR_INVALID, "fg_setup: only the compressible Neo-Hookean law runs on the GPU path");
+    if (!(phases[k].E > 0) || !(phases[k].nu > -1 && phases[k].nu < 0.5) || !(phases[k].D >= 0) ||
+        !(phases[k].sigma_max > 0))
+      fail(FG_ERR_INVALID, "fg_setup: bad phase constants");
+  }
+  fg_opts o;
+  if (opts) o = *opts;
+  else fg_default_opts(&o);
+  if (o.precision != FG_FP64 && o.precision != FG_MIXED) fail(FG_ERR_INVALID, "fg_setup: precision");
+  if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
+  fg_ctx* c = new fg_ctx();
+  try {
+    c->nx = g->nx;
+    c->ny = g->ny;
+    c->nz = g->nz;
+    c->hx = g->nx / 2 + 1;
+    c->V = (long long)g->nx * g->ny * g->nz;
+    c->VH = (long long)c->hx * g->ny * g->nz;
+    c->h[0] = g->hx;
+    c->h[1] = g->hy;
+    c->h[2] = g->hz;
+    c->o = o;
+    c->st = (cudaStream_t)o.cuda_stream;
+    const long long V = c->V;
+    // per-voxel material on the host
+    std::vector<double> lam(V), mu(V), Om(V), c0(V), D(V), sm(V), cin(V);
+    for (long long v = 0; v < V; ++v) {
+      const int id = phase_id[v];
+      if (id >= nphases) fail(FG_ERR_INVALID, "fg_setup: phase id out of range");
+      const fg_phase& p = phases[id];
+      double E = p.E;
+      if (log_E) E *= exp(log_E[v]);
+      lam[v] = E * p.nu / ((1.0 + p.nu) * (1.0 - 2.0 * p.nu));
+      mu[v] = E / (2.0 * (1.0 + p.nu));
+      Om[v] = p.Omega;
+      c0[v] = p.c0;
+      D[v] = p.D * (log_D ? exp(log_D[v]) : 1.0);
+      sm[v] = p.sigma_max;
+      cin[v] = c_init ? c_init[v] : p.c0;
+      if (!(cin[v] > 0.0 && cin[v] < 1.0)) fail(FG_ERR_DOMAIN, "fg_setup: initial c outside (0,1)");
+    }
+    auto up = [&](const std::vector<double>& h) {
+      double* d = alloc_n<double>(*c, V);
+      dcopy(d, h.data(), V * sizeof(double), c->st);
+      return d;
+    };
+    c->lam = up(lam);
+    c->mu_ = up(mu);
+    c->Om = up(Om);
+    c->c0 = up(c0);
+    c->D = up(D);
+    c->smax = up(sm);
+    c->c = up(cin);
+    c->cdotB = alloc_n<double>(*c, V);
+    dcopy(c->cdotB, cdot_B, V * sizeof(double), c->st);
+    c->F = alloc_n<double>(*c, 9 * V);
+    c->Ft = alloc_n<double>(*c, 9 * V);
+    c->P = alloc_n<double>(*c, 9 * V);
+    c->GP = alloc_n<double>(*c, 9 * V);
+    c->ct = alloc_n<double>(*c, V);
+    c->d = alloc_n<double>(*c, V);
+    c->dt = alloc_n<double>(*c, V);
+    c->H = alloc_n<double>(*c, V);
+    c->Ht = alloc_n<double>(*c, V);
+    c->mu = alloc_n<double>(*c, V);
+    c->base = alloc_n<double>(*c, V);
+    {
+      std::vector<double> F(9 * V, 0.0);
+      for (int i = 0; i < 3; ++i)
+        for (long long v = 0; v < V; ++v) F[(4 * i) * V + v] = 1.0;
+      dcopy(c->F, F.data(), 9 * V * sizeof(double), c->st);
+      dzero(c->d, V * sizeof(double), c->st);
+      dzero(c->H, V * sizeof(double), c->st);
+      dcopy(c->ct, c->c, V * sizeof(double), c->st);
+      dzero(c->dt, V * sizeof(double), c->st);
+      dzero(c->Ht, V * sizeof(double), c->st);
+      dcopy(c->Ft, c->F, 9 * V * sizeof(double), c->st);
+    }
+    c->npartials = (long long)g->ny * g->nz + VEC_BLOCKS + 64;
+    c->partials = alloc_n<double>(*c, c->npartials);
+    c->ks = alloc_n<KScal>(*c, KS_N);
+    dzero(c->ks, KS_N * sizeof(KScal), c->st);
+    c->flags = alloc_n<int>(*c, 1);
+    dzero(c->flags, sizeof(int), c->st);
+    c->ks_host = (KScal*)hpinned(KS_N * sizeof(KScal));
+    c->flags_host = (int*)hpinned(sizeof(int));
+    if (o.precision == FG_MIXED) {
+      setup_prec<double>(*c, c->pd, 1);
+      setup_prec<float>(*c, c->pf, 9);
+    } else {
+      setup_prec<double>(*c, c->pd, 9);
+    }
+    dsync(c->st);
+  } catch (...) {
+    fg_destroy(c);
+    throw;
+  }
+  *out = c;
+  FG_API_END
+}
+
+int fg_step(fg_ctx* c, double dt, const double Fbar[9], fg_stats* st) {
+  fg_stats s;
+  memset(&s, 0, sizeof(s));
+  int rc = FG_OK;
+  g_err.clear();
+  try {
+    if (!c || !Fbar || !(dt > 0)) fail(FG_ERR_INVALID, "fg_step: bad argument");
+    if (is_mixed(*c)) step_impl<float>(*c, c->pf, dt, Fbar, s);
+    else step_impl<double>(*c, c->pd, dt, Fbar, s);
+  } catch (Fail& f) {
+    rc = f.code;
+  }
+  s.status = rc;
+  if (st) *st = s;
+  return rc;
+}
+
+int fg_residual(fg_ctx* c, double* err_mech, double* err_chem, double* mass_sum) {
+  FG_API_BEGIN
+  if (!c) fail(FG_ERR_INVALID, "fg_residual: null context");
+  if (err_mech) {
+    const double den = residual_den(*c);
+    *err_mech = residual_mech<double>(*c, den, nullptr);
+  }
+  if (err_chem) {
+    *err_chem = 0.0;
+    if (c->stepped) {
+      chem_cond<double>(*c, c->pd, c->Ft, c->ct, c->dt);
+      chem_prep<double>(*c, c->pd, c->last_dt);
+      const int nb = op_chem_rhs(*c, c->pd.b, c->last_dt);
+      fin<FStore>(*c, KS_MISC, nb, nullptr);
+      read_ks(*c);
+      *err_chem = sqrt(c->ks_host[KS_MISC].aux);
+    }
+  }
+  if (mass_sum) *mass_sum = reduce_sum(*c, c->c, c->V, false);
+  dsync(c->st);
+  FG_API_END
+}
+
+int fg_apply(fg_ctx* c, int op, int prec, const void* x, void* y, double dt, double* dot) {
+  FG_API_BEGIN
+  if (!c || !x || !y) fail(FG_ERR_INVALID, "fg_apply: null argument");
+  double d = 0.0;
+  if (prec == 0) {
+    if (!c->pd.state && (op == FG_OP_MECH)) fail(FG_ERR_INVALID, "fg_apply: FP64 tangent needs an FP64 context");
+    if (c->pd.state == nullptr && op != FG_OP_GRES && !c->pd.on) fail(FG_ERR_INVALID, "fg_apply: FP64 operators unavailable");
+    d = do_apply<double>(*c, c->pd, op, (const double*)x, (double*)y, dt);
+  } else if (prec == 1) {
+    if (!c->pf.on) fail(FG_ERR_INVALID, "fg_apply: FP32 operators need a mixed-precision context");
+    if (op == FG_OP_GRES) fail(FG_ERR_INVALID, "fg_apply: residual projection is FP64 only");
+    d = do_apply<float>(*c, c->pf, op, (const float*)x, (float*)y, dt);
+  } else {
+    fail(FG_ERR_INVALID, "fg_apply: prec must be 0 or 1");
+  }
+  if (dot) *dot = d;
+  FG_API_END
+}
+
+int fg_get_field(fg_ctx* c, int field, void* dst, int on_device) {
+  FG_API_BEGIN
+  if (!c || !dst) fail(FG_ERR_INVALID, "fg_get_field: null argument");
+  const double* src = nullptr;
+  long long n = c->V;
+  switch (field) {
+    case FG_FIELD_C: src = c->c; break;
+    case FG_FIELD_F: src = c->F; n = 9 * c->V; break;
+    case FG_FIELD_D: src = c->d; break;
+    case FG_FIELD_H: src = c->H; break;
+    case FG_FIELD_P:
+      mech_state<double>(*c, c->F, nullptr, c->P, nullptr);
+      src = c->P;
+      n = 9 * c->V;
+      break;
+    default: fail(FG_ERR_INVALID, "fg_get_field: unknown field");
+  }
+  (void)on_device;
+  dcopy(dst, src, n * sizeof(double), c->st);
+  dsync(c->st);
+  FG_API_END
+}
+
+int fg_set_field(fg_ctx* c, int field, const void* src, int on_device) {
+  FG_API_BEGIN
+  if (!c || !src) fail(FG_ERR_INVALID, "fg_set_field: null argument");
+  double* dst = nullptr;
+  double* dst_t = nullptr;
+  long long n = c->V;
+  switch (field) {
+    case FG_FIELD_C: dst = c->c; dst_t = c->ct; break;
+    case FG_FIELD_F: dst = c->F; dst_t = c->Ft; n = 9 * c->V; break;
+    case FG_FIELD_D: dst = c->d; dst_t = c->dt; break;
+    case FG_FIELD_H: dst = c->H; dst_t = c->Ht; break;
+    default: fail(FG_ERR_INVALID, "fg_set_field: unknown or read-only field");
+  }
+  (void)on_device;
+  dcopy(dst, src, n * sizeof(double), c->st);
+  dcopy(dst_t, src, n * sizeof(double), c->st);
+  dsync(c->st);
+  FG_API_END
+}
+
+int fg_time_apply(fg_ctx* c, int op, int prec, int n, double* ms) {
+  FG_API_BEGIN
+  if (!c || n <= 0 || !ms) fail(FG_ERR_INVALID, "fg_time_apply: bad argument");
+#ifdef FG_EMU
+  fail(FG_ERR_INVALID, "fg_time_apply: needs the GPU build");
+#else
+  const long long nel = (op == FG_OP_MECH || op == FG_OP_GRES) ? 9 * c->V : c->V;
+  const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
+  void* x = dalloc(nel * es);
+  void* y = dalloc(nel * es);
+  dzero(x, nel * es, c->st);
+  // prepare the operator state once with a first application
+  double dummy;
+  if (prec == 0) dummy = do_apply<double>(*c, c->pd, op, (const double*)x, (double*)y, 1.0);
+  else dummy = do_apply<float>(*c, c->pf, op, (const float*)x, (float*)y, 1.0);
+  (void)dummy;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->st);
+  for (int i = 0; i < n; ++i) {
+    if (prec == 0) {
+      Prec<double>& P = c->pd;
+      switch (op) {
+        case FG_OP_MECH: op_mech(*c, P, (const double*)x, (double*)y, nullptr); break;
+        case FG_OP_GRES: op_gres(*c, P, (const double*)x, (double*)y, nullptr); break;
+        case FG_OP_PFF: op_pff(*c, P, (const double*)x, (double*)y, (const double*)c->H, nullptr); break;
+        case FG_OP_PFF_PREC: op_prec(*c, P, (const double*)x, (double*)y, nullptr); break;
+        case FG_OP_CHEM: op_chem(*c, P, (const double*)x, (double*)y, 1.0, nullptr); break;
+      }
+    } else {
+      Prec<float>& P = c->pf;
+      switch (op) {
+        case FG_OP_MECH: op_mech(*c, P, (const float*)x, (float*)y, nullptr); break;
+        case FG_OP_PFF: op_pff(*c, P, (const float*)x, (float*)y, (const float*)P.Hr, nullptr); break;
+        case FG_OP_PFF_PREC: op_prec(*c, P, (const float*)x, (float*)y, nullptr); break;
+        case FG_OP_CHEM: op_chem(*c, P, (const float*)x, (float*)y, 1.0, nullptr); break;
+      }
+    }
+  }
+  cudaEventRecord(e1, c->st);
+  cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(x);
+  dfree(y);
+  ccheck("fg_time_apply");
+  *ms = (double)t / n;
+#endif
+  FG_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,13 @@
+// Pass kernels of transform length 128, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize128 {
+  RegisterSize128() {
+    register_size_ops_f(make_size_ops<float, 128>());
+    register_size_ops_d(make_size_ops<double, 128>());
+  }
+} register_size_128;
+}  // namespace
+}  // namespace fg

@@ -1,0 +1,13 @@
+// Pass kernels of transform length 16, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize16 {
+  RegisterSize16() {
+    register_size_ops_f(make_size_ops<float, 16>());
+    register_size_ops_d(make_size_ops<double, 16>());
+  }
+} register_size_16;
+}  // namespace
+}  // namespace fg

@@ -1,0 +1,13 @@
+// Pass kernels of transform length 24, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize24 {
+  RegisterSize24() {
+    register_size_ops_f(make_size_ops<float, 24>());
+    register_size_ops_d(make_size_ops<double, 24>());
+  }
+} register_size_24;
+}  // namespace
+}  // namespace fg

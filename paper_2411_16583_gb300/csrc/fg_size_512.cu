@@ -1,0 +1,13 @@
+// Pass kernels of transform length 512, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize512 {
+  RegisterSize512() {
+    register_size_ops_f(make_size_ops<float, 512>());
+    register_size_ops_d(make_size_ops<double, 512>());
+  }
+} register_size_512;
+}  // namespace
+}  // namespace fg

@@ -1,0 +1,13 @@
+// Pass kernels of transform length 64, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize64 {
+  RegisterSize64() {
+    register_size_ops_f(make_size_ops<float, 64>());
+    register_size_ops_d(make_size_ops<double, 64>());
+  }
+} register_size_64;
+}  // namespace
+}  // namespace fg

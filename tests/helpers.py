@@ -1,0 +1,28 @@
+"""Shared test helpers: oracle parameters from a workload, error measures, tolerances."""
+import numpy as np
+
+from oracle import fg_oracle as O
+
+# Relative tolerances (max |gpu - oracle| / max |oracle|) of one operator application.
+# FP64: a few ulps per radix stage.  FP32: about eps32 x (log2 V + pointwise terms).
+TOL_APPLY_FP64 = 1e-12
+TOL_APPLY_FP32 = 1e-5
+# FP64 coupled step against the oracle (the GPU FP64 bar)
+TOL_STEP_FP64 = 1e-10
+
+
+def oracle_params(w_or_phases, phase_id=None, h=None, gc=1.0, lc=2e-7, RT=8.314462618 * 298.15,
+                  cmax=3.0e4):
+    if phase_id is None:
+        w = w_or_phases
+        return O.make_params([O.Phase(**vars(p)) for p in w.phases], w.phase_id, w.h, gc=w.gc,
+                             lc=w.lc, RT=w.RT, cmax=w.cmax, log_E=w.log_E, log_D=w.log_D)
+    return O.make_params([O.Phase(**vars(p)) for p in w_or_phases], phase_id, h, gc=gc, lc=lc,
+                         RT=RT, cmax=cmax)
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))

@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle on the same
+seeded inputs.  Operator applications are compared element by element; coupled steps
+field by field."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fg_oracle as O
+from paper_2411_16583_gb300 import binding as B, synth as S
+from tests.helpers import TOL_APPLY_FP32, TOL_APPLY_FP64, TOL_STEP_FP64, oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+H3 = (1.0e-7, 1.1e-7, 0.9e-7)
+
+# grids spanning several tiles, ragged last tiles (rows not a multiple of the tile) in the
+# X, Y and Z passes, mixed radix (12 = 4 x 3, 24 = 8 x 3, 48, 80 = 16 x 5), plane strain
+SHAPES = [(8, 12, 16), (12, 24, 16), (1, 12, 16), (1, 64, 64), (16, 32, 64), (24, 48, 80),
+          (32, 32, 32)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    assert torch.cuda.is_available()
+    return B.load_library()
+
+
+def _solver(lib, shape, precision, seed=1):
+    pid = S.random_phase_map(shape, seed)
+    phases = S.default_phases()
+    phases[1].E = 2e9  # moderate contrast keeps the operator well scaled
+    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=lib, precision=precision)
+    F, c, d = S.random_state(shape, seed=seed + 1)
+    Hh = np.random.default_rng(seed + 2).uniform(0, 1e6, shape)
+    for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d), (B.FIELD_H, Hh)):
+        sol.set(f, v)
+    prm = oracle_params(phases, pid, H3)
+    return sol, prm, F.reshape((3, 3) + shape), c, d, Hh
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_operator_parity(lib, shape, prec):
+    sol, prm, F, c, d, Hh = _solver(lib, shape, B.FG_MIXED if prec else B.FG_FP64)
+    tdt = torch.float32 if prec else torch.float64
+    tol = TOL_APPLY_FP32 if prec else TOL_APPLY_FP64
+    x9 = torch.from_numpy(S.random_tensor_field(shape, 3)).to("cuda", tdt)
+    x1 = torch.from_numpy(S.random_tensor_field(shape, 4, ncomp=1)[0]).to("cuda", tdt)
+    y9 = torch.empty_like(x9)
+    y1 = torch.empty_like(x1)
+    xn9 = x9.double().cpu().numpy().reshape(F.shape)
+    xn1 = x1.double().cpu().numpy()
+    # mechanics  G : F^-1[F[K : x]]
+    dot = sol.apply(B.OP_MECH, x9, y9, prec)
+    ref = O.mech_apply(F, c, d, prm, xn9)
+    assert rel_err(y9.cpu().numpy().reshape(ref.shape), ref) < tol
+    assert abs(dot - np.sum(xn9 * ref)) < 10 * tol * np.abs(xn9).sum() * np.abs(ref).max()
+    # phase field operator and preconditioner
+    sol.apply(B.OP_PFF, x1, y1, prec)
+    assert rel_err(y1.cpu().numpy(), O.pff_apply(xn1, Hh, prm)) < tol
+    sol.apply(B.OP_PFF_PREC, x1, y1, prec)
+    assert rel_err(y1.cpu().numpy(), O.pff_precond(xn1, Hh.mean(), prm)) < tol
+    # chemistry Newton operator
+    dt = 0.7
+    sol.apply(B.OP_CHEM, x1, y1, prec, dt=dt)
+    Kc = O.chem_conductivity(F, c, d, prm)
+    ref = O.chem_apply(xn1, 1.0 / (c * (1 - c)), Kc, dt, prm)
+    assert rel_err(y1.cpu().numpy(), ref) < tol
+    if prec == 0:
+        sol.apply(B.OP_GRES, x9, y9, 0)
+        assert rel_err(y9.cpu().numpy().reshape(F.shape), O.apply_G(xn9, H3)) < tol
+    # stress of the stored state
+    assert rel_err(sol.get(B.FIELD_P), O.stress(F, c, d, prm)) < 1e-13
+    sol.close()
+
+
+def test_operator_parity_full_size_fp32(lib):
+    """The FP32 mechanical operator at the benchmark size (256^3), element by element."""
+    shape = (256, 256, 256)
+    sol, prm, F, c, d, _ = _solver(lib, shape, B.FG_MIXED, seed=11)
+    x = torch.from_numpy(S.random_tensor_field(shape, 7)).to("cuda", torch.float32)
+    y = torch.empty_like(x)
+    sol.apply(B.OP_MECH, x, y, 1)
+    ref = O.mech_apply(F, c, d, prm, x.double().cpu().numpy().reshape(F.shape))
+    assert rel_err(y.cpu().numpy().reshape(ref.shape), ref) < TOL_APPLY_FP32
+    sol.close()
+
+
+def _oracle_run(w, nsteps):
+    prm = oracle_params(w)
+    st = O.CoupledState(prm, w.c_init, w.cdot_B, O.Tolerances(**w.tol))
+    for _ in range(nsteps):
+        st.step(w.dt, np.eye(3))
+    return prm, st
+
+
+def test_coupled_steps_fp64_disc(lib):
+    """64 x 64 plane-strain disc (10 steps of influx) in FP64 against the oracle."""
+    w = S.disc2d()
+    prm, ref = _oracle_run(w, w.nsteps)
+    sol = B.from_workload(w, lib=lib)
+    for _ in range(w.nsteps):
+        st = sol.step(w.dt)
+        assert abs(st["mass_err"]) < 1e-12
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < TOL_STEP_FP64
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < TOL_STEP_FP64
+    assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < TOL_STEP_FP64
+    sol.close()
+
+
+def test_coupled_steps_mixed_disc(lib):
+    """Mixed FP32/FP64 form on the same disc: per-field error against the oracle."""
+    w = S.disc2d()
+    nsteps = 4
+    prm, ref = _oracle_run(w, nsteps)
+    sol = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
+    for _ in range(nsteps):
+        sol.step(w.dt)
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-7
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-7
+    assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < 1e-6
+    sol.close()
+
+
+def test_coupled_step_3d_matches_oracle(lib):
+    """A 32^3 rough ellipsoid (the 128^3 particle recipe at a quarter of the size)."""
+    w = S.ellipsoid(n=32, axes=(12.5, 10.0, 8.75), rough_std=0.5, rough_corr=1.0, band=2, nsteps=50)
+    prm, ref = _oracle_run(w, 1)
+    sol = B.from_workload(w, lib=lib)
+    sol.step(w.dt)
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < TOL_STEP_FP64
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < TOL_STEP_FP64
+    sol.close()
+
+
+def test_full_size_step_properties(lib):
+    """The 128^3 rough ellipsoid, one FP64 step on the GPU; the oracle then evaluates the
+    equilibrium residual and the Fick residual of the GPU's fields, and mass balance."""
+    w = S.ellipsoid()
+    sol = B.from_workload(w, lib=lib)
+    c_t = sol.get(B.FIELD_C)
+    F_t = sol.get(B.FIELD_F)
+    st = sol.step(w.dt)
+    F, c, d = sol.get(B.FIELD_F), sol.get(B.FIELD_C), sol.get(B.FIELD_D)
+    prm = oracle_params(w)
+    _, err = O.mech_residual(F, c, d, prm, np.eye(3))
+    assert err <= 1.5 * w.tol["tol_stag"]
+    Kc = O.chem_conductivity(F_t, c_t, np.zeros_like(c), prm)
+    f = O.chem_residual(c, c_t, F_t, np.zeros_like(c), Kc, w.dt, w.cdot_B, prm)
+    assert np.abs(f).max() < 1e-8
+    assert abs(c.mean() - (c_t.mean() + w.dt * w.cdot_B.mean())) < 1e-12
+    assert st["stag"] >= 1
+    sol.close()
