@@ -1,13 +1,14 @@
 """Benchmark: coupled time steps of the FFT chemo-mechanical fracture method on GB300.
 
 Default workload: the 256^3 rough ellipsoidal particle (semi-axes 100/80/70 voxels,
-roughness std 3 / correlation 8, influx band 8 voxels, Gaussian concentration perturbation
-std 0.02), mixed FP32/FP64 precision, Newton tolerance 1e-9.  One bench step = one coupled
-time step (Alg. 4: chemistry Newton-CG, then staggered mechanics Newton-CG and phase-field
-PCG) through the C ABI.  Inputs are resident on the device before the timed region; the
-working set (~15 GB) is far larger than L2, so no flush is needed between steps.
+roughness std 3 / correlation 8, influx band 8 voxels, smooth Gaussian concentration
+perturbation of std 0.02), mixed FP32/FP64 precision, Newton tolerance 1e-9.  One bench
+step is one coupled time step (Alg. 4: chemistry Newton-CG, then the staggered mechanics
+Newton-CG and phase-field PCG) through the C ABI, every part of it in the CUDA library.
+Inputs are resident on the device when the timed region starts; the working set
+(~15 GB) is far larger than L2 (129 MB), so nothing stays cached between steps.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+Rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
 """
 from __future__ import annotations
 
@@ -25,6 +26,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("coupled time-step wall time & fused-matvec voxel-applies/s at 256³, "
           "mixed vs FP64")
+UNIT = "voxel-steps/s"
+
+# Algorithmic bytes per voxel of each profiled launch site of the FP32 mechanical CG
+# (9-component fields, 4-byte reals; the half spectrum holds (nx/2+1)/nx of a real field
+# as complex numbers, so a 9-component spectrum is 72 (nx/2+1)/nx bytes per voxel).
+def site_bytes(nx):
+    spec = 72.0 * (nx // 2 + 1) / nx
+    return {0: 36 + 48 + spec,       # X-fwd: read p (9) + tangent state (12), write spectrum
+            1: 2 * spec,             # Y-fwd: read + write spectrum
+            2: 2 * spec,             # Z + projection: read + write spectrum
+            3: 2 * spec,             # Y-inv: read + write spectrum
+            4: spec + 36 + 36,       # X-inv: read spectrum, write q, read p for <p, q>
+            5: 4 * 36 + 2 * 36}      # CG update: read x, p, r, q, write x, r
+
+
+SITE_NAMES = {0: "mech X-fwd + tangent (pass_kernel<XFwd<float,N,PTangentNH>>)",
+              1: "mech Y-fwd (pass_kernel<YPass<float,N,false>>)",
+              2: "mech Z + projection (pass_kernel<ZPass<float,N,ZProject>>)",
+              3: "mech Y-inv (pass_kernel<YPass<float,N,true>>)",
+              4: "mech X-inv + dot (pass_kernel<XInv<float,N,EStoreDot<9>>>)",
+              5: "mech CG update (pass_kernel<VecKernel<KCgXR<float>>>)"}
 
 
 def _args():
@@ -37,6 +59,7 @@ def _args():
     p.add_argument("--fp64-steps", type=int, default=1, help="FP64 comparison steps (0: skip)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
@@ -66,8 +89,7 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
         return self
@@ -82,8 +104,14 @@ class Clocks:
             self.proc.wait()
 
     def summary(self):
-        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if r and num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if len(r) > 1 and num(r[1]) is not None]
+        pw = [num(r[2]) for r in self.rows if len(r) > 2 and num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
         for r in self.rows:
@@ -91,8 +119,9 @@ class Clocks:
                 if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
 def _peaks():
@@ -103,10 +132,18 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(w, budget_s):
-    """The oracle as it stands on a bounded sample of the same workload: repeated FP64
-    mechanical operator applications on the full 256^3 fields (the operator a coupled step
-    spends its time in), single process."""
+# Per-step operator counts used to express the oracle's per-operator times in the
+# metric's unit when no GPU step is available (the --impl reference arm): the counts of
+# the first coupled steps of this workload (FP64 path, whose Krylov iterations follow the
+# oracle's), rounded.
+DEFAULT_STEP_PROFILE = {"cg_mech": 2400, "newton_mech": 3, "stag": 1, "cg_chem": 450,
+                        "newton_chem": 8, "cg_pff": 0}
+
+
+def oracle_step_seconds(w, budget_s, profile):
+    """Times the oracle's operators on the full-size fields of workload w (a bounded
+    sample, about budget_s seconds) and combines them with the operator counts of one
+    coupled step.  Returns (seconds per step, description of the sample)."""
     import numpy as np
     from oracle import fg_oracle as O
     from paper_2411_16583_gb300 import synth as S
@@ -114,15 +151,45 @@ def cpu_baseline(w, budget_s):
                         lc=w.lc, RT=w.RT, cmax=w.cmax)
     F, c, d = S.random_state(w.shape, seed=1, f_amp=0.01, c_lo=0.01, c_hi=0.3, d_hi=0.0)
     x = S.random_tensor_field(w.shape, 2).reshape((3, 3) + w.shape)
-    n, t0 = 0, time.perf_counter()
-    while True:
-        O.mech_apply(F, c, d, prm, x)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = (time.perf_counter() - t0) / n
-    return {"voxel_applies_per_s": w.nvox / dt, "seconds_per_apply": dt, "applies": n,
-            "cores": int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or 1}
+    y = S.random_tensor_field(w.shape, 3, ncomp=1)[0]
+    Kc = O.chem_conductivity(F, c, d, prm)
+    m = 1.0 / (c * (1.0 - c))
+    ops = {"mech": lambda: O.mech_apply(F, c, d, prm, x),
+           "gres": lambda: O.apply_G(x, prm.h),
+           "chem": lambda: O.chem_apply(y, m, Kc, 1.0, prm)}
+    times, counts = {}, {}
+    t_start = time.perf_counter()
+    share = budget_s / len(ops)
+    for k, f in ops.items():
+        n, t0 = 0, time.perf_counter()
+        while True:
+            f()
+            n += 1
+            if time.perf_counter() - t0 > share:
+                break
+        times[k] = (time.perf_counter() - t0) / n
+        counts[k] = n
+    p = profile
+    # a Newton iteration applies the residual projection once (twice in mixed mode, which
+    # also projects the correction); each staggered check applies it twice (residual and
+    # its normalisation); each chemistry Newton iteration evaluates its residual with one
+    # operator-equivalent round trip
+    step = (p["cg_mech"] * times["mech"]
+            + (p["newton_mech"] + 1 + 2 * (p["stag"] + 1)) * times["gres"]
+            + (p["cg_chem"] + p["newton_chem"]) * times["chem"])
+    desc = (f"oracle operators on the full {w.shape[2]}^3 fields: "
+            + ", ".join(f"{counts[k]} x {k} ({times[k]:.2f} s each)" for k in ops)
+            + f", combined with one step's operator counts {p}; "
+            + f"{time.perf_counter() - t_start:.0f} s of CPU work")
+    return step, desc
+
+
+def _cores():
+    try:
+        import numpy as np  # noqa: F401
+        return int(os.environ.get("OMP_NUM_THREADS") or 1)
+    except Exception:
+        return 1
 
 
 def main():
@@ -152,21 +219,52 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    for s in range(6):
+        sol.profile(s, True)
     stats = []
     with Clocks(local) as clk:
         barrier()
+        l0 = B.kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(a.steps):
             stats.append(sol.step(w.dt))
         e1.record(stream)
         barrier()
+        launches = B.kernel_launches() - l0
     ms = e0.elapsed_time(e1) / a.steps
+    prof = {s: sol.profile_read(s) for s in range(6)}
+    for s in range(6):
+        sol.profile(s, False)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    # fused matvec rates (FP32 in the mixed context)
+
+    # end to end through the same public calls with host buffers: each step copies the
+    # state (F, c, d, H) in from pinned host memory and the new (F, c, d) back out
+    e2e = None
+    if not a.no_e2e:
+        hF = torch.empty(9 * V, dtype=torch.float64).pin_memory()
+        hs = [torch.empty(V, dtype=torch.float64).pin_memory() for _ in range(3)]
+        lib = sol.lib
+        for f, buf in ((B.FIELD_F, hF), (B.FIELD_C, hs[0]), (B.FIELD_D, hs[1]), (B.FIELD_H, hs[2])):
+            sol._check(lib.fg_get_field(sol.ctx, f, B._ptr(buf), 0))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            for f, buf in ((B.FIELD_F, hF), (B.FIELD_C, hs[0]), (B.FIELD_D, hs[1]),
+                           (B.FIELD_H, hs[2])):
+                sol._check(lib.fg_set_field(sol.ctx, f, B._ptr(buf), 0))
+            sol.step(w.dt)
+            for f, buf in ((B.FIELD_F, hF), (B.FIELD_C, hs[0]), (B.FIELD_D, hs[1])):
+                sol._check(lib.fg_get_field(sol.ctx, f, B._ptr(buf), 0))
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / a.steps
+        e2e = {"value": V * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * V * 8,
+               "d2h_bytes_per_step": 11 * V * 8}
+
+    # fused matvec rates: FP32 operator of the mixed context
     mech32_ms = sol.time_apply(B.OP_MECH, 1, 20)
     sol.close()
     out = {}
@@ -184,10 +282,22 @@ def main():
     if rank != 0:
         return
     peaks, src = _peaks()
+    sb = site_bytes(w.shape[2])
+    sites = {}
+    for s, (n, t) in prof.items():
+        if n:
+            avg = t / n * 1e-3
+            sites[SITE_NAMES[s]] = {"launches": n, "total_ms": t, "avg_us": avg * 1e6,
+                                    "alg_bytes_per_voxel": sb[s],
+                                    "gbs": sb[s] * V / avg / 1e9}
+    dom = max((s for s in prof if prof[s][0]), key=lambda s: prof[s][1])
+    n_dom, t_dom = prof[dom]
+    avg_dom = t_dom / n_dom * 1e-3
+    ach = sb[dom] * V / avg_dom / 1e9
     line = {
         "metric": METRIC,
         "value": V * world / (ms * 1e-3),
-        "unit": "voxel-steps/s",
+        "unit": UNIT,
         "n_gpus": world,
         "steps": a.steps,
         "warmup": a.warmup,
@@ -195,30 +305,58 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 inner / f64 outer",
+        "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"rough ellipsoid particle {a.n}^3, mixed FP32/FP64, Newton tol 1e-9",
-                   "voxels": V, "l2": "working set >> L2 (no flush needed)"},
+        "config": {"workload": f"rough ellipsoid particle {a.n}^3 (coupled step, mixed "
+                               f"FP32 Krylov / FP64 Newton, tol 1e-9)",
+                   "voxels": V, "l2": "inputs larger than L2 (no flush)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": SITE_NAMES[dom], "achieved": ach,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                     "peak_source": src,
+                     "alg_bytes_per_launch": sb[dom] * V, "avg_launch_us": avg_dom * 1e6,
+                     "traffic": None},
+        "kernels": sites,
         "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),
                    "mech_fp32_ms": mech32_ms},
         "step_stats": stats[-1],
         "clocks": clk.summary(),
-        "peaks_source": src,
     }
     line.update(out)
     if not a.no_cpu_baseline:
-        cb = cpu_baseline(w, a.cpu_seconds)
-        line["cpu_baseline"] = {"value": cb["voxel_applies_per_s"], "unit": "voxel-applies/s",
-                                "cores": cb["cores"], "kind": "oracle",
-                                "sample": f"{cb['applies']} FP64 mechanical operator applications "
-                                          f"at {a.n}^3 (numpy oracle)"}
+        prof_counts = {k: stats[-1][k] for k in DEFAULT_STEP_PROFILE}
+        secs, desc = oracle_step_seconds(w, a.cpu_seconds, prof_counts)
+        line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": _cores(),
+                                "kind": "oracle", "sample": desc}
     print(json.dumps(line))
 
 
 def reference_arm(a, rank, world):
+    """The CPU oracle as it stands, on this arm's workload, metric and unit."""
     if rank != 0:
         return
-    print(json.dumps({"impl": "reference", "unavailable": "not implemented yet"}))
+    w = _workload(a.n, seed=0)
+    budget = max(3.0, min(a.cpu_seconds, 30.0))
+    secs, desc = None, None
+    total = 0.0
+    for _ in range(a.warmup + a.steps):
+        s, desc = oracle_step_seconds(w, budget / 3, DEFAULT_STEP_PROFILE)
+        total += s
+        secs = s
+    per_step = total / (a.warmup + a.steps)
+    value = w.nvox / per_step
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"rough ellipsoid particle {a.n}^3 (coupled step, oracle FP64)",
+                   "voxels": w.nvox},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
 
 
 if __name__ == "__main__":

@@ -139,8 +139,8 @@ int fg_step(fg_ctx* ctx, double dt, const double Fbar[9], fg_stats* st);
 /*
  * Residuals of the stored state: err_mech = ||G*P(F)|| / ||G*P(Fbar)|| (Eq. mechresiduum,
  * with the fallbacks ||P(Fbar)|| then 1 when the comparison stress has no incompatible
- * part), err_chem = ||f(c)|| of Eq. Chemresidualfc for the last step's data (0 before
- * the first step), mass_sum = sum of c.  Any output pointer may be NULL.
+ * part), err_chem = ||f(c)|| / ||c_t|| of Eq. Chemresidualfc for the last step's data
+ * (0 before the first step), mass_sum = sum of c.  Any output pointer may be NULL.
  */
 int fg_residual(fg_ctx* ctx, double* err_mech, double* err_chem, double* mass_sum);
 
@@ -166,8 +166,22 @@ int fg_set_field(fg_ctx* ctx, int field, const void* src, int on_device);
  * reports the mean time per application in ms (no synchronisation inside). */
 int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
 
+/* Launch-site profiling.  While a site is enabled, every launch at that site is
+ * bracketed by two CUDA events on the context stream (at most 4096 launches are recorded
+ * after each enable).  Sites: 0-4 the five passes of the mechanical operator (X-fwd with
+ * the tangent, Y-fwd, Z with the projection, Y-inv, X-inv with the dot product), 5 the
+ * x/r update of the mechanical CG.  fg_profile_read synchronises the stream and returns
+ * the number of recorded launches and their summed device time; launches shorter than a
+ * fifth of the median (kernels that returned at once because their Krylov loop had
+ * already converged) are left out of both. */
+int fg_profile(fg_ctx* ctx, int site, int enable);
+int fg_profile_read(fg_ctx* ctx, int site, int* launches, double* total_ms);
+
 /* Releases the context and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);
+
+/* Number of CUDA kernels the library has launched since it was loaded (all contexts). */
+long long fg_kernel_launches(void);
 
 /* Message of the calling thread's last failing call ("" if none). */
 const char* fg_last_error(void);

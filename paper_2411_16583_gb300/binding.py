@@ -21,6 +21,8 @@ FG_SVK, FG_NEOHOOKE = 0, 1
 FG_FP64, FG_MIXED = 0, 1
 OP_MECH, OP_PFF, OP_PFF_PREC, OP_CHEM, OP_GRES = 0, 1, 2, 3, 4
 FIELD_C, FIELD_F, FIELD_D, FIELD_H, FIELD_P = 0, 1, 2, 3, 4
+SITES = {0: "mech.xfwd_tangent", 1: "mech.yfwd", 2: "mech.z_project", 3: "mech.yinv",
+         4: "mech.xinv_dot", 5: "mech.cg_update"}
 
 
 class FgError(RuntimeError):
@@ -59,8 +61,8 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
-           "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_destroy",
-           "fg_last_error"]
+           "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
+           "fg_profile_read", "fg_kernel_launches", "fg_destroy", "fg_last_error"]
 
 _libs = {}
 
@@ -86,11 +88,18 @@ def load_library(path=LIB_PATH):
     lib.fg_get_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     lib.fg_set_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     lib.fg_time_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
+    lib.fg_profile.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    lib.fg_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), dp]
+    lib.fg_kernel_launches.restype = C.c_longlong
     lib.fg_destroy.argtypes = [C.c_void_p]
     lib.fg_destroy.restype = None
     lib.fg_last_error.restype = C.c_char_p
     _libs[path] = lib
     return lib
+
+
+def kernel_launches(lib=None):
+    return int((lib or load_library()).fg_kernel_launches())
 
 
 def default_opts(lib=None):
@@ -188,6 +197,14 @@ class Solver:
         dot = C.c_double()
         self._check(self.lib.fg_apply(self.ctx, op, prec, _ptr(x), _ptr(y), dt, C.byref(dot)))
         return dot.value
+
+    def profile(self, site, enable=True):
+        self._check(self.lib.fg_profile(self.ctx, site, int(enable)))
+
+    def profile_read(self, site):
+        n, ms = C.c_int(), C.c_double()
+        self._check(self.lib.fg_profile_read(self.ctx, site, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
 
     def time_apply(self, op, prec, n):
         ms = C.c_double()

@@ -17,11 +17,15 @@ __global__ void __launch_bounds__(K::NT) pass_kernel(A a) {
 }
 #endif
 
+// number of kernel launches issued by the library (all kernels, all contexts)
+long long& launch_counter();
+
 // Launches kernel K with arguments A on `grid` blocks of K::NT threads.  Returns the
 // number of blocks launched (the number of partial sums a reducing kernel writes).
 template <class K, class A>
 int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
   const size_t sm = K::smem_bytes();
+  ++launch_counter();
 #ifdef FG_EMU
   (void)st;
   std::vector<char> smem(sm);

@@ -392,6 +392,15 @@ struct KScaleTo {
   }
 };
 
+// out0 (FP64) = in0 (R)
+template <typename R>
+struct KWiden {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    ((double*)a.out[0])[i] = (double)((const R*)a.in[0])[i];
+  }
+};
+
 // out0 (FP64) += in0 (R)
 template <typename R>
 struct KAddTo {

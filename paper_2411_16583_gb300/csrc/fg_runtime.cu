@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -21,6 +23,11 @@ static std::map<int, SizeOps<R>>& registry() {
   static std::map<int, SizeOps<R>> m;
   return m;
 }
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+
 void register_size_ops_f(const SizeOps<float>& s) { registry<float>()[s.N] = s; }
 void register_size_ops_d(const SizeOps<double>& s) { registry<double>()[s.N] = s; }
 template <typename R>
@@ -138,8 +145,13 @@ struct fg_ctx {
   fg::Prec<double> pd;
   fg::Prec<float> pf;
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double Fbar_prev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double last_dt = 0.0;
   bool stepped = false;
+  // launch-site profiling: event pairs around every launch of the enabled sites
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> prof_ev[8];
+  int prof_used[8] = {0};
   int last_inner_refine = 0;
 };
 
@@ -245,6 +257,44 @@ static VArgs vbase(fg_ctx& c, long long n) {
   return v;
 }
 
+// ------------------------------------------------------------------ launch-site profiling
+
+enum { SITE_XF = 0, SITE_YF = 1, SITE_Z = 2, SITE_YI = 3, SITE_XI = 4, SITE_CGXR = 5, SITE_N = 8 };
+static constexpr int PROF_PAIRS = 4096;
+
+struct ProfScope {
+  fg_ctx& c;
+  int site;
+  bool on;
+  ProfScope(fg_ctx& cc, int s) : c(cc), site(s), on(false) {
+#ifndef FG_EMU
+    if ((c.prof_mask >> site) & 1u) {
+      auto& v = c.prof_ev[site];
+      const int k = c.prof_used[site];
+      if (k < PROF_PAIRS) {
+        if ((int)v.size() < 2 * (k + 1)) {
+          cudaEvent_t a, b;
+          cudaEventCreate(&a);
+          cudaEventCreate(&b);
+          v.push_back(a);
+          v.push_back(b);
+        }
+        cudaEventRecord(v[2 * k], c.st);
+        on = true;
+      }
+    }
+#endif
+  }
+  ~ProfScope() {
+#ifndef FG_EMU
+    if (on) {
+      cudaEventRecord(c.prof_ev[site][2 * c.prof_used[site] + 1], c.st);
+      c.prof_used[site] += 1;
+    }
+#endif
+  }
+};
+
 template <class F>
 static void fin(fg_ctx& c, int slot, long long nparts, const int* done, double s0 = 0, double s1 = 0,
                 double s2 = 0) {
@@ -326,14 +376,43 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
   a.rin = x;
   a.aux[0] = P.state;
   a.cout = P.S1;
-  P.ox->xf_tangent(a, c.st);
-  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
-  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr);
+  {
+    ProfScope ps(c, SITE_XF);
+    P.ox->xf_tangent(a, c.st);
+  }
+  a = pbase(c, P, done);
+  a.tw = P.twy;
+  a.cin = P.S1;
+  a.cout = P.S2;
+  a.ncomp = 9;
+  {
+    ProfScope ps(c, SITE_YF);
+    P.oy->yf(a, c.st);
+  }
+  a = pbase(c, P, done);
+  a.tw = P.twz;
+  a.cin = P.S2;
+  a.cout = P.S2;
+  a.coef[0] = (R)(1.0 / (double)c.V);
+  {
+    ProfScope ps(c, SITE_Z);
+    P.oz->z_proj(a, c.st);
+  }
+  a = pbase(c, P, done);
+  a.tw = P.twy;
+  a.cin = P.S2;
+  a.cout = P.S1;
+  a.ncomp = 9;
+  {
+    ProfScope ps(c, SITE_YI);
+    P.oy->yi(a, c.st);
+  }
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
   a.rout = y;
   a.aux[0] = x;
+  ProfScope ps(c, SITE_XI);
   return P.ox->xi_storedot9(a, c.st);
 }
 
@@ -509,7 +588,10 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
       u.in[1] = P.q;
       u.out[0] = P.x;
       u.out[1] = P.r;
-      launch_vec<KCgXR<R>>(u, c.st);
+      {
+        ProfScope ps(c, slot == KS_MECH ? SITE_CGXR : SITE_N - 1);
+        launch_vec<KCgXR<R>>(u, c.st);
+      }
       fin<FBetaCg>(c, slot, VEC_BLOCKS, done);
       VArgs w = vbase(c, n);
       w.ks = ks;
@@ -644,10 +726,25 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
                               [&](const R* p, R* q, const int* done) { return op_mech(c, P, p, q, done); });
     s.cg_mech += n;
     s.newton_mech += 1;
-    VArgs v = vbase(c, 9 * c.V);
-    v.in[0] = P.x;
-    v.out[0] = c.F;
-    launch_vec<KAddTo<R>>(v, c.st);
+    if (is_mixed(c)) {
+      // FP32 roundoff leaves traces of the correction in modes G never sees (the mean and
+      // the null modes of the rotated scheme); project it in FP64 onto compatible
+      // zero-mean fields before the update, as the exact correction is
+      VArgs u = vbase(c, 9 * c.V);
+      u.in[0] = P.x;
+      u.out[0] = c.P;
+      launch_vec<KWiden<R>>(u, c.st);
+      op_gres(c, c.pd, c.P, c.GP, nullptr);
+      VArgs v = vbase(c, 9 * c.V);
+      v.in[0] = c.GP;
+      v.out[0] = c.F;
+      launch_vec<KAddTo<double>>(v, c.st);
+    } else {
+      VArgs v = vbase(c, 9 * c.V);
+      v.in[0] = P.x;
+      v.out[0] = c.F;
+      launch_vec<KAddTo<R>>(v, c.st);
+    }
   }
 }
 
@@ -741,12 +838,12 @@ static void chem_cond(fg_ctx& c, Prec<R>& P, const double* F, const double* ct, 
 }
 
 template <typename R>
-static void chem_prep(fg_ctx& c, Prec<R>& P, double dt) {
+static void chem_prep(fg_ctx& c, Prec<R>& P, double dt, const double* F) {
   VArgs v = vbase(c, c.V);
   v.in[0] = c.c;
   v.in[1] = c.ct;
   v.in[2] = c.cdotB;
-  v.in[3] = c.F;
+  v.in[3] = F;
   v.in[4] = c.dt;
   v.in[5] = c.lam;
   v.in[6] = c.mu_;
@@ -769,7 +866,7 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
   const double nct = sqrt(reduce_sum(c, c.ct, c.V, true));
   for (int it = 0;; ++it) {
     if (it >= c.o.max_chem_newton) fail(FG_ERR_NOCONV, "chemical Newton hit max_chem_newton");
-    chem_prep<R>(c, P, dt);
+    chem_prep<R>(c, P, dt, c.F);
     read_ks(c);
     check_flags(c, "chemistry");
     double* b64 = is_mixed(c) ? c.pd.b : (double*)P.b;
@@ -839,6 +936,7 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
     dsync(c.st);
     throw;
   }
+  memcpy(c.Fbar_prev, Fbar_old, sizeof(Fbar_old));
   c.last_dt = dt;
   c.stepped = true;
   dsync(c.st);
@@ -878,7 +976,7 @@ static double do_apply(fg_ctx& c, Prec<R>& P, int op, const R* x, R* y, double d
       dcopy(c.ct, c.c, c.V * sizeof(double), c.st);
       dcopy(c.dt, c.d, c.V * sizeof(double), c.st);
       chem_cond<R>(c, P, c.F, c.c, c.d);
-      chem_prep<R>(c, P, dt);
+      chem_prep<R>(c, P, dt, c.F);
       nb = op_chem(c, P, x, y, dt, nullptr);
       break;
     default:
@@ -936,10 +1034,14 @@ int fg_supported_size(int n) {
 
 const char* fg_last_error(void) { return g_err.c_str(); }
 
+long long fg_kernel_launches(void) { return launch_counter(); }
+
 void fg_destroy(fg_ctx* ctx) {
   if (!ctx) return;
 #ifndef FG_EMU
   cudaStreamSynchronize(ctx->st);
+  for (auto& v : ctx->prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
 #endif
   free_all(*ctx);
   delete ctx;
@@ -1087,12 +1189,20 @@ int fg_residual(fg_ctx* c, double* err_mech, double* err_chem, double* mass_sum)
   if (err_chem) {
     *err_chem = 0.0;
     if (c->stepped) {
-      chem_cond<double>(*c, c->pd, c->Ft, c->ct, c->dt);
-      chem_prep<double>(*c, c->pd, c->last_dt);
+      // the last step's chemistry used F_t + (Fbar - Fbar_t), c_t and d_t
+      VArgs v = vbase(*c, 9 * c->V);
+      v.in[0] = c->Ft;
+      v.out[0] = c->P;
+      for (int k = 0; k < 9; ++k) v.s[k] = c->Fbar[k] - c->Fbar_prev[k];
+      launch_vec<KShiftF>(v, c->st);
+      chem_cond<double>(*c, c->pd, c->P, c->ct, c->dt);
+      chem_prep<double>(*c, c->pd, c->last_dt, c->P);
       const int nb = op_chem_rhs(*c, c->pd.b, c->last_dt);
       fin<FStore>(*c, KS_MISC, nb, nullptr);
       read_ks(*c);
-      *err_chem = sqrt(c->ks_host[KS_MISC].aux);
+      const double nf = sqrt(c->ks_host[KS_MISC].aux);
+      const double nct = sqrt(reduce_sum(*c, c->ct, c->V, true));
+      *err_chem = nf / nct;
     }
   }
   if (mass_sum) *mass_sum = reduce_sum(*c, c->c, c->V, false);
@@ -1159,6 +1269,42 @@ int fg_set_field(fg_ctx* c, int field, const void* src, int on_device) {
   dcopy(dst, src, n * sizeof(double), c->st);
   dcopy(dst_t, src, n * sizeof(double), c->st);
   dsync(c->st);
+  FG_API_END
+}
+
+int fg_profile(fg_ctx* c, int site, int enable) {
+  FG_API_BEGIN
+  if (!c || site < 0 || site >= SITE_N - 1) fail(FG_ERR_INVALID, "fg_profile: bad site");
+  if (enable) c->prof_mask |= 1u << site;
+  else c->prof_mask &= ~(1u << site);
+  c->prof_used[site] = 0;
+  FG_API_END
+}
+
+int fg_profile_read(fg_ctx* c, int site, int* launches, double* total_ms) {
+  FG_API_BEGIN
+  if (!c || site < 0 || site >= SITE_N - 1 || !launches || !total_ms)
+    fail(FG_ERR_INVALID, "fg_profile_read: bad argument");
+  double t = 0.0;
+  int n = 0;
+#ifndef FG_EMU
+  dsync(c->st);
+  std::vector<float> ms(c->prof_used[site]);
+  for (int k = 0; k < c->prof_used[site]; ++k)
+    cudaEventElapsedTime(&ms[k], c->prof_ev[site][2 * k], c->prof_ev[site][2 * k + 1]);
+  // launches that returned at once because their Krylov loop had converged (the tail of
+  // the last batch of iterations) are not counted: below a fifth of the median
+  std::vector<float> srt(ms);
+  std::sort(srt.begin(), srt.end());
+  const float med = srt.empty() ? 0.f : srt[srt.size() / 2];
+  for (float m : ms)
+    if (m >= 0.2f * med) {
+      t += m;
+      ++n;
+    }
+#endif
+  *launches = n;
+  *total_ms = t;
   FG_API_END
 }
 

@@ -17,7 +17,8 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
 * ``ellipsoid`` 128^3, semi-axes 50/40/35 with a Gaussian-filtered rough surface
   (std 1.5 voxels, correlation length 4 voxels), band 8 voxels, 50 steps.
 * ``ellipsoid`` at 256^3 scaled x2 (semi-axes 100/80/70, roughness std 3,
-  correlation 8) plus a Gaussian concentration perturbation of std 0.02, 100 steps.
+  correlation 8) plus a smooth Gaussian concentration perturbation of std 0.02
+  (correlation 8 voxels) around c = 0.07 inside the particle, 100 steps.
 * ``spheres``   64 RVEs with edge N in {48, 64, 80, 96} and sphere radius
   U(0.30, 0.45) N.
 * ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
@@ -110,7 +111,7 @@ def _rough_field(rng, shape, std, corr):
 
 
 def _finish(name, shape, h, particle, band_width, nsteps, dt, rng, phases=None, c_perturb=0.0,
-            target_c=0.5, gc=1.0, lc_vox=2.0):
+            target_c=0.5, gc=1.0, lc_vox=2.0, perturb_corr=8.0, perturb_mean=0.07):
     phases = phases or default_phases()
     phase_id = np.where(particle, PARTICLE, BUFFER).astype(np.uint8)
     band = influx_band(particle, band_width)
@@ -120,8 +121,10 @@ def _finish(name, shape, h, particle, band_width, nsteps, dt, rng, phases=None, 
     cdot_B = np.where(band, rate, 0.0)
     c_init = np.full(shape, c0)
     if c_perturb > 0.0:
-        pert = rng.normal(0.0, c_perturb, size=shape)
-        c_init = np.where(particle, np.clip(c0 + pert, 0.005, 0.995), c0)
+        # smooth Gaussian random field of standard deviation c_perturb (correlation length
+        # perturb_corr voxels) around perturb_mean inside the particle
+        pert = _rough_field(rng, shape, c_perturb, perturb_corr)
+        c_init = np.where(particle, np.clip(perturb_mean + pert, 0.005, 0.995), c0)
     return Workload(name=name, shape=shape, h=h, phases=phases, phase_id=phase_id,
                     cdot_B=cdot_B, c_init=c_init, gc=gc, lc=lc_vox * h[0], dt=dt, nsteps=nsteps)
 

@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every entry point ``include/fg.h`` declares, and
+its host-side argument checks return the documented error codes (through the host
+emulation build, so no GPU is needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2411_16583_gb300 import binding as B, build, synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert set(declared_symbols()) == set(B.EXPORTS)
+
+
+@pytest.mark.parametrize("which", ["gpu", "emu"])
+def test_library_exports_every_declared_symbol(which):
+    path = build.build_gpu() if which == "gpu" else build.build_emu()
+    import ctypes
+    lib = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+@pytest.fixture(scope="module")
+def emu():
+    return B.load_library(build.build_emu())
+
+
+def _disc(n=16):
+    return S.disc2d(n=n, radius=6.0, band=3, nsteps=10)
+
+
+def test_invalid_arguments(emu):
+    w = _disc()
+    with pytest.raises(B.FgError) as e:  # odd nx
+        B.Solver((1, 16, 15), w.h, w.phases, np.zeros((1, 16, 15)), np.zeros((1, 16, 15)), lib=emu)
+    assert e.value.code == -1
+    with pytest.raises(B.FgError) as e:  # a length that is not compiled in
+        B.Solver((1, 16, 18), w.h, w.phases, np.zeros((1, 16, 18)), np.zeros((1, 16, 18)), lib=emu)
+    assert e.value.code == -1
+    bad = w.phase_id.copy()
+    bad[0, 0, 0] = 7  # phase id out of range
+    with pytest.raises(B.FgError) as e:
+        B.Solver(w.shape, w.h, w.phases, bad, w.cdot_B, lib=emu)
+    assert e.value.code == -1
+    svk = S.default_phases(law=S.LAW_SVK)
+    with pytest.raises(B.FgError) as e:
+        B.Solver(w.shape, w.h, svk, w.phase_id, w.cdot_B, lib=emu)
+    assert e.value.code == -1
+    with pytest.raises(B.FgError) as e:  # initial concentration outside (0, 1)
+        B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=np.full(w.shape, 1.2), lib=emu)
+    assert e.value.code == -5
+    assert emu.fg_supported_size(64) == 1 and emu.fg_supported_size(18) == 0
+
+
+def test_iteration_cap_reports_noconv_and_keeps_state(emu):
+    w = _disc()
+    sol = B.from_workload(w, lib=emu, max_cg=2)
+    c0 = sol.get(B.FIELD_C)
+    st = sol.step(w.dt, check=False)
+    assert st["status"] == -4
+    np.testing.assert_array_equal(sol.get(B.FIELD_C), c0)  # state left at the step start
+    sol.close()
+
+
+def test_nan_input_is_reported(emu):
+    w = _disc()
+    sol = B.from_workload(w, lib=emu)
+    F = sol.get(B.FIELD_F)
+    F[0, 0, 0, 3, 3] = np.nan
+    sol.set(B.FIELD_F, F)
+    st = sol.step(w.dt, check=False)
+    assert st["status"] in (-5, -6)
+    sol.close()

@@ -1,0 +1,81 @@
+"""CPU checks of the CUDA kernel source through its host-emulation build.
+
+``libfg_emu.so`` compiles the same kernel and runtime sources with FG_EMU: every block of
+every kernel runs on the host, thread by thread between barriers.  These tests catch
+indexing, tiling and FFT-plan mistakes without a GPU; the product path never loads this
+library, and the parity that counts is the one of ``test_gpu_parity.py``.
+"""
+import numpy as np
+import pytest
+
+from oracle import fg_oracle as O
+from paper_2411_16583_gb300 import binding as B, build, synth as S
+from tests.helpers import TOL_APPLY_FP32, TOL_APPLY_FP64, oracle_params, rel_err
+
+H3 = (1.0e-7, 1.1e-7, 0.9e-7)
+
+
+@pytest.fixture(scope="module")
+def emu():
+    return B.load_library(build.build_emu())
+
+
+@pytest.mark.parametrize("shape", [(8, 12, 16), (1, 16, 24), (12, 8, 8)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_emulated_operators_match_oracle(emu, shape, prec):
+    pid = S.random_phase_map(shape, 1)
+    phases = S.default_phases()
+    phases[1].E = 2e9
+    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu,
+                   precision=B.FG_MIXED if prec else B.FG_FP64)
+    F, c, d = S.random_state(shape, seed=2)
+    Hh = np.random.default_rng(5).uniform(0, 1e6, shape)
+    for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d), (B.FIELD_H, Hh)):
+        sol.set(f, v)
+    prm = oracle_params(phases, pid, H3)
+    F = F.reshape((3, 3) + shape)
+    dt_ = np.float32 if prec else np.float64
+    tol = TOL_APPLY_FP32 if prec else TOL_APPLY_FP64
+    x9 = S.random_tensor_field(shape, 3).astype(dt_)
+    x1 = S.random_tensor_field(shape, 4, ncomp=1)[0].astype(dt_)
+    y9, y1 = np.zeros_like(x9), np.zeros_like(x1)
+    sol.apply(B.OP_MECH, x9, y9, prec)
+    assert rel_err(y9.reshape(F.shape), O.mech_apply(F, c, d, prm, x9.astype(float).reshape(F.shape))) < tol
+    sol.apply(B.OP_PFF, x1, y1, prec)
+    assert rel_err(y1, O.pff_apply(x1.astype(float), Hh, prm)) < tol
+    sol.apply(B.OP_PFF_PREC, x1, y1, prec)
+    assert rel_err(y1, O.pff_precond(x1.astype(float), Hh.mean(), prm)) < tol
+    sol.apply(B.OP_CHEM, x1, y1, prec, dt=0.7)
+    ref = O.chem_apply(x1.astype(float), 1 / (c * (1 - c)), O.chem_conductivity(F, c, d, prm), 0.7, prm)
+    assert rel_err(y1, ref) < tol
+    sol.close()
+
+
+def test_emulated_coupled_step_matches_oracle(emu):
+    w = S.disc2d(n=16, radius=6.0, band=3, nsteps=10)
+    prm = oracle_params(w)
+    ref = O.CoupledState(prm, w.c_init, w.cdot_B)
+    sol = B.from_workload(w, lib=emu)
+    for _ in range(2):
+        ref.step(w.dt, np.eye(3))
+        st = sol.step(w.dt)
+        assert abs(st["mass_err"]) < 1e-13
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-10
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
+    em, ec, mass = sol.residual()
+    assert em <= 1e-9 and ec < 1e-9
+    assert abs(mass - ref.c.sum()) < 1e-10 * mass
+    sol.close()
+
+
+def test_emulated_mixed_step_close_to_fp64(emu):
+    w = S.disc2d(n=16, radius=6.0, band=3, nsteps=10)
+    a = B.from_workload(w, lib=emu)
+    b = B.from_workload(w, lib=emu, precision=B.FG_MIXED)
+    for _ in range(2):
+        a.step(w.dt)
+        b.step(w.dt)
+    assert rel_err(b.get(B.FIELD_F), a.get(B.FIELD_F)) < 1e-7
+    assert rel_err(b.get(B.FIELD_C), a.get(B.FIELD_C)) < 1e-7
+    a.close()
+    b.close()
