@@ -95,6 +95,7 @@ typedef struct {
 typedef struct {
   int newton_chem, newton_mech, cg_chem, cg_mech, cg_pff, stag;
   int inner_refine;   /* FP64 residual refinements of mixed-mode phase-field solves */
+  int cg_truncated;   /* mechanical CG solves stopped at non-positive curvature */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */

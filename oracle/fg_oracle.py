@@ -364,8 +364,12 @@ def dot(a, b):
     return float(np.vdot(a.ravel(), b.ravel()).real)
 
 
-def cg(apply, b, tol, maxit, x0=None):
-    """Textbook conjugate gradients; stops when ||r|| <= tol ||b||.  Returns (x, iters)."""
+def cg(apply, b, tol, maxit, x0=None, stats=None):
+    """Textbook conjugate gradients; stops when ||r|| <= tol ||b||.  Returns (x, iters).
+
+    Away from equilibrium the mechanical tangent of a prestressed particle in a soft
+    buffer is not positive definite; CG then stops at the first search direction of
+    non-positive curvature and returns its current iterate (truncated CG)."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply(x) if x0 is not None else b.copy()
     bn = math.sqrt(dot(b, b))
@@ -376,7 +380,14 @@ def cg(apply, b, tol, maxit, x0=None):
     it = 0
     while math.sqrt(rr) > tol * bn and it < maxit:
         q = apply(p)
-        alpha = rr / dot(p, q)
+        pq = dot(p, q)
+        if not pq > 0.0:
+            if it == 0:
+                raise FloatingPointError("operator not positive along the residual")
+            if stats is not None:
+                stats["cg_truncated"] = stats.get("cg_truncated", 0) + 1
+            break
+        alpha = rr / pq
         x = x + alpha * p
         r = r - alpha * q
         rr_new = dot(r, r)
@@ -448,7 +459,7 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
             return F, err
         if n_newton >= max_newton:
             raise RuntimeError("mechanical Newton did not converge")
-        dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg)
+        dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats=stats)
         F = F + dF
         n_newton += 1
         if stats is not None:

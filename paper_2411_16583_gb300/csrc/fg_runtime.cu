@@ -566,7 +566,8 @@ static void check_flags(fg_ctx& c, const char* where) {
 // Conjugate gradients on P.b (n elements) from x = 0; result in P.x.  apply(p, q, done)
 // computes q = A p and the partial sums of <p, q>, returning their count.
 template <typename R, class Apply>
-static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, int maxit, Apply apply) {
+static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, int maxit, Apply apply,
+                    int* truncated = nullptr) {
   KScal* ks = c.ks + slot;
   VArgs v = vbase(c, n);
   v.in[0] = P.b;
@@ -606,7 +607,13 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   }
   const KScal& k = c.ks_host[slot];
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
-  if (k.status & ST_INDEFINITE) fail(FG_ERR_NUMERIC, "Krylov operator not positive definite");
+  if (k.status & ST_INDEFINITE) {
+    // truncated CG: the iterate before the first direction of non-positive curvature
+    // is kept; with no iterate yet there is nothing to return
+    if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
+    if (truncated) *truncated += 1;
+    return k.iters;
+  }
   if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
   return k.iters;
 }
@@ -723,7 +730,8 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
     to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
     const int n = cg_solve<R>(c, P, 9 * c.V, KS_MECH, mixed_tol(c, c.o.tol_cg), c.o.max_cg,
-                              [&](const R* p, R* q, const int* done) { return op_mech(c, P, p, q, done); });
+                              [&](const R* p, R* q, const int* done) { return op_mech(c, P, p, q, done); },
+                              &s.cg_truncated);
     s.cg_mech += n;
     s.newton_mech += 1;
     if (is_mixed(c)) {

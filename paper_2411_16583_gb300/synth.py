@@ -18,7 +18,8 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
   (std 1.5 voxels, correlation length 4 voxels), band 8 voxels, 50 steps.
 * ``ellipsoid`` at 256^3 scaled x2 (semi-axes 100/80/70, roughness std 3,
   correlation 8) plus a smooth Gaussian concentration perturbation of std 0.02
-  (correlation 8 voxels) around c = 0.07 inside the particle, 100 steps.
+  (correlation 8 voxels) around c = 0.07 inside the particle (its stress-free
+  concentration), 100 steps.
 * ``spheres``   64 RVEs with edge N in {48, 64, 80, 96} and sphere radius
   U(0.30, 0.45) N.
 * ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
@@ -122,9 +123,13 @@ def _finish(name, shape, h, particle, band_width, nsteps, dt, rng, phases=None, 
     c_init = np.full(shape, c0)
     if c_perturb > 0.0:
         # smooth Gaussian random field of standard deviation c_perturb (correlation length
-        # perturb_corr voxels) around perturb_mean inside the particle
+        # perturb_corr voxels) around perturb_mean inside the particle, whose stress-free
+        # concentration is set to that mean: only the fluctuation is an eigenstrain at t = 0
         pert = _rough_field(rng, shape, c_perturb, perturb_corr)
         c_init = np.where(particle, np.clip(perturb_mean + pert, 0.005, 0.995), c0)
+        p = phases[PARTICLE]
+        phases = [PhaseSpec(law=p.law, E=p.E, nu=p.nu, Omega=p.Omega, c0=perturb_mean, D=p.D,
+                            sigma_max=p.sigma_max)] + list(phases[1:])
     return Workload(name=name, shape=shape, h=h, phases=phases, phase_id=phase_id,
                     cdot_B=cdot_B, c_init=c_init, gc=gc, lc=lc_vox * h[0], dt=dt, nsteps=nsteps)
 

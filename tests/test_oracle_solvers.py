@@ -260,3 +260,19 @@ def test_coupled_steps_invariants():
         assert err <= 1e-9
         Hprev = st.H.copy()
     assert st.H.max() > 0.0  # the band's swelling mismatch reaches the damage threshold
+
+
+def test_cg_truncates_at_nonpositive_curvature():
+    """On an indefinite operator CG returns the iterate before the first search direction
+    of non-positive curvature: here diag(3, 1, -2) with b = (1, 1, 1), worked by hand.
+    x1 = a0 b, a0 = b.b / b.A.b = 3/2; r1 = b - a0 A b = (-7/2, -1/2, 4);
+    p1 = r1 + (r1.r1 / b.b) p0 = r1 + (33/2)/3 b = (2, 5, 19/2);
+    p1.A.p1 = 12 + 25 - 180.5 < 0  ->  stop with x = x1."""
+    A = np.array([3.0, 1.0, -2.0])
+    b = np.ones(3)
+    stats = {}
+    x, it = O.cg(lambda v: A * v, b, 1e-12, 10, stats=stats)
+    np.testing.assert_allclose(x, 1.5 * b, rtol=1e-15)
+    assert it == 1 and stats["cg_truncated"] == 1
+    with pytest.raises(FloatingPointError):
+        O.cg(lambda v: -v, b, 1e-12, 10)
