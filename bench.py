@@ -29,24 +29,22 @@ METRIC = ("coupled time-step wall time & fused-matvec voxel-applies/s at 256³, 
 UNIT = "voxel-steps/s"
 
 # Algorithmic bytes per voxel of each profiled launch site of the FP32 mechanical CG
-# (9-component fields, 4-byte reals; the half spectrum holds (nx/2+1)/nx of a real field
-# as complex numbers, so a 9-component spectrum is 72 (nx/2+1)/nx bytes per voxel).
+# iteration (9-component fields, 4-byte reals; the half spectrum holds (nx/2+1)/nx of a
+# real field as complex numbers, so a 9-component spectrum is 72 (nx/2+1)/nx B/voxel).
 def site_bytes(nx):
     spec = 72.0 * (nx // 2 + 1) / nx
-    return {0: 36 + 48 + spec,       # X-fwd: read p (9) + tangent state (12), write spectrum
-            1: 2 * spec,             # Y-fwd: read + write spectrum
-            2: 2 * spec,             # Z + projection: read + write spectrum
-            3: 2 * spec,             # Y-inv: read + write spectrum
-            4: spec + 36 + 36,       # X-inv: read spectrum, write q, read p for <p, q>
-            5: 4 * 36 + 2 * 36}      # CG update: read x, p, r, q, write x, r
+    return {0: 36 + 36 + 48 + 36 + spec,   # X-fwd: read r, p, tangent state; write p, spectrum
+            1: 2 * spec,                    # Y-fwd: read + write spectrum
+            2: 2 * spec,                    # Z + projection: read + write spectrum
+            3: 2 * spec,                    # Y-inv: read + write spectrum
+            4: spec + 3 * 36 + 2 * 36}      # X-inv: read spectrum, r, x, p; write r, x
 
 
-SITE_NAMES = {0: "mech X-fwd + tangent (pass_kernel<XFwd<float,N,PTangentNH>>)",
+SITE_NAMES = {0: "mech X-fwd: p = r + beta p, tangent, <p,Kp> (pass_kernel<XFwd<float,N,PCgTangentNH>>)",
               1: "mech Y-fwd (pass_kernel<YPass<float,N,false>>)",
               2: "mech Z + projection (pass_kernel<ZPass<float,N,ZProject>>)",
               3: "mech Y-inv (pass_kernel<YPass<float,N,true>>)",
-              4: "mech X-inv + dot (pass_kernel<XInv<float,N,EStoreDot<9>>>)",
-              5: "mech CG update (pass_kernel<VecKernel<KCgXR<float>>>)"}
+              4: "mech X-inv: r -= alpha q, x += alpha p, |r|^2 (pass_kernel<XInv<float,N,ECgUpdate>>)"}
 
 
 def _args():
@@ -219,7 +217,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    for s in range(6):
+    for s in range(5):
         sol.profile(s, True)
     stats = []
     with Clocks(local) as clk:
@@ -233,8 +231,8 @@ def main():
         barrier()
         launches = B.kernel_launches() - l0
     ms = e0.elapsed_time(e1) / a.steps
-    prof = {s: sol.profile_read(s) for s in range(6)}
-    for s in range(6):
+    prof = {s: sol.profile_read(s) for s in range(5)}
+    for s in range(5):
         sol.profile(s, False)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -284,16 +282,16 @@ def main():
     peaks, src = _peaks()
     sb = site_bytes(w.shape[2])
     sites = {}
-    for s, (n, t) in prof.items():
+    for s, (n, t, vol) in prof.items():
         if n:
-            avg = t / n * 1e-3
-            sites[SITE_NAMES[s]] = {"launches": n, "total_ms": t, "avg_us": avg * 1e6,
+            sites[SITE_NAMES[s]] = {"launches": n, "total_ms": t, "volumes": vol,
+                                    "us_per_volume": t * 1e3 / vol,
                                     "alg_bytes_per_voxel": sb[s],
-                                    "gbs": sb[s] * V / avg / 1e9}
+                                    "gbs": sb[s] * V * vol / (t * 1e-3) / 1e9}
     dom = max((s for s in prof if prof[s][0]), key=lambda s: prof[s][1])
-    n_dom, t_dom = prof[dom]
-    avg_dom = t_dom / n_dom * 1e-3
-    ach = sb[dom] * V / avg_dom / 1e9
+    n_dom, t_dom, vol_dom = prof[dom]
+    avg_dom = t_dom / n_dom * 1e-3           # seconds per launch
+    ach = sb[dom] * V * vol_dom / (t_dom * 1e-3) / 1e9
     line = {
         "metric": METRIC,
         "value": V * world / (ms * 1e-3),
@@ -315,7 +313,8 @@ def main():
         "roofline": {"bound": "hbm", "kernel": SITE_NAMES[dom], "achieved": ach,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                      "peak_source": src,
-                     "alg_bytes_per_launch": sb[dom] * V, "avg_launch_us": avg_dom * 1e6,
+                     "alg_bytes_per_launch": sb[dom] * V * vol_dom / n_dom,
+                     "avg_launch_us": avg_dom * 1e6,
                      "traffic": None},
         "kernels": sites,
         "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),

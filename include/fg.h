@@ -68,7 +68,7 @@ typedef struct {
 } fg_grid;
 
 typedef struct {
-  int law;           /* FG_NEOHOOKE (GPU path); FG_SVK is rejected with FG_ERR_INVALID */
+  int law;           /* FG_NEOHOOKE or FG_SVK; all phases of a context use one law */
   double E, nu;      /* Young's modulus (Pa), Poisson ratio */
   double Omega;      /* swelling: J_c = 1 + Omega (c - c0) (Eq. Fc) */
   double c0;         /* stress-free concentration */
@@ -90,12 +90,15 @@ typedef struct {
   double cg_forcing;  /* mixed mode: relative tolerance of each FP32 inner solve */
   int max_newton, max_cg, max_chem_newton, max_stag;
   void* cuda_stream;  /* cudaStream_t, NULL for the legacy default stream */
+  double l2_fraction; /* share of L2 one chunk of kx planes of the spectrum may take
+                         between the Y and Z passes (0: 0.4; >= 1: no chunking) */
 } fg_opts;
 
 typedef struct {
   int newton_chem, newton_mech, cg_chem, cg_mech, cg_pff, stag;
   int inner_refine;   /* FP64 residual refinements of mixed-mode phase-field solves */
   int cg_truncated;   /* mechanical CG solves stopped at non-positive curvature */
+  int newton_damped;  /* halvings of mechanical Newton corrections */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */
@@ -171,12 +174,14 @@ int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
  * bracketed by two CUDA events on the context stream (at most 4096 launches are recorded
  * after each enable).  Sites: 0-4 the five passes of the mechanical operator (X-fwd with
  * the tangent, Y-fwd, Z with the projection, Y-inv, X-inv with the dot product), 5 the
- * x/r update of the mechanical CG.  fg_profile_read synchronises the stream and returns
- * the number of recorded launches and their summed device time; launches shorter than a
+ * Krylov update of the mechanical CG (unfused path).  fg_profile_read synchronises the stream and returns
+ * the number of recorded launches, their summed device time and (volumes, may be NULL)
+ * the number of full grid volumes they covered (the Y and Z passes run on chunks of kx
+ * planes, each a fraction of the volume); launches shorter than a
  * fifth of the median (kernels that returned at once because their Krylov loop had
  * already converged) are left out of both. */
 int fg_profile(fg_ctx* ctx, int site, int enable);
-int fg_profile_read(fg_ctx* ctx, int site, int* launches, double* total_ms);
+int fg_profile_read(fg_ctx* ctx, int site, int* launches, double* total_ms, double* volumes);
 
 /* Releases the context and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);

@@ -449,10 +449,13 @@ def mech_residual(F, c, d, prm, Fbar):
 
 
 def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stats=None):
-    """Alg. 1 from the given F (the caller sets F^0 = F_t + dFbar)."""
+    """Alg. 1 from the given F (the caller sets F^0 = F_t + dFbar).
+
+    Each Newton correction dF is damped, lambda = 1, 1/2, ... (at most 10 halvings),
+    until F + lambda dF stays in the domain (det F > 0, J_c > 0) and lowers err_res."""
     n_newton = 0
+    GP, err = mech_residual(F, c, d, prm, Fbar)
     while True:
-        GP, err = mech_residual(F, c, d, prm, Fbar)
         if stats is not None:
             stats.setdefault("err_mech", []).append(err)
         if err <= tol_newton:
@@ -460,11 +463,25 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
         if n_newton >= max_newton:
             raise RuntimeError("mechanical Newton did not converge")
         dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats=stats)
-        F = F + dF
         n_newton += 1
         if stats is not None:
             stats["newton_mech"] = stats.get("newton_mech", 0) + 1
             stats["cg_mech"] = stats.get("cg_mech", 0) + it
+        lam = 1.0
+        for _ in range(11):
+            Fn = F + lam * dF
+            ok = bool(np.all(tdet(Fn) > 0.0)) and bool(np.all(swelling_J(c, prm) > 0.0))
+            if ok:
+                with np.errstate(all="ignore"):
+                    GPn, errn = mech_residual(Fn, c, d, prm, Fbar)
+                if errn < err:
+                    break
+            if stats is not None:
+                stats["newton_damped"] = stats.get("newton_damped", 0) + 1
+            lam *= 0.5
+        else:
+            raise RuntimeError("mechanical Newton: no decrease of err_res along the correction")
+        F, GP, err = Fn, GPn, errn
 
 
 # --------------------------------------------------------------------------------------

@@ -47,13 +47,14 @@ class Opts(C.Structure):
                 ("tol_cg", C.c_double), ("tol_chem", C.c_double), ("tol_chem_cg", C.c_double),
                 ("tol_pff_cg", C.c_double), ("tol_stag", C.c_double), ("cg_forcing", C.c_double),
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
-                ("max_stag", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("newton_chem", C.c_int), ("newton_mech", C.c_int), ("cg_chem", C.c_int),
                 ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
-                ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("err_mech", C.c_double), ("err_chem", C.c_double),
+                ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("newton_damped", C.c_int),
+                ("err_mech", C.c_double), ("err_chem", C.c_double),
                 ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
 
     def as_dict(self):
@@ -89,7 +90,7 @@ def load_library(path=LIB_PATH):
     lib.fg_set_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     lib.fg_time_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
     lib.fg_profile.argtypes = [C.c_void_p, C.c_int, C.c_int]
-    lib.fg_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), dp]
+    lib.fg_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), dp, dp]
     lib.fg_kernel_launches.restype = C.c_longlong
     lib.fg_destroy.argtypes = [C.c_void_p]
     lib.fg_destroy.restype = None
@@ -202,9 +203,10 @@ class Solver:
         self._check(self.lib.fg_profile(self.ctx, site, int(enable)))
 
     def profile_read(self, site):
-        n, ms = C.c_int(), C.c_double()
-        self._check(self.lib.fg_profile_read(self.ctx, site, C.byref(n), C.byref(ms)))
-        return n.value, ms.value
+        """(launches, total ms, full volumes covered) of a profiled launch site."""
+        n, ms, vol = C.c_int(), C.c_double(), C.c_double()
+        self._check(self.lib.fg_profile_read(self.ctx, site, C.byref(n), C.byref(ms), C.byref(vol)))
+        return n.value, ms.value, vol.value
 
     def time_apply(self, op, prec, n):
         ms = C.c_double()

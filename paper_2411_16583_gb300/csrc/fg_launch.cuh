@@ -54,9 +54,10 @@ using PassFn = int (*)(const PassArgs<R>&, cudaStream_t);
 template <typename R>
 struct SizeOps {
   int N;
-  PassFn<R> xf_tangent, xf_copy1, xf_copy3, xf_copy9;
+  PassFn<R> xf_tangent, xf_cgtangent, xf_tangent_svk, xf_cgtangent_svk, xf_copy1, xf_copy3,
+      xf_copy9;
   PassFn<R> xi_store1, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
-      xi_chemrhs;
+      xi_chemrhs, xi_cgupdate;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
 };
@@ -65,13 +66,16 @@ template <class K, typename R>
 int run_x(const PassArgs<R>& a, cudaStream_t st) {
   return launch_pass<K>(a, Dim3{K::grid_x(a.ny, a.nz), 1, 1}, st);
 }
+// Y and Z passes cover rows [row_lo, row_hi) when row_hi > 0 (a range of kx planes)
 template <class K, typename R>
 int run_y(const PassArgs<R>& a, cudaStream_t st) {
-  return launch_pass<K>(a, Dim3{K::grid_x(a.hx, a.nz), a.ncomp, 1}, st);
+  const int rows = a.row_hi > 0 ? a.row_hi - a.row_lo : a.hx * a.nz;
+  return launch_pass<K>(a, Dim3{(rows + K::ROWS - 1) / K::ROWS, a.ncomp, 1}, st);
 }
 template <class K, typename R>
 int run_z(const PassArgs<R>& a, cudaStream_t st) {
-  return launch_pass<K>(a, Dim3{K::grid_x(a.hx, a.ny), 1, 1}, st);
+  const int rows = a.row_hi > 0 ? a.row_hi - a.row_lo : a.hx * a.ny;
+  return launch_pass<K>(a, Dim3{(rows + K::ROWS - 1) / K::ROWS, 1, 1}, st);
 }
 
 template <typename R, int N>
@@ -80,6 +84,10 @@ SizeOps<R> make_size_ops() {
   s.N = N;
   if constexpr (N % 2 == 0) {
     s.xf_tangent = run_x<XFwd<R, N, PTangentNH<R>>, R>;
+    s.xf_cgtangent = run_x<XFwd<R, N, PCgTangentNH<R>>, R>;
+    s.xf_tangent_svk = run_x<XFwd<R, N, PTangentSVK<R>>, R>;
+    s.xf_cgtangent_svk = run_x<XFwd<R, N, PCgTangentSVK<R>>, R>;
+    s.xi_cgupdate = run_x<XInv<R, N, ECgUpdate<R>>, R>;
     s.xf_copy1 = run_x<XFwd<R, N, PCopy<R, 1>>, R>;
     s.xf_copy3 = run_x<XFwd<R, N, PCopy<R, 3>>, R>;
     s.xf_copy9 = run_x<XFwd<R, N, PCopy<R, 9>>, R>;

@@ -114,6 +114,69 @@ FG_DEV void tangent_nh(const R* B, R s1, R s2, R s3, const R* p, R* t) {
     }
 }
 
+// Saint-Venant-Kirchhoff tangent from the packed state (F, S, s1 = g a^2,
+// s2 = g a^4 lam, s3 = g a^4 G): with M = F^T dF,
+//   K : dF = s1 dF S + F (s2 tr(M) I + s3 (M + M^T)).
+template <typename R>
+FG_DEV void tangent_svk(const R* st, long long V, long long v, const R* p, R* t) {
+  R F[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) F[k] = st[k * V + v];
+  const R Sxx = st[9 * V + v], Syy = st[10 * V + v], Szz = st[11 * V + v];
+  const R Sxy = st[12 * V + v], Sxz = st[13 * V + v], Syz = st[14 * V + v];
+  const R s1 = st[15 * V + v], s2 = st[16 * V + v], s3 = st[17 * V + v];
+  const R S[9] = {Sxx, Sxy, Sxz, Sxy, Syy, Syz, Sxz, Syz, Szz};
+  R M[9];  // M_ij = sum_k F_ki p_kj
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = F[i] * p[j] + F[3 + i] * p[3 + j] + F[6 + i] * p[6 + j];
+  const R tr = M[0] + M[4] + M[8];
+  R W[9];  // s2 tr(M) I + s3 (M + M^T)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) W[3 * i + j] = s3 * (M[3 * i + j] + M[3 * j + i]) + (i == j ? s2 * tr : (R)0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const R pS = p[3 * i] * S[j] + p[3 * i + 1] * S[3 + j] + p[3 * i + 2] * S[6 + j];
+      const R FW = F[3 * i] * W[j] + F[3 * i + 1] * W[3 + j] + F[3 * i + 2] * W[6 + j];
+      t[3 * i + j] = s1 * pS + FW;
+    }
+}
+
+template <typename R>
+struct PTangentSVK {
+  static constexpr int COUT = 9;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+    R p[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) p[c] = a.rin[c * a.V + v];
+    tangent_svk(a.aux[0], a.V, v, p, out);
+  }
+};
+
+template <typename R>
+struct PCgTangentSVK {
+  static constexpr int COUT = 9;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
+    const R beta = (R)a.dscal[1];
+    R p[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      p[c] = a.rin[c * a.V + v] + beta * a.rout[c * a.V + v];
+      a.rout[c * a.V + v] = p[c];
+    }
+    tangent_svk(a.aux[0], a.V, v, p, out);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
+  }
+};
+
 template <typename R>
 struct PTangentNH {
   static constexpr int COUT = 9;
@@ -129,7 +192,53 @@ struct PTangentNH {
   }
 };
 
+// Conjugate-gradient direction update fused with the tangent (mechanical CG):
+//   p = r + beta p  (written back, in place),  tau = K : p,  accumulates <p, K p>.
+// For a compatible p (every CG direction is a combination of projected fields)
+// <p, K p> = <p, G K p>, so the step length is known before the inverse transform.
+// rin = r, rout = p, aux0 = packed state, dscal[1] = beta.
+template <typename R>
+struct PCgTangentNH {
+  static constexpr int COUT = 9;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
+    const R beta = (R)a.dscal[1];
+    R p[9], B[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      p[c] = a.rin[c * a.V + v] + beta * a.rout[c * a.V + v];
+      a.rout[c * a.V + v] = p[c];
+    }
+    const R* st = a.aux[0];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) B[c] = st[c * a.V + v];
+    tangent_nh(B, st[9 * a.V + v], st[10 * a.V + v], st[11 * a.V + v], p, out);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
+  }
+};
+
 // ================================================================== X-inv epilogues
+
+// Conjugate-gradient update fused with the inverse transform (mechanical CG): with
+// q = G K p arriving as `val`, r -= alpha q and x += alpha p; accumulates <r, r>.
+// rout = r, rout2 = x, aux0 = p, dscal[0] = alpha.
+template <typename R>
+struct ECgUpdate {
+  static constexpr int CIN = 9;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+    const R al = (R)a.dscal[0];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const long long i = c * a.V + v;
+      const R rn = a.rout[i] - al * val[c];
+      a.rout[i] = rn;
+      a.rout2[i] += al * a.aux[0][i];
+      acc += (double)rn * (double)rn;
+    }
+  }
+};
 
 template <typename R, int NC>
 struct EStore {

@@ -24,6 +24,7 @@ struct PassArgs {
   long long V, VH;      // voxels, half-spectrum points per component
   const R* rin;         // real input fields (X-fwd prologue)
   R* rout;              // real output fields (X-inv epilogue)
+  R* rout2;             // second real output (fused Krylov updates)
   const C* cin;         // complex input
   C* cout;              // complex output
   const C* tw;          // exp(-2 pi i m / N), m < N, for this pass's axis
@@ -38,6 +39,7 @@ struct PassArgs {
   double* partials;     // one partial sum per block (reducing epilogues)
   const int* done;      // early exit when *done != 0 (converged Krylov loop)
   int ncomp;            // components (Y passes)
+  int row_lo, row_hi;   // Y and Z passes: rows [row_lo, row_hi) only (row_hi = 0: all)
 };
 
 // ------------------------------------------------------------------ tile sizing
@@ -277,8 +279,8 @@ struct YPass {
     C* tile = (C*)smem;
     C* tw = tile + ROWS * PITCH;
     const int c = bid.y;
-    const int nrows = a.hx * a.nz;
-    const int row0 = bid.x * ROWS;
+    const int nrows = a.row_hi > 0 ? a.row_hi : a.hx * a.nz;
+    const int row0 = a.row_lo + bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     const C* in = a.cin + c * a.VH;
     C* out = a.cout + c * a.VH;
@@ -332,8 +334,8 @@ struct ZPass {
     if (a.done && *a.done) return;
     C* tile = (C*)smem;
     C* tw = tile + CM * ROWS * PITCH;
-    const int nrows = a.hx * a.ny;
-    const int row0 = bid.x * ROWS;
+    const int nrows = a.row_hi > 0 ? a.row_hi : a.hx * a.ny;
+    const int row0 = a.row_lo + bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     FG_PHASE(NT)
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];

@@ -158,48 +158,82 @@ struct MatPtrs {
   const double* c0;
 };
 
-// Neo-Hookean pieces at voxel v: a = J_c^{-1/3}, F_e = a F.
-struct NHPoint {
-  double a, g, lam, mu, lnJe, B[9];  // B = F^-T
-  double Fe[9];
+// Elastic state of one voxel for either law: a = J_c^{-1/3}, F_e = a F, g = (1-d)^2,
+// the pristine stress P0(F_e) and the power P0 : F_e (Eqs. Fc, Ee, psie0, pristine).
+enum : int { LAW_SVK_ = 0, LAW_NH_ = 1 };
+
+struct ElasticPoint {
+  double a, g, Jc, lam, mu;
+  double Fe[9], P0[9], P0Fe;
+  double B[9], lnJe;  // Neo-Hookean: F^-T and ln J_e
+  double S[6];        // Saint-Venant-Kirchhoff: S(E_e) as (xx, yy, zz, xy, xz, yz)
 };
 
-FG_DEV bool nh_point(const double* F, double c, double d, double lam, double mu, double Om,
-                    double c0, NHPoint& P) {
-  const double Jc = 1.0 + Om * (c - c0);
+template <int LAW>
+FG_DEV bool elastic_point(const double* F, double c, double d, double lam, double mu, double Om,
+                          double c0, ElasticPoint& P) {
+  P.Jc = 1.0 + Om * (c - c0);
   const double J = det3(F);
-  if (!(Jc > 0.0) || !(J > 0.0)) return false;
-  P.a = 1.0 / cbrt(Jc);
+  if (!(P.Jc > 0.0) || !(J > 0.0)) return false;
+  P.a = 1.0 / cbrt(P.Jc);
   P.g = (1.0 - d) * (1.0 - d);
   P.lam = lam;
   P.mu = mu;
-  P.lnJe = log(P.a * P.a * P.a * J);
-  double C[9];
-  cof3(F, C);
-  const double iJ = 1.0 / J;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    P.B[k] = C[k] * iJ;
-    P.Fe[k] = P.a * F[k];
+  for (int k = 0; k < 9; ++k) P.Fe[k] = P.a * F[k];
+  if constexpr (LAW == LAW_NH_) {
+    // P0 = G (F_e - F_e^-T) + lam ln J_e F_e^-T, with F_e^-T = F^-T / a
+    P.lnJe = log(P.a * P.a * P.a * J);
+    double C[9];
+    cof3(F, C);
+    const double iJ = 1.0 / J, ia = 1.0 / P.a;
+    double trCe = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      P.B[k] = C[k] * iJ;
+      const double FeiT = P.B[k] * ia;
+      P.P0[k] = mu * (P.Fe[k] - FeiT) + lam * P.lnJe * FeiT;
+      trCe += P.Fe[k] * P.Fe[k];
+    }
+    P.P0Fe = mu * (trCe - 3.0) + 3.0 * lam * P.lnJe;
+  } else {
+    // E_e = (F_e^T F_e - I)/2, S = lam tr(E_e) I + 2 G E_e, P0 = F_e S
+    double Ce[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Ce[3 * i + j] = P.Fe[i] * P.Fe[j] + P.Fe[3 + i] * P.Fe[3 + j] + P.Fe[6 + i] * P.Fe[6 + j];
+    const double trE = 0.5 * (Ce[0] + Ce[4] + Ce[8] - 3.0);
+    const double Sxx = lam * trE + mu * (Ce[0] - 1.0), Syy = lam * trE + mu * (Ce[4] - 1.0);
+    const double Szz = lam * trE + mu * (Ce[8] - 1.0);
+    const double Sxy = mu * Ce[1], Sxz = mu * Ce[2], Syz = mu * Ce[5];
+    P.S[0] = Sxx; P.S[1] = Syy; P.S[2] = Szz; P.S[3] = Sxy; P.S[4] = Sxz; P.S[5] = Syz;
+    const double Sm[9] = {Sxx, Sxy, Sxz, Sxy, Syy, Syz, Sxz, Syz, Szz};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        P.P0[3 * i + j] = P.Fe[3 * i] * Sm[j] + P.Fe[3 * i + 1] * Sm[3 + j] + P.Fe[3 * i + 2] * Sm[6 + j];
+    double sc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sc += Sm[k] * Ce[k];
+    P.P0Fe = sc;
   }
   return true;
 }
 
-// P0(F_e) of the compressible Neo-Hookean law: G (F_e - F_e^-T) + lam ln J_e F_e^-T.
-FG_DEV void nh_P0(const NHPoint& P, double* P0) {
-  const double ia = 1.0 / P.a;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const double FeiT = P.B[k] * ia;
-    P0[k] = P.mu * (P.Fe[k] - FeiT) + P.lam * P.lnJe * FeiT;
-  }
-}
+// reals per voxel of the packed tangent state
+constexpr int state_size(int law) { return law == LAW_NH_ ? 12 : 18; }
 
 // ---------------------------------------------------------------- mechanics state
 // in: F (9 V) or uniform Fbar (s[0..8], when in[0] == null), c, d, material
-// out0: P (9 V, FP64, may be null), out1: packed tangent state (12 V, precision R)
+// out0: P = (1-d)^2 a P0(a F) (9 V, FP64, may be null)
+// out1: packed tangent state (precision R, may be null):
+//   Neo-Hookean   B = F^-T (9), g a^2 G, g (G - lam ln J_e), g lam
+//   St-V-Kirchhoff F (9), S (6), g a^2, g a^4 lam, g a^4 G
 
-template <typename R>
+template <typename R, int LAW = LAW_NH_>
 struct KMechState {
   static constexpr bool RED = false;
   FG_DEV static void apply(const VArgs& a, long long v, double&) {
@@ -212,26 +246,35 @@ struct KMechState {
     const double d = ((const double*)a.in[2])[v];
     const double lam = ((const double*)a.in[3])[v], mu = ((const double*)a.in[4])[v];
     const double Om = ((const double*)a.in[5])[v], c0 = ((const double*)a.in[6])[v];
-    NHPoint P;
-    if (!nh_point(F, c, d, lam, mu, Om, c0, P)) {
+    ElasticPoint P;
+    if (!elastic_point<LAW>(F, c, d, lam, mu, Om, c0, P)) {
       atomicOr(a.flags, ST_DOMAIN);
       return;
     }
     if (a.out[0]) {
-      double P0[9];
-      nh_P0(P, P0);
       double* Po = (double*)a.out[0];
       const double ga = P.g * P.a;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Po[k * V + v] = ga * P0[k];
+      for (int k = 0; k < 9; ++k) Po[k * V + v] = ga * P.P0[k];
     }
     if (a.out[1]) {
       R* st = (R*)a.out[1];
+      if constexpr (LAW == LAW_NH_) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) st[k * V + v] = (R)P.B[k];
-      st[9 * V + v] = (R)(P.g * P.a * P.a * P.mu);
-      st[10 * V + v] = (R)(P.g * (P.mu - P.lam * P.lnJe));
-      st[11 * V + v] = (R)(P.g * P.lam);
+        for (int k = 0; k < 9; ++k) st[k * V + v] = (R)P.B[k];
+        st[9 * V + v] = (R)(P.g * P.a * P.a * P.mu);
+        st[10 * V + v] = (R)(P.g * (P.mu - P.lam * P.lnJe));
+        st[11 * V + v] = (R)(P.g * P.lam);
+      } else {
+        const double a2 = P.a * P.a;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) st[k * V + v] = (R)F[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st[(9 + k) * V + v] = (R)P.S[k];
+        st[15 * V + v] = (R)(P.g * a2);
+        st[16 * V + v] = (R)(P.g * a2 * a2 * P.lam);
+        st[17 * V + v] = (R)(P.g * a2 * a2 * P.mu);
+      }
     }
   }
 };
@@ -240,6 +283,7 @@ struct KMechState {
 // H = max(H_t, g_c/(2 l_c) D_f), D_f from the principal values of the undegraded Cauchy
 // stress sigma = J^-1 a P0(a F) F^T (Eqs. Hist, SigDrivingForce).  Accumulates sum H.
 // in: F, c, H_t, lam, mu, Om, c0, smax ; out0: H ; s0 = g_c/(2 l_c)
+template <int LAW = LAW_NH_>
 struct KHistory {
   static constexpr bool RED = true;
   FG_DEV static void apply(const VArgs& a, long long v, double& acc) {
@@ -250,12 +294,11 @@ struct KHistory {
     for (int k = 0; k < 9; ++k) F[k] = Fp[k * V + v];
     const double c = ((const double*)a.in[1])[v];
     const double Ht = ((const double*)a.in[2])[v];
-    NHPoint P;
+    ElasticPoint P;
     double Hn = Ht;
-    if (nh_point(F, c, 0.0, ((const double*)a.in[3])[v], ((const double*)a.in[4])[v],
-                 ((const double*)a.in[5])[v], ((const double*)a.in[6])[v], P)) {
-      double P0[9];
-      nh_P0(P, P0);
+    if (elastic_point<LAW>(F, c, 0.0, ((const double*)a.in[3])[v], ((const double*)a.in[4])[v],
+                           ((const double*)a.in[5])[v], ((const double*)a.in[6])[v], P)) {
+      const double* P0 = P.P0;
       const double J = det3(F);
       const double s = P.a / J;
       double sg[9];
@@ -323,9 +366,9 @@ struct KChemCond {
 //   out0 = mu~(c) = log(c/(1-c)) + mu_e / RT        (Eqs. muc, mue)
 //   out1 = c - c_t - dt cdot_B                     (residual without the flux term)
 //   out2 = c (1 - c) in precision R                (1/m of the Jacobian)
-// mu_e = -(1-d)^2 Omega / (3 J_c) P0(F_e) : F_e / c_max.
+// mu_e = -(1-d)^2 Omega / (3 J_c) P0(F_e) : F_e / c_max  (d psi_e / dc at fixed F).
 // in: c, c_t, cdot_B, F, d_t, lam, mu, Om, c0 ; s0 = dt, s1 = 1/RT, s2 = 1/c_max
-template <typename R>
+template <typename R, int LAW = LAW_NH_>
 struct KChemPrep {
   static constexpr bool RED = false;
   FG_DEV static void apply(const VArgs& a, long long v, double&) {
@@ -346,14 +389,9 @@ struct KChemPrep {
     const double Om = ((const double*)a.in[7])[v], c0 = ((const double*)a.in[8])[v];
     double mue = 0.0;
     if (Om != 0.0) {
-      NHPoint P;
-      if (nh_point(F, c, d, lam, mu, Om, c0, P)) {
-        double trC = 0.0;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) trC += P.Fe[k] * P.Fe[k];
-        const double P0Fe = mu * (trC - 3.0) + 3.0 * lam * P.lnJe;
-        const double Jc = 1.0 + Om * (c - c0);
-        mue = -P.g * Om / (3.0 * Jc) * P0Fe * a.s[2];
+      ElasticPoint P;
+      if (elastic_point<LAW>(F, c, d, lam, mu, Om, c0, P)) {
+        mue = -P.g * Om / (3.0 * P.Jc) * P.P0Fe * a.s[2];
       } else {
         atomicOr(a.flags, ST_DOMAIN);
       }
@@ -407,6 +445,14 @@ struct KAddTo {
   static constexpr bool RED = false;
   FG_DEV static void apply(const VArgs& a, long long i, double&) {
     ((double*)a.out[0])[i] += (double)((const R*)a.in[0])[i];
+  }
+};
+
+// out0 (FP64) = in0 + s0 * in1 (FP64)
+struct KAxpyTo {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+    ((double*)a.out[0])[i] = ((const double*)a.in[0])[i] + a.s[0] * ((const double*)a.in[1])[i];
   }
 };
 
@@ -508,6 +554,7 @@ struct FCgStart {
     k->rr = t;
     k->rz = t;
     k->tol2 = a.s[0] * a.s[0] * t;
+    k->beta = 0.0;
     k->iters = 0;
     k->maxit = (int)a.s[1];
     k->status = 0;

@@ -126,6 +126,7 @@ struct Prec {
 
 struct fg_ctx {
   int nx = 0, ny = 0, nz = 0, hx = 0;
+  int law = FG_NEOHOOKE;
   long long V = 0, VH = 0;
   double h[3] = {0, 0, 0};
   fg_opts o{};
@@ -134,6 +135,7 @@ struct fg_ctx {
   // FP64 fields
   double *F = nullptr, *Ft = nullptr, *c = nullptr, *ct = nullptr, *d = nullptr, *dt = nullptr;
   double *H = nullptr, *Ht = nullptr, *cdotB = nullptr, *P = nullptr, *GP = nullptr;
+  double *Fbk = nullptr, *dF = nullptr;  // Newton line search: F before the update, dF
   double *mu = nullptr, *base = nullptr;
   double *lam = nullptr, *mu_ = nullptr, *Om = nullptr, *c0 = nullptr, *D = nullptr, *smax = nullptr;
   double* partials = nullptr;
@@ -151,7 +153,9 @@ struct fg_ctx {
   // launch-site profiling: event pairs around every launch of the enabled sites
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> prof_ev[8];
+  std::vector<double> prof_frac[8];  // share of the full volume each recorded launch covers
   int prof_used[8] = {0};
+  int kx_chunk[2] = {1, 1};          // kx planes per Y-Z-Y chunk (FP32, FP64)
   int last_inner_refine = 0;
 };
 
@@ -243,7 +247,7 @@ static void setup_prec(fg_ctx& c, Prec<R>& P, int krylov_comps) {
   P.w = alloc_n<R>(c, c.V);
   P.Hr = alloc_n<R>(c, c.V);
   P.tmp3 = alloc_n<R>(c, 3 * c.V);
-  if (krylov_comps == 9) P.state = alloc_n<R>(c, 12 * c.V);
+  if (krylov_comps == 9) P.state = alloc_n<R>(c, (long long)state_size(c.law) * c.V);
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -266,7 +270,7 @@ struct ProfScope {
   fg_ctx& c;
   int site;
   bool on;
-  ProfScope(fg_ctx& cc, int s) : c(cc), site(s), on(false) {
+  ProfScope(fg_ctx& cc, int s, double frac = 1.0) : c(cc), site(s), on(false) {
 #ifndef FG_EMU
     if ((c.prof_mask >> site) & 1u) {
       auto& v = c.prof_ev[site];
@@ -279,10 +283,14 @@ struct ProfScope {
           v.push_back(a);
           v.push_back(b);
         }
+        if ((int)c.prof_frac[site].size() < k + 1) c.prof_frac[site].push_back(0.0);
+        c.prof_frac[site][k] = frac;
         cudaEventRecord(v[2 * k], c.st);
         on = true;
       }
     }
+#else
+    (void)frac;
 #endif
   }
   ~ProfScope() {
@@ -344,28 +352,52 @@ static PassArgs<R> pbase(fg_ctx& c, Prec<R>& P, const int* done) {
 }
 
 // Y-fwd, Z op, Y-inv on the spectrum in S1 (ncomp_in comps) -> S1 (ncomp_out comps)
+// Y-fwd, Z op, Y-inv on the spectrum in S1 (cin comps) -> S1 (cout comps).  The three
+// passes run on chunks of consecutive kx planes sized to stay in L2 between them, so the
+// intermediate spectrum S2 of a chunk is written and read back from L2 instead of HBM.
+// `sites` (or null) names the profiling sites of the three passes.
 template <typename R>
 static void yzy(fg_ctx& c, Prec<R>& P, const int* done, int cin, PassFn<R> zop, int cout,
-                const R* zcoef, const double* dscal) {
-  PassArgs<R> a = pbase(c, P, done);
-  a.tw = P.twy;
-  a.cin = P.S1;
-  a.cout = P.S2;
-  a.ncomp = cin;
-  P.oy->yf(a, c.st);
-  a = pbase(c, P, done);
-  a.tw = P.twz;
-  a.cin = P.S2;
-  a.cout = P.S2;
-  for (int k = 0; k < 4; ++k) a.coef[k] = zcoef[k];
-  a.dscal = dscal;
-  zop(a, c.st);
-  a = pbase(c, P, done);
-  a.tw = P.twy;
-  a.cin = P.S2;
-  a.cout = P.S1;
-  a.ncomp = cout;
-  P.oy->yi(a, c.st);
+                const R* zcoef, const double* dscal, const int* sites = nullptr) {
+  const int chunk = c.kx_chunk[sizeof(R) == 8 ? 1 : 0];
+  for (int k0 = 0; k0 < c.hx; k0 += chunk) {
+    const int k1 = k0 + chunk < c.hx ? k0 + chunk : c.hx;
+    const double frac = (double)(k1 - k0) / (double)c.hx;
+    PassArgs<R> a = pbase(c, P, done);
+    a.tw = P.twy;
+    a.cin = P.S1;
+    a.cout = P.S2;
+    a.ncomp = cin;
+    a.row_lo = k0 * c.nz;
+    a.row_hi = k1 * c.nz;
+    {
+      ProfScope ps(c, sites ? sites[0] : SITE_N - 1, frac);
+      P.oy->yf(a, c.st);
+    }
+    a = pbase(c, P, done);
+    a.tw = P.twz;
+    a.cin = P.S2;
+    a.cout = P.S2;
+    for (int k = 0; k < 4; ++k) a.coef[k] = zcoef[k];
+    a.dscal = dscal;
+    a.row_lo = k0 * c.ny;
+    a.row_hi = k1 * c.ny;
+    {
+      ProfScope ps(c, sites ? sites[1] : SITE_N - 1, frac);
+      zop(a, c.st);
+    }
+    a = pbase(c, P, done);
+    a.tw = P.twy;
+    a.cin = P.S2;
+    a.cout = P.S1;
+    a.ncomp = cout;
+    a.row_lo = k0 * c.nz;
+    a.row_hi = k1 * c.nz;
+    {
+      ProfScope ps(c, sites ? sites[2] : SITE_N - 1, frac);
+      P.oy->yi(a, c.st);
+    }
+  }
 }
 
 // y = G : F^-1[ F[K : x] ] ; accumulates <x, y>; returns partial count
@@ -378,35 +410,11 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
   a.cout = P.S1;
   {
     ProfScope ps(c, SITE_XF);
-    P.ox->xf_tangent(a, c.st);
+    (c.law == FG_SVK ? P.ox->xf_tangent_svk : P.ox->xf_tangent)(a, c.st);
   }
-  a = pbase(c, P, done);
-  a.tw = P.twy;
-  a.cin = P.S1;
-  a.cout = P.S2;
-  a.ncomp = 9;
-  {
-    ProfScope ps(c, SITE_YF);
-    P.oy->yf(a, c.st);
-  }
-  a = pbase(c, P, done);
-  a.tw = P.twz;
-  a.cin = P.S2;
-  a.cout = P.S2;
-  a.coef[0] = (R)(1.0 / (double)c.V);
-  {
-    ProfScope ps(c, SITE_Z);
-    P.oz->z_proj(a, c.st);
-  }
-  a = pbase(c, P, done);
-  a.tw = P.twy;
-  a.cin = P.S2;
-  a.cout = P.S1;
-  a.ncomp = 9;
-  {
-    ProfScope ps(c, SITE_YI);
-    P.oy->yi(a, c.st);
-  }
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
+  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -538,7 +546,8 @@ static void mech_state(fg_ctx& c, const double* F, const double* Fbar, double* P
   v.in[6] = c.c0;
   v.out[0] = Pout;
   v.out[1] = state;
-  launch_vec<KMechState<R>>(v, c.st);
+  if (c.law == FG_SVK) launch_vec<KMechState<R, LAW_SVK_>>(v, c.st);
+  else launch_vec<KMechState<R, LAW_NH_>>(v, c.st);
 }
 
 template <typename R>
@@ -610,6 +619,72 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   if (k.status & ST_INDEFINITE) {
     // truncated CG: the iterate before the first direction of non-positive curvature
     // is kept; with no iterate yet there is nothing to return
+    if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
+    if (truncated) *truncated += 1;
+    return k.iters;
+  }
+  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+  return k.iters;
+}
+
+// Mechanical CG (Alg. 1) on P.b from x = 0 with the vector updates fused into the
+// operator passes: X-fwd forms p = r + beta p and <p, K p>, X-inv applies r -= alpha q,
+// x += alpha p and sums |r|^2.  Per iteration: 5 passes + 2 single-block finalisers.
+template <typename R>
+static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* truncated) {
+  const long long n = 9 * c.V;
+  const int slot = KS_MECH;
+  KScal* ks = c.ks + slot;
+  VArgs v = vbase(c, n);
+  v.in[0] = P.b;
+  v.out[0] = P.x;
+  v.out[1] = P.r;
+  v.out[2] = P.p;
+  launch_vec<KCgInit<R>>(v, c.st);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit);
+  const int* done = &ks->done;
+  const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  int chunk = 4;
+  while (true) {
+    for (int j = 0; j < chunk; ++j) {
+      PassArgs<R> a = pbase(c, P, done);
+      a.tw = P.twx;
+      a.rin = P.r;
+      a.rout = P.p;
+      a.aux[0] = P.state;
+      a.dscal = sc;
+      a.cout = P.S1;
+      int nb;
+      {
+        ProfScope ps(c, SITE_XF);
+        nb = (c.law == FG_SVK ? P.ox->xf_cgtangent_svk : P.ox->xf_cgtangent)(a, c.st);
+      }
+      fin<FAlpha>(c, slot, nb, done);
+      {
+        static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
+        yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
+      }
+      a = pbase(c, P, done);
+      a.tw = P.twx;
+      a.cin = P.S1;
+      a.rout = P.r;
+      a.rout2 = P.x;
+      a.aux[0] = P.p;
+      a.dscal = sc;
+      {
+        ProfScope ps(c, SITE_XI);
+        nb = P.ox->xi_cgupdate(a, c.st);
+      }
+      fin<FBetaCg>(c, slot, nb, done);
+    }
+    read_ks(c);
+    if (c.ks_host[slot].done) break;
+    if (chunk < 16) chunk *= 2;
+  }
+  const KScal& k = c.ks_host[slot];
+  if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
+  if (k.status & ST_INDEFINITE) {
     if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
     if (truncated) *truncated += 1;
     return k.iters;
@@ -720,20 +795,22 @@ static double residual_mech(fg_ctx& c, double den, R* state) {
   return sqrt(c.ks_host[KS_MISC].aux) / den;
 }
 
+// Alg. 1 from the current F.  Each Newton correction is damped by halving (at most 10
+// times) while F + lambda dF leaves the domain (det F <= 0 or J_c <= 0) or does not lower
+// err_res; the residual of the accepted iterate is the next iteration's residual.
 template <typename R>
 static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
+  double err = residual_mech<R>(c, den, P.state);
   for (int it = 0;; ++it) {
-    const double err = residual_mech<R>(c, den, P.state);
     s.err_mech = err;
     if (!(err == err)) fail(FG_ERR_NUMERIC, "mechanical residual is not finite");
     if (err <= c.o.tol_newton) return;
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
     to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
-    const int n = cg_solve<R>(c, P, 9 * c.V, KS_MECH, mixed_tol(c, c.o.tol_cg), c.o.max_cg,
-                              [&](const R* p, R* q, const int* done) { return op_mech(c, P, p, q, done); },
-                              &s.cg_truncated);
+    const int n = cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s.cg_truncated);
     s.cg_mech += n;
     s.newton_mech += 1;
+    const double* dF;
     if (is_mixed(c)) {
       // FP32 roundoff leaves traces of the correction in modes G never sees (the mean and
       // the null modes of the rotated scheme); project it in FP64 onto compatible
@@ -742,17 +819,36 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
       u.in[0] = P.x;
       u.out[0] = c.P;
       launch_vec<KWiden<R>>(u, c.st);
-      op_gres(c, c.pd, c.P, c.GP, nullptr);
-      VArgs v = vbase(c, 9 * c.V);
-      v.in[0] = c.GP;
-      v.out[0] = c.F;
-      launch_vec<KAddTo<double>>(v, c.st);
+      op_gres(c, c.pd, c.P, c.dF, nullptr);
+      dF = c.dF;
     } else {
-      VArgs v = vbase(c, 9 * c.V);
-      v.in[0] = P.x;
-      v.out[0] = c.F;
-      launch_vec<KAddTo<R>>(v, c.st);
+      dF = (const double*)P.x;
     }
+    dcopy(c.Fbk, c.F, 9 * c.V * sizeof(double), c.st);
+    double lam = 1.0;
+    bool ok = false;
+    for (int ls = 0; ls <= 10; ++ls, lam *= 0.5) {
+      VArgs v = vbase(c, 9 * c.V);  // F = F_bk + lam dF
+      v.in[0] = c.Fbk;
+      v.in[1] = dF;
+      v.out[0] = c.F;
+      v.s[0] = lam;
+      launch_vec<KAxpyTo>(v, c.st);
+      double e = 0.0;
+      try {
+        e = residual_mech<R>(c, den, P.state);
+      } catch (Fail& f) {
+        if (f.code != FG_ERR_DOMAIN) throw;
+        continue;
+      }
+      if (e < err) {
+        err = e;
+        ok = true;
+        break;
+      }
+      s.newton_damped += 1;
+    }
+    if (!ok) fail(FG_ERR_NOCONV, "mechanical Newton: no decrease of err_res along the correction");
   }
 }
 
@@ -773,7 +869,8 @@ static void history(fg_ctx& c) {
   v.in[7] = c.smax;
   v.out[0] = c.H;
   v.s[0] = c.o.gc / (2.0 * c.o.lc);
-  launch_vec<KHistory>(v, c.st);
+  if (c.law == FG_SVK) launch_vec<KHistory<LAW_SVK_>>(v, c.st);
+  else launch_vec<KHistory<LAW_NH_>>(v, c.st);
   fin<FScaleAux>(c, KS_HBAR, VEC_BLOCKS, nullptr, 1.0 / (double)c.V);
 }
 
@@ -863,7 +960,8 @@ static void chem_prep(fg_ctx& c, Prec<R>& P, double dt, const double* F) {
   v.s[0] = dt;
   v.s[1] = 1.0 / c.o.RT;
   v.s[2] = 1.0 / c.o.cmax;
-  launch_vec<KChemPrep<R>>(v, c.st);
+  if (c.law == FG_SVK) launch_vec<KChemPrep<R, LAW_SVK_>>(v, c.st);
+  else launch_vec<KChemPrep<R, LAW_NH_>>(v, c.st);
 }
 
 template <typename R>
@@ -1068,8 +1166,10 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (!fg_supported_size(g->nx) || !fg_supported_size(g->ny) || !fg_supported_size(g->nz))
     fail(FG_ERR_INVALID, "fg_setup: transform length not compiled in");
   for (int k = 0; k < nphases; ++k) {
-    if (phases[k].law != FG_NEOHOOKE)
-      fail(FG_ERR_INVALID, "fg_setup: only the compressible Neo-Hookean law runs on the GPU path");
+    if (phases[k].law != FG_NEOHOOKE && phases[k].law != FG_SVK)
+      fail(FG_ERR_INVALID, "fg_setup: unknown constitutive law");
+    if (phases[k].law != phases[0].law)
+      fail(FG_ERR_INVALID, "fg_setup: every phase must use the same constitutive law");
     if (!(phases[k].E > 0) || !(phases[k].nu > -1 && phases[k].nu < 0.5) || !(phases[k].D >= 0) ||
         !(phases[k].sigma_max > 0))
       fail(FG_ERR_INVALID, "fg_setup: bad phase constants");
@@ -1081,6 +1181,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
   fg_ctx* c = new fg_ctx();
   try {
+    c->law = phases[0].law;
     c->nx = g->nx;
     c->ny = g->ny;
     c->nz = g->nz;
@@ -1128,6 +1229,8 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     c->Ft = alloc_n<double>(*c, 9 * V);
     c->P = alloc_n<double>(*c, 9 * V);
     c->GP = alloc_n<double>(*c, 9 * V);
+    c->Fbk = alloc_n<double>(*c, 9 * V);
+    c->dF = alloc_n<double>(*c, 9 * V);
     c->ct = alloc_n<double>(*c, V);
     c->d = alloc_n<double>(*c, V);
     c->dt = alloc_n<double>(*c, V);
@@ -1155,6 +1258,23 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     dzero(c->flags, sizeof(int), c->st);
     c->ks_host = (KScal*)hpinned(KS_N * sizeof(KScal));
     c->flags_host = (int*)hpinned(sizeof(int));
+    {
+      // kx planes per Y-Z-Y chunk: a chunk of the 9-component S2 spectrum should take
+      // at most l2_fraction of the L2 cache
+      double l2 = 64.0 * 1024.0;  // host emulation: a small cache so that tests cover chunking
+#ifndef FG_EMU
+      l2 = 0.0;
+      int dev = 0, bytes = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&bytes, cudaDevAttrL2CacheSize, dev) == cudaSuccess) l2 = bytes;
+#endif
+      const double frac = o.l2_fraction > 0.0 ? o.l2_fraction : 0.4;
+      for (int k = 0; k < 2; ++k) {
+        const double slab = 9.0 * g->ny * g->nz * (k ? 16.0 : 8.0);
+        int ch = (l2 > 0.0 && frac < 1.0) ? (int)(frac * l2 / slab) : c->hx;
+        c->kx_chunk[k] = ch < 1 ? 1 : (ch > c->hx ? c->hx : ch);
+      }
+    }
     if (o.precision == FG_MIXED) {
       setup_prec<double>(*c, c->pd, 1);
       setup_prec<float>(*c, c->pf, 9);
@@ -1289,11 +1409,11 @@ int fg_profile(fg_ctx* c, int site, int enable) {
   FG_API_END
 }
 
-int fg_profile_read(fg_ctx* c, int site, int* launches, double* total_ms) {
+int fg_profile_read(fg_ctx* c, int site, int* launches, double* total_ms, double* volumes) {
   FG_API_BEGIN
   if (!c || site < 0 || site >= SITE_N - 1 || !launches || !total_ms)
     fail(FG_ERR_INVALID, "fg_profile_read: bad argument");
-  double t = 0.0;
+  double t = 0.0, vol = 0.0;
   int n = 0;
 #ifndef FG_EMU
   dsync(c->st);
@@ -1305,14 +1425,16 @@ int fg_profile_read(fg_ctx* c, int site, int* launches, double* total_ms) {
   std::vector<float> srt(ms);
   std::sort(srt.begin(), srt.end());
   const float med = srt.empty() ? 0.f : srt[srt.size() / 2];
-  for (float m : ms)
-    if (m >= 0.2f * med) {
-      t += m;
+  for (size_t k = 0; k < ms.size(); ++k)
+    if (ms[k] >= 0.2f * med) {
+      t += ms[k];
+      vol += c->prof_frac[site][k];
       ++n;
     }
 #endif
   *launches = n;
   *total_ms = t;
+  if (volumes) *volumes = vol;
   FG_API_END
 }
 

@@ -53,9 +53,10 @@ def test_invalid_arguments(emu):
     with pytest.raises(B.FgError) as e:
         B.Solver(w.shape, w.h, w.phases, bad, w.cdot_B, lib=emu)
     assert e.value.code == -1
-    svk = S.default_phases(law=S.LAW_SVK)
-    with pytest.raises(B.FgError) as e:
-        B.Solver(w.shape, w.h, svk, w.phase_id, w.cdot_B, lib=emu)
+    mixed_laws = S.default_phases()
+    mixed_laws[1].law = S.LAW_SVK
+    with pytest.raises(B.FgError) as e:  # one law per context
+        B.Solver(w.shape, w.h, mixed_laws, w.phase_id, w.cdot_B, lib=emu)
     assert e.value.code == -1
     with pytest.raises(B.FgError) as e:  # initial concentration outside (0, 1)
         B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=np.full(w.shape, 1.2), lib=emu)

@@ -22,9 +22,10 @@ def emu():
 
 @pytest.mark.parametrize("shape", [(8, 12, 16), (1, 16, 24), (12, 8, 8)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_emulated_operators_match_oracle(emu, shape, prec):
+@pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
+def test_emulated_operators_match_oracle(emu, shape, prec, law):
     pid = S.random_phase_map(shape, 1)
-    phases = S.default_phases()
+    phases = S.default_phases(law=law)
     phases[1].E = 2e9
     sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu,
                    precision=B.FG_MIXED if prec else B.FG_FP64)
@@ -48,6 +49,22 @@ def test_emulated_operators_match_oracle(emu, shape, prec):
     sol.apply(B.OP_CHEM, x1, y1, prec, dt=0.7)
     ref = O.chem_apply(x1.astype(float), 1 / (c * (1 - c)), O.chem_conductivity(F, c, d, prm), 0.7, prm)
     assert rel_err(y1, ref) < tol
+    assert rel_err(sol.get(B.FIELD_P), O.stress(F, c, d, prm)) < 1e-13
+    sol.close()
+
+
+@pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
+def test_emulated_step_law(emu, law):
+    """One coupled step of a small disc with each law against the oracle."""
+    w = S.disc2d(n=16, radius=6.0, band=3, nsteps=10)
+    w.phases = S.default_phases(law=law)
+    prm = oracle_params(w)
+    ref = O.CoupledState(prm, w.c_init, w.cdot_B)
+    ref.step(w.dt, np.eye(3))
+    sol = B.from_workload(w, lib=emu)
+    sol.step(w.dt)
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-10
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
     sol.close()
 
 

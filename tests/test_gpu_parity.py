@@ -26,11 +26,11 @@ def lib():
     return B.load_library()
 
 
-def _solver(lib, shape, precision, seed=1):
+def _solver(lib, shape, precision, seed=1, law=S.LAW_NEOHOOKE, **kw):
     pid = S.random_phase_map(shape, seed)
-    phases = S.default_phases()
+    phases = S.default_phases(law=law)
     phases[1].E = 2e9  # moderate contrast keeps the operator well scaled
-    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=lib, precision=precision)
+    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=lib, precision=precision, **kw)
     F, c, d = S.random_state(shape, seed=seed + 1)
     Hh = np.random.default_rng(seed + 2).uniform(0, 1e6, shape)
     for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d), (B.FIELD_H, Hh)):
@@ -39,10 +39,17 @@ def _solver(lib, shape, precision, seed=1):
     return sol, prm, F.reshape((3, 3) + shape), c, d, Hh
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+CASES = [(s, S.LAW_NEOHOOKE, 0.0) for s in SHAPES] + [
+    ((16, 32, 64), S.LAW_SVK, 0.0),        # the paper's Saint-Venant-Kirchhoff law
+    ((32, 32, 32), S.LAW_NEOHOOKE, 1e-5),  # Y-Z-Y passes on many small chunks of kx planes
+]
+
+
+@pytest.mark.parametrize("shape,law,l2f", CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_operator_parity(lib, shape, prec):
-    sol, prm, F, c, d, Hh = _solver(lib, shape, B.FG_MIXED if prec else B.FG_FP64)
+def test_operator_parity(lib, shape, law, l2f, prec):
+    sol, prm, F, c, d, Hh = _solver(lib, shape, B.FG_MIXED if prec else B.FG_FP64, law=law,
+                                    l2_fraction=l2f)
     tdt = torch.float32 if prec else torch.float64
     tol = TOL_APPLY_FP32 if prec else TOL_APPLY_FP64
     x9 = torch.from_numpy(S.random_tensor_field(shape, 3)).to("cuda", tdt)
@@ -120,6 +127,19 @@ def test_coupled_steps_mixed_disc(lib):
     assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-7
     assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-7
     assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < 1e-6
+    sol.close()
+
+
+def test_coupled_step_svk_disc(lib):
+    """The paper's Saint-Venant-Kirchhoff law: 3 FP64 steps of the disc against the oracle."""
+    w = S.disc2d()
+    w.phases = S.default_phases(law=S.LAW_SVK)
+    prm, ref = _oracle_run(w, 3)
+    sol = B.from_workload(w, lib=lib)
+    for _ in range(3):
+        sol.step(w.dt)
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < TOL_STEP_FP64
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < TOL_STEP_FP64
     sol.close()
 
 
