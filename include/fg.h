@@ -186,6 +186,37 @@ int fg_profile_read(fg_ctx* ctx, int site, int* launches, double* total_ms, doub
 /* Releases the context and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);
 
+/*
+ * fg_mech_apply_noalloc -- the FP32 mechanical operator application of fg_apply
+ * (FG_OP_MECH, prec 1), for callers that cannot allocate GPU memory.  The paper has no
+ * counterpart: this is a deployment variant.  It suits code that may only hand over
+ * pointers, e.g. a plug-in running inside a host framework that owns all device memory
+ * through its own pool, or a service whose device-memory budget is fixed after start-up,
+ * where a library that calls cudaMalloc would break the pool or the budget.
+ *
+ * Inputs are the caller's device arrays: F (9 V doubles, component (i, j) at
+ * (3 i + j) V), c, d and the per-voxel Lame constants lam, mu, swelling Omega and
+ * stress-free c0 (V doubles each); x (9 V floats) in, y (9 V floats) out, y = G : F^-1[
+ * F[K(F, c, d) : x]].  dot (host, may be NULL) receives <x, y>.  Work is enqueued on
+ * `stream` (cudaStream_t, NULL: legacy default) and the call returns when it is done.
+ *
+ * All scratch (spectra, packed tangent, tables, partial sums: about 32 MB) is one
+ * static device array that every GPU loading the library holds until the process exits.
+ * Limits: nx even, every edge <= 64 (so V <= 262,144) and a compiled transform length;
+ * larger grids return FG_ERR_INVALID without touching the GPU.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make the first call on a device before any stream capture.  Every call
+ * reuses the same array and leaves the last call's contents in it; calls that overlap on
+ * the GPU (other streams, other host threads) race on it.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.  Errors: FG_ERR_INVALID, FG_ERR_DOMAIN
+ * (det F <= 0 or J_c <= 0), FG_ERR_CUDA; message in fg_last_error().
+ */
+int fg_mech_apply_noalloc(int nx, int ny, int nz, double hx, double hy, double hz,
+                          const double* F, const double* c, const double* d,
+                          const double* lam, const double* mu, const double* Omega,
+                          const double* c0, const float* x, float* y, double* dot,
+                          void* stream);
+
 /* Number of CUDA kernels the library has launched since it was loaded (all contexts). */
 long long fg_kernel_launches(void);
 

@@ -63,7 +63,8 @@ class Stats(C.Structure):
 
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
-           "fg_profile_read", "fg_kernel_launches", "fg_destroy", "fg_last_error"]
+           "fg_profile_read", "fg_mech_apply_noalloc", "fg_kernel_launches", "fg_destroy",
+           "fg_last_error"]
 
 _libs = {}
 
@@ -91,6 +92,8 @@ def load_library(path=LIB_PATH):
     lib.fg_time_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
     lib.fg_profile.argtypes = [C.c_void_p, C.c_int, C.c_int]
     lib.fg_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), dp, dp]
+    lib.fg_mech_apply_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                          C.c_double] + [C.c_void_p] * 9 + [dp, C.c_void_p]
     lib.fg_kernel_launches.restype = C.c_longlong
     lib.fg_destroy.argtypes = [C.c_void_p]
     lib.fg_destroy.restype = None

@@ -40,6 +40,7 @@ const SizeOps<R>* size_ops(int N) {
 // ------------------------------------------------------------------ errors
 
 static thread_local std::string g_err;
+void set_last_error(const std::string& msg) { g_err = msg; }
 
 struct Fail {
   int code;
