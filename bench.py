@@ -44,7 +44,7 @@ SITE_NAMES = {0: "mech X-fwd: p = r + beta p, tangent, <p,Kp> (pass_kernel<XFwd<
               1: "mech Y-fwd (pass_kernel<YPass<float,N,false>>)",
               2: "mech Z + projection (pass_kernel<ZPass<float,N,ZProject>>)",
               3: "mech Y-inv (pass_kernel<YPass<float,N,true>>)",
-              4: "mech X-inv: r -= alpha q, x += alpha p, |r|^2 (pass_kernel<XInv<float,N,ECgUpdate>>)"}
+              4: "mech X-inv: r -= alpha q, x += alpha p, |r|^2 (pass_kernel<XInv<float,N,ECgUpdate1,true>> per component, or ECgUpdate)"}
 
 
 def _args():
@@ -58,6 +58,8 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--batch", type=int, default=0,
+                   help="batched RVEs: N particles of seeded sizes {48,64,80,96}^3 (0: off)")
     return p.parse_args()
 
 
@@ -197,6 +199,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         return reference_arm(a, rank, world)
+    if a.batch:
+        return batch_mode(a)
     import numpy as np
     import torch
     from paper_2411_16583_gb300 import binding as B
@@ -209,6 +213,7 @@ def main():
     stream = torch.cuda.current_stream()
     sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
     V = w.nvox
+    tuned_ms = sol.autotune()
     for _ in range(a.warmup):
         sol.step(w.dt)
 
@@ -320,6 +325,7 @@ def main():
         "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),
                    "mech_fp32_ms": mech32_ms},
         "step_stats": stats[-1],
+        "autotuned_apply_ms": tuned_ms,
         "clocks": clk.summary(),
     }
     line.update(out)
@@ -329,6 +335,50 @@ def main():
         line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": _cores(),
                                 "kind": "oracle", "sample": desc}
     print(json.dumps(line))
+
+
+def batch_mode(a):
+    """Many independent particle RVEs of uneven size: one batched coupled step (members
+    on their own streams, driven concurrently) against the same members stepped one by
+    one.  Reports aggregate voxel-steps/s of both."""
+    import torch
+    from paper_2411_16583_gb300 import binding as B, synth as S
+    ws = S.sphere_batch(count=a.batch, nsteps=20, seed=0)
+    V = sum(w.nvox for w in ws)
+    mk = lambda: [B.from_workload(w, precision=B.FG_MIXED) for w in ws]
+    seq = mk()
+    for s_, w in zip(seq, ws):
+        s_.autotune()
+    for _ in range(a.warmup):
+        for s_, w in zip(seq, ws):
+            s_.step(w.dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        for s_, w in zip(seq, ws):
+            s_.step(w.dt)
+    torch.cuda.synchronize()
+    t_seq = (time.perf_counter() - t0) / a.steps
+    for s_ in seq:
+        s_.close()
+    mem = mk()
+    for s_ in mem:
+        s_.autotune()
+    batch = B.Batch(mem)
+    for _ in range(a.warmup):
+        batch.step(1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        st = batch.step(1.0)
+    torch.cuda.synchronize()
+    t_b = (time.perf_counter() - t0) / a.steps
+    batch.close()
+    print(json.dumps({"mode": "batch", "rves": len(ws), "voxels": V,
+                      "sizes": sorted({w.shape[0] for w in ws}),
+                      "batched_voxel_steps_per_s": V / t_b, "sequential_voxel_steps_per_s": V / t_seq,
+                      "batched_ms_per_step": t_b * 1e3, "sequential_ms_per_step": t_seq * 1e3,
+                      "speedup": t_seq / t_b, "cg_mech_total": sum(x["cg_mech"] for x in st)}))
 
 
 def reference_arm(a, rank, world):

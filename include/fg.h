@@ -91,13 +91,14 @@ typedef struct {
   int max_newton, max_cg, max_chem_newton, max_stag;
   void* cuda_stream;  /* cudaStream_t, NULL for the legacy default stream */
   double l2_fraction; /* share of L2 one chunk of kx planes of the spectrum may take
-                         between the Y and Z passes (0: 0.4; >= 1: no chunking) */
+                         between the Y and Z passes (0 or >= 1: no chunking) */
 } fg_opts;
 
 typedef struct {
   int newton_chem, newton_mech, cg_chem, cg_mech, cg_pff, stag;
   int inner_refine;   /* FP64 residual refinements of mixed-mode phase-field solves */
-  int cg_truncated;   /* mechanical CG solves stopped at non-positive curvature */
+  int cg_truncated;   /* Krylov solves stopped early: mechanical CG at non-positive
+                         curvature, or an FP32 inner solve of the mixed mode at max_cg */
   int newton_damped;  /* halvings of mechanical Newton corrections */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
@@ -170,8 +171,29 @@ int fg_set_field(fg_ctx* ctx, int field, const void* src, int on_device);
  * reports the mean time per application in ms (no synchronisation inside). */
 int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
 
+/* Mechanical equilibrium alone (Alg. 1) at the stored c and d: the stored F is shifted by
+ * Fbar - (previous Fbar) and brought to err_res <= tol_newton in place. */
+int fg_solve_mech(fg_ctx* ctx, const double Fbar[9], fg_stats* st);
+
+/*
+ * Hand-written adjoint of that equilibrium at the stored (converged) F, c, d.  For a loss
+ * L(F) with dL/dF = W (9 V doubles, host or device), solves the transposed tangent system
+ * G K G lambda = G W with the same fused mechanical CG (the tangent is self-adjoint) and
+ * writes the gradient of L with respect to the per-voxel log stiffness,
+ * grad_logE[v] = -lambda(v) : P(v) (V doubles, host or device).  iters (may be NULL)
+ * receives the adjoint CG iterations.
+ */
+int fg_adjoint_mech(fg_ctx* ctx, const double* W, double* grad_logE, int* iters);
+
+/* Autotuner: times the run-time selectable schedule of the mechanical operator on this
+ * context's grid (how many kx planes the Y-Z-Y passes take per L2-sized chunk, and a
+ * one-component-per-block or nine-component X-inv CG update) and keeps the fastest.
+ * ms_per_iteration (may be NULL) receives the best operator time.  Allocates two
+ * temporary 9 V vectors. */
+int fg_autotune(fg_ctx* ctx, double* ms_per_iteration);
+
 /* Launch-site profiling.  While a site is enabled, every launch at that site is
- * bracketed by two CUDA events on the context stream (at most 4096 launches are recorded
+ * bracketed by two CUDA events on the context stream (at most 32768 launches are recorded
  * after each enable).  Sites: 0-4 the five passes of the mechanical operator (X-fwd with
  * the tangent, Y-fwd, Z with the projection, Y-inv, X-inv with the dot product), 5 the
  * Krylov update of the mechanical CG (unfused path).  fg_profile_read synchronises the stream and returns
@@ -182,6 +204,20 @@ int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
  * already converged) are left out of both. */
 int fg_profile(fg_ctx* ctx, int site, int enable);
 int fg_profile_read(fg_ctx* ctx, int site, int* launches, double* total_ms, double* volumes);
+
+/*
+ * Batches of independent RVEs (many particles of uneven grid sizes).  fg_batch_setup
+ * gives every member context its own non-blocking CUDA stream (restored by
+ * fg_batch_destroy; members must outlive the batch and not be stepped on their own
+ * meanwhile).  fg_batch_step advances every member by one time step of Alg. 4 with the
+ * same dt and Fbar; a pool of host threads drives the members concurrently, so their
+ * kernels overlap on the GPU.  st (may be NULL) receives n fg_stats.  Returns FG_OK or
+ * the first member's error (every member is attempted; a failed member keeps its state).
+ */
+typedef struct fg_batch fg_batch;
+int fg_batch_setup(fg_batch** out, int n, fg_ctx* const* members);
+int fg_batch_step(fg_batch* batch, double dt, const double Fbar[9], fg_stats* st);
+void fg_batch_destroy(fg_batch* batch);
 
 /* Releases the context and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);

@@ -484,6 +484,15 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
         F, GP, err = Fn, GPn, errn
 
 
+def mech_adjoint(F, c, d, prm, W, tol_cg, max_cg):
+    """Gradient with respect to the per-voxel log stiffness of a loss L(F) with dL/dF = W,
+    at an equilibrium G*P(F) = 0 (Eq. mechanicalsolve): with lambda solving the transposed
+    tangent system G K G lambda = G W (K is symmetric) and dP/dlogE = P at fixed F,
+    dL/dlogE(v) = -lambda(v) : P(v)."""
+    lam, _ = cg(lambda x: mech_apply(F, c, d, prm, x), apply_G(W, prm.h), tol_cg, max_cg)
+    return -np.sum(lam * stress(F, c, d, prm), axis=(0, 1))
+
+
 # --------------------------------------------------------------------------------------
 # Phase field  (Eqs. PFFrearranged, PFFA, PFFb, PFFprecond; Alg. 2)
 # --------------------------------------------------------------------------------------

@@ -63,8 +63,9 @@ class Stats(C.Structure):
 
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
-           "fg_profile_read", "fg_mech_apply_noalloc", "fg_kernel_launches", "fg_destroy",
-           "fg_last_error"]
+           "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
+           "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
+           "fg_kernel_launches", "fg_destroy", "fg_last_error"]
 
 _libs = {}
 
@@ -94,6 +95,13 @@ def load_library(path=LIB_PATH):
     lib.fg_profile_read.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), dp, dp]
     lib.fg_mech_apply_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double] + [C.c_void_p] * 9 + [dp, C.c_void_p]
+    lib.fg_autotune.argtypes = [C.c_void_p, dp]
+    lib.fg_solve_mech.argtypes = [C.c_void_p, dp, C.POINTER(Stats)]
+    lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.fg_batch_setup.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
+    lib.fg_batch_step.argtypes = [C.c_void_p, C.c_double, dp, C.POINTER(Stats)]
+    lib.fg_batch_destroy.argtypes = [C.c_void_p]
+    lib.fg_batch_destroy.restype = None
     lib.fg_kernel_launches.restype = C.c_longlong
     lib.fg_destroy.argtypes = [C.c_void_p]
     lib.fg_destroy.restype = None
@@ -211,10 +219,64 @@ class Solver:
         self._check(self.lib.fg_profile_read(self.ctx, site, C.byref(n), C.byref(ms), C.byref(vol)))
         return n.value, ms.value, vol.value
 
+    def solve_mech(self, Fbar=None, check=True):
+        Fb = _f64(np.eye(3) if Fbar is None else Fbar).ravel()
+        st = Stats()
+        rc = self.lib.fg_solve_mech(self.ctx, Fb.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st))
+        if check:
+            self._check(rc)
+        return st.as_dict()
+
+    def adjoint_mech(self, W):
+        """dL/dlogE for a loss with dL/dF = W (host array (3, 3, ...) or device tensor)."""
+        Wh = W if hasattr(W, "data_ptr") else _f64(W).ravel()
+        g = np.empty(self.shape)
+        it = C.c_int()
+        self._check(self.lib.fg_adjoint_mech(self.ctx, _ptr(Wh), _ptr(g), C.byref(it)))
+        return g, it.value
+
+    def autotune(self):
+        ms = C.c_double()
+        self._check(self.lib.fg_autotune(self.ctx, C.byref(ms)))
+        return ms.value
+
     def time_apply(self, op, prec, n):
         ms = C.c_double()
         self._check(self.lib.fg_time_apply(self.ctx, op, prec, n, C.byref(ms)))
         return ms.value
+
+
+class Batch:
+    """Independent RVEs stepped together (fg_batch_*); members are ``Solver`` objects."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.lib = self.solvers[0].lib
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        h = C.c_void_p()
+        rc = self.lib.fg_batch_setup(C.byref(h), len(self.solvers), arr)
+        if rc != FG_OK:
+            raise FgError(rc, self.lib.fg_last_error().decode())
+        self.h = h
+
+    def step(self, dt, Fbar=None, check=True):
+        Fb = _f64(np.eye(3) if Fbar is None else Fbar).ravel()
+        st = (Stats * len(self.solvers))()
+        rc = self.lib.fg_batch_step(self.h, dt, Fb.ctypes.data_as(C.POINTER(C.c_double)), st)
+        if check and rc != FG_OK:
+            raise FgError(rc, self.lib.fg_last_error().decode())
+        return [s.as_dict() for s in st]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, precision=FG_FP64, lib=None, stream=None, **opt_kw):

@@ -1,6 +1,7 @@
 // Launch of the FFT pass kernels, and the per-size table of launchers that the runtime
 // dispatches through (one table per transform length N and precision).
 #pragma once
+#include <atomic>
 #include <vector>
 #include <cstring>
 #include "fg_ops.cuh"
@@ -18,7 +19,7 @@ __global__ void __launch_bounds__(K::NT) pass_kernel(A a) {
 #endif
 
 // number of kernel launches issued by the library (all kernels, all contexts)
-long long& launch_counter();
+std::atomic<long long>& launch_counter();
 
 // Launches kernel K with arguments A on `grid` blocks of K::NT threads.  Returns the
 // number of blocks launched (the number of partial sums a reducing kernel writes).
@@ -37,11 +38,11 @@ int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
         K::body(a, Dim3{x, y, z}, grid, smem.data(), Ls.data());
       }
 #else
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [sm]() {  // once per kernel, thread-safe
     cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   pass_kernel<K, A><<<dim3(grid.x, grid.y, grid.z), K::NT, sm, st>>>(a);
 #endif
   return grid.x * grid.y * grid.z;
@@ -57,7 +58,7 @@ struct SizeOps {
   PassFn<R> xf_tangent, xf_cgtangent, xf_tangent_svk, xf_cgtangent_svk, xf_copy1, xf_copy3,
       xf_copy9;
   PassFn<R> xi_store1, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
-      xi_chemrhs, xi_cgupdate;
+      xi_chemrhs, xi_cgupdate, xi_cgupdate_pc;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
 };
@@ -65,6 +66,11 @@ struct SizeOps {
 template <class K, typename R>
 int run_x(const PassArgs<R>& a, cudaStream_t st) {
   return launch_pass<K>(a, Dim3{K::grid_x(a.ny, a.nz), 1, 1}, st);
+}
+// one block row per component (9 components)
+template <class K, typename R>
+int run_x9(const PassArgs<R>& a, cudaStream_t st) {
+  return launch_pass<K>(a, Dim3{K::grid_x(a.ny, a.nz), 9, 1}, st);
 }
 // Y and Z passes cover rows [row_lo, row_hi) when row_hi > 0 (a range of kx planes)
 template <class K, typename R>
@@ -88,6 +94,7 @@ SizeOps<R> make_size_ops() {
     s.xf_tangent_svk = run_x<XFwd<R, N, PTangentSVK<R>>, R>;
     s.xf_cgtangent_svk = run_x<XFwd<R, N, PCgTangentSVK<R>>, R>;
     s.xi_cgupdate = run_x<XInv<R, N, ECgUpdate<R>>, R>;
+    s.xi_cgupdate_pc = run_x9<XInv<R, N, ECgUpdate1<R>, true>, R>;
     s.xf_copy1 = run_x<XFwd<R, N, PCopy<R, 1>>, R>;
     s.xf_copy3 = run_x<XFwd<R, N, PCopy<R, 3>>, R>;
     s.xf_copy9 = run_x<XFwd<R, N, PCopy<R, 9>>, R>;

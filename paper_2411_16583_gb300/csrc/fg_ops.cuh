@@ -165,13 +165,15 @@ struct PCgTangentSVK {
   static constexpr bool RED = true;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
     const R beta = (R)a.dscal[1];
+    const R* __restrict__ r = a.rin;
+    R* __restrict__ pp = a.rout;
+    const long long V = a.V;
     R p[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      p[c] = a.rin[c * a.V + v] + beta * a.rout[c * a.V + v];
-      a.rout[c * a.V + v] = p[c];
-    }
-    tangent_svk(a.aux[0], a.V, v, p, out);
+    for (int c = 0; c < 9; ++c) p[c] = r[c * V + v] + beta * pp[c * V + v];
+    tangent_svk(a.aux[0], V, v, p, out);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
 #pragma unroll
     for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
   }
@@ -203,22 +205,45 @@ struct PCgTangentNH {
   static constexpr bool RED = true;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
     const R beta = (R)a.dscal[1];
+    const R* __restrict__ r = a.rin;
+    const R* __restrict__ st = a.aux[0];
+    R* __restrict__ pp = a.rout;
+    const long long V = a.V;
+    // every load before the first store (r, p and the state never alias)
     R p[9], B[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      p[c] = a.rin[c * a.V + v] + beta * a.rout[c * a.V + v];
-      a.rout[c * a.V + v] = p[c];
-    }
-    const R* st = a.aux[0];
+    for (int c = 0; c < 9; ++c) p[c] = r[c * V + v] + beta * pp[c * V + v];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) B[c] = st[c * a.V + v];
-    tangent_nh(B, st[9 * a.V + v], st[10 * a.V + v], st[11 * a.V + v], p, out);
+    for (int c = 0; c < 9; ++c) B[c] = st[c * V + v];
+    const R s1 = st[9 * V + v], s2 = st[10 * V + v], s3 = st[11 * V + v];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
+    tangent_nh(B, s1, s2, s3, p, out);
 #pragma unroll
     for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
   }
 };
 
 // ================================================================== X-inv epilogues
+
+// One component of the fused CG update (pointers already shifted to the component):
+// r -= alpha q, x += alpha p; accumulates r^2.  rout = r, rout2 = x, aux0 = p.
+template <typename R>
+struct ECgUpdate1 {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+    const R al = (R)a.dscal[0];
+    R* __restrict__ r = a.rout;
+    R* __restrict__ x = a.rout2;
+    const R* __restrict__ p = a.aux[0];
+    const R r0 = r[v], x0 = x[v], p0 = p[v];  // loads before stores
+    const R rn = r0 - al * val[0];
+    r[v] = rn;
+    x[v] = x0 + al * p0;
+    acc += (double)rn * (double)rn;
+  }
+};
 
 // Conjugate-gradient update fused with the inverse transform (mechanical CG): with
 // q = G K p arriving as `val`, r -= alpha q and x += alpha p; accumulates <r, r>.

@@ -177,7 +177,10 @@ struct XFwd {
 
 // ------------------------------------------------------------------ X-inv
 
-template <typename R, int N, class Op>
+// PERCOMP: one component per block (component = blockIdx.y), for epilogues that act on
+// each component separately; the 1-component tile is 8x taller, so the transposed reads
+// of the spectrum are runs of 64 rows.
+template <typename R, int N, class Op, bool PERCOMP = false>
 struct XInv {
   using C = cplx<R>;
   static constexpr int CI = Op::CIN;
@@ -195,8 +198,16 @@ struct XInv {
   static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
 
   template <class Loc>
-  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
-    if (a.done && *a.done) return;
+  FG_DEV static void body(const PassArgs<R>& a0, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a0.done && *a0.done) return;
+    PassArgs<R> a = a0;
+    if constexpr (PERCOMP) {  // component bid.y: shift every per-component pointer
+      const int cc = bid.y;
+      a.cin += cc * a.VH;
+      a.rout += cc * a.V;
+      if (a.rout2) a.rout2 += cc * a.V;
+      if (a.aux[0]) a.aux[0] += cc * a.V;
+    }
     C* tile = (C*)smem;
     C* tw = tile + NROWS * PITCH;
     double* red = (double*)(tw + N);

@@ -448,6 +448,20 @@ struct KAddTo {
   }
 };
 
+// out0 (FP64) = -sum_c in0[c] (R) * in1[c] (FP64), c < 9: minus the contraction of the
+// adjoint field with the stress (the gradient of a loss with respect to log E)
+template <typename R>
+struct KAdjGradE {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      s += (double)((const R*)a.in[0])[c * a.V + v] * ((const double*)a.in[1])[c * a.V + v];
+    ((double*)a.out[0])[v] = -s;
+  }
+};
+
 // out0 (FP64) = in0 + s0 * in1 (FP64)
 struct KAxpyTo {
   static constexpr bool RED = false;

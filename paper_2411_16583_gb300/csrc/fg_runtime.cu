@@ -9,6 +9,8 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "fg_pointwise.cuh"
@@ -23,8 +25,8 @@ static std::map<int, SizeOps<R>>& registry() {
   static std::map<int, SizeOps<R>> m;
   return m;
 }
-long long& launch_counter() {
-  static long long n = 0;
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> n{0};
   return n;
 }
 
@@ -126,6 +128,7 @@ struct Prec {
 }  // namespace fg
 
 struct fg_ctx {
+  int device = 0;  // CUDA device the context lives on
   int nx = 0, ny = 0, nz = 0, hx = 0;
   int law = FG_NEOHOOKE;
   long long V = 0, VH = 0;
@@ -157,6 +160,7 @@ struct fg_ctx {
   std::vector<double> prof_frac[8];  // share of the full volume each recorded launch covers
   int prof_used[8] = {0};
   int kx_chunk[2] = {1, 1};          // kx planes per Y-Z-Y chunk (FP32, FP64)
+  int xi_percomp = 1;                // fused CG update: one component per block
   int last_inner_refine = 0;
 };
 
@@ -265,7 +269,7 @@ static VArgs vbase(fg_ctx& c, long long n) {
 // ------------------------------------------------------------------ launch-site profiling
 
 enum { SITE_XF = 0, SITE_YF = 1, SITE_Z = 2, SITE_YI = 3, SITE_XI = 4, SITE_CGXR = 5, SITE_N = 8 };
-static constexpr int PROF_PAIRS = 4096;
+static constexpr int PROF_PAIRS = 32768;
 
 struct ProfScope {
   fg_ctx& c;
@@ -624,7 +628,12 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
     if (truncated) *truncated += 1;
     return k.iters;
   }
-  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+  if (k.rr > k.tol2 && k.iters >= maxit) {
+    // an FP32 inner solve of the mixed mode is an inexact Newton step: its iterate is kept
+    // and the FP64 outer residual decides; in FP64 mode the cap is an error
+    if (!is_mixed(c)) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+    if (truncated) *truncated += 1;
+  }
   return k.iters;
 }
 
@@ -675,7 +684,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
       a.dscal = sc;
       {
         ProfScope ps(c, SITE_XI);
-        nb = P.ox->xi_cgupdate(a, c.st);
+        nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
       }
       fin<FBetaCg>(c, slot, nb, done);
     }
@@ -690,7 +699,10 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
     if (truncated) *truncated += 1;
     return k.iters;
   }
-  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+  if (k.rr > k.tol2 && k.iters >= maxit) {
+    if (!is_mixed(c)) fail(FG_ERR_NOCONV, "mechanical CG hit max_cg");
+    if (truncated) *truncated += 1;  // mixed mode: inexact Newton step, see cg_solve
+  }
   return k.iters;
 }
 
@@ -759,7 +771,7 @@ static int pcg_pff(fg_ctx& c, Prec<R>& P, const R* H, double tol, int maxit) {
   const KScal& k = c.ks_host[slot];
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "phase-field solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) fail(FG_ERR_NUMERIC, "phase-field operator not positive definite");
-  if (k.rr > k.tol2 && k.iters >= maxit) fail(FG_ERR_NOCONV, "phase-field PCG hit max_cg");
+  if (k.rr > k.tol2 && k.iters >= maxit && !is_mixed(c)) fail(FG_ERR_NOCONV, "phase-field PCG hit max_cg");
   return k.iters;
 }
 
@@ -980,7 +992,8 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
     op_chem_rhs(c, b64, dt);
     if (is_mixed(c)) to_prec<R>(c, b64, P.b, c.V, 1.0);
     const int n = cg_solve<R>(c, P, c.V, KS_CHEM, mixed_tol(c, c.o.tol_chem_cg), c.o.max_cg,
-                              [&](const R* p, R* q, const int* done) { return op_chem(c, P, p, q, dt, done); });
+                              [&](const R* p, R* q, const int* done) { return op_chem(c, P, p, q, dt, done); },
+                              &s.cg_truncated);
     s.cg_chem += n;
     s.newton_chem += 1;
     VArgs v = vbase(c, c.V);
@@ -1141,7 +1154,7 @@ int fg_supported_size(int n) {
 
 const char* fg_last_error(void) { return g_err.c_str(); }
 
-long long fg_kernel_launches(void) { return launch_counter(); }
+long long fg_kernel_launches(void) { return launch_counter().load(); }
 
 void fg_destroy(fg_ctx* ctx) {
   if (!ctx) return;
@@ -1183,6 +1196,9 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;
+#ifndef FG_EMU
+    cudaGetDevice(&c->device);
+#endif
     c->nx = g->nx;
     c->ny = g->ny;
     c->nz = g->nz;
@@ -1251,7 +1267,9 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
       dzero(c->Ht, V * sizeof(double), c->st);
       dcopy(c->Ft, c->F, 9 * V * sizeof(double), c->st);
     }
-    c->npartials = (long long)g->ny * g->nz + VEC_BLOCKS + 64;
+    // one partial per block of the largest reducing launch (per-component X passes: 9
+    // block rows of at least 2 rows each)
+    c->npartials = 9LL * g->ny * g->nz + VEC_BLOCKS + 64;
     c->partials = alloc_n<double>(*c, c->npartials);
     c->ks = alloc_n<KScal>(*c, KS_N);
     dzero(c->ks, KS_N * sizeof(KScal), c->st);
@@ -1269,7 +1287,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
       cudaGetDevice(&dev);
       if (cudaDeviceGetAttribute(&bytes, cudaDevAttrL2CacheSize, dev) == cudaSuccess) l2 = bytes;
 #endif
-      const double frac = o.l2_fraction > 0.0 ? o.l2_fraction : 0.4;
+      const double frac = o.l2_fraction > 0.0 ? o.l2_fraction : 1.0;
       for (int k = 0; k < 2; ++k) {
         const double slab = 9.0 * g->ny * g->nz * (k ? 16.0 : 8.0);
         int ch = (l2 > 0.0 && frac < 1.0) ? (int)(frac * l2 / slab) : c->hx;
@@ -1436,6 +1454,247 @@ int fg_profile_read(fg_ctx* c, int site, int* launches, double* total_ms, double
   *launches = n;
   *total_ms = t;
   if (volumes) *volumes = vol;
+  FG_API_END
+}
+
+}  // extern "C"
+
+struct fg_batch {
+  std::vector<fg_ctx*> members;
+  std::vector<cudaStream_t> own;    // streams created for the members
+  std::vector<cudaStream_t> saved;  // the members' streams before the batch
+  int threads = 1;
+};
+
+extern "C" {
+
+int fg_batch_setup(fg_batch** out, int n, fg_ctx* const* members) {
+  FG_API_BEGIN
+  if (!out || n <= 0 || !members) fail(FG_ERR_INVALID, "fg_batch_setup: bad argument");
+  for (int i = 0; i < n; ++i)
+    if (!members[i]) fail(FG_ERR_INVALID, "fg_batch_setup: null member");
+  fg_batch* b = new fg_batch();
+  b->members.assign(members, members + n);
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t s = nullptr;
+#ifndef FG_EMU
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(members[i]->device);
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaSetDevice(prev);
+      for (size_t k = 0; k < b->own.size(); ++k) {
+        b->members[k]->st = b->saved[k];
+        cudaStreamDestroy(b->own[k]);
+      }
+      delete b;
+      fail(FG_ERR_CUDA, "fg_batch_setup: cudaStreamCreate failed");
+    }
+    cudaSetDevice(prev);
+#endif
+    b->own.push_back(s);
+    b->saved.push_back(members[i]->st);
+    members[i]->st = s;
+  }
+  const unsigned hw = std::thread::hardware_concurrency();
+  b->threads = (int)std::min<unsigned>(std::max(1u, hw ? hw : 1u), (unsigned)std::min(n, 32));
+  *out = b;
+  FG_API_END
+}
+
+int fg_batch_step(fg_batch* b, double dt, const double Fbar[9], fg_stats* st) {
+  if (!b || !Fbar || !(dt > 0)) {
+    g_err = "fg_batch_step: bad argument";
+    return FG_ERR_INVALID;
+  }
+  const int n = (int)b->members.size();
+  std::vector<int> rc(n, FG_OK);
+  std::vector<fg_stats> ss(n);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) return;
+#ifndef FG_EMU
+      cudaSetDevice(b->members[i]->device);
+#endif
+      rc[i] = fg_step(b->members[i], dt, Fbar, &ss[i]);
+      msg[i] = g_err;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < b->threads; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  int first = FG_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st) st[i] = ss[i];
+    if (rc[i] != FG_OK && first == FG_OK) {
+      first = rc[i];
+      g_err = "member " + std::to_string(i) + ": " + msg[i];
+    }
+  }
+  return first;
+}
+
+void fg_batch_destroy(fg_batch* b) {
+  if (!b) return;
+  for (size_t k = 0; k < b->members.size(); ++k) {
+#ifndef FG_EMU
+    cudaStreamSynchronize(b->own[k]);
+    cudaStreamDestroy(b->own[k]);
+#endif
+    b->members[k]->st = b->saved[k];
+  }
+  delete b;
+}
+
+int fg_solve_mech(fg_ctx* c, const double Fbar[9], fg_stats* st) {
+  fg_stats s;
+  memset(&s, 0, sizeof(s));
+  int rc = FG_OK;
+  g_err.clear();
+  try {
+    if (!c || !Fbar) fail(FG_ERR_INVALID, "fg_solve_mech: bad argument");
+    VArgs v = vbase(*c, 9 * c->V);  // F += Fbar - Fbar_old
+    v.in[0] = c->F;
+    v.out[0] = c->Fbk;
+    for (int k = 0; k < 9; ++k) v.s[k] = Fbar[k] - c->Fbar[k];
+    launch_vec<KShiftF>(v, c->st);
+    dcopy(c->F, c->Fbk, 9 * c->V * sizeof(double), c->st);
+    memcpy(c->Fbar, Fbar, sizeof(c->Fbar));
+    const double den = residual_den(*c);
+    if (is_mixed(*c)) mech_newton<float>(*c, c->pf, den, s);
+    else mech_newton<double>(*c, c->pd, den, s);
+    dsync(c->st);
+  } catch (Fail& f) {
+    rc = f.code;
+  }
+  s.status = rc;
+  if (st) *st = s;
+  return rc;
+}
+
+int fg_adjoint_mech(fg_ctx* c, const double* W, double* grad_logE, int* iters) {
+  FG_API_BEGIN
+  if (!c || !W || !grad_logE) fail(FG_ERR_INVALID, "fg_adjoint_mech: null argument");
+  fg_stats s;
+  memset(&s, 0, sizeof(s));
+  const long long V = c->V;
+  dcopy(c->P, W, 9 * V * sizeof(double), c->st);  // W -> device (P is scratch here)
+  op_gres(*c, c->pd, c->P, c->GP, nullptr);        // G W
+  int n = 0;
+  auto run = [&](auto& P) {
+    using R = typename std::remove_reference<decltype(*P.x)>::type;
+    to_prec<R>(*c, c->GP, P.b, 9 * V, 1.0);
+    mech_state<R>(*c, c->F, nullptr, c->P, P.state);  // tangent and stress at the solution
+    n = cg_solve_mech<R>(*c, P, mixed_tol(*c, c->o.tol_cg), c->o.max_cg, nullptr);
+    VArgs v = vbase(*c, V);
+    v.in[0] = P.x;
+    v.in[1] = c->P;
+    v.out[0] = c->base;
+    launch_vec<KAdjGradE<R>>(v, c->st);
+  };
+  if (is_mixed(*c)) run(c->pf);
+  else run(c->pd);
+  read_ks(*c);
+  check_flags(*c, "adjoint");
+  dcopy(grad_logE, c->base, V * sizeof(double), c->st);
+  dsync(c->st);
+  if (iters) *iters = n;
+  FG_API_END
+}
+
+// Times the schedule choices of the mechanical CG that are selectable at run time and
+// keeps the fastest: kx planes per Y-Z-Y chunk (whole volume, 40 % or 15 % of L2) and the
+// per-component or 9-component X-inv update.
+int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
+  FG_API_BEGIN
+  if (!c) fail(FG_ERR_INVALID, "fg_autotune: null context");
+#ifdef FG_EMU
+  if (ms_per_iteration) *ms_per_iteration = 0.0;
+#else
+  const bool mixed = is_mixed(*c);
+  const int k = mixed ? 0 : 1;
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  int dev = 0, l2b = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2b, cudaDevAttrL2CacheSize, dev);
+  const double slab = 9.0 * c->ny * c->nz * (mixed ? 8.0 : 16.0);
+  std::vector<int> chunks = {c->hx};
+  for (double f : {0.4, 0.15}) {
+    int ch = (int)(f * l2b / slab);
+    ch = ch < 1 ? 1 : (ch > c->hx ? c->hx : ch);
+    if (std::find(chunks.begin(), chunks.end(), ch) == chunks.end()) chunks.push_back(ch);
+  }
+  void* x = dalloc(9 * c->V * es);
+  void* y = dalloc(9 * c->V * es);
+  dzero(x, 9 * c->V * es, c->st);
+  if (mixed) mech_state<float>(*c, c->F, nullptr, nullptr, c->pf.state);
+  else mech_state<double>(*c, c->F, nullptr, nullptr, c->pd.state);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_it = [&](auto&& f, int reps) {
+    for (int i = 0; i < 2; ++i) f();
+    cudaEventRecord(e0, c->st);
+    for (int i = 0; i < reps; ++i) f();
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    return (double)t / reps;
+  };
+  double best = 1e300;
+  int best_ch = c->kx_chunk[k];
+  for (int ch : chunks) {
+    c->kx_chunk[k] = ch;
+    const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
+                           : time_it([&] { op_mech(*c, c->pd, (const double*)x, (double*)y, nullptr); }, 3);
+    if (t < best) {
+      best = t;
+      best_ch = ch;
+    }
+  }
+  c->kx_chunk[k] = best_ch;
+  // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
+  double* zero = (double*)dalloc(4 * sizeof(double));
+  dzero(zero, 4 * sizeof(double), c->st);
+  double tv[2];
+  for (int pc = 0; pc < 2; ++pc) {
+    auto run = [&]() {
+      if (mixed) {
+        PassArgs<float> a = pbase(*c, c->pf, nullptr);
+        a.tw = c->pf.twx;
+        a.cin = c->pf.S1;
+        a.rout = (float*)y;
+        a.rout2 = (float*)x;
+        a.aux[0] = (const float*)x;
+        a.dscal = zero;
+        (pc ? c->pf.ox->xi_cgupdate_pc : c->pf.ox->xi_cgupdate)(a, c->st);
+      } else {
+        PassArgs<double> a = pbase(*c, c->pd, nullptr);
+        a.tw = c->pd.twx;
+        a.cin = c->pd.S1;
+        a.rout = (double*)y;
+        a.rout2 = (double*)x;
+        a.aux[0] = (const double*)x;
+        a.dscal = zero;
+        (pc ? c->pd.ox->xi_cgupdate_pc : c->pd.ox->xi_cgupdate)(a, c->st);
+      }
+    };
+    tv[pc] = time_it(run, 5);
+  }
+  c->xi_percomp = tv[1] <= tv[0] ? 1 : 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dsync(c->st);
+  dfree(zero);
+  dfree(x);
+  dfree(y);
+  ccheck("fg_autotune");
+  if (ms_per_iteration) *ms_per_iteration = best;
+#endif
   FG_API_END
 }
 

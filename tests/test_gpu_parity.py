@@ -172,3 +172,57 @@ def test_full_size_step_properties(lib):
     assert abs(c.mean() - (c_t.mean() + w.dt * w.cdot_B.mean())) < 1e-12
     assert st["stag"] >= 1
     sol.close()
+
+
+def test_mech_adjoint_autograd_vs_fd_and_oracle(lib):
+    """torch.autograd through the hand-written adjoint: dL/dlogE of L = <W, F(logE)>
+    against central differences of the GPU forward (h = 1e-6) and the oracle adjoint."""
+    from paper_2411_16583_gb300.autograd import mech_equilibrium
+    shape = (16, 16, 16)
+    rng = np.random.default_rng(21)
+    pid = S.random_phase_map(shape, 3)
+    phases = S.default_phases()
+    phases[1].E = 2e9
+    c = rng.uniform(0.05, 0.4, shape)
+    d = rng.uniform(0.0, 0.3, shape)
+    spec = dict(shape=shape, h=H3, phases=phases, phase_id=pid, c=c, d=d, lib=lib,
+                opts=dict(tol_newton=1e-13, tol_cg=1e-14))
+    logE = torch.tensor(rng.normal(0, 0.1, shape), dtype=torch.float64, device="cuda",
+                        requires_grad=True)
+    W = torch.tensor(rng.standard_normal((3, 3) + shape), dtype=torch.float64, device="cuda")
+    F = mech_equilibrium(logE, spec)
+    (W * F).sum().backward()
+    g = logE.grad.cpu().numpy()
+    prm = O.make_params([O.Phase(**vars(p)) for p in phases], pid, H3, gc=1.0, lc=2e-7,
+                        log_E=logE.detach().cpu().numpy())
+    ref = O.mech_adjoint(F.detach().cpu().numpy(), c, d, prm, W.cpu().numpy(), 1e-14, 3000)
+    assert rel_err(g, ref) < 1e-6
+    h = 1e-6
+    for v in [(0, 0, 0), (5, 9, 3), (15, 2, 11), (8, 8, 8)]:
+        lp, lm = logE.detach().clone(), logE.detach().clone()
+        lp[v] += h
+        lm[v] -= h
+        fd = ((W * mech_equilibrium(lp, spec)).sum() - (W * mech_equilibrium(lm, spec)).sum()).item() / (2 * h)
+        assert abs(fd - g[v]) <= 1e-6 * np.abs(g).max() + 1e-6 * abs(fd)
+
+
+def test_batch_members_equal_solo_runs(lib):
+    """Uneven RVEs (48^3 to 96^3 spheres) stepped as one batch on concurrent streams give
+    the same fields as each RVE stepped alone."""
+    ws = [S.sphere(n, r, band=3, nsteps=20, seed=i)
+          for i, (n, r) in enumerate([(48, 0.3), (64, 0.4), (80, 0.35), (96, 0.45)])]
+    solo = [B.from_workload(w, precision=B.FG_MIXED, lib=lib) for w in ws]
+    for s_, w in zip(solo, ws):
+        s_.step(w.dt)
+    members = [B.from_workload(w, precision=B.FG_MIXED, lib=lib) for w in ws]
+    for m in members:
+        m.autotune()
+    batch = B.Batch(members)
+    stats = batch.step(1.0)
+    assert all(st["status"] == 0 for st in stats)
+    for a, b in zip(members, solo):
+        assert rel_err(a.get(B.FIELD_F), b.get(B.FIELD_F)) < 1e-12
+        assert rel_err(a.get(B.FIELD_C), b.get(B.FIELD_C)) < 1e-12
+    batch.close()
+    for s_ in solo + members:
+        s_.close()

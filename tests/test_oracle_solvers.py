@@ -276,3 +276,32 @@ def test_cg_truncates_at_nonpositive_curvature():
     assert it == 1 and stats["cg_truncated"] == 1
     with pytest.raises(FloatingPointError):
         O.cg(lambda v: -v, b, 1e-12, 10)
+
+
+def test_mech_adjoint_matches_central_differences():
+    """dL/dlogE of L = <W, F(logE)> at equilibrium, against central differences of the
+    converged solve on a few voxels."""
+    shape = (2, 4, 4)
+    rng = np.random.default_rng(3)
+    pid = rng.integers(0, 2, size=shape)
+    phases = [O.Phase(E=10e9, nu=0.3, Omega=0.2, c0=0.01), O.Phase(E=2e9, nu=0.25, Omega=0.0, c0=0.01)]
+    logE = rng.normal(0, 0.1, shape)
+    c = rng.uniform(0.05, 0.4, shape)
+    d = rng.uniform(0.0, 0.3, shape)
+    W = rng.standard_normal((3, 3) + shape)
+
+    def solve(le):
+        prm = O.make_params(phases, pid, H, gc=1.0, lc=2e-7, log_E=le)
+        F0 = identity(shape)
+        F, _ = O.mech_newton(F0, c, d, prm, np.eye(3), 1e-14, 1e-15, 30, 2000)
+        return F, prm
+
+    F, prm = solve(logE)
+    g = O.mech_adjoint(F, c, d, prm, W, 1e-15, 2000)
+    h = 1e-6
+    for v in [(0, 0, 0), (1, 2, 3), (0, 3, 1), (1, 1, 2)]:
+        lp, lm = logE.copy(), logE.copy()
+        lp[v] += h
+        lm[v] -= h
+        fd = (np.sum(W * solve(lp)[0]) - np.sum(W * solve(lm)[0])) / (2 * h)
+        assert abs(fd - g[v]) <= 1e-6 * np.abs(g).max() + 1e-7 * abs(fd)
