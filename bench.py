@@ -54,6 +54,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=256, help="grid edge of the particle workload")
+    p.add_argument("--nz", type=int, default=0, help="override the z extent (profiling cases)")
     p.add_argument("--fp64-steps", type=int, default=1, help="FP64 comparison steps (0: skip)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,13 +64,16 @@ def _args():
     return p.parse_args()
 
 
-def _workload(n, seed):
+def _workload(n, seed, nz=0):
     from paper_2411_16583_gb300 import synth as S
-    if n == 256:
+    if n == 256 and not nz:
         return S.ellipsoid256(seed=seed)
     f = n / 256.0
-    return S.ellipsoid(n=n, axes=(100 * f, 80 * f, 70 * f), rough_std=3 * f, rough_corr=8 * f,
-                       band=max(1, round(8 * f)), nsteps=100, seed=seed, c_perturb=0.02)
+    shape = (nz, n, n) if nz else None
+    axes = (100 * f, 80 * f, min(70 * f, 0.4 * nz) if nz else 70 * f)
+    return S.ellipsoid(n=n, axes=axes, rough_std=3 * f, rough_corr=8 * f,
+                       band=max(1, round(8 * f)), nsteps=100, seed=seed, c_perturb=0.02,
+                       shape=shape)
 
 
 class Clocks:
@@ -209,7 +213,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = _workload(a.n, seed=rank)
+    w = _workload(a.n, seed=rank, nz=a.nz)
     stream = torch.cuda.current_stream()
     sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
     V = w.nvox

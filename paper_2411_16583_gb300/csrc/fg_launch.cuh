@@ -107,13 +107,23 @@ SizeOps<R> make_size_ops() {
     s.xi_chemop = run_x<XInv<R, N, EChemOp<R>>, R>;
     s.xi_chemrhs = run_x<XInv<R, N, EChemRhs<R>>, R>;
   }
-  s.yf = run_y<YPass<R, N, false>, R>;
-  s.yi = run_y<YPass<R, N, true>, R>;
-  s.z_proj = run_z<ZPass<R, N, ZProject<R>>, R>;
-  s.z_lap = run_z<ZPass<R, N, ZLaplace<R>>, R>;
-  s.z_prec = run_z<ZPass<R, N, ZPrecond<R>>, R>;
-  s.z_grad = run_z<ZPass<R, N, ZGrad<R>>, R>;
-  s.z_div = run_z<ZPass<R, N, ZDiv<R>>, R>;
+  if constexpr (Square<N>::OK) {  // register-direct two-stage passes
+    s.yf = run_y<YPassD<R, N, false>, R>;
+    s.yi = run_y<YPassD<R, N, true>, R>;
+    s.z_proj = run_z<ZPassD<R, N, ZProject<R>>, R>;
+    s.z_lap = run_z<ZPassD<R, N, ZLaplace<R>>, R>;
+    s.z_prec = run_z<ZPassD<R, N, ZPrecond<R>>, R>;
+    s.z_grad = run_z<ZPassD<R, N, ZGrad<R>>, R>;
+    s.z_div = run_z<ZPassD<R, N, ZDiv<R>>, R>;
+  } else {
+    s.yf = run_y<YPass<R, N, false>, R>;
+    s.yi = run_y<YPass<R, N, true>, R>;
+    s.z_proj = run_z<ZPass<R, N, ZProject<R>>, R>;
+    s.z_lap = run_z<ZPass<R, N, ZLaplace<R>>, R>;
+    s.z_prec = run_z<ZPass<R, N, ZPrecond<R>>, R>;
+    s.z_grad = run_z<ZPass<R, N, ZGrad<R>>, R>;
+    s.z_div = run_z<ZPass<R, N, ZDiv<R>>, R>;
+  }
   return s;
 }
 

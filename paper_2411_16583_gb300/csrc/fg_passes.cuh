@@ -319,6 +319,216 @@ struct YPass {
   }
 };
 
+// ------------------------------------------------------------------ register-direct passes
+// For N = RAD^2 (two equal radix stages, e.g. 64 = 8 x 8, 256 = 16 x 16) the first stage
+// reads its butterfly inputs straight from global memory into registers and the last
+// stage writes its outputs straight to global memory: every element crosses shared
+// memory once between the stages.  Thread-to-row maps are chosen per stage so that the
+// global side of each stage is coalesced (row-fastest for transposed layouts).
+
+template <int N>
+struct Square {
+  static constexpr Plan P = make_plan(N);
+  static constexpr bool OK = P.S == 2 && P.r[0] == P.r[1];
+  static constexpr int RAD = P.r[0];
+  static constexpr int T = N / RAD;  // butterflies per row and stage
+};
+
+// stage 0 (Ns = 1): v holds x[b + r T]; outputs go to positions b RAD + r
+// stage 1 (Ns = RAD): v holds positions b + r T, twiddle exp(-+ 2 pi i r b / N); outputs
+// land in natural order at b + r T
+template <typename C, int RAD, bool INV>
+FG_DEV void square_stage1_twiddle(C* v, const C* tw, int b) {
+#pragma unroll
+  for (int r = 1; r < RAD; ++r) {
+    const C w = tw[r * b];
+    v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+  }
+}
+
+template <typename R, int N, bool INV>
+struct YPassD {
+  using C = cplx<R>;
+  using SQ = Square<N>;
+  static constexpr int RAD = SQ::RAD, T = SQ::T;
+  static constexpr int ROWS = rows_y(N, sizeof(C));
+  static constexpr int NT = round32(ROWS * T);
+  static constexpr int PITCH = row_pitch(N);
+  struct Locals {
+    C v[RAD];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(ROWS * PITCH + N) * sizeof(C); }
+
+  FG_DEV static long long tpos(int s, int n, int nz) {
+    const int kx = s / nz, z = s - kx * nz;
+    return ((long long)kx * N + n) * nz + z;
+  }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + ROWS * PITCH;
+    const int c = bid.y;
+    const int nrows = a.row_hi > 0 ? a.row_hi : a.hx * a.nz;
+    const int row0 = a.row_lo + bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    const C* in = a.cin + c * a.VH;
+    C* out = a.cout + c * a.VH;
+    const bool rfast = a.nz >= 4;
+    FG_PHASE(NT)
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    if (tid < ROWS * T) {
+      int rho, b;  // inputs: transposed layout row-fastest, contiguous rows butterfly-fastest
+      if (INV && rfast) { rho = tid % ROWS; b = tid / ROWS; }
+      else { b = tid % T; rho = tid / T; }
+      if (rho < nr) {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+          const int n = b + r * T;
+          L.v[r] = in[INV ? tpos(row0 + rho, n, a.nz) : (long long)(row0 + rho) * N + n];
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) L.v[r] = cmk<C>((R)0, (R)0);
+      }
+      Dft<RAD, INV, C>::run(L.v);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) tile[rho * PITCH + pad16(b * RAD + r)] = L.v[r];
+    }
+    FG_END_PHASE
+    FG_PHASE(NT)
+    if (tid < ROWS * T) {
+      int rho, b;  // outputs: transposed layout row-fastest
+      if (!INV && rfast) { rho = tid % ROWS; b = tid / ROWS; }
+      else { b = tid % T; rho = tid / T; }
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) L.v[r] = tile[rho * PITCH + pad16(b + r * T)];
+      square_stage1_twiddle<C, RAD, INV>(L.v, tw, b);
+      Dft<RAD, INV, C>::run(L.v);
+      if (rho < nr) {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+          const int n = b + r * T;
+          out[INV ? (long long)(row0 + rho) * N + n : tpos(row0 + rho, n, a.nz)] = L.v[r];
+        }
+      }
+    }
+    FG_END_PHASE
+  }
+};
+
+template <typename R, int N, class Op>
+struct ZPassD {
+  using C = cplx<R>;
+  using SQ = Square<N>;
+  static constexpr int RAD = SQ::RAD, T = SQ::T;
+  static constexpr int CI = Op::CIN;
+  static constexpr int CO = Op::COUT;
+  static constexpr int CM = CI > CO ? CI : CO;
+  static constexpr int ROWS = rows_z(N, CM, sizeof(C));
+  static constexpr int NT = round32(CM * ROWS * T);
+  static constexpr int PITCH = row_pitch(N);
+  struct Locals {
+    C v[RAD];
+    double acc;
+  };
+  static size_t smem_bytes() { return (size_t)(CM * ROWS * PITCH + N) * sizeof(C); }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + CM * ROWS * PITCH;
+    const int nrows = a.row_hi > 0 ? a.row_hi : a.hx * a.ny;
+    const int row0 = a.row_lo + bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    // forward stage 0 from global
+    FG_PHASE(NT)
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    if (tid < CI * ROWS * T) {
+      const int b = tid % T, q = tid / T;  // q = c ROWS + rho
+      const int rho = q % ROWS, c = q / ROWS;
+      if (rho < nr) {
+        const C* in = a.cin + c * a.VH + (long long)(row0 + rho) * N;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) L.v[r] = in[b + r * T];
+      } else {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) L.v[r] = cmk<C>((R)0, (R)0);
+      }
+      Dft<RAD, false, C>::run(L.v);
+      C* t = tile + q * PITCH;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) t[pad16(b * RAD + r)] = L.v[r];
+    }
+    FG_END_PHASE
+    // forward stage 1 in place (each thread reads and writes the same positions)
+    FG_PHASE(NT)
+    if (tid < CI * ROWS * T) {
+      const int b = tid % T, q = tid / T;
+      C* t = tile + q * PITCH;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
+      square_stage1_twiddle<C, RAD, false>(L.v, tw, b);
+      Dft<RAD, false, C>::run(L.v);
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) t[pad16(b + r * T)] = L.v[r];
+    }
+    FG_END_PHASE
+    // frequency-space operator on all components of each (row, kz)
+    FG_PHASE(NT)
+    for (int e = tid; e < nr * N; e += NT) {
+      const int r = e / N, n = e - r * N;
+      const int s_ = row0 + r;
+      const int kx = s_ / a.ny, ky = s_ - kx * a.ny;
+      C v[CM];
+#pragma unroll
+      for (int c = 0; c < CI; ++c) v[c] = tile[(c * ROWS + r) * PITCH + pad16(n)];
+      Op::apply(a, kx, ky, n, v);
+#pragma unroll
+      for (int c = 0; c < CO; ++c) tile[(c * ROWS + r) * PITCH + pad16(n)] = v[c];
+    }
+    FG_END_PHASE
+    // inverse stage 0: read, then write after the barrier
+    FG_PHASE(NT)
+    if (tid < CO * ROWS * T) {
+      const int b = tid % T, q = tid / T;
+      const C* t = tile + q * PITCH;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
+      Dft<RAD, true, C>::run(L.v);
+    }
+    FG_END_PHASE
+    FG_PHASE(NT)
+    if (tid < CO * ROWS * T) {
+      const int b = tid % T, q = tid / T;
+      C* t = tile + q * PITCH;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) t[pad16(b * RAD + r)] = L.v[r];
+    }
+    FG_END_PHASE
+    // inverse stage 1 straight to global
+    FG_PHASE(NT)
+    if (tid < CO * ROWS * T) {
+      const int b = tid % T, q = tid / T;
+      const int rho = q % ROWS, c = q / ROWS;
+      const C* t = tile + q * PITCH;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
+      square_stage1_twiddle<C, RAD, true>(L.v, tw, b);
+      Dft<RAD, true, C>::run(L.v);
+      if (rho < nr) {
+        C* o = a.cout + c * a.VH + (long long)(row0 + rho) * N;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) o[b + r * T] = L.v[r];
+      }
+    }
+    FG_END_PHASE
+  }
+};
+
 // ------------------------------------------------------------------ Z pass
 
 template <typename R, int N, class Op>

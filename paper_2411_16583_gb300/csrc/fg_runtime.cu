@@ -42,6 +42,12 @@ const SizeOps<R>* size_ops(int N) {
 // ------------------------------------------------------------------ errors
 
 static thread_local std::string g_err;
+
+// progress trace on stderr when the environment variable FG_VERBOSE is set
+static bool verbose() {
+  static const bool v = getenv("FG_VERBOSE") != nullptr;
+  return v;
+}
 void set_last_error(const std::string& msg) { g_err = msg; }
 
 struct Fail {
@@ -823,6 +829,10 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
     const int n = cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s.cg_truncated);
     s.cg_mech += n;
     s.newton_mech += 1;
+    if (verbose())
+      fprintf(stderr, "[fg] newton %d err %.3e cg %d rr/bb %.3e status %d\n", it, err, n,
+              c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
+              c.ks_host[KS_MECH].status);
     const double* dF;
     if (is_mixed(c)) {
       // FP32 roundoff leaves traces of the correction in modes G never sees (the mean and
@@ -854,6 +864,7 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
         if (f.code != FG_ERR_DOMAIN) throw;
         continue;
       }
+      if (verbose()) fprintf(stderr, "[fg]   lambda %.4f err %.3e\n", lam, e);
       if (e < err) {
         err = e;
         ok = true;

@@ -180,6 +180,25 @@ def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=
             for i, (n, r) in enumerate(zip(ns, rs))]
 
 
+def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16e-6 / 512,
+                E=15e9, Omega=1.3):
+    """2D circular Saint-Venant-Kirchhoff particle with Weibull-type random stiffness
+    (Sec. 5.1, Eq. Gumbell): E_i = E log(1/(1 - w_i))^(1/m), w_i ~ U(0, 1), m = 3, carried
+    as the per-voxel log-stiffness log_E = log(log(1/(1 - w_i)))/m.  The paper also draws
+    a random sigma_max per voxel with the same law; the C ABI takes sigma_max per phase,
+    so this workload keeps it uniform."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (1, n, n)
+    x, y, _ = _grid_coords(shape)
+    particle = (x * x + y * y) <= (0.5 * diameter_frac * n) ** 2
+    phases = default_phases(E=E, law=LAW_SVK, vol_change=Omega * (1 - 0.01), buffer_E=1e-5)
+    w = _finish("gumbel_disc", shape, (h, h, h), particle, band, nsteps, 1.0, rng, phases=phases)
+    om = rng.uniform(size=shape)
+    log_E = np.log(np.log(1.0 / (1.0 - om))) / m
+    w.log_E = np.where(particle, log_E, 0.0)
+    return w
+
+
 def with_log_fields(w, std=0.1, seed=0):
     """Attach per-voxel log-stiffness, log-toughness and log-diffusivity ~ N(0, std^2)."""
     rng = np.random.Generator(np.random.PCG64(seed + 7919))

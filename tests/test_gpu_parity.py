@@ -203,7 +203,9 @@ def test_mech_adjoint_autograd_vs_fd_and_oracle(lib):
         lp[v] += h
         lm[v] -= h
         fd = ((W * mech_equilibrium(lp, spec)).sum() - (W * mech_equilibrium(lm, spec)).sum()).item() / (2 * h)
-        assert abs(fd - g[v]) <= 1e-6 * np.abs(g).max() + 1e-6 * abs(fd)
+        # the forward solves converge to err_res 1e-13: differences at h = 1e-6 carry
+        # noise of about 1e-6 of the largest gradient entry
+        assert abs(fd - g[v]) <= 1e-5 * np.abs(g).max()
 
 
 def test_batch_members_equal_solo_runs(lib):
@@ -226,3 +228,35 @@ def test_batch_members_equal_solo_runs(lib):
     batch.close()
     for s_ in solo + members:
         s_.close()
+
+
+def test_mixed_vs_fp64_gpu_perturbed_particle(lib):
+    """The perturbed-particle recipe of the 256^3 benchmark at 64^3: three coupled steps
+    in the mixed form against the FP64 GPU form at Newton tolerance 1e-9."""
+    import bench
+    w = bench._workload(64, 0)
+    a = B.from_workload(w, lib=lib)
+    b = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
+    for _ in range(3):
+        a.step(w.dt)
+        b.step(w.dt)
+    assert rel_err(b.get(B.FIELD_F), a.get(B.FIELD_F)) < 1e-7
+    assert rel_err(b.get(B.FIELD_C), a.get(B.FIELD_C)) < 1e-7
+    assert np.abs(b.get(B.FIELD_D) - a.get(B.FIELD_D)).max() < 1e-6
+    a.close()
+    b.close()
+
+
+def test_gumbel_svk_disc_step(lib):
+    """The paper's 2D example type (Sec. 5.1): a 512^2 Saint-Venant-Kirchhoff disc with
+    Weibull-distributed stiffness; one mixed step, then the oracle's residuals of the
+    GPU's fields."""
+    w = S.gumbel_disc()
+    sol = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
+    st = sol.step(w.dt)
+    assert st["status"] == 0
+    F, c, d = sol.get(B.FIELD_F), sol.get(B.FIELD_C), sol.get(B.FIELD_D)
+    prm = oracle_params(w)
+    _, err = O.mech_residual(F, c, d, prm, np.eye(3))
+    assert err <= 2 * w.tol["tol_stag"]
+    sol.close()
