@@ -563,7 +563,9 @@ def chem_apply(y, m, Kc, dt, prm):
 
 
 def chem_solve(c_t, F, d_t, dt, cdot_B, prm, tol_chem, tol_cg, max_newton, max_cg, stats=None):
-    """Alg. 3: Newton-CG from c^0 = c_t until ||dc|| / ||c_t|| < tol_chem."""
+    """Alg. 3: Newton-CG from c^0 = c_t until ||dc|| / ||c_t|| < tol_chem.  A correction
+    that would take c out of (0, 1), where mu_c = RT log(c/(1-c)) is undefined, is halved
+    (at most 10 times) until the update stays inside."""
     Kc = chem_conductivity(F, c_t, d_t, prm)
     c = c_t.copy()
     nct = math.sqrt(dot(c_t, c_t))
@@ -572,12 +574,17 @@ def chem_solve(c_t, F, d_t, dt, cdot_B, prm, tol_chem, tol_cg, max_newton, max_c
         m = 1.0 / (c * (1.0 - c))
         y, it = cg(lambda v: chem_apply(v, m, Kc, dt, prm), -f, tol_cg, max_cg)
         dc = y / m
-        c = c + dc
+        for _ in range(11):
+            cn = c + dc
+            if np.all(cn > 0.0) and np.all(cn < 1.0):
+                break
+            dc = 0.5 * dc
+        else:
+            raise FloatingPointError("concentration left (0, 1)")
+        c = cn
         if stats is not None:
             stats["newton_chem"] = stats.get("newton_chem", 0) + 1
             stats["cg_chem"] = stats.get("cg_chem", 0) + it
-        if np.any(c <= 0.0) or np.any(c >= 1.0):
-            raise FloatingPointError("concentration left (0, 1)")
         if math.sqrt(dot(dc, dc)) / nct < tol_chem:
             return c
     raise RuntimeError("chemical Newton did not converge")

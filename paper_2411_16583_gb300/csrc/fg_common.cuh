@@ -53,6 +53,30 @@ struct Dim3 {
   int x, y, z;
 };
 
+// ------------------------------------------------------------------ per-thread sums
+// FP64 kernels accumulate in FP64.  FP32 kernels accumulate a compensated pair of floats
+// (Neumaier's summation): GB300 runs FP64 instructions at a small fraction of the FP32
+// rate, and one FP64 operation per element throttled the FP32 passes.  The block
+// reduction converts the pair to FP64.
+
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+  double s;
+  FG_HD void zero() { s = 0.0; }
+  FG_HD void add(double x) { s += x; }
+  FG_HD double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float s, c;
+  FG_HD void zero() { s = 0.f; c = 0.f; }
+  FG_HD void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  FG_HD double value() const { return (double)s + (double)c; }
+};
+
 // ------------------------------------------------------------------ complex arithmetic
 
 template <typename R> struct ctype;

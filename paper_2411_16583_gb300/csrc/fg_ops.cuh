@@ -14,7 +14,7 @@ template <typename R>
 struct ZProject {
   using C = cplx<R>;
   static constexpr int CIN = 9, COUT = 9;
-  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
     const R n0 = a.rs[0][kx] * a.rc[1][ky] * a.rc[2][kz];
     const R n1 = a.rs[1][ky] * a.rc[0][kx] * a.rc[2][kz];
     const R n2 = a.rs[2][kz] * a.rc[0][kx] * a.rc[1][ky];
@@ -36,7 +36,7 @@ template <typename R>
 struct ZLaplace {
   using C = cplx<R>;
   static constexpr int CIN = 1, COUT = 1;
-  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
     const R l = a.lap[0][kx] + a.lap[1][ky] + a.lap[2][kz];
     v[0] = cscale(v[0], a.coef[0] * l);
   }
@@ -48,9 +48,9 @@ template <typename R>
 struct ZPrecond {
   using C = cplx<R>;
   static constexpr int CIN = 1, COUT = 1;
-  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
     const R l = a.lap[0][kx] + a.lap[1][ky] + a.lap[2][kz];
-    const R den = a.coef[1] + (R)(2.0 * a.dscal[0]) + a.coef[2] * l;
+    const R den = a.coef[1] + (R)2 * zs + a.coef[2] * l;
     v[0] = cscale(v[0], a.coef[0] / den);
   }
 };
@@ -60,7 +60,7 @@ template <typename R>
 struct ZGrad {
   using C = cplx<R>;
   static constexpr int CIN = 1, COUT = 3;
-  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
     const C u = cscale(v[0], a.coef[0]);
     v[0] = cmul(a.xi[0][kx], u);
     v[1] = cmul(a.xi[1][ky], u);
@@ -73,7 +73,7 @@ template <typename R>
 struct ZDiv {
   using C = cplx<R>;
   static constexpr int CIN = 3, COUT = 1;
-  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v) {
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
     C s = cadd(cadd(cmulc(v[0], a.xi[0][kx]), cmulc(v[1], a.xi[1][ky])), cmulc(v[2], a.xi[2][kz]));
     v[0] = cscale(s, a.coef[0]);
   }
@@ -85,7 +85,7 @@ template <typename R, int NC>
 struct PCopy {
   static constexpr int COUT = NC;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) out[c] = a.rin[c * a.V + v];
   }
@@ -151,7 +151,7 @@ template <typename R>
 struct PTangentSVK {
   static constexpr int COUT = 9;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
     R p[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) p[c] = a.rin[c * a.V + v];
@@ -163,8 +163,8 @@ template <typename R>
 struct PCgTangentSVK {
   static constexpr int COUT = 9;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
-    const R beta = (R)a.dscal[1];
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>& acc, const R* sc) {
+    const R beta = sc[1];
     const R* __restrict__ r = a.rin;
     R* __restrict__ pp = a.rout;
     const long long V = a.V;
@@ -175,7 +175,7 @@ struct PCgTangentSVK {
 #pragma unroll
     for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
+    for (int c = 0; c < 9; ++c) acc.add(p[c] * out[c]);
   }
 };
 
@@ -183,7 +183,7 @@ template <typename R>
 struct PTangentNH {
   static constexpr int COUT = 9;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double&) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
     R p[9], B[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) p[c] = a.rin[c * a.V + v];
@@ -203,8 +203,8 @@ template <typename R>
 struct PCgTangentNH {
   static constexpr int COUT = 9;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, double& acc) {
-    const R beta = (R)a.dscal[1];
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>& acc, const R* sc) {
+    const R beta = sc[1];
     const R* __restrict__ r = a.rin;
     const R* __restrict__ st = a.aux[0];
     R* __restrict__ pp = a.rout;
@@ -220,7 +220,7 @@ struct PCgTangentNH {
     for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
     tangent_nh(B, s1, s2, s3, p, out);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc += (double)p[c] * (double)out[c];
+    for (int c = 0; c < 9; ++c) acc.add(p[c] * out[c]);
   }
 };
 
@@ -232,8 +232,8 @@ template <typename R>
 struct ECgUpdate1 {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
-    const R al = (R)a.dscal[0];
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    const R al = sc[0];
     R* __restrict__ r = a.rout;
     R* __restrict__ x = a.rout2;
     const R* __restrict__ p = a.aux[0];
@@ -241,7 +241,7 @@ struct ECgUpdate1 {
     const R rn = r0 - al * val[0];
     r[v] = rn;
     x[v] = x0 + al * p0;
-    acc += (double)rn * (double)rn;
+    acc.add(rn * rn);
   }
 };
 
@@ -252,15 +252,15 @@ template <typename R>
 struct ECgUpdate {
   static constexpr int CIN = 9;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
-    const R al = (R)a.dscal[0];
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    const R al = sc[0];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const long long i = c * a.V + v;
       const R rn = a.rout[i] - al * val[c];
       a.rout[i] = rn;
       a.rout2[i] += al * a.aux[0][i];
-      acc += (double)rn * (double)rn;
+      acc.add(rn * rn);
     }
   }
 };
@@ -269,7 +269,7 @@ template <typename R, int NC>
 struct EStore {
   static constexpr int CIN = NC;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double&) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>&, const R*) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) a.rout[c * a.V + v] = val[c];
   }
@@ -280,11 +280,11 @@ template <typename R, int NC>
 struct EStoreDot {
   static constexpr int CIN = NC;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       a.rout[c * a.V + v] = val[c];
-      acc += (double)val[c] * (double)a.aux[0][c * a.V + v];
+      acc.add(val[c] * a.aux[0][c * a.V + v]);
     }
   }
 };
@@ -294,11 +294,11 @@ template <typename R, int NC>
 struct ENorm {
   static constexpr int CIN = NC;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       a.rout[c * a.V + v] = val[c];
-      acc += (double)val[c] * (double)val[c];
+      acc.add(val[c] * val[c]);
     }
   }
 };
@@ -308,11 +308,11 @@ template <typename R>
 struct EPff {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R p = a.aux[0][v];
     const R y = (a.coef[0] + (R)2 * a.aux[1][v]) * p + val[0];
     a.rout[v] = y;
-    acc += (double)p * (double)y;
+    acc.add(p * y);
   }
 };
 
@@ -321,7 +321,7 @@ template <typename R>
 struct EChemFlux {
   static constexpr int CIN = 3;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* g, double&) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* g, Acc<R>&, const R*) {
     const R* K = a.aux[0];
     const long long V = a.V;
     const R kxx = K[v], kyy = K[V + v], kzz = K[2 * V + v];
@@ -338,11 +338,11 @@ template <typename R>
 struct EChemOp {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R y = a.aux[0][v];
     const R o = a.aux[1][v] * y + a.coef[0] * val[0];
     a.rout[v] = o;
-    acc += (double)y * (double)o;
+    acc.add(y * o);
   }
 };
 
@@ -353,10 +353,10 @@ template <typename R>
 struct EChemRhs {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, double& acc) {
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R o = -(a.aux[0][v] + a.coef[0] * val[0]);
     a.rout[v] = o;
-    acc += (double)o * (double)o;
+    acc.add(o * o);
   }
 };
 

@@ -74,13 +74,13 @@ constexpr int rows_z(int N, int ncomp, int csize) {
 #define FG_BLOCK_REDUCE(NT_, red, out)                     \
   {                                                        \
     double s_ = 0.0;                                       \
-    for (int t_ = 0; t_ < (NT_); ++t_) s_ += Ls[t_].acc;   \
+    for (int t_ = 0; t_ < (NT_); ++t_) s_ += Ls[t_].acc.value(); \
     out = s_;                                              \
   }
 #else
 #define FG_BLOCK_REDUCE(NT_, red, out)                                      \
   {                                                                         \
-    double v_ = Ls[0].acc;                                                  \
+    double v_ = Ls[0].acc.value();                                          \
     for (int o_ = 16; o_ > 0; o_ >>= 1) v_ += __shfl_down_sync(0xffffffffu, v_, o_); \
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v_;                \
     __syncthreads();                                                        \
@@ -110,7 +110,7 @@ struct XFwd {
   static constexpr int PITCH = TF::PITCH;
   struct Locals {
     C v[TF::VMAX];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
   static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
@@ -126,13 +126,15 @@ struct XFwd {
     const int row0 = bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     FG_PHASE(NT)
-    L.acc = 0.0;
+    L.acc.zero();
+    // device scalars of the fused Krylov updates, converted once per thread
+    const R sc[2] = {a.dscal ? (R)a.dscal[0] : (R)0, a.dscal ? (R)a.dscal[1] : (R)0};
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
     for (int e = tid; e < ROWS * N; e += NT) {
       const int r = e / N, x = e - r * N;
       R out[CO];
       if (r < nr) {
-        Op::apply(a, (long long)(row0 + r) * N + x, out, L.acc);
+        Op::apply(a, (long long)(row0 + r) * N + x, out, L.acc, sc);
       } else {
 #pragma unroll
         for (int c = 0; c < CO; ++c) out[c] = (R)0;
@@ -192,7 +194,7 @@ struct XInv {
   static constexpr int PITCH = TF::PITCH;
   struct Locals {
     C v[TF::VMAX];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
   static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
@@ -216,7 +218,7 @@ struct XInv {
     const int row0 = bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     FG_PHASE(NT)
-    L.acc = 0.0;
+    L.acc.zero();
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
     constexpr int H = N / 2 + 1;
     for (int e = tid; e < CI * CR * H; e += NT) {
@@ -239,6 +241,7 @@ struct XInv {
     FG_END_PHASE
     tile_fft<TF, 0>(Ls, tile, tw, NT);
     FG_PHASE(NT)
+    const R sc[2] = {a.dscal ? (R)a.dscal[0] : (R)0, a.dscal ? (R)a.dscal[1] : (R)0};
     for (int e = tid; e < nr * N; e += NT) {
       const int r = e / N, x = e - r * N;
       R val[CI];
@@ -247,7 +250,7 @@ struct XInv {
         const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
         val[c] = (r & 1) ? z.y : z.x;
       }
-      Op::apply(a, (long long)(row0 + r) * N + x, val, L.acc);
+      Op::apply(a, (long long)(row0 + r) * N + x, val, L.acc, sc);
     }
     FG_END_PHASE
     if constexpr (Op::RED) {
@@ -273,7 +276,7 @@ struct YPass {
   static constexpr int PITCH = TF::PITCH;
   struct Locals {
     C v[TF::VMAX];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(ROWS * PITCH + N) * sizeof(C); }
   static int grid_x(int hx, int nz) { return (hx * nz + ROWS - 1) / ROWS; }
@@ -356,7 +359,7 @@ struct YPassD {
   static constexpr int PITCH = row_pitch(N);
   struct Locals {
     C v[RAD];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(ROWS * PITCH + N) * sizeof(C); }
 
@@ -432,7 +435,7 @@ struct ZPassD {
   static constexpr int PITCH = row_pitch(N);
   struct Locals {
     C v[RAD];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(CM * ROWS * PITCH + N) * sizeof(C); }
 
@@ -479,6 +482,7 @@ struct ZPassD {
     FG_END_PHASE
     // frequency-space operator on all components of each (row, kz)
     FG_PHASE(NT)
+    const R zs = a.dscal ? (R)a.dscal[0] : (R)0;
     for (int e = tid; e < nr * N; e += NT) {
       const int r = e / N, n = e - r * N;
       const int s_ = row0 + r;
@@ -486,7 +490,7 @@ struct ZPassD {
       C v[CM];
 #pragma unroll
       for (int c = 0; c < CI; ++c) v[c] = tile[(c * ROWS + r) * PITCH + pad16(n)];
-      Op::apply(a, kx, ky, n, v);
+      Op::apply(a, kx, ky, n, v, zs);
 #pragma unroll
       for (int c = 0; c < CO; ++c) tile[(c * ROWS + r) * PITCH + pad16(n)] = v[c];
     }
@@ -545,7 +549,7 @@ struct ZPass {
   static constexpr int VMAX = TFf::VMAX > TFi::VMAX ? TFf::VMAX : TFi::VMAX;
   struct Locals {
     C v[VMAX];
-    double acc;
+    Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(CM * ROWS * PITCH + N) * sizeof(C); }
   static int grid_x(int hx, int ny) { return (hx * ny + ROWS - 1) / ROWS; }
@@ -568,6 +572,7 @@ struct ZPass {
     FG_END_PHASE
     tile_fft<TFf, 0>(Ls, tile, tw, NT);
     FG_PHASE(NT)
+    const R zs = a.dscal ? (R)a.dscal[0] : (R)0;
     for (int e = tid; e < nr * N; e += NT) {
       const int r = e / N, n = e - r * N;
       const int s = row0 + r;
@@ -575,7 +580,7 @@ struct ZPass {
       C v[CM];
 #pragma unroll
       for (int c = 0; c < CI; ++c) v[c] = tile[(c * ROWS + r) * PITCH + pad16(n)];
-      Op::apply(a, kx, ky, n, v);
+      Op::apply(a, kx, ky, n, v, zs);
 #pragma unroll
       for (int c = 0; c < CO; ++c) tile[(c * ROWS + r) * PITCH + pad16(n)] = v[c];
     }

@@ -35,12 +35,22 @@ struct VArgs {
   int* flags;           // error flags (domain / numeric)
 };
 
-// Generic grid-stride kernel: F::apply(a, i, acc) for every element i.
+// Base of the element functors: AR is the type their per-thread sums accumulate in (the
+// arithmetic type of the kernel), Pre the device scalars each thread reads once.
+template <typename AR>
+struct VecOp {
+  using AccReal = AR;
+  struct Pre {};
+  FG_DEV static Pre pre(const VArgs&) { return Pre{}; }
+};
+
+// Generic grid-stride kernel: F::apply(a, i, acc, pre) for every element i.
 template <class F>
 struct VecKernel {
   static constexpr int NT = VEC_NT;
+  using AR = typename F::AccReal;
   struct Locals {
-    double acc;
+    Acc<AR> acc;
   };
   static size_t smem_bytes() { return NT * sizeof(double); }
   template <class Loc>
@@ -49,9 +59,10 @@ struct VecKernel {
     double* red = (double*)smem;
     (void)red;
     FG_PHASE(NT)
-    L.acc = 0.0;
+    L.acc.zero();
+    const typename F::Pre pre = F::pre(a);
     for (long long i = (long long)bid.x * NT + tid; i < a.n; i += (long long)grid.x * NT)
-      F::apply(a, i, L.acc);
+      F::apply(a, i, L.acc, pre);
     FG_END_PHASE
     if constexpr (F::RED) {
       double s = 0.0;
@@ -78,7 +89,7 @@ template <class F>
 struct FinKernel {
   static constexpr int NT = 256;
   struct Locals {
-    double acc;
+    Acc<double> acc;
   };
   static size_t smem_bytes() { return NT * sizeof(double); }
   template <class Loc>
@@ -234,9 +245,9 @@ constexpr int state_size(int law) { return law == LAW_NH_ ? 12 : 18; }
 //   St-V-Kirchhoff F (9), S (6), g a^2, g a^4 lam, g a^4 G
 
 template <typename R, int LAW = LAW_NH_>
-struct KMechState {
+struct KMechState : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>&, const Pre&) {
     const long long V = a.V;
     const double* Fp = (const double*)a.in[0];
     double F[9];
@@ -284,9 +295,9 @@ struct KMechState {
 // stress sigma = J^-1 a P0(a F) F^T (Eqs. Hist, SigDrivingForce).  Accumulates sum H.
 // in: F, c, H_t, lam, mu, Om, c0, smax ; out0: H ; s0 = g_c/(2 l_c)
 template <int LAW = LAW_NH_>
-struct KHistory {
+struct KHistory : VecOp<double> {
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long v, double& acc) {
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>& acc, const Pre&) {
     const long long V = a.V;
     const double* Fp = (const double*)a.in[0];
     double F[9];
@@ -325,7 +336,7 @@ struct KHistory {
       atomicOr(a.flags, ST_DOMAIN);
     }
     ((double*)a.out[0])[v] = Hn;
-    acc += Hn;
+    acc.add(Hn);
   }
 };
 
@@ -333,9 +344,9 @@ struct KHistory {
 // K_c = D phi(d_t) c_t (1-c_t) C^-1, C = F^T F, stored (xx, yy, zz, xy, xz, yz) in R.
 // in: F, c_t, d_t, D ; out0: K (6 V)
 template <typename R>
-struct KChemCond {
+struct KChemCond : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>&, const Pre&) {
     const long long V = a.V;
     const double* Fp = (const double*)a.in[0];
     double F[9], C[9], Ci[9];
@@ -369,9 +380,9 @@ struct KChemCond {
 // mu_e = -(1-d)^2 Omega / (3 J_c) P0(F_e) : F_e / c_max  (d psi_e / dc at fixed F).
 // in: c, c_t, cdot_B, F, d_t, lam, mu, Om, c0 ; s0 = dt, s1 = 1/RT, s2 = 1/c_max
 template <typename R, int LAW = LAW_NH_>
-struct KChemPrep {
+struct KChemPrep : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>&, const Pre&) {
     const long long V = a.V;
     const double c = ((const double*)a.in[0])[v];
     const double ct = ((const double*)a.in[1])[v];
@@ -402,18 +413,18 @@ struct KChemPrep {
   }
 };
 
-// c += dc with dc = y c (1 - c) (y = m dc); accumulates |dc|^2.  in0 = y (R); out0 = c
+// c = c_i + s0 dc with dc = y c_i (1 - c_i) (y = m dc); accumulates |s0 dc|^2.
+// in0 = y (R), in1 = c_i; out0 = c
 template <typename R>
-struct KChemUpdate {
+struct KChemUpdate : VecOp<double> {
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long v, double& acc) {
-    double* c = (double*)a.out[0];
-    const double ci = c[v];
-    const double dc = (double)((const R*)a.in[0])[v] * ci * (1.0 - ci);
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>& acc, const Pre&) {
+    const double ci = ((const double*)a.in[1])[v];
+    const double dc = a.s[0] * (double)((const R*)a.in[0])[v] * ci * (1.0 - ci);
     const double cn = ci + dc;
-    c[v] = cn;
+    ((double*)a.out[0])[v] = cn;
     if (!(cn > 0.0 && cn < 1.0)) atomicOr(a.flags, ST_DOMAIN);
-    acc += dc * dc;
+    acc.add(dc * dc);
   }
 };
 
@@ -421,29 +432,29 @@ struct KChemUpdate {
 
 // out0 (R) = s0 * in0 (FP64); accumulates |out|^2
 template <typename R>
-struct KScaleTo {
+struct KScaleTo : VecOp<double> {
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
     const R o = (R)(a.s[0] * ((const double*)a.in[0])[i]);
     ((R*)a.out[0])[i] = o;
-    acc += (double)o * (double)o;
+    acc.add(o * o);
   }
 };
 
 // out0 (FP64) = in0 (R)
 template <typename R>
-struct KWiden {
+struct KWiden : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
     ((double*)a.out[0])[i] = (double)((const R*)a.in[0])[i];
   }
 };
 
 // out0 (FP64) += in0 (R)
 template <typename R>
-struct KAddTo {
+struct KAddTo : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
     ((double*)a.out[0])[i] += (double)((const R*)a.in[0])[i];
   }
 };
@@ -451,9 +462,9 @@ struct KAddTo {
 // out0 (FP64) = -sum_c in0[c] (R) * in1[c] (FP64), c < 9: minus the contraction of the
 // adjoint field with the stress (the gradient of a loss with respect to log E)
 template <typename R>
-struct KAdjGradE {
+struct KAdjGradE : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long v, double&) {
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>&, const Pre&) {
     double s = 0.0;
 #pragma unroll
     for (int c = 0; c < 9; ++c)
@@ -463,31 +474,31 @@ struct KAdjGradE {
 };
 
 // out0 (FP64) = in0 + s0 * in1 (FP64)
-struct KAxpyTo {
+struct KAxpyTo : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
     ((double*)a.out[0])[i] = ((const double*)a.in[0])[i] + a.s[0] * ((const double*)a.in[1])[i];
   }
 };
 
 // sum of in0 (FP64) and of in0^2 into (partials, partials + VEC_BLOCKS)
-struct KSum {
+struct KSum : VecOp<double> {
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
-    acc += ((const double*)a.in[0])[i];
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
+    acc.add(((const double*)a.in[0])[i]);
   }
 };
-struct KSumSq {
+struct KSumSq : VecOp<double> {
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
     const double x = ((const double*)a.in[0])[i];
-    acc += x * x;
+    acc.add(x * x);
   }
 };
 // out0 (FP64) = in0 (FP64) + s0..s8 pattern: F = F_t + dFbar (component = i / V)
-struct KShiftF {
+struct KShiftF : VecOp<double> {
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
     ((double*)a.out[0])[i] = ((const double*)a.in[0])[i] + a.s[i / a.V];
   }
 };
@@ -496,64 +507,82 @@ struct KShiftF {
 
 // CG start from x = 0: x = 0, r = b, p = b (in0 = b, out0 = x, out1 = r, out2 = p); sum b^2
 template <typename R>
-struct KCgInit {
+struct KCgInit : VecOp<R> {
+  using AccReal = R;
+  using Pre = typename VecOp<R>::Pre;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
     const R b = ((const R*)a.in[0])[i];
     ((R*)a.out[0])[i] = (R)0;
     ((R*)a.out[1])[i] = b;
     if (a.out[2]) ((R*)a.out[2])[i] = b;
-    acc += (double)b * (double)b;
+    acc.add(b * b);
   }
 };
 
 // x += alpha p, r -= alpha q; sum r^2 (in0 = p, in1 = q, out0 = x, out1 = r)
 template <typename R>
-struct KCgXR {
+struct KCgXR : VecOp<R> {
+  using AccReal = R;
+  struct Pre {
+    R al;
+  };
+  FG_DEV static Pre pre(const VArgs& a) { return Pre{(R)a.ks->alpha}; }
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
-    const R al = (R)a.ks->alpha;
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre& pr) {
+    const R al = pr.al;
     R* x = (R*)a.out[0];
     R* r = (R*)a.out[1];
     x[i] += al * ((const R*)a.in[0])[i];
     const R rn = r[i] - al * ((const R*)a.in[1])[i];
     r[i] = rn;
-    acc += (double)rn * (double)rn;
+    acc.add(rn * rn);
   }
 };
 
 // p = z + beta p (in0 = z, out0 = p)
 template <typename R>
-struct KCgP {
+struct KCgP : VecOp<R> {
+  using AccReal = R;
+  struct Pre {
+    R beta;
+  };
+  FG_DEV static Pre pre(const VArgs& a) { return Pre{(R)a.ks->beta}; }
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre& pr) {
     R* p = (R*)a.out[0];
-    p[i] = ((const R*)a.in[0])[i] + (R)a.ks->beta * p[i];
+    p[i] = ((const R*)a.in[0])[i] + pr.beta * p[i];
   }
 };
 
 // r = b - q (in0 = b, in1 = q, out0 = r); sum r^2 and b^2 (two passes of partials)
 template <typename R>
-struct KResid {
+struct KResid : VecOp<R> {
+  using AccReal = R;
+  using Pre = typename VecOp<R>::Pre;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
     const R rv = ((const R*)a.in[0])[i] - ((const R*)a.in[1])[i];
     ((R*)a.out[0])[i] = rv;
-    acc += (double)rv * (double)rv;
+    acc.add(rv * rv);
   }
 };
 template <typename R>
-struct KSumSqR {
+struct KSumSqR : VecOp<R> {
+  using AccReal = R;
+  using Pre = typename VecOp<R>::Pre;
   static constexpr bool RED = true;
-  FG_DEV static void apply(const VArgs& a, long long i, double& acc) {
-    const double x = (double)((const R*)a.in[0])[i];
-    acc += x * x;
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>& acc, const Pre&) {
+    const R x = ((const R*)a.in[0])[i];
+    acc.add(x * x);
   }
 };
 template <typename R>
-struct KCopy {
+struct KCopy : VecOp<R> {
+  using AccReal = R;
+  using Pre = typename VecOp<R>::Pre;
   static constexpr bool RED = false;
-  FG_DEV static void apply(const VArgs& a, long long i, double&) {
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
     ((R*)a.out[0])[i] = ((const R*)a.in[0])[i];
   }
 };
@@ -635,6 +664,13 @@ struct FPcgStart {
 // PCG start, after z0 = P r0: rz = t
 struct FPcgRz {
   FG_DEV static void fin(const VArgs& a, double t) { a.ks->rz = t; }
+};
+// after re-projecting the CG residual: rr = rz = |r|^2
+struct FSetResidual {
+  FG_DEV static void fin(const VArgs& a, double t) {
+    a.ks->rr = t;
+    a.ks->rz = t;
+  }
 };
 // store a plain sum into ks->aux
 struct FStore {

@@ -662,6 +662,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
   const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
   int chunk = 4;
+  long long launched = 0;
   while (true) {
     for (int j = 0; j < chunk; ++j) {
       PassArgs<R> a = pbase(c, P, done);
@@ -693,6 +694,13 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
         nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
       }
       fin<FBetaCg>(c, slot, nb, done);
+      if (++launched % 32 == 0) {
+        // every CG vector is compatible in exact arithmetic; re-project r and p so that
+        // roundoff in modes G does not see cannot build up and corrupt <p, K p>
+        nb = op_gres(c, P, P.r, P.r, done);
+        fin<FSetResidual>(c, slot, nb, done);
+        op_gres(c, P, P.p, P.p, done);
+      }
     }
     read_ks(c);
     if (c.ks_host[slot].done) break;
@@ -1007,12 +1015,23 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
                               &s.cg_truncated);
     s.cg_chem += n;
     s.newton_chem += 1;
-    VArgs v = vbase(c, c.V);
-    v.in[0] = P.x;
-    v.out[0] = c.c;
-    launch_vec<KChemUpdate<R>>(v, c.st);
-    fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
-    read_ks(c);
+    // c = c_i + lambda y c_i (1 - c_i): halved (at most 10 times) while it leaves (0, 1)
+    dcopy(c.base, c.c, c.V * sizeof(double), c.st);
+    double lam = 1.0;
+    for (int ls = 0;; ++ls, lam *= 0.5) {
+      VArgs v = vbase(c, c.V);
+      v.in[0] = P.x;
+      v.in[1] = c.base;
+      v.out[0] = c.c;
+      v.s[0] = lam;
+      launch_vec<KChemUpdate<R>>(v, c.st);
+      fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+      read_ks(c);
+      if (!(*c.flags_host & ST_DOMAIN)) break;
+      dzero(c.flags, sizeof(int), c.st);
+      if (ls >= 10) fail(FG_ERR_DOMAIN, "chemistry: c left (0,1) along the whole Newton correction");
+      s.newton_damped += 1;
+    }
     check_flags(c, "chemistry");
     const double rel = sqrt(c.ks_host[KS_MISC].aux) / nct;
     s.err_chem = rel;
