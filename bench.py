@@ -41,9 +41,9 @@ def site_bytes(nx):
 
 
 SITE_NAMES = {0: "mech X-fwd: p = r + beta p, tangent, <p,Kp> (pass_kernel<XFwd<float,N,PCgTangentNH>>)",
-              1: "mech Y-fwd (pass_kernel<YPass<float,N,false>>)",
-              2: "mech Z + projection (pass_kernel<ZPass<float,N,ZProject>>)",
-              3: "mech Y-inv (pass_kernel<YPass<float,N,true>>)",
+              1: "mech Y-fwd (pass_kernel<YPassD<float,N,false>>, register-direct for N = 16^2)",
+              2: "mech Z + projection (pass_kernel<ZPassD<float,N,ZProject>>)",
+              3: "mech Y-inv (pass_kernel<YPassD<float,N,true>>)",
               4: "mech X-inv: r -= alpha q, x += alpha p, |r|^2 (pass_kernel<XInv<float,N,ECgUpdate1,true>> per component, or ECgUpdate)"}
 
 
