@@ -1,0 +1,99 @@
+"""Planted mistakes: each test injects a plausible error into the oracle (a dropped term,
+a wrong sign or index, a transposed operand) and checks that the pins of
+test_oracle_*.py catch it.  All on the CPU; the oracle module is restored afterwards."""
+import numpy as np
+import pytest
+
+from oracle import fg_oracle as O
+from tests import test_oracle_constitutive as TC
+from tests import test_oracle_solvers as TS
+from tests import test_oracle_spectral as TSP
+
+
+def test_projection_without_normalisation_is_caught(monkeypatch):
+    def bad(A, n):  # drops the 1/|n|^2
+        An = np.einsum("im...,m...->i...", A, n)
+        return np.einsum("i...,j...->ij...", An, n)
+    monkeypatch.setattr(O, "project_G", bad)
+    with pytest.raises(AssertionError):
+        TSP.test_projection_properties((4, 6, 8))
+
+
+def test_projection_transposed_is_caught(monkeypatch):
+    good = O.project_G
+
+    def bad(A, n):  # projects columns instead of rows
+        return np.swapaxes(good(np.swapaxes(A, 0, 1), n), 0, 1)
+    monkeypatch.setattr(O, "project_G", bad)
+    with pytest.raises(AssertionError):
+        TSP.test_projection_properties((4, 6, 8))
+
+
+def test_wrong_rotated_symbol_is_caught(monkeypatch):
+    good = O.rotated_frequencies
+
+    def bad(shape, h):  # forgets the cos factor of the other axes (central difference)
+        n = good(shape, h)
+        return n * 0 + O.fd_laplacian_symbol(shape, h)[None] ** 0.5
+    monkeypatch.setattr(O, "rotated_frequencies", bad)
+    with pytest.raises(AssertionError):
+        TSP.test_rotated_symbol_is_corner_stencil((4, 6, 8))
+
+
+def test_tangent_missing_term_is_caught(monkeypatch):
+    good = O.dP0
+
+    def bad(Fe, dFe, prm):  # drops the geometric (dF S) term of both laws
+        out = good(Fe, dFe, prm)
+        return out - 0.01 * dFe * prm.mu
+    monkeypatch.setattr(O, "dP0", bad)
+    with pytest.raises(AssertionError):
+        TC.test_tangent_is_stress_derivative_and_symmetric(O.LAW_NEOHOOKE)
+
+
+def test_swelling_sign_is_caught(monkeypatch):
+    def bad(c, prm):  # J_c = 1 - Omega (c - c0)
+        return 1.0 - prm.Omega * (c - prm.c0)
+    monkeypatch.setattr(O, "swelling_J", bad)
+    with pytest.raises(AssertionError):
+        TC.test_free_swelling_and_degradation(O.LAW_NEOHOOKE)
+
+
+def test_elastic_potential_sign_is_caught(monkeypatch):
+    good = O.mu_elastic
+    monkeypatch.setattr(O, "mu_elastic", lambda F, c, d, prm: -good(F, c, d, prm))
+    with pytest.raises(AssertionError):
+        TC.test_elastic_chemical_potential_is_energy_derivative(O.LAW_NEOHOOKE)
+
+
+def test_divergence_without_conjugate_is_caught(monkeypatch):
+    def bad(u, Kc, prm):  # uses xi instead of conj(xi) for the divergence
+        xi = O.fd_frequencies(prm.shape, prm.h)
+        g = O.irfft3(xi * O.rfft3(u)[None], prm.shape)
+        flux = np.einsum("jl...,l...->j...", Kc, g)
+        return -O.irfft3(np.sum(xi * O.rfft3(flux), axis=0), prm.shape)
+    monkeypatch.setattr(O, "chem_L", bad)
+    with pytest.raises(AssertionError):
+        TS.test_chem_operator_is_divergence_stencil()
+
+
+def test_phase_field_laplacian_sign_is_caught(monkeypatch):
+    def bad(dd, H, prm):
+        lap = O.fd_laplacian_symbol(prm.shape, prm.h)
+        return (prm.gc / prm.lc + 2.0 * H) * dd - O.irfft3(prm.gc * prm.lc * lap * O.rfft3(dd), prm.shape)
+    monkeypatch.setattr(O, "pff_apply", bad)
+    with pytest.raises((AssertionError, FloatingPointError, RuntimeError)):
+        TS.test_pff_1d_crack_discrete_closed_form()
+
+
+def test_mobility_factor_is_caught(monkeypatch):
+    monkeypatch.setattr(O, "mobility_phi", lambda d: (1.0 - d) ** 2)  # drops 0.9 and 0.1 d^2
+    with pytest.raises(AssertionError):
+        TS.test_chem_single_mode_decay()
+
+
+def test_adjoint_sign_is_caught(monkeypatch):
+    good = O.mech_adjoint
+    monkeypatch.setattr(O, "mech_adjoint", lambda *a, **k: -good(*a, **k))
+    with pytest.raises(AssertionError):
+        TS.test_mech_adjoint_matches_central_differences()
