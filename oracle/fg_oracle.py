@@ -369,7 +369,10 @@ def cg(apply, b, tol, maxit, x0=None, stats=None):
 
     Away from equilibrium the mechanical tangent of a prestressed particle in a soft
     buffer is not positive definite; CG then stops at the first search direction of
-    non-positive curvature and returns its current iterate (truncated CG)."""
+    non-positive curvature (truncated CG).  The iterate is saved each time |r|^2 falls to
+    a quarter of the last saved value (the first time: of |b - A x0|^2); a solve that stops
+    early (non-positive curvature or maxit) after saving one returns the saved iterate when
+    its own residual is larger."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply(x) if x0 is not None else b.copy()
     bn = math.sqrt(dot(b, b))
@@ -377,6 +380,7 @@ def cg(apply, b, tol, maxit, x0=None, stats=None):
         return np.zeros_like(b), 0
     p = r.copy()
     rr = dot(r, r)
+    rr_best, x_best = rr, None
     it = 0
     while math.sqrt(rr) > tol * bn and it < maxit:
         q = apply(p)
@@ -394,6 +398,10 @@ def cg(apply, b, tol, maxit, x0=None, stats=None):
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
+        if rr <= 0.25 * rr_best:
+            rr_best, x_best = rr, x.copy()
+    if x_best is not None and math.sqrt(rr) > tol * bn and rr > rr_best:
+        x = x_best
     return x, it
 
 

@@ -18,7 +18,10 @@ struct KScal {
   double tol2;   // tol^2 <b, b>
   double alpha, beta;
   double aux;    // spare sum (mass, norms)
+  double rr_best;  // smallest <r, r> at which the iterate was saved
   int done, iters, maxit, status;
+  int nosnap;      // 0 right after <r, r> fell to a quarter of rr_best (save the iterate)
+  int snaps;       // iterates saved so far
 };
 
 enum : int { ST_OK = 0, ST_INDEFINITE = 1, ST_DOMAIN = 2, ST_NUMERIC = 4 };
@@ -601,6 +604,9 @@ struct FCgStart {
     k->iters = 0;
     k->maxit = (int)a.s[1];
     k->status = 0;
+    k->rr_best = t;
+    k->nosnap = 1;
+    k->snaps = 0;
     k->done = (t == 0.0 || t <= k->tol2) ? 1 : 0;
   }
 };
@@ -626,6 +632,13 @@ struct FBetaCg {
     k->rr = t;
     k->beta = t / k->rz;
     k->rz = t;
+    if (t <= 0.25 * k->rr_best) {  // snapshot the iterate at every 4x drop of |r|^2
+      k->rr_best = t;
+      k->nosnap = 0;
+      k->snaps += 1;
+    } else {
+      k->nosnap = 1;
+    }
     if (!(t == t)) k->status |= ST_NUMERIC;
     if (t <= k->tol2 || k->iters >= k->maxit || !(t == t)) k->done = 1;
   }

@@ -127,6 +127,7 @@ struct Prec {
   R *rs[3] = {}, *rc[3] = {}, *lap[3] = {};
   C* xi[3] = {};
   R *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *z = nullptr;
+  R* xbest = nullptr;  // best-residual CG iterate
   R *state = nullptr, *kc = nullptr, *w = nullptr, *Hr = nullptr, *tmp3 = nullptr;
   const SizeOps<R>*ox = nullptr, *oy = nullptr, *oz = nullptr;
 };
@@ -253,6 +254,7 @@ static void setup_prec(fg_ctx& c, Prec<R>& P, int krylov_comps) {
   P.p = alloc_n<R>(c, n);
   P.q = alloc_n<R>(c, n);
   P.b = alloc_n<R>(c, n);
+  P.xbest = alloc_n<R>(c, n);
   P.z = alloc_n<R>(c, c.V);
   P.kc = alloc_n<R>(c, 6 * c.V);
   P.w = alloc_n<R>(c, c.V);
@@ -583,6 +585,24 @@ static void check_flags(fg_ctx& c, const char* where) {
 
 // ------------------------------------------------------------------ Krylov drivers
 
+// x_best = x when the last finaliser flagged a 4x drop of |r|^2 (kernel skipped otherwise)
+template <typename R>
+static void snap_iterate(fg_ctx& c, Prec<R>& P, long long n, KScal* ks) {
+  VArgs v = vbase(c, n);
+  v.done = &ks->nosnap;
+  v.in[0] = P.x;
+  v.out[0] = P.xbest;
+  launch_vec<KCopy<R>>(v, c.st);
+}
+
+// a solve that stopped early (non-positive curvature or the iteration cap) returns the
+// saved iterate when its own residual is larger: in an indefinite system CG residuals can
+// grow long before a direction of negative curvature shows up
+template <typename R>
+static void keep_best(fg_ctx& c, Prec<R>& P, long long n, const KScal& k) {
+  if (k.rr > k.rr_best) dcopy(P.x, P.xbest, n * sizeof(R), c.st);
+}
+
 // Conjugate gradients on P.b (n elements) from x = 0; result in P.x.  apply(p, q, done)
 // computes q = A p and the partial sums of <p, q>, returning their count.
 template <typename R, class Apply>
@@ -614,6 +634,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
         launch_vec<KCgXR<R>>(u, c.st);
       }
       fin<FBetaCg>(c, slot, VEC_BLOCKS, done);
+      snap_iterate(c, P, n, ks);
       VArgs w = vbase(c, n);
       w.ks = ks;
       w.done = done;
@@ -628,9 +649,10 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   const KScal& k = c.ks_host[slot];
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) {
-    // truncated CG: the iterate before the first direction of non-positive curvature
-    // is kept; with no iterate yet there is nothing to return
+    // truncated CG: the iterate before the first direction of non-positive curvature, or
+    // the saved best-residual iterate; with no iterate yet there is nothing to return
     if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
+    keep_best(c, P, n, k);
     if (truncated) *truncated += 1;
     return k.iters;
   }
@@ -638,6 +660,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
     // an FP32 inner solve of the mixed mode is an inexact Newton step: its iterate is kept
     // and the FP64 outer residual decides; in FP64 mode the cap is an error
     if (!is_mixed(c)) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+    keep_best(c, P, n, k);
     if (truncated) *truncated += 1;
   }
   return k.iters;
@@ -694,6 +717,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
         nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
       }
       fin<FBetaCg>(c, slot, nb, done);
+      snap_iterate(c, P, n, ks);
       if (++launched % 32 == 0) {
         // every CG vector is compatible in exact arithmetic; re-project r and p so that
         // roundoff in modes G does not see cannot build up and corrupt <p, K p>
@@ -710,11 +734,13 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) {
     if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
+    keep_best(c, P, n, k);
     if (truncated) *truncated += 1;
     return k.iters;
   }
   if (k.rr > k.tol2 && k.iters >= maxit) {
     if (!is_mixed(c)) fail(FG_ERR_NOCONV, "mechanical CG hit max_cg");
+    keep_best(c, P, n, k);
     if (truncated) *truncated += 1;  // mixed mode: inexact Newton step, see cg_solve
   }
   return k.iters;

@@ -181,17 +181,20 @@ def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=
 
 
 def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16e-6 / 512,
-                E=15e9, Omega=1.3):
+                E=15e9, vol_change=0.10):
     """2D circular Saint-Venant-Kirchhoff particle with Weibull-type random stiffness
     (Sec. 5.1, Eq. Gumbell): E_i = E log(1/(1 - w_i))^(1/m), w_i ~ U(0, 1), m = 3, carried
     as the per-voxel log-stiffness log_E = log(log(1/(1 - w_i)))/m.  The paper also draws
     a random sigma_max per voxel with the same law; the C ABI takes sigma_max per phase,
-    so this workload keeps it uniform."""
+    so this workload keeps it uniform.  The paper's Omega = 1.3 is not used: with
+    E = 15 GPa the elastic chemical potential reaches several RT and the Newton of Alg. 3,
+    whose Jacobian keeps only the ideal-solution part, stops converging (the oracle fails
+    the same way), so the swelling is the 10 % volume change of the other workloads."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (1, n, n)
     x, y, _ = _grid_coords(shape)
     particle = (x * x + y * y) <= (0.5 * diameter_frac * n) ** 2
-    phases = default_phases(E=E, law=LAW_SVK, vol_change=Omega * (1 - 0.01), buffer_E=1e-5)
+    phases = default_phases(E=E, law=LAW_SVK, vol_change=vol_change, buffer_E=1e-5)
     w = _finish("gumbel_disc", shape, (h, h, h), particle, band, nsteps, 1.0, rng, phases=phases)
     om = rng.uniform(size=shape)
     log_E = np.log(np.log(1.0 / (1.0 - om))) / m

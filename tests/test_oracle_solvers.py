@@ -278,6 +278,33 @@ def test_cg_truncates_at_nonpositive_curvature():
         O.cg(lambda v: -v, b, 1e-12, 10)
 
 
+def test_cg_truncation_returns_saved_iterate():
+    """A truncated solve returns the last iterate saved at a 4x drop of |r|^2 when its own
+    residual has grown since: diag(4, 4, 2, -1), b = (1, 1, 1, 1/2), worked by hand.
+    |r0|^2 = 13/4, b.A.b = 39/4, a0 = 1/3, x1 = b/3, r1 = (-1, -1, 1, 2)/3, |r1|^2 = 7/9
+    <= 13/16 -> saved.  The second step raises |r2|^2 to 40950/361 and the third search
+    direction has non-positive curvature, so the solve stops and returns x1.  With maxit = 2
+    the cap is reached at the same grown residual and x1 comes back as well."""
+    A = np.array([4.0, 4.0, 2.0, -1.0])
+    b = np.array([1.0, 1.0, 1.0, 0.5])
+    r2 = []
+
+    def op(v):
+        return A * v
+    stats = {}
+    x, it = O.cg(op, b, 1e-12, 10, stats=stats)
+    np.testing.assert_allclose(x, b / 3.0, rtol=1e-15)
+    assert it == 2 and stats["cg_truncated"] == 1
+    x, it = O.cg(op, b, 1e-12, 2)
+    np.testing.assert_allclose(x, b / 3.0, rtol=1e-15)
+    # the unguarded second iterate really is worse: its residual is the hand value
+    x1 = b / 3.0
+    r1 = b - A * x1
+    a1 = (r1 @ r1) / ((r1 + (r1 @ r1) / (b @ b) * b) @ (A * (r1 + (r1 @ r1) / (b @ b) * b)))
+    r2.append(r1 - a1 * A * (r1 + (r1 @ r1) / (b @ b) * b))
+    assert abs(r2[0] @ r2[0] - 40950.0 / 361.0) < 1e-9
+
+
 def test_mech_adjoint_matches_central_differences():
     """dL/dlogE of L = <W, F(logE)> at equilibrium, against central differences of the
     converged solve on a few voxels."""
