@@ -212,6 +212,12 @@ class Params:
     h: tuple
     shape: tuple
     extra: dict = field(default_factory=dict)
+    gcr: np.ndarray | None = None  # per-voxel g_c(x) / g_c (None: uniform g_c)
+
+
+def gc_ratio(prm):
+    """g_c(x) / g_c per voxel (ones for a uniform toughness)."""
+    return np.ones(prm.shape) if prm.gcr is None else prm.gcr
 
 
 def lame(E, nu):
@@ -221,8 +227,9 @@ def lame(E, nu):
 
 
 def make_params(phases, phase_id, h, gc, lc, RT=8.314462618 * 298.15, cmax=3.0e4,
-                log_E=None, log_D=None):
-    """Gather per-phase constants onto the voxel grid (optionally times exp(log-field))."""
+                log_E=None, log_D=None, log_gc=None):
+    """Gather per-phase constants onto the voxel grid (optionally times exp(log-field):
+    stiffness E, diffusivity D and toughness g_c(x) = g_c exp(log_gc))."""
     phase_id = np.asarray(phase_id)
     laws = {p.law for p in phases}
     if len(laws) != 1:
@@ -237,7 +244,8 @@ def make_params(phases, phase_id, h, gc, lc, RT=8.314462618 * 298.15, cmax=3.0e4
     lam, mu = lame(E, tab("nu"))
     return Params(law=phases[0].law, lam=lam, mu=mu, Omega=tab("Omega"), c0=tab("c0"), D=D,
                   sigma_max=tab("sigma_max"), gc=float(gc), lc=float(lc), RT=float(RT),
-                  cmax=float(cmax), h=tuple(float(x) for x in h), shape=phase_id.shape)
+                  cmax=float(cmax), h=tuple(float(x) for x in h), shape=phase_id.shape,
+                  gcr=None if log_gc is None else np.exp(np.asarray(log_gc, dtype=float)))
 
 
 # --------------------------------------------------------------------------------------
@@ -351,8 +359,8 @@ def driving_force(F, c, prm):
 
 
 def history_update(H_t, F, c, prm):
-    """H = max(H_t, g_c/(2 l_c) D_f)."""
-    return np.maximum(H_t, prm.gc / (2.0 * prm.lc) * driving_force(F, c, prm))
+    """H = max(H_t, g_c(x)/(2 l_c) D_f)."""
+    return np.maximum(H_t, prm.gc * gc_ratio(prm) / (2.0 * prm.lc) * driving_force(F, c, prm))
 
 
 # --------------------------------------------------------------------------------------
@@ -364,15 +372,17 @@ def dot(a, b):
     return float(np.vdot(a.ravel(), b.ravel()).real)
 
 
-def cg(apply, b, tol, maxit, x0=None, stats=None):
+def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True):
     """Textbook conjugate gradients; stops when ||r|| <= tol ||b||.  Returns (x, iters).
 
-    Away from equilibrium the mechanical tangent of a prestressed particle in a soft
-    buffer is not positive definite; CG then stops at the first search direction of
-    non-positive curvature (truncated CG).  The iterate is saved each time |r|^2 falls to
-    a quarter of the last saved value (the first time: of |b - A x0|^2); a solve that stops
-    early (non-positive curvature or maxit) after saving one returns the saved iterate when
-    its own residual is larger."""
+    Near a prestressed equilibrium the mechanical tangent of a particle in a soft buffer
+    is not always positive definite.  With indefinite=True a direction of negative
+    curvature <p, Ap> < 0 is taken like any other (the Galerkin iterate of the symmetric
+    system exists while <p, Ap> != 0); with indefinite=False CG stops at the first one and
+    keeps its iterate (truncated CG).  <p, Ap> = 0 or a non-finite value always stops.
+    The iterate is saved each time |r|^2 falls to a quarter of the last saved value (the
+    first time: of |b - A x0|^2); a solve that stops early (truncation or maxit) after
+    saving one returns the saved iterate when its own residual is larger."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply(x) if x0 is not None else b.copy()
     bn = math.sqrt(dot(b, b))
@@ -385,7 +395,10 @@ def cg(apply, b, tol, maxit, x0=None, stats=None):
     while math.sqrt(rr) > tol * bn and it < maxit:
         q = apply(p)
         pq = dot(p, q)
-        if not pq > 0.0:
+        if indefinite and pq < 0.0:
+            if stats is not None:
+                stats["cg_negcurv"] = stats.get("cg_negcurv", 0) + 1
+        elif not pq > 0.0:
             if it == 0:
                 raise FloatingPointError("operator not positive along the residual")
             if stats is not None:
@@ -456,7 +469,8 @@ def mech_residual(F, c, d, prm, Fbar):
     return GP, math.sqrt(dot(GP, GP)) / den
 
 
-def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stats=None):
+def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stats=None,
+                indefinite=True):
     """Alg. 1 from the given F (the caller sets F^0 = F_t + dFbar).
 
     Each Newton correction dF is damped, lambda = 1, 1/2, ... (at most 10 halvings),
@@ -470,7 +484,8 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
             return F, err
         if n_newton >= max_newton:
             raise RuntimeError("mechanical Newton did not converge")
-        dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats=stats)
+        dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats=stats,
+                    indefinite=indefinite)
         n_newton += 1
         if stats is not None:
             stats["newton_mech"] = stats.get("newton_mech", 0) + 1
@@ -519,9 +534,13 @@ def pff_precond(r, Hbar, prm):
 
 
 def pff_solve(H, d0, prm, tol, maxit, stats=None):
-    Hbar = float(np.mean(H))
-    d, it = pcg(lambda x: pff_apply(x, H, prm), lambda r: pff_precond(r, Hbar, prm),
-                2.0 * H, tol, maxit, d0)
+    """Alg. 2.  With a per-voxel toughness g_c(x) the strong form
+    g_c(x) (d/l_c - l_c lap d) = 2 (1 - d) H is divided by g_c(x)/g_c, which keeps the
+    symmetric operator of Eq. PFFA with H replaced by H g_c / g_c(x)."""
+    Heff = H / gc_ratio(prm)
+    Hbar = float(np.mean(Heff))
+    d, it = pcg(lambda x: pff_apply(x, Heff, prm), lambda r: pff_precond(r, Hbar, prm),
+                2.0 * Heff, tol, maxit, d0)
     if stats is not None:
         stats["cg_pff"] = stats.get("cg_pff", 0) + it
     return d
@@ -615,6 +634,7 @@ class Tolerances:
     max_cg: int = 5000
     max_chem_newton: int = 50
     max_stag: int = 50
+    cg_indefinite: bool = True
 
 
 class CoupledState:
@@ -654,7 +674,7 @@ class CoupledState:
             if stag >= tol.max_stag:
                 raise RuntimeError("staggered scheme did not converge")
             F, _ = mech_newton(F, c, d, prm, Fbar_new, tol.tol_newton, tol.tol_cg,
-                               tol.max_newton, tol.max_cg, stats)
+                               tol.max_newton, tol.max_cg, stats, tol.cg_indefinite)
             H = history_update(H_t, F, c, prm)
             d = pff_solve(H, d, prm, tol.tol_pff_cg, tol.max_cg, stats)
             stag += 1
@@ -667,6 +687,6 @@ def crack_energy(d, prm, gc_field=None):
     """Fracture energy  sum_voxels g_c (d^2/(2 l_c) + l_c/2 |grad_f d|^2) h^3  (Eq. crack)."""
     xi = fd_frequencies(prm.shape, prm.h)
     g = irfft3(xi * rfft3(d)[None], prm.shape)
-    gc = prm.gc if gc_field is None else gc_field
+    gc = prm.gc * gc_ratio(prm) if gc_field is None else gc_field
     dens = gc * (d * d / (2.0 * prm.lc) + 0.5 * prm.lc * np.sum(g * g, axis=0))
     return float(np.sum(dens) * prm.h[0] * prm.h[1] * prm.h[2])

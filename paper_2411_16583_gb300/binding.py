@@ -47,14 +47,15 @@ class Opts(C.Structure):
                 ("tol_cg", C.c_double), ("tol_chem", C.c_double), ("tol_chem_cg", C.c_double),
                 ("tol_pff_cg", C.c_double), ("tol_stag", C.c_double), ("cg_forcing", C.c_double),
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
-                ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double)]
+                ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double),
+                ("cg_indefinite", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("newton_chem", C.c_int), ("newton_mech", C.c_int), ("cg_chem", C.c_int),
                 ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
                 ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("newton_damped", C.c_int),
-                ("err_mech", C.c_double), ("err_chem", C.c_double),
+                ("cg_negcurv", C.c_int), ("err_mech", C.c_double), ("err_chem", C.c_double),
                 ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
 
     def as_dict(self):

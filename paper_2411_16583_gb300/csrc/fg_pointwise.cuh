@@ -22,6 +22,8 @@ struct KScal {
   int done, iters, maxit, status;
   int nosnap;      // 0 right after <r, r> fell to a quarter of rr_best (save the iterate)
   int snaps;       // iterates saved so far
+  int indef;       // 1: continue through directions of negative curvature (Galerkin iterates)
+  int negc;        // directions of negative curvature met
 };
 
 enum : int { ST_OK = 0, ST_INDEFINITE = 1, ST_DOMAIN = 2, ST_NUMERIC = 4 };
@@ -607,14 +609,23 @@ struct FCgStart {
     k->rr_best = t;
     k->nosnap = 1;
     k->snaps = 0;
+    k->indef = (int)a.s[2];
+    k->negc = 0;
     k->done = (t == 0.0 || t <= k->tol2) ? 1 : 0;
   }
 };
-// alpha = rz / <p, Ap>
+// alpha = rz / <p, Ap>.  A direction of negative curvature either ends the solve
+// (truncated CG) or, with indef set, is taken like any other: the Galerkin iterate exists
+// whenever <p, Ap> != 0; only <p, Ap> = 0 or a non-finite value stops the solve.
 struct FAlpha {
   FG_DEV static void fin(const VArgs& a, double t) {
     KScal* k = a.ks;
     k->pq = t;
+    if (k->indef && t < 0.0) {
+      k->negc += 1;
+      k->alpha = k->rz / t;
+      return;
+    }
     if (!(t > 0.0)) {
       k->status |= ST_INDEFINITE;
       k->done = 1;
@@ -671,6 +682,8 @@ struct FPcgStart {
     k->iters = 0;
     k->maxit = (int)a.s[2];
     k->status = 0;
+    k->indef = 0;
+    k->negc = 0;
     k->done = (a.s[1] == 0.0 || t <= k->tol2) ? 1 : 0;
   }
 };

@@ -605,9 +605,11 @@ static void keep_best(fg_ctx& c, Prec<R>& P, long long n, const KScal& k) {
 
 // Conjugate gradients on P.b (n elements) from x = 0; result in P.x.  apply(p, q, done)
 // computes q = A p and the partial sums of <p, q>, returning their count.
+// Early stops and directions of negative curvature are counted into st (may be null).
 template <typename R, class Apply>
 static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, int maxit, Apply apply,
-                    int* truncated = nullptr) {
+                    fg_stats* st = nullptr) {
+  int* truncated = st ? &st->cg_truncated : nullptr;
   KScal* ks = c.ks + slot;
   VArgs v = vbase(c, n);
   v.in[0] = P.b;
@@ -615,7 +617,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   v.out[1] = P.r;
   v.out[2] = P.p;
   launch_vec<KCgInit<R>>(v, c.st);
-  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)c.o.cg_indefinite);
   const int* done = &ks->done;
   int chunk = 4;
   while (true) {
@@ -647,6 +649,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
     if (chunk < 16) chunk *= 2;
   }
   const KScal& k = c.ks_host[slot];
+  if (st) st->cg_negcurv += k.negc;
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) {
     // truncated CG: the iterate before the first direction of non-positive curvature, or
@@ -670,7 +673,8 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
 // operator passes: X-fwd forms p = r + beta p and <p, K p>, X-inv applies r -= alpha q,
 // x += alpha p and sums |r|^2.  Per iteration: 5 passes + 2 single-block finalisers.
 template <typename R>
-static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* truncated) {
+static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats* st) {
+  int* truncated = st ? &st->cg_truncated : nullptr;
   const long long n = 9 * c.V;
   const int slot = KS_MECH;
   KScal* ks = c.ks + slot;
@@ -680,7 +684,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
   v.out[1] = P.r;
   v.out[2] = P.p;
   launch_vec<KCgInit<R>>(v, c.st);
-  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)c.o.cg_indefinite);
   const int* done = &ks->done;
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
   const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
@@ -731,6 +735,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, int* trun
     if (chunk < 16) chunk *= 2;
   }
   const KScal& k = c.ks_host[slot];
+  if (st) st->cg_negcurv += k.negc;
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) {
     if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
@@ -860,13 +865,13 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
     if (err <= c.o.tol_newton) return;
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
     to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
-    const int n = cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s.cg_truncated);
+    const int n = cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s);
     s.cg_mech += n;
     s.newton_mech += 1;
     if (verbose())
-      fprintf(stderr, "[fg] newton %d err %.3e cg %d rr/bb %.3e status %d\n", it, err, n,
-              c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
-              c.ks_host[KS_MECH].status);
+      fprintf(stderr, "[fg] newton %d err %.3e cg %d rr/bb %.3e status %d negc %d snaps %d\n", it,
+              err, n, c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
+              c.ks_host[KS_MECH].status, c.ks_host[KS_MECH].negc, c.ks_host[KS_MECH].snaps);
     const double* dF;
     if (is_mixed(c)) {
       // FP32 roundoff leaves traces of the correction in modes G never sees (the mean and
@@ -1038,7 +1043,7 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
     if (is_mixed(c)) to_prec<R>(c, b64, P.b, c.V, 1.0);
     const int n = cg_solve<R>(c, P, c.V, KS_CHEM, mixed_tol(c, c.o.tol_chem_cg), c.o.max_cg,
                               [&](const R* p, R* q, const int* done) { return op_chem(c, P, p, q, dt, done); },
-                              &s.cg_truncated);
+                              &s);
     s.cg_chem += n;
     s.newton_chem += 1;
     // c = c_i + lambda y c_i (1 - c_i): halved (at most 10 times) while it leaves (0, 1)
@@ -1201,6 +1206,7 @@ void fg_default_opts(fg_opts* o) {
   o->max_chem_newton = 50;
   o->max_stag = 50;
   o->cuda_stream = nullptr;
+  o->cg_indefinite = 1;
 }
 
 int fg_supported_size(int n) {
@@ -1249,6 +1255,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   else fg_default_opts(&o);
   if (o.precision != FG_FP64 && o.precision != FG_MIXED) fail(FG_ERR_INVALID, "fg_setup: precision");
   if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
+  if (o.cg_indefinite != 0 && o.cg_indefinite != 1) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;

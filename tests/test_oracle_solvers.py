@@ -271,11 +271,25 @@ def test_cg_truncates_at_nonpositive_curvature():
     A = np.array([3.0, 1.0, -2.0])
     b = np.ones(3)
     stats = {}
-    x, it = O.cg(lambda v: A * v, b, 1e-12, 10, stats=stats)
+    x, it = O.cg(lambda v: A * v, b, 1e-12, 10, stats=stats, indefinite=False)
     np.testing.assert_allclose(x, 1.5 * b, rtol=1e-15)
     assert it == 1 and stats["cg_truncated"] == 1
     with pytest.raises(FloatingPointError):
-        O.cg(lambda v: -v, b, 1e-12, 10)
+        O.cg(lambda v: -v, b, 1e-12, 10, indefinite=False)
+
+
+def test_cg_continues_through_negative_curvature():
+    """Taking the direction of negative curvature of the example above, CG reaches the
+    exact solution of the 3x3 indefinite system in 3 steps, as it does for any symmetric
+    system with 3 distinct eigenvalues while no <p, Ap> vanishes: x = (1/3, 1, -1/2).
+    A vanishing <p, Ap> stops it: diag(1, -1) with b = (1, 1) has <b, Ab> = 0."""
+    A = np.array([3.0, 1.0, -2.0])
+    stats = {}
+    x, it = O.cg(lambda v: A * v, np.ones(3), 1e-12, 10, stats=stats)
+    np.testing.assert_allclose(x, [1.0 / 3.0, 1.0, -0.5], rtol=1e-13)
+    assert it == 3 and stats["cg_negcurv"] >= 1 and "cg_truncated" not in stats
+    with pytest.raises(FloatingPointError):
+        O.cg(lambda v: np.array([1.0, -1.0]) * v, np.ones(2), 1e-12, 10)
 
 
 def test_cg_truncation_returns_saved_iterate():
@@ -292,7 +306,7 @@ def test_cg_truncation_returns_saved_iterate():
     def op(v):
         return A * v
     stats = {}
-    x, it = O.cg(op, b, 1e-12, 10, stats=stats)
+    x, it = O.cg(op, b, 1e-12, 10, stats=stats, indefinite=False)
     np.testing.assert_allclose(x, b / 3.0, rtol=1e-15)
     assert it == 2 and stats["cg_truncated"] == 1
     x, it = O.cg(op, b, 1e-12, 2)
