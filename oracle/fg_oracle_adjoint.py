@@ -12,9 +12,10 @@ One converged step maps the state (c_t, F_t, d_t, H_t) to (c, F, d, H) through
   phase      (g_c/l_c + 2 r H) d - g_c l_c lap d - 2 r H = 0,  r = g_c/g_c(x)   (Eq. PFFA).
 The reverse step takes the seeds dL/d(c, F, d, H) of the outputs and returns the seeds of
 the inputs plus dL/d(log E, log g_c, log D) per voxel:
-  * the (F, H, d) block by transposed block Gauss-Seidel (G K G and the phase-field
-    operator are symmetric; the couplings are dP/dd and dpsi/dF on the active branch
-    chi = [psi > H_t] of the max),
+  * the (F, H, d) block by transposed block Gauss-Seidel sweeps (G K G and the
+    phase-field operator are symmetric; the couplings are dP/dd and dpsi/dF on the active
+    branch chi = [psi > H_t] of the max), accelerated by GMRES on the phase-field
+    multiplier,
   * the chemistry by its exact Jacobian transpose I + dt M L with M = dmu~/dc, solved
     as the symmetric system (M^-1 + dt L) y = M^-1 g (the forward Newton of Alg. 3 uses
     only the ideal part of M; its root is the same).
@@ -129,6 +130,30 @@ def fd_divergence_adj(f, prm):
     return O.irfft3(np.sum(np.conj(xi) * O.rfft3(f), axis=0), prm.shape)
 
 
+def gmres(apply, b, tol, maxit):
+    """Unrestarted GMRES from x = 0 (Arnoldi with modified Gram-Schmidt, the small least
+    squares problem solved by numpy) until ||b - A x|| <= tol ||b||.  Returns (x, iters)."""
+    beta = math.sqrt(O.dot(b, b))
+    if beta == 0.0:
+        return np.zeros_like(b), 0
+    Q = [b / beta]
+    Hm = np.zeros((maxit + 1, maxit))
+    for k in range(maxit):
+        w = apply(Q[k])
+        for j in range(k + 1):
+            Hm[j, k] = O.dot(Q[j], w)
+            w = w - Hm[j, k] * Q[j]
+        Hm[k + 1, k] = math.sqrt(O.dot(w, w))
+        e1 = np.zeros(k + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(Hm[:k + 2, :k + 1], e1, rcond=None)[0]
+        res = np.linalg.norm(Hm[:k + 2, :k + 1] @ y - e1)
+        if res <= tol * beta or Hm[k + 1, k] == 0.0:
+            return sum(y[j] * Q[j] for j in range(k + 1)), k + 1
+        Q.append(w / Hm[k + 1, k])
+    raise RuntimeError("GMRES did not converge")
+
+
 # --------------------------------------------------------------------------------------
 # Trajectory and reverse step
 # --------------------------------------------------------------------------------------
@@ -193,23 +218,27 @@ def step_adjoint(prm, s_in, s_out, dt, seeds, tol, stats=None):
             stats["cg_pff"] = stats.get("cg_pff", 0) + it
         return lam
 
-    lamH = seeds["H"].copy()
-    lamD_old = None
-    for sweep in range(tol.max_stag + 1):
-        lamM = solve_M(seeds["F"] + chi * lamH * Z)
-        lamD = solve_D(seeds["d"] - O.ddot(Pd, lamM))
-        lamH = seeds["H"] + 2.0 * r * (1.0 - d) * lamD
-        if stats is not None:
-            stats["sweeps"] = stats.get("sweeps", 0) + 1
-        if not chi.any():
-            break  # lamM does not depend on lamH: one sweep is exact
-        if lamD_old is not None:
-            dn = math.sqrt(O.dot(lamD - lamD_old, lamD - lamD_old))
-            if dn <= tol.tol_stag * max(math.sqrt(O.dot(lamD, lamD)), 1e-300):
-                break
-        lamD_old = lamD
-    else:
-        raise RuntimeError("adjoint Gauss-Seidel did not converge")
+    def sweep(seedF, seedD, lamH):
+        lamM = solve_M(seedF + chi * lamH * Z)
+        return lamM, solve_D(seedD - O.ddot(Pd, lamM))
+
+    # lamD = lamD0 + T lamD with T x = sweep(0, 0, 2 r (1-d) x): one transposed
+    # Gauss-Seidel sweep is lamD0, and GMRES solves (I - T) lamD = lamD0 (T has rank at most
+    # the number of voxels on the active branch of the history)
+    lamM, lamD = sweep(seeds["F"], seeds["d"], seeds["H"])
+    if stats is not None:
+        stats["sweeps"] = stats.get("sweeps", 0) + 1
+    if chi.any():
+        zF = np.zeros_like(seeds["F"])
+        zD = np.zeros_like(seeds["d"])
+
+        def IminusT(x):
+            if stats is not None:
+                stats["sweeps"] = stats.get("sweeps", 0) + 1
+            return x - sweep(zF, zD, 2.0 * r * (1.0 - d) * x)[1]
+        lamD, _ = gmres(IminusT, lamD, tol.tol_stag, tol.max_stag)
+        lamM = solve_M(seeds["F"] + chi * (seeds["H"] + 2.0 * r * (1.0 - d) * lamD) * Z)
+    lamH = seeds["H"] + 2.0 * r * (1.0 - d) * lamD
 
     P = O.stress(F, c, d, prm)
     gE = -O.ddot(lamM, P) + chi * lamH * psi_E
