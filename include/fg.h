@@ -92,10 +92,16 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t, NULL for the legacy default stream */
   double l2_fraction; /* share of L2 one chunk of kx planes of the spectrum may take
                          between the Y and Z passes (0 or >= 1: no chunking) */
-  int cg_indefinite;  /* a CG direction of negative curvature <p, A p> < 0:
-                         1 = take it (the Galerkin iterate of the symmetric Newton system
-                         exists; default), 0 = stop there and keep the iterate (truncated
-                         CG).  <p, A p> = 0 or a non-finite value always stops the solve */
+  int cg_indefinite;  /* a CG direction p of negative curvature <p, A p> < 0 in the
+                         mechanical Newton system A dF = -G P:
+                         2 = shift (default): solve again with A + sigma I,
+                             sigma = 2 (sigma + |<p, (A + sigma) p>| / |p|^2), that
+                             quotient at least 1e-6 of <b, A b> / |b|^2, until no such
+                             direction is met; sigma shrinks 4-fold per Newton iteration
+                             (Levenberg-Marquardt-type Newton),
+                         1 = take it (the Galerkin iterate exists while <p, A p> != 0),
+                         0 = stop there and keep the iterate (truncated CG).
+                         <p, A p> = 0 or a non-finite value always stops a solve */
 } fg_opts;
 
 typedef struct {
@@ -104,7 +110,8 @@ typedef struct {
   int cg_truncated;   /* Krylov solves stopped early: mechanical CG at non-positive
                          curvature, or an FP32 inner solve of the mixed mode at max_cg */
   int newton_damped;  /* halvings of mechanical Newton corrections */
-  int cg_negcurv;     /* CG directions of negative curvature met */
+  int cg_negcurv;     /* CG directions of negative curvature taken (cg_indefinite 1) */
+  int newton_shifted; /* mechanical Newton systems solved again with a larger shift */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */
@@ -116,7 +123,7 @@ typedef struct fg_ctx fg_ctx;
 
 /* Default options: FP64, gc = 1, lc = 2e-7, RT = 8.314462618 * 298.15, cmax = 3e4,
  * tolerances 1e-9 (Newton, chem, staggered) and 1e-10 (Krylov), cg_forcing 1e-5,
- * caps 30 / 5000 / 50 / 50, no L2 chunking, cg_indefinite 1. */
+ * caps 30 / 5000 / 50 / 50, no L2 chunking, cg_indefinite 2. */
 void fg_default_opts(fg_opts* o);
 
 /* 1 when the transform length n is compiled in, else 0. */

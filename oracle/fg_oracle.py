@@ -372,7 +372,7 @@ def dot(a, b):
     return float(np.vdot(a.ravel(), b.ravel()).real)
 
 
-def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True):
+def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True, info=None):
     """Textbook conjugate gradients; stops when ||r|| <= tol ||b||.  Returns (x, iters).
 
     Near a prestressed equilibrium the mechanical tangent of a particle in a soft buffer
@@ -382,7 +382,9 @@ def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True):
     keeps its iterate (truncated CG).  <p, Ap> = 0 or a non-finite value always stops.
     The iterate is saved each time |r|^2 falls to a quarter of the last saved value (the
     first time: of |b - A x0|^2); a solve that stops early (truncation or maxit) after
-    saving one returns the saved iterate when its own residual is larger."""
+    saving one returns the saved iterate when its own residual is larger.  With an `info`
+    dict a stop at non-positive curvature returns at once and leaves in info the Rayleigh
+    quotients rq = <p, Ap>/|p|^2 of that direction and rq0 = <b, Ab>/|b|^2."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - apply(x) if x0 is not None else b.copy()
     bn = math.sqrt(dot(b, b))
@@ -392,9 +394,16 @@ def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True):
     rr = dot(r, r)
     rr_best, x_best = rr, None
     it = 0
+    rq0 = None
     while math.sqrt(rr) > tol * bn and it < maxit:
         q = apply(p)
         pq = dot(p, q)
+        if rq0 is None:
+            rq0 = pq / dot(p, p)
+        if info is not None and not pq > 0.0 and not (indefinite and pq < 0.0):
+            info["rq"] = pq / dot(p, p)
+            info["rq0"] = rq0
+            return x, it
         if indefinite and pq < 0.0:
             if stats is not None:
                 stats["cg_negcurv"] = stats.get("cg_negcurv", 0) + 1
@@ -416,6 +425,28 @@ def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True):
     if x_best is not None and math.sqrt(rr) > tol * bn and rr > rr_best:
         x = x_best
     return x, it
+
+
+def shifted_cg(apply, b, tol, maxit, stats=None):
+    """CG on the Newton system, shifted where it is not positive definite: a solve that
+    meets a direction p with <p, (A + sigma) p> <= 0 sets sigma to 2 (sigma + |rq|), rq
+    its Rayleigh quotient (|rq| at least 1e-6 |<b, Ab>|/|b|^2), and starts again from
+    zero, until a solve meets none (at most 13 solves).  A Rayleigh quotient only bounds
+    the lowest eigenvalue from above, so the shift grows geometrically instead of
+    stopping just above it, where the system would be nearly singular.
+    Returns (x, iterations, sigma)."""
+    sigma, its = 0.0, 0
+    for _ in range(13):
+        info = {}
+        x, it = cg(lambda v: apply(v) + sigma * v, b, tol, maxit, stats=stats,
+                   indefinite=False, info=info)
+        its += it
+        if "rq" not in info:
+            return x, its, sigma
+        sigma = 2.0 * (sigma + max(abs(info["rq"]), 1e-6 * abs(info["rq0"])))
+        if stats is not None:
+            stats["newton_shifted"] = stats.get("newton_shifted", 0) + 1
+    raise FloatingPointError("shifted system still not positive")
 
 
 def pcg(apply, precond, b, tol, maxit, x0):
@@ -470,12 +501,17 @@ def mech_residual(F, c, d, prm, Fbar):
 
 
 def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stats=None,
-                indefinite=True):
+                indefinite=2):
     """Alg. 1 from the given F (the caller sets F^0 = F_t + dFbar).
+
+    indefinite selects what a CG direction of negative curvature does: 2 = the shifted
+    re-solve of shifted_cg, with the shift of the previous Newton iteration divided by 4 as
+    the starting shift; 1 = CG takes it; 0 = truncated CG.
 
     Each Newton correction dF is damped, lambda = 1, 1/2, ... (at most 10 halvings),
     until F + lambda dF stays in the domain (det F > 0, J_c > 0) and lowers err_res."""
     n_newton = 0
+    sigma = 0.0
     GP, err = mech_residual(F, c, d, prm, Fbar)
     while True:
         if stats is not None:
@@ -484,8 +520,14 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
             return F, err
         if n_newton >= max_newton:
             raise RuntimeError("mechanical Newton did not converge")
-        dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats=stats,
-                    indefinite=indefinite)
+        if indefinite == 2:
+            s0 = sigma / 4.0
+            dF, it, sigma = shifted_cg(lambda x: mech_apply(F, c, d, prm, x) + s0 * x, -GP,
+                                       tol_cg, max_cg, stats)
+            sigma += s0
+        else:
+            dF, it = cg(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg,
+                        stats=stats, indefinite=bool(indefinite))
         n_newton += 1
         if stats is not None:
             stats["newton_mech"] = stats.get("newton_mech", 0) + 1
@@ -634,7 +676,7 @@ class Tolerances:
     max_cg: int = 5000
     max_chem_newton: int = 50
     max_stag: int = 50
-    cg_indefinite: bool = True
+    cg_indefinite: int = 2
 
 
 class CoupledState:

@@ -174,8 +174,9 @@ struct PCgTangentSVK {
     tangent_svk(a.aux[0], V, v, p, out);
 #pragma unroll
     for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
+    const R sig = a.coef[1];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc.add(p[c] * out[c]);
+    for (int c = 0; c < 9; ++c) acc.add(p[c] * (out[c] + sig * p[c]));
   }
 };
 
@@ -198,7 +199,8 @@ struct PTangentNH {
 //   p = r + beta p  (written back, in place),  tau = K : p,  accumulates <p, K p>.
 // For a compatible p (every CG direction is a combination of projected fields)
 // <p, K p> = <p, G K p>, so the step length is known before the inverse transform.
-// rin = r, rout = p, aux0 = packed state, dscal[1] = beta.
+// A shifted system (G K G + sigma I) adds sigma |p|^2.
+// rin = r, rout = p, aux0 = packed state, dscal[1] = beta, coef[1] = sigma.
 template <typename R>
 struct PCgTangentNH {
   static constexpr int COUT = 9;
@@ -219,15 +221,17 @@ struct PCgTangentNH {
 #pragma unroll
     for (int c = 0; c < 9; ++c) pp[c * V + v] = p[c];
     tangent_nh(B, s1, s2, s3, p, out);
+    const R sig = a.coef[1];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc.add(p[c] * out[c]);
+    for (int c = 0; c < 9; ++c) acc.add(p[c] * (out[c] + sig * p[c]));
   }
 };
 
 // ================================================================== X-inv epilogues
 
 // One component of the fused CG update (pointers already shifted to the component):
-// r -= alpha q, x += alpha p; accumulates r^2.  rout = r, rout2 = x, aux0 = p.
+// r -= alpha (q + sigma p), x += alpha p; accumulates r^2.  rout = r, rout2 = x, aux0 = p,
+// coef[1] = sigma (0 unless the system is shifted).
 template <typename R>
 struct ECgUpdate1 {
   static constexpr int CIN = 1;
@@ -238,7 +242,7 @@ struct ECgUpdate1 {
     R* __restrict__ x = a.rout2;
     const R* __restrict__ p = a.aux[0];
     const R r0 = r[v], x0 = x[v], p0 = p[v];  // loads before stores
-    const R rn = r0 - al * val[0];
+    const R rn = r0 - al * (val[0] + a.coef[1] * p0);
     r[v] = rn;
     x[v] = x0 + al * p0;
     acc.add(rn * rn);
@@ -246,20 +250,22 @@ struct ECgUpdate1 {
 };
 
 // Conjugate-gradient update fused with the inverse transform (mechanical CG): with
-// q = G K p arriving as `val`, r -= alpha q and x += alpha p; accumulates <r, r>.
-// rout = r, rout2 = x, aux0 = p, dscal[0] = alpha.
+// q = G K p arriving as `val`, r -= alpha (q + sigma p) and x += alpha p; accumulates
+// <r, r>.  rout = r, rout2 = x, aux0 = p, dscal[0] = alpha, coef[1] = sigma.
 template <typename R>
 struct ECgUpdate {
   static constexpr int CIN = 9;
   static constexpr bool RED = true;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R al = sc[0];
+    const R sig = a.coef[1];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const long long i = c * a.V + v;
-      const R rn = a.rout[i] - al * val[c];
+      const R pc = a.aux[0][i];
+      const R rn = a.rout[i] - al * (val[c] + sig * pc);
       a.rout[i] = rn;
-      a.rout2[i] += al * a.aux[0][i];
+      a.rout2[i] += al * pc;
       acc.add(rn * rn);
     }
   }

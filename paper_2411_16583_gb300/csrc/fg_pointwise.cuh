@@ -19,6 +19,7 @@ struct KScal {
   double alpha, beta;
   double aux;    // spare sum (mass, norms)
   double rr_best;  // smallest <r, r> at which the iterate was saved
+  double pq0;      // <p, A p> of the first direction (p = b)
   int done, iters, maxit, status;
   int nosnap;      // 0 right after <r, r> fell to a quarter of rr_best (save the iterate)
   int snaps;       // iterates saved so far
@@ -621,6 +622,7 @@ struct FAlpha {
   FG_DEV static void fin(const VArgs& a, double t) {
     KScal* k = a.ks;
     k->pq = t;
+    if (k->iters == 0) k->pq0 = t;
     if (k->indef && t < 0.0) {
       k->negc += 1;
       k->alpha = k->rz / t;

@@ -344,6 +344,17 @@ static double reduce_sum(fg_ctx& c, const double* x, long long n, bool sq) {
   return c.ks_host[KS_MISC].aux;
 }
 
+// |x|^2 of a vector of precision R
+template <typename R>
+static double reduce_sum_r(fg_ctx& c, const R* x, long long n) {
+  VArgs v = vbase(c, n);
+  v.in[0] = x;
+  launch_vec<KSumSqR<R>>(v, c.st);
+  fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+  read_ks(c);
+  return c.ks_host[KS_MISC].aux;
+}
+
 template <typename R>
 static PassArgs<R> pbase(fg_ctx& c, Prec<R>& P, const int* done) {
   PassArgs<R> a{};
@@ -617,7 +628,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   v.out[1] = P.r;
   v.out[2] = P.p;
   launch_vec<KCgInit<R>>(v, c.st);
-  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)c.o.cg_indefinite);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)(c.o.cg_indefinite == 1));
   const int* done = &ks->done;
   int chunk = 4;
   while (true) {
@@ -672,8 +683,12 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
 // Mechanical CG (Alg. 1) on P.b from x = 0 with the vector updates fused into the
 // operator passes: X-fwd forms p = r + beta p and <p, K p>, X-inv applies r -= alpha q,
 // x += alpha p and sums |r|^2.  Per iteration: 5 passes + 2 single-block finalisers.
+// sigma shifts the system to G K G + sigma I.  With negcurv != null a direction of negative
+// curvature ends the solve without keeping an iterate: *negcurv is set and the caller
+// re-solves (the shifted Newton of mech_newton); P.p then holds that direction.
 template <typename R>
-static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats* st) {
+static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats* st, double sigma = 0.0,
+                         bool* negcurv = nullptr) {
   int* truncated = st ? &st->cg_truncated : nullptr;
   const long long n = 9 * c.V;
   const int slot = KS_MECH;
@@ -684,7 +699,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
   v.out[1] = P.r;
   v.out[2] = P.p;
   launch_vec<KCgInit<R>>(v, c.st);
-  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)c.o.cg_indefinite);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)(c.o.cg_indefinite == 1));
   const int* done = &ks->done;
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
   const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
@@ -698,6 +713,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
       a.rout = P.p;
       a.aux[0] = P.state;
       a.dscal = sc;
+      a.coef[1] = (R)sigma;
       a.cout = P.S1;
       int nb;
       {
@@ -716,6 +732,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
       a.rout2 = P.x;
       a.aux[0] = P.p;
       a.dscal = sc;
+      a.coef[1] = (R)sigma;
       {
         ProfScope ps(c, SITE_XI);
         nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
@@ -738,6 +755,10 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
   if (st) st->cg_negcurv += k.negc;
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) {
+    if (negcurv) {
+      *negcurv = true;
+      return k.iters;
+    }
     if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
     keep_best(c, P, n, k);
     if (truncated) *truncated += 1;
@@ -856,16 +877,41 @@ static double residual_mech(fg_ctx& c, double den, R* state) {
 // Alg. 1 from the current F.  Each Newton correction is damped by halving (at most 10
 // times) while F + lambda dF leaves the domain (det F <= 0 or J_c <= 0) or does not lower
 // err_res; the residual of the accepted iterate is the next iteration's residual.
+// With cg_indefinite == 2 a Newton system met with negative curvature is shifted,
+// (G K G + sigma I) dF = -G P, sigma found as in the loop below; sigma shrinks 4-fold after
+// each Newton iteration, so near a stable equilibrium the iteration is plain Newton again.
 template <typename R>
 static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
   double err = residual_mech<R>(c, den, P.state);
-  for (int it = 0;; ++it) {
+  double sigma = 0.0;
+  for (int it = 0;; ++it, sigma *= 0.25) {
     s.err_mech = err;
     if (!(err == err)) fail(FG_ERR_NUMERIC, "mechanical residual is not finite");
     if (err <= c.o.tol_newton) return;
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
     to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
-    const int n = cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s);
+    int n = 0;
+    for (int rs = 0;; ++rs) {
+      bool neg = false;
+      n += cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s, sigma,
+                            c.o.cg_indefinite == 2 ? &neg : nullptr);
+      if (!neg) break;
+      // shifted Newton: the direction p of negative curvature has Rayleigh quotient
+      // lam = <p, (A + sigma) p> / |p|^2 <= 0; sigma = 2 (sigma + |lam|), |lam| at least
+      // 1e-6 of the Rayleigh quotient of the right-hand side, and solve again from zero
+      // (a Rayleigh quotient only bounds the lowest eigenvalue from above: the geometric
+      // growth keeps the shifted system away from singular)
+      const KScal k = c.ks_host[KS_MECH];
+      const double pp = reduce_sum_r<R>(c, P.p, 9 * c.V);
+      const double lam = pp > 0.0 ? k.pq / pp : 0.0;
+      const double rho0 = k.bb > 0.0 ? fabs(k.pq0) / k.bb : 0.0;
+      sigma = 2.0 * (sigma + std::max(fabs(lam), 1e-6 * rho0));
+      s.newton_shifted += 1;
+      if (verbose())
+        fprintf(stderr, "[fg]   negative curvature at cg %d (lam %.3e): sigma %.3e\n", k.iters, lam, sigma);
+      if (!(sigma == sigma) || sigma <= 0.0 || rs >= 12)
+        fail(FG_ERR_NUMERIC, "mechanical Newton: shifted system still not positive");
+    }
     s.cg_mech += n;
     s.newton_mech += 1;
     if (verbose())
@@ -1206,7 +1252,7 @@ void fg_default_opts(fg_opts* o) {
   o->max_chem_newton = 50;
   o->max_stag = 50;
   o->cuda_stream = nullptr;
-  o->cg_indefinite = 1;
+  o->cg_indefinite = 2;
 }
 
 int fg_supported_size(int n) {
@@ -1255,7 +1301,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   else fg_default_opts(&o);
   if (o.precision != FG_FP64 && o.precision != FG_MIXED) fail(FG_ERR_INVALID, "fg_setup: precision");
   if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
-  if (o.cg_indefinite != 0 && o.cg_indefinite != 1) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
+  if (o.cg_indefinite < 0 || o.cg_indefinite > 2) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;

@@ -266,8 +266,8 @@ def test_cg_truncates_at_nonpositive_curvature():
     """On an indefinite operator CG returns the iterate before the first search direction
     of non-positive curvature: here diag(3, 1, -2) with b = (1, 1, 1), worked by hand.
     x1 = a0 b, a0 = b.b / b.A.b = 3/2; r1 = b - a0 A b = (-7/2, -1/2, 4);
-    p1 = r1 + (r1.r1 / b.b) p0 = r1 + (33/2)/3 b = (2, 5, 19/2);
-    p1.A.p1 = 12 + 25 - 180.5 < 0  ->  stop with x = x1."""
+    p1 = r1 + (r1.r1 / b.b) p0 = r1 + (57/2)/3 b = (6, 9, 27/2);
+    p1.A.p1 = 108 + 81 - 364.5 < 0  ->  stop with x = x1."""
     A = np.array([3.0, 1.0, -2.0])
     b = np.ones(3)
     stats = {}
@@ -290,6 +290,26 @@ def test_cg_continues_through_negative_curvature():
     assert it == 3 and stats["cg_negcurv"] >= 1 and "cg_truncated" not in stats
     with pytest.raises(FloatingPointError):
         O.cg(lambda v: np.array([1.0, -1.0]) * v, np.ones(2), 1e-12, 10)
+
+
+def test_shifted_cg_on_indefinite_system():
+    """The shifted re-solve of the mechanical Newton, worked in exact fractions on
+    diag(3, 1, -2), b = (1, 1, 1).  Solve 1 (sigma = 0) meets p1 = (6, 9, 27/2) with
+    Rayleigh quotient rq = -175.5 / 299.25 = -78/133, so sigma = 2 * 78/133 = 156/133.
+    Solve 2 meets p1 = (-2793, 143640, 726579/2) / 134689 with rq = -11307270/26842459, so
+    sigma = 2 (156/133 + 11307270/26842459) = 12226188/3834637; A + sigma I is then
+    positive definite and solve 3 returns x_i = 1 / (a_i + sigma)."""
+    A = np.array([3.0, 1.0, -2.0])
+    stats = {}
+    x, it, sigma = O.shifted_cg(lambda v: A * v, np.ones(3), 1e-13, 10, stats)
+    s_hand = 12226188.0 / 3834637.0
+    assert abs(sigma - s_hand) < 1e-13 * s_hand
+    np.testing.assert_allclose(x, 1.0 / (A + s_hand), rtol=1e-12)
+    assert stats["newton_shifted"] == 2
+    # positive definite: no shift, plain CG
+    x, it, sigma = O.shifted_cg(lambda v: np.array([3.0, 1.0, 2.0]) * v, np.ones(3), 1e-13, 10)
+    assert sigma == 0.0
+    np.testing.assert_allclose(x, [1.0 / 3.0, 1.0, 0.5], rtol=1e-12)
 
 
 def test_cg_truncation_returns_saved_iterate():
