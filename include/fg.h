@@ -112,6 +112,8 @@ typedef struct {
   int newton_damped;  /* halvings of mechanical Newton corrections */
   int cg_negcurv;     /* CG directions of negative curvature taken (cg_indefinite 1) */
   int newton_shifted; /* mechanical Newton systems solved again with a larger shift */
+  int newton_fp64;    /* mixed mode: mechanical solves that fell back to FP64 Krylov after
+                         an FP32 correction failed to lower the FP64 residual */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */

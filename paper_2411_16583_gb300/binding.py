@@ -55,7 +55,8 @@ class Stats(C.Structure):
     _fields_ = [("newton_chem", C.c_int), ("newton_mech", C.c_int), ("cg_chem", C.c_int),
                 ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
                 ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("newton_damped", C.c_int),
-                ("cg_negcurv", C.c_int), ("newton_shifted", C.c_int), ("err_mech", C.c_double), ("err_chem", C.c_double),
+                ("cg_negcurv", C.c_int), ("newton_shifted", C.c_int), ("newton_fp64", C.c_int),
+                ("err_mech", C.c_double), ("err_chem", C.c_double),
                 ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
 
     def as_dict(self):

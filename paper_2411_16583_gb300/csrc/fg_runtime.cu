@@ -874,52 +874,67 @@ static double residual_mech(fg_ctx& c, double den, R* state) {
   return sqrt(c.ks_host[KS_MISC].aux) / den;
 }
 
+// Newton correction of Alg. 1 in precision X: CG on (G K G + sigma I) dF = -G P from the
+// tangent state in PX.state.  With cg_indefinite == 2 a solve that meets a direction p of
+// negative curvature, Rayleigh quotient lam = <p, (A + sigma) p> / |p|^2 <= 0, sets
+// sigma = 2 (sigma + |lam|), |lam| at least 1e-6 of the Rayleigh quotient of the
+// right-hand side, and solves again from zero (a Rayleigh quotient only bounds the lowest
+// eigenvalue from above: the geometric growth keeps the shifted system away from
+// singular).  The correction is left in PX.x; returns the CG iterations.
+template <typename X>
+static int newton_solve(fg_ctx& c, Prec<X>& PX, double& sigma, fg_stats& s) {
+  to_prec<X>(c, c.GP, PX.b, 9 * c.V, -1.0);
+  int n = 0;
+  for (int rs = 0;; ++rs) {
+    bool neg = false;
+    n += cg_solve_mech<X>(c, PX, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s, sigma,
+                          c.o.cg_indefinite == 2 ? &neg : nullptr);
+    if (!neg) return n;
+    const KScal k = c.ks_host[KS_MECH];
+    const double pp = reduce_sum_r<X>(c, PX.p, 9 * c.V);
+    const double lam = pp > 0.0 ? k.pq / pp : 0.0;
+    const double rho0 = k.bb > 0.0 ? fabs(k.pq0) / k.bb : 0.0;
+    sigma = 2.0 * (sigma + std::max(fabs(lam), 1e-6 * rho0));
+    s.newton_shifted += 1;
+    if (verbose())
+      fprintf(stderr, "[fg]   negative curvature at cg %d (lam %.3e): sigma %.3e\n", k.iters, lam, sigma);
+    if (!(sigma == sigma) || sigma <= 0.0 || rs >= 12)
+      fail(FG_ERR_NUMERIC, "mechanical Newton: shifted system still not positive");
+  }
+}
+
 // Alg. 1 from the current F.  Each Newton correction is damped by halving (at most 10
 // times) while F + lambda dF leaves the domain (det F <= 0 or J_c <= 0) or does not lower
-// err_res; the residual of the accepted iterate is the next iteration's residual.
-// With cg_indefinite == 2 a Newton system met with negative curvature is shifted,
-// (G K G + sigma I) dF = -G P, sigma found as in the loop below; sigma shrinks 4-fold after
-// each Newton iteration, so near a stable equilibrium the iteration is plain Newton again.
+// err_res; the residual of the accepted iterate is the next iteration's residual.  The
+// shift sigma of newton_solve shrinks 4-fold per Newton iteration, so near a stable
+// equilibrium the iteration is plain Newton.  Mixed mode: FP32 cannot resolve eigenvalues
+// of G K G below about 1e-7 of its norm (the rigid motions of a particle in a very soft
+// buffer come close to that), so when an FP32 correction fails to lower the FP64
+// residual the iteration is redone with an FP64 Krylov solve, and the rest of this solve
+// stays in FP64 (iterative refinement falling back to the working precision).
 template <typename R>
 static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
-  double err = residual_mech<R>(c, den, P.state);
+  bool hi = !is_mixed(c);  // Krylov in FP64
+  auto resid = [&]() {
+    return hi ? residual_mech<double>(c, den, c.pd.state) : residual_mech<R>(c, den, P.state);
+  };
+  double err = resid();
   double sigma = 0.0;
   for (int it = 0;; ++it, sigma *= 0.25) {
     s.err_mech = err;
     if (!(err == err)) fail(FG_ERR_NUMERIC, "mechanical residual is not finite");
     if (err <= c.o.tol_newton) return;
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
-    to_prec<R>(c, c.GP, P.b, 9 * c.V, -1.0);
-    int n = 0;
-    for (int rs = 0;; ++rs) {
-      bool neg = false;
-      n += cg_solve_mech<R>(c, P, mixed_tol(c, c.o.tol_cg), c.o.max_cg, &s, sigma,
-                            c.o.cg_indefinite == 2 ? &neg : nullptr);
-      if (!neg) break;
-      // shifted Newton: the direction p of negative curvature has Rayleigh quotient
-      // lam = <p, (A + sigma) p> / |p|^2 <= 0; sigma = 2 (sigma + |lam|), |lam| at least
-      // 1e-6 of the Rayleigh quotient of the right-hand side, and solve again from zero
-      // (a Rayleigh quotient only bounds the lowest eigenvalue from above: the geometric
-      // growth keeps the shifted system away from singular)
-      const KScal k = c.ks_host[KS_MECH];
-      const double pp = reduce_sum_r<R>(c, P.p, 9 * c.V);
-      const double lam = pp > 0.0 ? k.pq / pp : 0.0;
-      const double rho0 = k.bb > 0.0 ? fabs(k.pq0) / k.bb : 0.0;
-      sigma = 2.0 * (sigma + std::max(fabs(lam), 1e-6 * rho0));
-      s.newton_shifted += 1;
-      if (verbose())
-        fprintf(stderr, "[fg]   negative curvature at cg %d (lam %.3e): sigma %.3e\n", k.iters, lam, sigma);
-      if (!(sigma == sigma) || sigma <= 0.0 || rs >= 12)
-        fail(FG_ERR_NUMERIC, "mechanical Newton: shifted system still not positive");
-    }
+    const int n = hi ? newton_solve<double>(c, c.pd, sigma, s) : newton_solve<R>(c, P, sigma, s);
     s.cg_mech += n;
     s.newton_mech += 1;
     if (verbose())
-      fprintf(stderr, "[fg] newton %d err %.3e cg %d rr/bb %.3e status %d negc %d snaps %d\n", it,
-              err, n, c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
-              c.ks_host[KS_MECH].status, c.ks_host[KS_MECH].negc, c.ks_host[KS_MECH].snaps);
+      fprintf(stderr, "[fg] newton %d%s err %.3e cg %d rr/bb %.3e status %d snaps %d\n", it,
+              hi && is_mixed(c) ? " (fp64)" : "", err, n,
+              c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
+              c.ks_host[KS_MECH].status, c.ks_host[KS_MECH].snaps);
     const double* dF;
-    if (is_mixed(c)) {
+    if (!hi) {
       // FP32 roundoff leaves traces of the correction in modes G never sees (the mean and
       // the null modes of the rotated scheme); project it in FP64 onto compatible
       // zero-mean fields before the update, as the exact correction is
@@ -930,7 +945,7 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
       op_gres(c, c.pd, c.P, c.dF, nullptr);
       dF = c.dF;
     } else {
-      dF = (const double*)P.x;
+      dF = c.pd.x;
     }
     dcopy(c.Fbk, c.F, 9 * c.V * sizeof(double), c.st);
     double lam = 1.0;
@@ -944,7 +959,7 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
       launch_vec<KAxpyTo>(v, c.st);
       double e = 0.0;
       try {
-        e = residual_mech<R>(c, den, P.state);
+        e = resid();
       } catch (Fail& f) {
         if (f.code != FG_ERR_DOMAIN) throw;
         continue;
@@ -956,6 +971,16 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
         break;
       }
       s.newton_damped += 1;
+    }
+    if (!ok && !hi) {
+      // the FP32 correction did not lower the FP64 residual: back to F_bk, FP64 from here
+      dcopy(c.F, c.Fbk, 9 * c.V * sizeof(double), c.st);
+      hi = true;
+      s.newton_fp64 += 1;
+      err = resid();
+      sigma = 0.0;
+      if (verbose()) fprintf(stderr, "[fg]   FP32 correction rejected: FP64 Krylov from here\n");
+      continue;
     }
     if (!ok) fail(FG_ERR_NOCONV, "mechanical Newton: no decrease of err_res along the correction");
   }
@@ -1403,12 +1428,10 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
         c->kx_chunk[k] = ch < 1 ? 1 : (ch > c->hx ? c->hx : ch);
       }
     }
-    if (o.precision == FG_MIXED) {
-      setup_prec<double>(*c, c->pd, 1);
-      setup_prec<float>(*c, c->pf, 9);
-    } else {
-      setup_prec<double>(*c, c->pd, 9);
-    }
+    // FP64 set with nine-component Krylov vectors in both modes: the mixed mode falls
+    // back to it in the mechanical Newton
+    setup_prec<double>(*c, c->pd, 9);
+    if (o.precision == FG_MIXED) setup_prec<float>(*c, c->pf, 9);
     dsync(c->st);
   } catch (...) {
     fg_destroy(c);
