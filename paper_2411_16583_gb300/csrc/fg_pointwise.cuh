@@ -297,9 +297,11 @@ struct KMechState : VecOp<double> {
 };
 
 // ---------------------------------------------------------------- damage history
-// H = max(H_t, g_c/(2 l_c) D_f), D_f from the principal values of the undegraded Cauchy
-// stress sigma = J^-1 a P0(a F) F^T (Eqs. Hist, SigDrivingForce).  Accumulates sum H.
-// in: F, c, H_t, lam, mu, Om, c0, smax ; out0: H ; s0 = g_c/(2 l_c)
+// H = max(H_t, g_c(x)/(2 l_c) D_f), D_f from the principal values of the undegraded
+// Cauchy stress sigma = J^-1 a P0(a F) F^T (Eqs. Hist, SigDrivingForce).
+// in: F, c, H_t, lam, mu, Om, c0, smax, gcr = g_c(x)/g_c (null: uniform) ; s0 = g_c/(2 l_c)
+// out0: H ; out1 (when gcr): H_eff = H / gcr, the history the phase-field operator sees.
+// Accumulates sum H_eff.
 template <int LAW = LAW_NH_>
 struct KHistory : VecOp<double> {
   static constexpr bool RED = true;
@@ -336,13 +338,20 @@ struct KHistory : VecOp<double> {
         t += u * u;
       }
       const double Df = t - 1.0 > 0.0 ? t - 1.0 : 0.0;
-      const double Hc = a.s[0] * Df;
+      const double* gcr = (const double*)a.in[8];
+      const double Hc = a.s[0] * (gcr ? gcr[v] : 1.0) * Df;
       Hn = Hc > Ht ? Hc : Ht;
     } else {
       atomicOr(a.flags, ST_DOMAIN);
     }
     ((double*)a.out[0])[v] = Hn;
-    acc.add(Hn);
+    if (a.out[1]) {
+      const double He = Hn / ((const double*)a.in[8])[v];
+      ((double*)a.out[1])[v] = He;
+      acc.add(He);
+    } else {
+      acc.add(Hn);
+    }
   }
 };
 
@@ -476,6 +485,14 @@ struct KAdjGradE : VecOp<double> {
     for (int c = 0; c < 9; ++c)
       s += (double)((const R*)a.in[0])[c * a.V + v] * ((const double*)a.in[1])[c * a.V + v];
     ((double*)a.out[0])[v] = -s;
+  }
+};
+
+// out0 = in0 / in1 (FP64)
+struct KDivTo : VecOp<double> {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
+    ((double*)a.out[0])[i] = ((const double*)a.in[0])[i] / ((const double*)a.in[1])[i];
   }
 };
 

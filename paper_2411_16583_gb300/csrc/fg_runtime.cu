@@ -146,6 +146,8 @@ struct fg_ctx {
   // FP64 fields
   double *F = nullptr, *Ft = nullptr, *c = nullptr, *ct = nullptr, *d = nullptr, *dt = nullptr;
   double *H = nullptr, *Ht = nullptr, *cdotB = nullptr, *P = nullptr, *GP = nullptr;
+  double* gcr = nullptr;   // per-voxel g_c(x) / g_c, null for a uniform toughness
+  double* Heff = nullptr;  // H g_c / g_c(x): the history of the phase-field operator (= H)
   double *Fbk = nullptr, *dF = nullptr;  // Newton line search: F before the update, dF
   double *mu = nullptr, *base = nullptr;
   double *lam = nullptr, *mu_ = nullptr, *Om = nullptr, *c0 = nullptr, *D = nullptr, *smax = nullptr;
@@ -1001,17 +1003,29 @@ static void history(fg_ctx& c) {
   v.in[5] = c.Om;
   v.in[6] = c.c0;
   v.in[7] = c.smax;
+  v.in[8] = c.gcr;
   v.out[0] = c.H;
+  v.out[1] = c.gcr ? c.Heff : nullptr;
   v.s[0] = c.o.gc / (2.0 * c.o.lc);
   if (c.law == FG_SVK) launch_vec<KHistory<LAW_SVK_>>(v, c.st);
   else launch_vec<KHistory<LAW_NH_>>(v, c.st);
   fin<FScaleAux>(c, KS_HBAR, VEC_BLOCKS, nullptr, 1.0 / (double)c.V);
 }
 
-// Hbar = mean H of the stored H
-static void hbar_from_sum(fg_ctx& c) {
+// H_eff = H / gcr after H was set or restored (nothing to do for a uniform toughness)
+static void refresh_heff(fg_ctx& c) {
+  if (!c.gcr) return;
   VArgs v = vbase(c, c.V);
   v.in[0] = c.H;
+  v.in[1] = c.gcr;
+  v.out[0] = c.Heff;
+  launch_vec<KDivTo>(v, c.st);
+}
+
+// Hbar = mean H_eff of the stored history
+static void hbar_from_sum(fg_ctx& c) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = c.Heff;
   launch_vec<KSum>(v, c.st);
   fin<FScaleAux>(c, KS_HBAR, VEC_BLOCKS, nullptr, 1.0 / (double)c.V);
 }
@@ -1019,25 +1033,25 @@ static void hbar_from_sum(fg_ctx& c) {
 template <typename R>
 static void pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
   if (!is_mixed(c)) {
-    to_prec<double>(c, c.H, c.pd.b, c.V, 2.0);
+    to_prec<double>(c, c.Heff, c.pd.b, c.V, 2.0);
     dcopy(c.pd.x, c.d, c.V * sizeof(double), c.st);
-    s.cg_pff += pcg_pff<double>(c, c.pd, c.H, c.o.tol_pff_cg, c.o.max_cg);
+    s.cg_pff += pcg_pff<double>(c, c.pd, c.Heff, c.o.tol_pff_cg, c.o.max_cg);
     dcopy(c.d, c.pd.x, c.V * sizeof(double), c.st);
     return;
   }
   // mixed: FP64 residual b - A d, FP32 PCG corrections
-  to_prec<R>(c, c.H, P.Hr, c.V, 1.0);
-  const double bb = 4.0 * reduce_sum(c, c.H, c.V, true);
+  to_prec<R>(c, c.Heff, P.Hr, c.V, 1.0);
+  const double bb = 4.0 * reduce_sum(c, c.Heff, c.V, true);
   if (bb == 0.0) {
     dzero(c.d, c.V * sizeof(double), c.st);
     return;
   }
   Prec<double>& D = c.pd;
   for (int it = 0;; ++it) {
-    op_pff(c, D, c.d, D.q, c.H, nullptr);  // q = A d in FP64
+    op_pff(c, D, c.d, D.q, c.Heff, nullptr);  // q = A d in FP64
     {
       VArgs t = vbase(c, c.V);  // b = 2H
-      t.in[0] = c.H;
+      t.in[0] = c.Heff;
       t.out[0] = D.b;
       t.s[0] = 2.0;
       launch_vec<KScaleTo<double>>(t, c.st);
@@ -1184,6 +1198,7 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
     dcopy(c.c, c.ct, V * sizeof(double), c.st);
     dcopy(c.d, c.dt, V * sizeof(double), c.st);
     dcopy(c.H, c.Ht, V * sizeof(double), c.st);
+    refresh_heff(c);
     memcpy(c.Fbar, Fbar_old, sizeof(c.Fbar));
     dsync(c.st);
     throw;
@@ -1212,9 +1227,9 @@ static double do_apply(fg_ctx& c, Prec<R>& P, int op, const R* x, R* y, double d
       break;
     case FG_OP_PFF: {
       const R* H;
-      if constexpr (sizeof(R) == 8) H = (const R*)c.H;
+      if constexpr (sizeof(R) == 8) H = (const R*)c.Heff;
       else {
-        to_prec<R>(c, c.H, P.Hr, c.V, 1.0);
+        to_prec<R>(c, c.Heff, P.Hr, c.V, 1.0);
         H = P.Hr;
       }
       nb = op_pff(c, P, x, y, H, nullptr);
@@ -1302,7 +1317,8 @@ void fg_destroy(fg_ctx* ctx) {
 
 int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases,
              const uint8_t* phase_id, const double* cdot_B, const double* c_init,
-             const double* log_E, const double* log_D, const fg_opts* opts) {
+             const double* log_E, const double* log_D, const double* log_gc,
+             const fg_opts* opts) {
   FG_API_BEGIN
   if (!out || !g || !phases || nphases <= 0 || nphases > 255 || !phase_id || !cdot_B)
     fail(FG_ERR_INVALID, "fg_setup: null argument or bad phase count");
@@ -1387,6 +1403,15 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     c->dt = alloc_n<double>(*c, V);
     c->H = alloc_n<double>(*c, V);
     c->Ht = alloc_n<double>(*c, V);
+    if (log_gc) {
+      std::vector<double> g(V);
+      for (long long v = 0; v < V; ++v) g[v] = exp(log_gc[v]);
+      c->gcr = up(g);
+      c->Heff = alloc_n<double>(*c, V);
+      dzero(c->Heff, V * sizeof(double), c->st);
+    } else {
+      c->Heff = c->H;
+    }
     c->mu = alloc_n<double>(*c, V);
     c->base = alloc_n<double>(*c, V);
     {
@@ -1547,6 +1572,7 @@ int fg_set_field(fg_ctx* c, int field, const void* src, int on_device) {
   (void)on_device;
   dcopy(dst, src, n * sizeof(double), c->st);
   dcopy(dst_t, src, n * sizeof(double), c->st);
+  if (field == FG_FIELD_H) refresh_heff(*c);
   dsync(c->st);
   FG_API_END
 }
@@ -1856,7 +1882,7 @@ int fg_time_apply(fg_ctx* c, int op, int prec, int n, double* ms) {
       switch (op) {
         case FG_OP_MECH: op_mech(*c, P, (const double*)x, (double*)y, nullptr); break;
         case FG_OP_GRES: op_gres(*c, P, (const double*)x, (double*)y, nullptr); break;
-        case FG_OP_PFF: op_pff(*c, P, (const double*)x, (double*)y, (const double*)c->H, nullptr); break;
+        case FG_OP_PFF: op_pff(*c, P, (const double*)x, (double*)y, (const double*)c->Heff, nullptr); break;
         case FG_OP_PFF_PREC: op_prec(*c, P, (const double*)x, (double*)y, nullptr); break;
         case FG_OP_CHEM: op_chem(*c, P, (const double*)x, (double*)y, 1.0, nullptr); break;
       }

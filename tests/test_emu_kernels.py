@@ -141,3 +141,26 @@ def test_emulated_mech_adjoint_matches_oracle(emu, law):
     ref = O.mech_adjoint(F, c, d, prm, W, 1e-14, 2000)
     assert it > 0 and rel_err(g, ref) < 1e-9
     sol.close()
+
+
+def test_emulated_damage_with_log_fields_matches_oracle(emu):
+    """Two steps of a 12 x 12 disc whose second step damages, with per-voxel log E, log D
+    and log g_c: the history H = max(H_t, g_c(x)/(2 l_c) D_f) and the phase field solved
+    with H g_c/g_c(x) against the oracle."""
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, prm_of, phases, pid = _disc(n=12, smax=21e6)
+    prm = prm_of(*logs)
+    tols = dict(tol_newton=1e-12, tol_stag=1e-10, max_stag=400)
+    ref = O.CoupledState(prm, np.full(shape, 0.01), src, O.Tolerances(**tols))
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], lib=emu, gc=1.0, lc=2e-7,
+                   **tols)
+    for _ in range(2):
+        ref.step(1.0, np.eye(3))
+        sol.step(1.0)
+    assert ref.d.max() > 0.01
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-8
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-8
+    assert rel_err(sol.get(B.FIELD_H), ref.H) < 1e-8
+    assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < 1e-8
+    sol.close()

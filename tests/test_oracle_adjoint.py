@@ -172,7 +172,7 @@ def _disc(n=10, smax=17e6, seed=3):
 
     def prm_of(lE, lG, lD):
         return O.make_params(phases, pid, H, gc=1.0, lc=2e-7, log_E=lE, log_D=lD, log_gc=lG)
-    return shape, logs, src, tol, prm_of
+    return shape, logs, src, tol, prm_of, phases, pid
 
 
 @pytest.mark.slow
@@ -181,7 +181,7 @@ def test_step_adjoint_matches_central_differences():
     of the third step: a random linear functional of its outputs (c, F, d, H), perturbed
     along random directions of its inputs (c_t, compatible F_t, d_t, H_t) and of the log
     parameters of single voxels.  The history has voxels on both branches of its max."""
-    shape, logs, src, tol, prm_of = _disc()
+    shape, logs, src, tol, prm_of, _, _ = _disc()
     prm = prm_of(*logs)
     traj = A.forward(prm, np.full(shape, 0.01), src, [1.0, 1.0], [np.eye(3)] * 2, tol)
     s_in = traj[-1]
@@ -238,7 +238,7 @@ def test_crack_energy_gradient_matches_central_differences():
     """dGamma_E/dlog(E, g_c, D) after two steps (damage starts in the second) against
     central differences of the whole forward run, at the voxel of the largest gradient
     of each parameter and at one voxel in the particle's interior."""
-    shape, logs, src, tol, prm_of = _disc()
+    shape, logs, src, tol, prm_of, _, _ = _disc()
     prm = prm_of(*logs)
     stats = {}
     val, g = A.crack_energy_gradient(prm, np.full(shape, 0.01), src, [1.0, 1.0],
