@@ -112,8 +112,8 @@ typedef struct {
   int newton_damped;  /* halvings of mechanical Newton corrections */
   int cg_negcurv;     /* CG directions of negative curvature taken (cg_indefinite 1) */
   int newton_shifted; /* mechanical Newton systems solved again with a larger shift */
-  int newton_fp64;    /* mixed mode: mechanical solves that fell back to FP64 Krylov after
-                         an FP32 correction failed to lower the FP64 residual */
+  int newton_minres;  /* mechanical solves that fell back to FP64 MINRES after a CG
+                         correction failed to lower the FP64 residual */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */
@@ -239,7 +239,54 @@ int fg_batch_setup(fg_batch** out, int n, fg_ctx* const* members);
 int fg_batch_step(fg_batch* batch, double dt, const double Fbar[9], fg_stats* st);
 void fg_batch_destroy(fg_batch* batch);
 
-/* Releases the context and its device memory.  NULL is ignored. */
+/*
+ * Discrete adjoint of recorded time steps (a hand-written reverse of Alg. 4; the paper's
+ * forward equations Eqs. Chemresidualfc, mechanicalsolve, Hist, SigDrivingForce, PFFA
+ * differentiated at each converged step).
+ *
+ * fg_tape_begin starts recording at the stored state: every later successful fg_step is
+ * recorded (dt, Fbar), and the state before every ckpt_every-th recorded step is kept as a
+ * checkpoint (12 V doubles of device memory each).  A new call drops the old tape.
+ *
+ * fg_adjoint runs the recorded steps backwards.  Each segment between checkpoints is
+ * recomputed forward from its checkpoint (ckpt_every + 1 states of 12 V doubles held at a
+ * time), then every step is reversed: the (F, H, d) block by transposed block Gauss-Seidel
+ * sweeps accelerated by GMRES on the phase-field multiplier (mechanical CG on G K G,
+ * phase-field PCG; the couplings are dP/dd and dpsi/dF on the active branch of
+ * H = max(H_t, psi)), then the chemistry by its exact Jacobian transpose
+ * I + dt dmu~/dc L, solved as a symmetric system by CG.  All adjoint solves run in FP64
+ * at the options' tolerances (tol_cg, tol_pff_cg, tol_chem_cg; GMRES to tol_stag within
+ * max_stag), and an iteration cap is an error in both precision modes.
+ *   loss        FG_LOSS_CRACK_ENERGY: Gamma_E = sum g_c(x) (d^2/(2 l_c) + l_c/2 |grad_f d|^2)
+ *               h^3 of the final phase field (Eq. crack); the seeds are ignored.
+ *               FG_LOSS_SEEDS: L with dL/dc, dL/dF, dL/dd of the final state given in
+ *               seed_c (V), seed_F (9 V, component (i, j) at (3 i + j) V), seed_d (V),
+ *               host arrays, NULL meaning zero.
+ *   loss_value  (may be NULL) Gamma_E, or 0 for FG_LOSS_SEEDS
+ *   grad_*      (host, V doubles each, may be NULL) dL/dlog E, dL/dlog g_c, dL/dlog D per
+ *               voxel (log g_c as in fg_setup's log_gc)
+ * On return the stored state is the one at the call and the tape is kept.  Errors:
+ * FG_ERR_INVALID (no recorded step, bad loss), FG_ERR_NOCONV (an adjoint solve hit its
+ * cap), FG_ERR_NUMERIC (dmu~/dc <= 0 somewhere: the chemistry Jacobian is not positive),
+ * FG_ERR_DOMAIN, FG_ERR_OOM, FG_ERR_CUDA.
+ */
+#define FG_LOSS_CRACK_ENERGY 0
+#define FG_LOSS_SEEDS 1
+
+typedef struct {
+  int steps;       /* steps reversed */
+  int recomputed;  /* forward steps recomputed from checkpoints */
+  int sweeps;      /* transposed Gauss-Seidel sweeps (one mechanical + one phase-field solve) */
+  int gmres;       /* GMRES iterations on the phase-field multiplier */
+  int cg_mech, cg_pff, cg_chem;  /* Krylov iterations of the adjoint solves */
+} fg_adjoint_stats;
+
+int fg_tape_begin(fg_ctx* ctx, int ckpt_every);
+int fg_adjoint(fg_ctx* ctx, int loss, const double* seed_c, const double* seed_F,
+               const double* seed_d, double* loss_value, double* grad_logE, double* grad_loggc,
+               double* grad_logD, fg_adjoint_stats* st);
+
+/* Releases the context, its tape and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);
 
 /*

@@ -449,6 +449,53 @@ def shifted_cg(apply, b, tol, maxit, stats=None):
     raise FloatingPointError("shifted system still not positive")
 
 
+def minres(apply, b, tol, maxit, stats=None):
+    """MINRES (Paige and Saunders 1975) for a symmetric, possibly indefinite operator, from
+    x = 0 until |b - A x| <= tol |b|.  Lanczos: A v_k = b_k v_{k-1} + a_k v_k + b_{k+1} v_{k+1}
+    (b_1 = 0 in column 1).  Column k of the tridiagonal matrix, (b_k, a_k, b_{k+1}) in rows
+    k-1, k, k+1, is rotated by the Givens rotations G_{k-2}, G_{k-1} into (e_k, d_k, gbar_k)
+    plus b_{k+1}, which G_k = (c, s) = (gbar_k, b_{k+1}) / gamma_k removes; the rotated
+    right-hand side gives phi_k = c phibar_{k-1}, phibar_k = -s phibar_{k-1}, |phibar_k| the
+    residual norm, and x_k = x_{k-1} + phi_k w_k with w_k = (v_k - d_k w_{k-1} - e_k w_{k-2})
+    / gamma_k.  Returns (x, iterations)."""
+    x = np.zeros_like(b)
+    beta1 = math.sqrt(dot(b, b))
+    if beta1 == 0.0:
+        return x, 0
+    v_prev = np.zeros_like(b)
+    v = b / beta1
+    beta = 0.0  # b_k, the coupling of v_k to v_{k-1}
+    w1 = np.zeros_like(b)  # w_{k-1}
+    w2 = np.zeros_like(b)  # w_{k-2}
+    c1, s1, c2, s2 = 1.0, 0.0, 1.0, 0.0  # G_{k-1}, G_{k-2}
+    phibar = beta1
+    it = 0
+    while abs(phibar) > tol * beta1 and it < maxit:
+        Av = apply(v)
+        alpha = dot(v, Av)
+        u = Av - alpha * v - beta * v_prev
+        beta_next = math.sqrt(dot(u, u))
+        e = s2 * beta
+        t = c2 * beta
+        d = c1 * t + s1 * alpha
+        gbar = -s1 * t + c1 * alpha
+        gamma = math.hypot(gbar, beta_next)
+        c, s = (gbar / gamma, beta_next / gamma) if gamma > 0.0 else (1.0, 0.0)
+        phi = c * phibar
+        phibar = -s * phibar
+        w = (v - d * w1 - e * w2) / gamma
+        x = x + phi * w
+        w2, w1 = w1, w
+        c2, s2, c1, s1 = c1, s1, c, s
+        it += 1
+        if beta_next == 0.0:
+            break
+        v_prev, v, beta = v, u / beta_next, beta_next
+    if stats is not None:
+        stats["minres"] = stats.get("minres", 0) + it
+    return x, it
+
+
 def pcg(apply, precond, b, tol, maxit, x0):
     """Preconditioned conjugate gradients from x0; stops when ||r|| <= tol ||b||."""
     bn = math.sqrt(dot(b, b))
@@ -509,9 +556,14 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
     the starting shift; 1 = CG takes it; 0 = truncated CG.
 
     Each Newton correction dF is damped, lambda = 1, 1/2, ... (at most 10 halvings),
-    until F + lambda dF stays in the domain (det F > 0, J_c > 0) and lowers err_res."""
+    until F + lambda dF stays in the domain (det F > 0, J_c > 0) and lowers err_res.  When a
+    CG correction fails that (the tangent of the current state has negative eigenvalues
+    along which a shifted or truncated direction cannot lower the residual), the iteration
+    is redone with MINRES on the unshifted Newton system, and MINRES serves the rest of
+    the solve."""
     n_newton = 0
     sigma = 0.0
+    use_minres = False
     GP, err = mech_residual(F, c, d, prm, Fbar)
     while True:
         if stats is not None:
@@ -520,7 +572,9 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
             return F, err
         if n_newton >= max_newton:
             raise RuntimeError("mechanical Newton did not converge")
-        if indefinite == 2:
+        if use_minres:
+            dF, it = minres(lambda x: mech_apply(F, c, d, prm, x), -GP, tol_cg, max_cg, stats)
+        elif indefinite == 2:
             s0 = sigma / 4.0
             dF, it, sigma = shifted_cg(lambda x: mech_apply(F, c, d, prm, x) + s0 * x, -GP,
                                        tol_cg, max_cg, stats)
@@ -545,7 +599,12 @@ def mech_newton(F, c, d, prm, Fbar, tol_newton, tol_cg, max_newton, max_cg, stat
                 stats["newton_damped"] = stats.get("newton_damped", 0) + 1
             lam *= 0.5
         else:
-            raise RuntimeError("mechanical Newton: no decrease of err_res along the correction")
+            if use_minres:
+                raise RuntimeError("mechanical Newton: no decrease of err_res along the correction")
+            use_minres = True
+            if stats is not None:
+                stats["newton_minres"] = stats.get("newton_minres", 0) + 1
+            continue
         F, GP, err = Fn, GPn, errn
 
 

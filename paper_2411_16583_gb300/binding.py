@@ -55,7 +55,7 @@ class Stats(C.Structure):
     _fields_ = [("newton_chem", C.c_int), ("newton_mech", C.c_int), ("cg_chem", C.c_int),
                 ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
                 ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("newton_damped", C.c_int),
-                ("cg_negcurv", C.c_int), ("newton_shifted", C.c_int), ("newton_fp64", C.c_int),
+                ("cg_negcurv", C.c_int), ("newton_shifted", C.c_int), ("newton_minres", C.c_int),
                 ("err_mech", C.c_double), ("err_chem", C.c_double),
                 ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
 
@@ -63,10 +63,22 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AdjStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("recomputed", C.c_int), ("sweeps", C.c_int),
+                ("gmres", C.c_int), ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("cg_chem", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FG_LOSS_CRACK_ENERGY = 0
+FG_LOSS_SEEDS = 1
+
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
            "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
+           "fg_tape_begin", "fg_adjoint",
            "fg_kernel_launches", "fg_destroy", "fg_last_error"]
 
 _libs = {}
@@ -100,6 +112,9 @@ def load_library(path=LIB_PATH):
     lib.fg_autotune.argtypes = [C.c_void_p, dp]
     lib.fg_solve_mech.argtypes = [C.c_void_p, dp, C.POINTER(Stats)]
     lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    lib.fg_tape_begin.argtypes = [C.c_void_p, C.c_int]
+    lib.fg_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, dp,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdjStats)]
     lib.fg_batch_setup.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
     lib.fg_batch_step.argtypes = [C.c_void_p, C.c_double, dp, C.POINTER(Stats)]
     lib.fg_batch_destroy.argtypes = [C.c_void_p]
@@ -236,6 +251,23 @@ class Solver:
         it = C.c_int()
         self._check(self.lib.fg_adjoint_mech(self.ctx, _ptr(Wh), _ptr(g), C.byref(it)))
         return g, it.value
+
+    def tape(self, ckpt_every=1):
+        """Starts recording the following steps for ``adjoint`` (checkpoint every k steps)."""
+        self._check(self.lib.fg_tape_begin(self.ctx, int(ckpt_every)))
+
+    def adjoint(self, loss=FG_LOSS_CRACK_ENERGY, seed_c=None, seed_F=None, seed_d=None):
+        """Reverse of the recorded steps: returns (loss value, dict(E, gc, D) of per-voxel
+        dL/dlog E, dL/dlog g_c, dL/dlog D, statistics)."""
+        seeds = [None if a is None else _f64(a).ravel() for a in (seed_c, seed_F, seed_d)]
+        g = {k: np.empty(self.shape) for k in ("E", "gc", "D")}
+        val = C.c_double()
+        st = AdjStats()
+        self._check(self.lib.fg_adjoint(self.ctx, int(loss),
+                                        *[None if a is None else _ptr(a) for a in seeds],
+                                        C.byref(val), _ptr(g["E"]), _ptr(g["gc"]), _ptr(g["D"]),
+                                        C.byref(st)))
+        return val.value, g, st.as_dict()
 
     def autotune(self):
         ms = C.c_double()

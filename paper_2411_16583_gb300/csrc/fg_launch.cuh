@@ -57,7 +57,7 @@ struct SizeOps {
   int N;
   PassFn<R> xf_tangent, xf_cgtangent, xf_tangent_svk, xf_cgtangent_svk, xf_copy1, xf_copy3,
       xf_copy9;
-  PassFn<R> xi_store1, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
+  PassFn<R> xi_store1, xi_store3, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
       xi_chemrhs, xi_cgupdate, xi_cgupdate_pc;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
@@ -99,6 +99,7 @@ SizeOps<R> make_size_ops() {
     s.xf_copy3 = run_x<XFwd<R, N, PCopy<R, 3>>, R>;
     s.xf_copy9 = run_x<XFwd<R, N, PCopy<R, 9>>, R>;
     s.xi_store1 = run_x<XInv<R, N, EStore<R, 1>>, R>;
+    s.xi_store3 = run_x<XInv<R, N, EStore<R, 3>>, R>;
     s.xi_storedot1 = run_x<XInv<R, N, EStoreDot<R, 1>>, R>;
     s.xi_storedot9 = run_x<XInv<R, N, EStoreDot<R, 9>>, R>;
     s.xi_norm9 = run_x<XInv<R, N, ENorm<R, 9>>, R>;

@@ -32,7 +32,7 @@ enum : int { ST_OK = 0, ST_INDEFINITE = 1, ST_DOMAIN = 2, ST_NUMERIC = 4 };
 struct VArgs {
   long long n;          // elements processed
   long long V;          // voxels
-  const void* in[10];   // inputs (meaning per kernel)
+  const void* in[16];   // inputs (meaning per kernel)
   void* out[6];         // outputs
   double s[10];         // scalars
   double* partials;     // per-block partial sums
@@ -485,6 +485,17 @@ struct KAdjGradE : VecOp<double> {
     for (int c = 0; c < 9; ++c)
       s += (double)((const R*)a.in[0])[c * a.V + v] * ((const double*)a.in[1])[c * a.V + v];
     ((double*)a.out[0])[v] = -s;
+  }
+};
+
+// out0 = s0 in0 + s1 in1 + s2 in2 (FP64; in1, in2 may be null)
+struct KLin3 : VecOp<double> {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
+    double o = a.s[0] * ((const double*)a.in[0])[i];
+    if (a.in[1]) o += a.s[1] * ((const double*)a.in[1])[i];
+    if (a.in[2]) o += a.s[2] * ((const double*)a.in[2])[i];
+    ((double*)a.out[0])[i] = o;
   }
 };
 

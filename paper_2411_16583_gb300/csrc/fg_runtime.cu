@@ -5,6 +5,7 @@
 #include <cstring>
 #include <cmath>
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "fg_pointwise.cuh"
+#include "fg_adjoint.cuh"
 #include "../../include/fg.h"
 
 namespace fg {
@@ -132,6 +134,17 @@ struct Prec {
   const SizeOps<R>*ox = nullptr, *oy = nullptr, *oz = nullptr;
 };
 
+// Recorded trajectory of fg_step calls for the adjoint: the step sizes and macroscopic
+// deformation gradients, and checkpoints (c, F, d, H and Fbar, 12 V doubles) of the state
+// before every `every`-th step.
+struct Tape {
+  int every = 1;
+  std::vector<double> dts;
+  std::vector<std::array<double, 9>> fbars;
+  std::vector<double*> ckpt;
+  std::vector<std::array<double, 9>> ckpt_fbar;
+};
+
 }  // namespace fg
 
 struct fg_ctx {
@@ -171,6 +184,9 @@ struct fg_ctx {
   int kx_chunk[2] = {1, 1};          // kx planes per Y-Z-Y chunk (FP32, FP64)
   int xi_percomp = 1;                // fused CG update: one component per block
   int last_inner_refine = 0;
+  bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
+  double* mr[6] = {};         // MINRES work vectors (9 V doubles each), allocated on first use
+  fg::Tape* tape = nullptr;   // recorded steps for fg_adjoint
 };
 
 namespace fg {
@@ -675,7 +691,7 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   if (k.rr > k.tol2 && k.iters >= maxit) {
     // an FP32 inner solve of the mixed mode is an inexact Newton step: its iterate is kept
     // and the FP64 outer residual decides; in FP64 mode the cap is an error
-    if (!is_mixed(c)) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+    if (!is_mixed(c) || c.strict) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
     keep_best(c, P, n, k);
     if (truncated) *truncated += 1;
   }
@@ -687,10 +703,11 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
 // x += alpha p and sums |r|^2.  Per iteration: 5 passes + 2 single-block finalisers.
 // sigma shifts the system to G K G + sigma I.  With negcurv != null a direction of negative
 // curvature ends the solve without keeping an iterate: *negcurv is set and the caller
-// re-solves (the shifted Newton of mech_newton); P.p then holds that direction.
+// re-solves (the shifted Newton of mech_newton); P.p then holds that direction.  indef
+// overrides the option's treatment of negative curvature (1: take it, 0: stop; -1: option).
 template <typename R>
 static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats* st, double sigma = 0.0,
-                         bool* negcurv = nullptr) {
+                         bool* negcurv = nullptr, int indef = -1) {
   int* truncated = st ? &st->cg_truncated : nullptr;
   const long long n = 9 * c.V;
   const int slot = KS_MECH;
@@ -701,7 +718,8 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
   v.out[1] = P.r;
   v.out[2] = P.p;
   launch_vec<KCgInit<R>>(v, c.st);
-  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)(c.o.cg_indefinite == 1));
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit,
+                (double)(indef >= 0 ? indef : c.o.cg_indefinite == 1));
   const int* done = &ks->done;
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
   const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
@@ -767,7 +785,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
     return k.iters;
   }
   if (k.rr > k.tol2 && k.iters >= maxit) {
-    if (!is_mixed(c)) fail(FG_ERR_NOCONV, "mechanical CG hit max_cg");
+    if (!is_mixed(c) || c.strict) fail(FG_ERR_NOCONV, "mechanical CG hit max_cg");
     keep_best(c, P, n, k);
     if (truncated) *truncated += 1;  // mixed mode: inexact Newton step, see cg_solve
   }
@@ -839,7 +857,8 @@ static int pcg_pff(fg_ctx& c, Prec<R>& P, const R* H, double tol, int maxit) {
   const KScal& k = c.ks_host[slot];
   if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "phase-field solve produced a non-finite value");
   if (k.status & ST_INDEFINITE) fail(FG_ERR_NUMERIC, "phase-field operator not positive definite");
-  if (k.rr > k.tol2 && k.iters >= maxit && !is_mixed(c)) fail(FG_ERR_NOCONV, "phase-field PCG hit max_cg");
+  if (k.rr > k.tol2 && k.iters >= maxit && (!is_mixed(c) || c.strict))
+    fail(FG_ERR_NOCONV, "phase-field PCG hit max_cg");
   return k.iters;
 }
 
@@ -876,6 +895,97 @@ static double residual_mech(fg_ctx& c, double den, R* state) {
   return sqrt(c.ks_host[KS_MISC].aux) / den;
 }
 
+static double dotd(fg_ctx& c, const double* x, const double* y, long long n) {
+  VArgs v = vbase(c, n);
+  v.in[0] = x;
+  v.in[1] = y;
+  launch_vec<KDot>(v, c.st);
+  fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+  read_ks(c);
+  return c.ks_host[KS_MISC].aux;
+}
+
+static void lin3(fg_ctx& c, double* out, long long n, double s0, const double* x0, double s1 = 0.0,
+                 const double* x1 = nullptr, double s2 = 0.0, const double* x2 = nullptr) {
+  VArgs v = vbase(c, n);
+  v.in[0] = x0;
+  v.in[1] = x1;
+  v.in[2] = x2;
+  v.out[0] = out;
+  v.s[0] = s0;
+  v.s[1] = s1;
+  v.s[2] = s2;
+  launch_vec<KLin3>(v, c.st);
+}
+
+// MINRES (Paige and Saunders, SIAM J. Numer. Anal. 12 (1975) 617) on the FP64 Newton
+// system G K G dF = b, b = c.pd.b, from dF = 0 into c.pd.x.  Lanczos: A v_k = b_k v_{k-1} +
+// a_k v_k + b_{k+1} v_{k+1} (b_1 = 0 in column 1); column k of the tridiagonal matrix is
+// rotated by the Givens rotations G_{k-2}, G_{k-1} into (e_k, d_k, gbar_k), and G_k =
+// (gbar_k, b_{k+1}) / gamma_k removes b_{k+1}; the rotated right-hand side gives
+// phi_k = c phibar_{k-1}, phibar_k = -s phibar_{k-1}, |phibar_k| = |b - A x_k| (monotone),
+// and x_k = x_{k-1} + phi_k w_k, w_k = (v_k - d_k w_{k-1} - e_k w_{k-2}) / gamma_k.  It is
+// the fallback of the mechanical Newton where CG directions fail (a state whose tangent
+// has negative eigenvalues).  Stops at |r| <= tol |b| or maxit (an error when strict or in
+// FP64 mode).  Returns the iterations.
+static int minres_mech(fg_ctx& c, double tol, int maxit) {
+  Prec<double>& D = c.pd;
+  const long long n = 9 * c.V;
+  for (auto& p : c.mr)
+    if (!p) p = alloc_n<double>(c, n);
+  double *vp = c.mr[0], *v = c.mr[1], *u = c.mr[2], *w1 = c.mr[3], *w2 = c.mr[4], *w = c.mr[5];
+  dzero(D.x, n * sizeof(double), c.st);
+  dzero(vp, n * sizeof(double), c.st);
+  dzero(w1, n * sizeof(double), c.st);
+  dzero(w2, n * sizeof(double), c.st);
+  const double beta1 = sqrt(dotd(c, D.b, D.b, n));
+  if (beta1 == 0.0) return 0;
+  lin3(c, v, n, 1.0 / beta1, D.b);
+  double beta = 0.0, phibar = beta1, c1 = 1.0, s1 = 0.0, c2 = 1.0, s2 = 0.0;
+  int it = 0;
+  while (fabs(phibar) > tol * beta1) {
+    if (it >= maxit) {
+      if (!is_mixed(c) || c.strict) fail(FG_ERR_NOCONV, "mechanical MINRES hit max_cg");
+      break;
+    }
+    ++it;
+    op_mech(c, D, v, u, nullptr);  // u = A v_k
+    const double alpha = dotd(c, v, u, n);
+    lin3(c, u, n, 1.0, u, -alpha, v, -beta, vp);  // u = b_{k+1} v_{k+1}
+    const double beta_next = sqrt(dotd(c, u, u, n));
+    const double e = s2 * beta, t = c2 * beta;
+    const double d = c1 * t + s1 * alpha;
+    const double gbar = -s1 * t + c1 * alpha;
+    const double gamma = hypot(gbar, beta_next);
+    const double cr = gamma > 0.0 ? gbar / gamma : 1.0, sr = gamma > 0.0 ? beta_next / gamma : 0.0;
+    const double phi = cr * phibar;
+    phibar = -sr * phibar;
+    if (!(gamma > 0.0) || !(phibar == phibar)) fail(FG_ERR_NUMERIC, "mechanical MINRES broke down");
+    lin3(c, w, n, 1.0 / gamma, v, -d / gamma, w1, -e / gamma, w2);
+    lin3(c, D.x, n, 1.0, D.x, phi, w);
+    double* t3 = w2;  // w_{k-2} <- w_{k-1} <- w_k
+    w2 = w1;
+    w1 = w;
+    w = t3;
+    c2 = c1;
+    s2 = s1;
+    c1 = cr;
+    s1 = sr;
+    if (beta_next == 0.0) break;  // invariant subspace: x is exact
+    double* t2 = vp;              // v_{k-1} <- v_k, v_{k+1} = u / b_{k+1}
+    vp = v;
+    v = t2;
+    lin3(c, v, n, 1.0 / beta_next, u);
+    beta = beta_next;
+  }
+  c.mr[0] = vp;
+  c.mr[1] = v;
+  c.mr[3] = w1;
+  c.mr[4] = w2;
+  c.mr[5] = w;
+  return it;
+}
+
 // Newton correction of Alg. 1 in precision X: CG on (G K G + sigma I) dF = -G P from the
 // tangent state in PX.state.  With cg_indefinite == 2 a solve that meets a direction p of
 // negative curvature, Rayleigh quotient lam = <p, (A + sigma) p> / |p|^2 <= 0, sets
@@ -909,14 +1019,14 @@ static int newton_solve(fg_ctx& c, Prec<X>& PX, double& sigma, fg_stats& s) {
 // times) while F + lambda dF leaves the domain (det F <= 0 or J_c <= 0) or does not lower
 // err_res; the residual of the accepted iterate is the next iteration's residual.  The
 // shift sigma of newton_solve shrinks 4-fold per Newton iteration, so near a stable
-// equilibrium the iteration is plain Newton.  Mixed mode: FP32 cannot resolve eigenvalues
-// of G K G below about 1e-7 of its norm (the rigid motions of a particle in a very soft
-// buffer come close to that), so when an FP32 correction fails to lower the FP64
-// residual the iteration is redone with an FP64 Krylov solve, and the rest of this solve
-// stays in FP64 (iterative refinement falling back to the working precision).
+// equilibrium the iteration is plain Newton.  Where the tangent has negative eigenvalues
+// at the equilibrium itself, a shifted correction cannot lower the residual along them:
+// when a CG correction (FP32 or FP64) fails the line search, the iteration is redone
+// with FP64 MINRES on the unshifted system, and the rest of this solve uses it.
 template <typename R>
 static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
   bool hi = !is_mixed(c);  // Krylov in FP64
+  bool mr = false;         // MINRES
   auto resid = [&]() {
     return hi ? residual_mech<double>(c, den, c.pd.state) : residual_mech<R>(c, den, P.state);
   };
@@ -927,12 +1037,18 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
     if (!(err == err)) fail(FG_ERR_NUMERIC, "mechanical residual is not finite");
     if (err <= c.o.tol_newton) return;
     if (it >= c.o.max_newton) fail(FG_ERR_NOCONV, "mechanical Newton hit max_newton");
-    const int n = hi ? newton_solve<double>(c, c.pd, sigma, s) : newton_solve<R>(c, P, sigma, s);
+    int n;
+    if (mr) {
+      to_prec<double>(c, c.GP, c.pd.b, 9 * c.V, -1.0);
+      n = minres_mech(c, mixed_tol(c, c.o.tol_cg), c.o.max_cg);
+    } else {
+      n = hi ? newton_solve<double>(c, c.pd, sigma, s) : newton_solve<R>(c, P, sigma, s);
+    }
     s.cg_mech += n;
     s.newton_mech += 1;
     if (verbose())
       fprintf(stderr, "[fg] newton %d%s err %.3e cg %d rr/bb %.3e status %d snaps %d\n", it,
-              hi && is_mixed(c) ? " (fp64)" : "", err, n,
+              mr ? " (minres)" : "", err, n,
               c.ks_host[KS_MECH].rr / (c.ks_host[KS_MECH].bb > 0 ? c.ks_host[KS_MECH].bb : 1.0),
               c.ks_host[KS_MECH].status, c.ks_host[KS_MECH].snaps);
     const double* dF;
@@ -974,14 +1090,14 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
       }
       s.newton_damped += 1;
     }
-    if (!ok && !hi) {
-      // the FP32 correction did not lower the FP64 residual: back to F_bk, FP64 from here
+    if (!ok && !mr) {
+      // the CG correction did not lower the FP64 residual: back to F_bk, FP64 MINRES from here
       dcopy(c.F, c.Fbk, 9 * c.V * sizeof(double), c.st);
       hi = true;
-      s.newton_fp64 += 1;
+      mr = true;
+      s.newton_minres += 1;
       err = resid();
-      sigma = 0.0;
-      if (verbose()) fprintf(stderr, "[fg]   FP32 correction rejected: FP64 Krylov from here\n");
+      if (verbose()) fprintf(stderr, "[fg]   CG correction rejected: FP64 MINRES from here\n");
       continue;
     }
     if (!ok) fail(FG_ERR_NOCONV, "mechanical Newton: no decrease of err_res along the correction");
@@ -1209,6 +1325,501 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
   dsync(c.st);
 }
 
+// ------------------------------------------------------------------ adjoint
+
+// state vector of the tape: c (V), F (9 V), d (V), H (V)
+static void save_state(fg_ctx& c, double* buf) {
+  const long long V = c.V;
+  dcopy(buf, c.c, V * sizeof(double), c.st);
+  dcopy(buf + V, c.F, 9 * V * sizeof(double), c.st);
+  dcopy(buf + 10 * V, c.d, V * sizeof(double), c.st);
+  dcopy(buf + 11 * V, c.H, V * sizeof(double), c.st);
+}
+
+static void load_state(fg_ctx& c, const double* buf, double* cc, double* F, double* d, double* H) {
+  const long long V = c.V;
+  dcopy(cc, buf, V * sizeof(double), c.st);
+  dcopy(F, buf + V, 9 * V * sizeof(double), c.st);
+  dcopy(d, buf + 10 * V, V * sizeof(double), c.st);
+  dcopy(H, buf + 11 * V, V * sizeof(double), c.st);
+}
+
+static void free_tape(fg_ctx& c) {
+  if (!c.tape) return;
+  for (double* p : c.tape->ckpt) dfree(p);
+  delete c.tape;
+  c.tape = nullptr;
+}
+
+// grad_f u (3 V) and grad_f^H f (V) of the chemistry operator, FP64
+static void grad3(fg_ctx& c, const double* u, double* out) {
+  Prec<double>& P = c.pd;
+  PassArgs<double> a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.rin = u;
+  a.cout = P.S1;
+  P.ox->xf_copy1(a, c.st);
+  const double zc[4] = {1.0 / (double)c.V, 0, 0, 0};
+  yzy(c, P, nullptr, 1, P.oz->z_grad, 3, zc, nullptr);
+  a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = out;
+  P.ox->xi_store3(a, c.st);
+}
+
+static void divadj(fg_ctx& c, const double* f, double* out) {
+  Prec<double>& P = c.pd;
+  PassArgs<double> a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.rin = f;
+  a.cout = P.S1;
+  P.ox->xf_copy3(a, c.st);
+  const double zc[4] = {1.0 / (double)c.V, 0, 0, 0};
+  yzy(c, P, nullptr, 3, P.oz->z_div, 1, zc, nullptr);
+  a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = out;
+  P.ox->xi_store1(a, c.st);
+}
+
+static void axpy64(fg_ctx& c, double* out, const double* x, double s, const double* y, long long n) {
+  VArgs v = vbase(c, n);  // out = x + s y
+  v.in[0] = x;
+  v.in[1] = y;
+  v.out[0] = out;
+  v.s[0] = s;
+  launch_vec<KAxpyTo>(v, c.st);
+}
+
+// work space of the reverse pass (FP64)
+struct AdjWork {
+  double *lamM, *lamD, *lamH, *chi, *lamC, *gl, *gm, *Ll, *gctot, *tmpV, *sweepD;
+  double* seeds[2];  // two seed sets (c V, F 9 V, d V, H V) = 12 V each
+  double *gE, *gG, *gD;
+  std::vector<double*> Q;  // GMRES basis
+  std::vector<void*> mem;
+  fg_ctx* c = nullptr;
+  double* get(long long n) {
+    double* p = (double*)dalloc((size_t)n * sizeof(double));
+    mem.push_back(p);
+    dzero(p, (size_t)n * sizeof(double), c->st);
+    return p;
+  }
+  ~AdjWork() {
+    for (void* p : mem) dfree(p);
+  }
+};
+
+static const double* seed_c(const double* S, long long) { return S; }
+static const double* seed_F(const double* S, long long V) { return S + V; }
+static const double* seed_d(const double* S, long long V) { return S + 10 * V; }
+static const double* seed_H(const double* S, long long V) { return S + 11 * V; }
+
+// GKG lam = G rhs, lam in W.lamM (FP64 CG, negative curvature taken, caps are errors)
+static int adj_solve_M(fg_ctx& c, const double* rhs, double* out) {
+  Prec<double>& D = c.pd;
+  op_gres(c, D, rhs, D.b, nullptr);
+  const int n = cg_solve_mech<double>(c, D, c.o.tol_cg, c.o.max_cg, nullptr, 0.0, nullptr, 1);
+  dcopy(out, D.x, 9 * c.V * sizeof(double), c.st);
+  return n;
+}
+
+// A(H_eff) lam = rhs (phase-field PCG from zero)
+static int adj_solve_D(fg_ctx& c, const double* rhs, double* out) {
+  Prec<double>& D = c.pd;
+  dcopy(D.b, rhs, c.V * sizeof(double), c.st);
+  dzero(D.x, c.V * sizeof(double), c.st);
+  const int n = pcg_pff<double>(c, D, c.Heff, c.o.tol_pff_cg, c.o.max_cg);
+  dcopy(out, D.x, c.V * sizeof(double), c.st);
+  return n;
+}
+
+template <int LAW>
+static void adj_rhs_M(fg_ctx& c, const double* sF, const double* lamH, double* out, double* chi) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = sF;
+  v.in[1] = lamH;
+  v.in[2] = c.F;
+  v.in[3] = c.c;
+  v.in[4] = c.Ht;
+  v.in[5] = c.lam;
+  v.in[6] = c.mu_;
+  v.in[7] = c.Om;
+  v.in[8] = c.c0;
+  v.in[9] = c.smax;
+  v.in[10] = c.gcr;
+  v.out[0] = out;
+  v.out[1] = chi;
+  v.s[0] = c.o.gc / (2.0 * c.o.lc);
+  launch_vec<KAdjRhsM<LAW>>(v, c.st);
+}
+
+template <int LAW>
+static void adj_rhs_D(fg_ctx& c, const double* sd, const double* lamM, double* out) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = sd;
+  v.in[1] = lamM;
+  v.in[2] = c.F;
+  v.in[3] = c.c;
+  v.in[4] = c.d;
+  v.in[5] = c.lam;
+  v.in[6] = c.mu_;
+  v.in[7] = c.Om;
+  v.in[8] = c.c0;
+  v.out[0] = out;
+  launch_vec<KAdjRhsD<LAW>>(v, c.st);
+}
+
+static void adj_lamH(fg_ctx& c, const double* sH, const double* lamD, double* out) {
+  VArgs v = vbase(c, c.V);
+  v.in[0] = sH;
+  v.in[1] = lamD;
+  v.in[2] = c.d;
+  v.in[3] = c.gcr;
+  v.out[0] = out;
+  launch_vec<KAdjLamH>(v, c.st);
+}
+
+// one transposed Gauss-Seidel sweep: lamM = (GKG)^-1 G (sF + chi lamH Z),
+// lamD = A^-1 (sd - dP/dd : lamM)
+template <int LAW>
+static void adj_sweep(fg_ctx& c, AdjWork& W, const double* sF, const double* sd, const double* lamH,
+                      double* lamM, double* lamD, fg_adjoint_stats* as) {
+  adj_rhs_M<LAW>(c, sF, lamH, c.dF, W.chi);
+  const int nm = adj_solve_M(c, c.dF, lamM);
+  adj_rhs_D<LAW>(c, sd, lamM, W.tmpV);
+  const int nd = adj_solve_D(c, W.tmpV, lamD);
+  if (as) {
+    as->cg_mech += nm;
+    as->cg_pff += nd;
+    as->sweeps += 1;
+  }
+}
+
+// Reverse of one converged step: the context holds the step's output state (c, F, d, H)
+// and its t-state (c_t, F_t, d_t, H_t); S_out are the seeds of the outputs, S_in receives
+// those of the inputs; gradients accumulate into W.gE, W.gG, W.gD.
+template <int LAW>
+static void adj_step(fg_ctx& c, AdjWork& W, const double* S_out, double* S_in, double dt,
+                     const double* dFbar, fg_adjoint_stats* as) {
+  const long long V = c.V;
+  Prec<double>& D = c.pd;
+  refresh_heff(c);
+  hbar_from_sum(c);
+  mech_state<double>(c, c.F, nullptr, nullptr, D.state);
+  check_flags(c, "adjoint state");
+  // (F, H, d) block
+  adj_sweep<LAW>(c, W, seed_F(S_out, V), seed_d(S_out, V), seed_H(S_out, V), W.lamM, W.lamD, as);
+  const double nchi = reduce_sum(c, W.chi, V, false);
+  if (nchi > 0.0) {
+    // GMRES on (I - T) lamD = lamD0, T x = sweep(0, 0, 2 r (1 - d) x).lamD
+    const int m = std::max(1, std::min(c.o.max_stag, 60));
+    while ((int)W.Q.size() < m + 1) W.Q.push_back(W.get(V));
+    std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+    const double beta = sqrt(dotd(c, W.lamD, W.lamD, V));
+    int k = 0;
+    bool conv = beta == 0.0;
+    if (!conv) {
+      VArgs v = vbase(c, V);
+      v.in[0] = W.lamD;
+      v.out[0] = W.Q[0];
+      v.s[0] = 1.0 / beta;
+      launch_vec<KScaleTo<double>>(v, c.st);
+      g[0] = beta;
+    }
+    for (; !conv && k < m; ++k) {
+      double* w = W.Q[k + 1];
+      adj_lamH(c, nullptr, W.Q[k], W.tmpV);
+      double* tM = c.Fbk;  // 9 V scratch
+      adj_sweep<LAW>(c, W, nullptr, nullptr, W.tmpV, tM, W.sweepD, as);
+      axpy64(c, w, W.Q[k], -1.0, W.sweepD, V);  // w = Q_k - T Q_k
+      for (int j = 0; j <= k; ++j) {  // modified Gram-Schmidt
+        const double h = dotd(c, W.Q[j], w, V);
+        Hm[(size_t)j * m + k] = h;
+        axpy64(c, w, w, -h, W.Q[j], V);
+      }
+      const double hn = sqrt(dotd(c, w, w, V));
+      Hm[(size_t)(k + 1) * m + k] = hn;
+      // Givens rotations of the Hessenberg column
+      for (int j = 0; j < k; ++j) {
+        const double a = Hm[(size_t)j * m + k], b = Hm[(size_t)(j + 1) * m + k];
+        Hm[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
+        Hm[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * b;
+      }
+      const double a = Hm[(size_t)k * m + k], b = Hm[(size_t)(k + 1) * m + k];
+      const double r = hypot(a, b);
+      cs[k] = r > 0.0 ? a / r : 1.0;
+      sn[k] = r > 0.0 ? b / r : 0.0;
+      Hm[(size_t)k * m + k] = r;
+      Hm[(size_t)(k + 1) * m + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      if (as) as->gmres += 1;
+      if (fabs(g[k + 1]) <= c.o.tol_stag * beta || hn == 0.0) {
+        conv = true;
+        ++k;
+        break;
+      }
+      VArgs v = vbase(c, V);
+      v.in[0] = w;
+      v.out[0] = w;
+      v.s[0] = 1.0 / hn;
+      launch_vec<KScaleTo<double>>(v, c.st);
+    }
+    if (!conv) fail(FG_ERR_NOCONV, "adjoint: GMRES on the phase-field multiplier hit max_stag");
+    std::vector<double> y(k, 0.0);  // back substitution
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int j = i + 1; j < k; ++j) t -= Hm[(size_t)i * m + j] * y[j];
+      y[i] = t / Hm[(size_t)i * m + i];
+    }
+    dzero(W.lamD, V * sizeof(double), c.st);
+    for (int j = 0; j < k; ++j) axpy64(c, W.lamD, W.lamD, y[j], W.Q[j], V);
+    adj_lamH(c, seed_H(S_out, V), W.lamD, W.lamH);
+    adj_rhs_M<LAW>(c, seed_F(S_out, V), W.lamH, c.dF, W.chi);
+    const int nm = adj_solve_M(c, c.dF, W.lamM);
+    if (as) as->cg_mech += nm;
+  }
+  adj_lamH(c, seed_H(S_out, V), W.lamD, W.lamH);
+  {
+    VArgs v = vbase(c, V);
+    v.in[0] = W.lamM;
+    v.in[1] = W.lamD;
+    v.in[2] = W.lamH;
+    v.in[3] = seed_c(S_out, V);
+    v.in[4] = c.F;
+    v.in[5] = c.c;
+    v.in[6] = c.d;
+    v.in[7] = c.H;
+    v.in[8] = c.Ht;
+    v.in[9] = c.lam;
+    v.in[10] = c.mu_;
+    v.in[11] = c.Om;
+    v.in[12] = c.c0;
+    v.in[13] = c.smax;
+    v.in[14] = c.gcr;
+    v.out[0] = W.gE;
+    v.out[1] = W.gG;
+    v.out[2] = (double*)seed_H(S_in, V);
+    v.out[3] = W.gctot;
+    v.s[0] = c.o.gc / (2.0 * c.o.lc);
+    launch_vec<KAdjBlockOut<LAW>>(v, c.st);
+  }
+  // chemistry: F~ = F_t + (Fbar - Fbar_t)
+  {
+    VArgs v = vbase(c, 9 * V);
+    v.in[0] = c.Ft;
+    v.out[0] = c.Fbk;
+    for (int k = 0; k < 9; ++k) v.s[k] = dFbar[k];
+    launch_vec<KShiftF>(v, c.st);
+  }
+  chem_cond<double>(c, D, c.Fbk, c.ct, c.dt);
+  chem_prep<double>(c, D, dt, c.Fbk);
+  {
+    VArgs v = vbase(c, V);
+    v.in[0] = c.c;
+    v.in[1] = W.gctot;
+    v.in[2] = c.Fbk;
+    v.in[3] = c.dt;
+    v.in[4] = c.lam;
+    v.in[5] = c.mu_;
+    v.in[6] = c.Om;
+    v.in[7] = c.c0;
+    v.out[0] = D.w;
+    v.out[1] = D.b;
+    v.s[0] = 1.0 / c.o.RT;
+    v.s[1] = 1.0 / c.o.cmax;
+    launch_vec<KAdjChemM<LAW>>(v, c.st);
+  }
+  read_ks(c);
+  if (*c.flags_host & ST_NUMERIC) {
+    dzero(c.flags, sizeof(int), c.st);
+    fail(FG_ERR_NUMERIC, "adjoint: chemistry Jacobian dmu/dc not positive");
+  }
+  check_flags(c, "adjoint chemistry");
+  const int nc = cg_solve<double>(c, D, V, KS_CHEM, c.o.tol_chem_cg, c.o.max_cg,
+                                  [&](const double* p, double* q, const int* done) {
+                                    return op_chem(c, D, p, q, dt, done);
+                                  });
+  if (as) as->cg_chem += nc;
+  dcopy(W.lamC, D.x, V * sizeof(double), c.st);
+  grad3(c, W.lamC, W.gl);
+  grad3(c, c.mu, W.gm);
+  op_chem_L(c, D, W.lamC, nullptr);
+  {
+    PassArgs<double> a = pbase(c, D, nullptr);
+    a.tw = D.twx;
+    a.cin = D.S1;
+    a.rout = W.Ll;
+    D.ox->xi_store1(a, c.st);
+  }
+  {
+    VArgs v = vbase(c, V);
+    v.in[0] = W.lamC;
+    v.in[1] = W.gl;
+    v.in[2] = W.gm;
+    v.in[3] = W.Ll;
+    v.in[4] = c.c;
+    v.in[5] = c.ct;
+    v.in[6] = c.dt;
+    v.in[7] = c.Fbk;
+    v.in[8] = c.D;
+    v.in[9] = c.lam;
+    v.in[10] = c.mu_;
+    v.in[11] = c.Om;
+    v.in[12] = c.c0;
+    v.out[0] = (double*)seed_c(S_in, V);
+    v.out[1] = (double*)seed_d(S_in, V);
+    v.out[2] = (double*)seed_F(S_in, V);
+    v.out[3] = W.gD;
+    v.out[4] = W.gE;
+    v.s[0] = dt;
+    v.s[1] = 1.0 / c.o.RT;
+    v.s[2] = 1.0 / c.o.cmax;
+    launch_vec<KAdjChemOut<LAW>>(v, c.st);
+  }
+  check_flags(c, "adjoint chemistry");
+  if (as) as->steps += 1;
+}
+
+// Gamma_E of the stored phase field into the d seed of S; its direct log g_c gradient into gG
+static double crack_loss(fg_ctx& c, AdjWork& W, double* S) {
+  const long long V = c.V;
+  grad3(c, c.d, W.gl);
+  VArgs v = vbase(c, V);
+  v.in[0] = c.d;
+  v.in[1] = W.gl;
+  v.in[2] = c.gcr;
+  v.out[0] = W.gG;
+  v.out[1] = W.gm;
+  v.s[0] = c.o.gc;
+  v.s[1] = c.o.lc;
+  v.s[2] = c.h[0] * c.h[1] * c.h[2];
+  launch_vec<KCrackLoss>(v, c.st);
+  fin<FStore>(c, KS_MISC, VEC_BLOCKS, nullptr);
+  read_ks(c);
+  const double loss = c.ks_host[KS_MISC].aux;
+  divadj(c, W.gm, W.tmpV);
+  VArgs u = vbase(c, V);
+  u.in[0] = c.d;
+  u.in[1] = W.tmpV;
+  u.in[2] = c.gcr;
+  u.out[0] = (double*)seed_d(S, V);
+  u.s[0] = c.o.gc;
+  u.s[1] = c.o.lc;
+  u.s[2] = c.h[0] * c.h[1] * c.h[2];
+  launch_vec<KCrackSeed>(u, c.st);
+  return loss;
+}
+
+template <typename R>
+static double adjoint_impl(fg_ctx& c, Prec<R>& P, int loss, const double* sc, const double* sF,
+                           const double* sd, double* gE, double* gG, double* gD, fg_adjoint_stats* as) {
+  Tape& T = *c.tape;
+  const long long V = c.V;
+  const int nsteps = (int)T.dts.size();
+  AdjWork W;
+  W.c = &c;
+  W.lamM = W.get(9 * V);
+  W.lamD = W.get(V);
+  W.lamH = W.get(V);
+  W.chi = W.get(V);
+  W.lamC = W.get(V);
+  W.gl = W.get(3 * V);
+  W.gm = W.get(3 * V);
+  W.Ll = W.get(V);
+  W.gctot = W.get(V);
+  W.tmpV = W.get(V);
+  W.sweepD = W.get(V);
+  W.seeds[0] = W.get(12 * V);
+  W.seeds[1] = W.get(12 * V);
+  W.gE = W.get(V);
+  W.gG = W.get(V);
+  W.gD = W.get(V);
+  // the state at the call (returned to afterwards): current and t-state
+  double* fin_now = W.get(12 * V);
+  double* fin_t = W.get(12 * V);
+  save_state(c, fin_now);
+  dcopy(fin_t, c.ct, V * sizeof(double), c.st);
+  dcopy(fin_t + V, c.Ft, 9 * V * sizeof(double), c.st);
+  dcopy(fin_t + 10 * V, c.dt, V * sizeof(double), c.st);
+  dcopy(fin_t + 11 * V, c.Ht, V * sizeof(double), c.st);
+  double fb_now[9], fb_prev[9];
+  memcpy(fb_now, c.Fbar, sizeof(fb_now));
+  memcpy(fb_prev, c.Fbar_prev, sizeof(fb_prev));
+  const double last_dt = c.last_dt;
+  const bool stepped = c.stepped;
+  // loss seeds of the final state
+  double* Sout = W.seeds[0];
+  double* Sin = W.seeds[1];
+  double value = 0.0;
+  if (loss == FG_LOSS_CRACK_ENERGY) {
+    value = crack_loss(c, W, Sout);
+  } else {
+    if (sc) dcopy(Sout, sc, V * sizeof(double), c.st);
+    if (sF) dcopy(Sout + V, sF, 9 * V * sizeof(double), c.st);
+    if (sd) dcopy(Sout + 10 * V, sd, V * sizeof(double), c.st);
+  }
+  const int every = T.every;
+  std::vector<double*> snap(every + 1);
+  for (auto& p : snap) p = W.get(12 * V);
+  std::vector<std::array<double, 9>> snap_fb(every + 1);
+  c.strict = true;
+  try {
+    for (int s = (int)T.ckpt.size() - 1; s >= 0; --s) {
+      const int k0 = s * every, k1 = std::min(nsteps, k0 + every);
+      // recompute the segment from its checkpoint
+      load_state(c, T.ckpt[s], c.c, c.F, c.d, c.H);
+      refresh_heff(c);
+      memcpy(c.Fbar, T.ckpt_fbar[s].data(), sizeof(c.Fbar));
+      dcopy(snap[0], T.ckpt[s], 12 * V * sizeof(double), c.st);
+      snap_fb[0] = T.ckpt_fbar[s];
+      for (int k = k0; k < k1; ++k) {
+        fg_stats st{};
+        step_impl<R>(c, P, T.dts[k], T.fbars[k].data(), st);
+        if (as) as->recomputed += 1;
+        save_state(c, snap[k - k0 + 1]);
+        snap_fb[k - k0 + 1] = T.fbars[k];
+      }
+      // reverse through the segment
+      for (int k = k1 - 1; k >= k0; --k) {
+        const int j = k - k0;
+        load_state(c, snap[j + 1], c.c, c.F, c.d, c.H);
+        load_state(c, snap[j], c.ct, c.Ft, c.dt, c.Ht);
+        double dFb[9];
+        for (int q = 0; q < 9; ++q) dFb[q] = snap_fb[j + 1][q] - snap_fb[j][q];
+        dzero(Sin, 12 * V * sizeof(double), c.st);
+        if (c.law == FG_SVK) adj_step<LAW_SVK_>(c, W, Sout, Sin, T.dts[k], dFb, as);
+        else adj_step<LAW_NH_>(c, W, Sout, Sin, T.dts[k], dFb, as);
+        std::swap(Sout, Sin);
+      }
+    }
+  } catch (...) {
+    c.strict = false;
+    load_state(c, fin_now, c.c, c.F, c.d, c.H);
+    load_state(c, fin_t, c.ct, c.Ft, c.dt, c.Ht);
+    refresh_heff(c);
+    memcpy(c.Fbar, fb_now, sizeof(fb_now));
+    dsync(c.st);
+    throw;
+  }
+  c.strict = false;
+  load_state(c, fin_now, c.c, c.F, c.d, c.H);
+  load_state(c, fin_t, c.ct, c.Ft, c.dt, c.Ht);
+  refresh_heff(c);
+  memcpy(c.Fbar, fb_now, sizeof(fb_now));
+  memcpy(c.Fbar_prev, fb_prev, sizeof(fb_prev));
+  c.last_dt = last_dt;
+  c.stepped = stepped;
+  if (gE) dcopy(gE, W.gE, V * sizeof(double), c.st);
+  if (gG) dcopy(gG, W.gG, V * sizeof(double), c.st);
+  if (gD) dcopy(gD, W.gD, V * sizeof(double), c.st);
+  dsync(c.st);
+  return value;
+}
+
 }  // namespace fg
 
 using namespace fg;
@@ -1311,8 +1922,35 @@ void fg_destroy(fg_ctx* ctx) {
   for (auto& v : ctx->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
 #endif
+  free_tape(*ctx);
   free_all(*ctx);
   delete ctx;
+}
+
+int fg_tape_begin(fg_ctx* c, int ckpt_every) {
+  FG_API_BEGIN
+  if (!c || ckpt_every < 1) fail(FG_ERR_INVALID, "fg_tape_begin: bad argument");
+  free_tape(*c);
+  c->tape = new Tape();
+  c->tape->every = ckpt_every;
+  FG_API_END
+}
+
+int fg_adjoint(fg_ctx* c, int loss, const double* seed_c, const double* seed_F, const double* seed_d,
+               double* loss_value, double* grad_logE, double* grad_loggc, double* grad_logD,
+               fg_adjoint_stats* st) {
+  FG_API_BEGIN
+  if (!c) fail(FG_ERR_INVALID, "fg_adjoint: null context");
+  if (!c->tape || c->tape->dts.empty()) fail(FG_ERR_INVALID, "fg_adjoint: no recorded steps (fg_tape_begin, fg_step)");
+  if (loss != FG_LOSS_CRACK_ENERGY && loss != FG_LOSS_SEEDS) fail(FG_ERR_INVALID, "fg_adjoint: loss");
+  fg_adjoint_stats as;
+  memset(&as, 0, sizeof(as));
+  double v = is_mixed(*c)
+                 ? adjoint_impl<float>(*c, c->pf, loss, seed_c, seed_F, seed_d, grad_logE, grad_loggc, grad_logD, &as)
+                 : adjoint_impl<double>(*c, c->pd, loss, seed_c, seed_F, seed_d, grad_logE, grad_loggc, grad_logD, &as);
+  if (loss_value) *loss_value = v;
+  if (st) *st = as;
+  FG_API_END
 }
 
 int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases,
@@ -1473,8 +2111,33 @@ int fg_step(fg_ctx* c, double dt, const double Fbar[9], fg_stats* st) {
   g_err.clear();
   try {
     if (!c || !Fbar || !(dt > 0)) fail(FG_ERR_INVALID, "fg_step: bad argument");
-    if (is_mixed(*c)) step_impl<float>(*c, c->pf, dt, Fbar, s);
-    else step_impl<double>(*c, c->pd, dt, Fbar, s);
+    Tape* T = c->tape;
+    const bool ck = T && T->dts.size() % (size_t)T->every == 0;
+    if (ck) {  // checkpoint of the state before this step
+      double* buf = (double*)dalloc((size_t)12 * c->V * sizeof(double));
+      T->ckpt.push_back(buf);
+      std::array<double, 9> fb;
+      memcpy(fb.data(), c->Fbar, sizeof(c->Fbar));
+      T->ckpt_fbar.push_back(fb);
+      save_state(*c, buf);
+    }
+    try {
+      if (is_mixed(*c)) step_impl<float>(*c, c->pf, dt, Fbar, s);
+      else step_impl<double>(*c, c->pd, dt, Fbar, s);
+    } catch (Fail&) {
+      if (ck) {
+        dfree(T->ckpt.back());
+        T->ckpt.pop_back();
+        T->ckpt_fbar.pop_back();
+      }
+      throw;
+    }
+    if (T) {
+      T->dts.push_back(dt);
+      std::array<double, 9> fb;
+      memcpy(fb.data(), Fbar, sizeof(fb));
+      T->fbars.push_back(fb);
+    }
   } catch (Fail& f) {
     rc = f.code;
   }

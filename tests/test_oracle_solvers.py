@@ -312,6 +312,27 @@ def test_shifted_cg_on_indefinite_system():
     np.testing.assert_allclose(x, [1.0 / 3.0, 1.0, 0.5], rtol=1e-12)
 
 
+def test_minres_solves_indefinite_systems_with_monotone_residual():
+    """MINRES on symmetric matrices with eigenvalues of both signs (one of them near zero)
+    reaches the dense solution in n steps, and the residual |b - A x_k| of its k-th iterate
+    never grows with k, as its minimising property requires."""
+    rng = np.random.default_rng(0)
+    for n in (6, 10):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        ev = np.concatenate([rng.uniform(0.5, 3.0, n - 3), [-1.0, -0.2, 0.05]])
+        A = Q @ np.diag(ev) @ Q.T
+        b = rng.standard_normal(n)
+        x, it = O.minres(lambda v: A @ v, b, 1e-13, 100)
+        np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+        assert it <= n + 2
+        res = [np.linalg.norm(b - A @ O.minres(lambda v: A @ v, b, 0.0, k)[0]) for k in range(1, n + 1)]
+        assert all(res[i + 1] <= res[i] * (1 + 1e-12) for i in range(n - 1))
+    # a symmetric positive definite system: the same solution as CG
+    A = np.diag([3.0, 1.0, 2.0])
+    x, _ = O.minres(lambda v: A @ v, np.ones(3), 1e-14, 10)
+    np.testing.assert_allclose(x, [1.0 / 3.0, 1.0, 0.5], rtol=1e-13)
+
+
 def test_cg_truncation_returns_saved_iterate():
     """A truncated solve returns the last iterate saved at a 4x drop of |r|^2 when its own
     residual has grown since: diag(4, 4, 2, -1), b = (1, 1, 1, 1/2), worked by hand.
