@@ -313,3 +313,16 @@ def test_coupled_adjoint_3d_checkpoints_and_seeds(lib):
         for k in ("E", "gc", "D"):
             assert rel_err(out[ckpt][1][k], out[1][1][k]) < 1e-9, (ckpt, k)
     assert out[4][2]["recomputed"] == 4 and out[1][2]["steps"] == 4
+    # the same gradients through FG_LOSS_SEEDS with the crack energy's seed dGamma/dd
+    from oracle import fg_oracle_adjoint as A
+    sol = B.from_workload(w, lib=lib, **ADJ_TOLS)
+    sol.tape(2)
+    for _ in range(4):
+        sol.step(w.dt)
+    val, seed_d, dens = A.crack_energy_seed(sol.get(B.FIELD_D), oracle_params(w))
+    assert abs(val - out[1][0]) < 1e-10 * val
+    _, gs, _ = sol.adjoint(B.FG_LOSS_SEEDS, seed_d=seed_d)
+    assert rel_err(gs["E"], out[1][1]["E"]) < 1e-9
+    assert rel_err(gs["D"], out[1][1]["D"]) < 1e-9
+    assert rel_err(gs["gc"] + dens, out[1][1]["gc"]) < 1e-9
+    sol.close()
