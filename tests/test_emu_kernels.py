@@ -194,3 +194,38 @@ def test_emulated_coupled_adjoint_matches_oracle(emu, ckpt):
         assert rel_err(g2[k], g[k]) < 1e-9, k
     np.testing.assert_array_equal(sol.get(B.FIELD_D), d_before)  # state restored
     sol.close()
+
+
+def test_emulated_coupled_steps_autograd(emu):
+    """torch autograd through CoupledSteps: the gradient of a loss on the final (c, F, d)
+    equals the one fg_adjoint returns for the same seeds, and a directional derivative
+    of the loss agrees with central differences of the forward."""
+    import torch
+    from paper_2411_16583_gb300.autograd import coupled_steps
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, prm_of, phases, pid = _disc(n=12, smax=21e6)
+    w = S.Workload(name="disc12", shape=shape, h=(1e-7,) * 3, phases=phases,
+                   phase_id=pid.astype(np.uint8), cdot_B=src, c_init=np.full(shape, 0.01),
+                   gc=1.0, lc=2e-7, dt=1.0, nsteps=2)
+    w.tol = dict(tol_newton=1e-12, tol_cg=1e-13, tol_chem=1e-12, tol_chem_cg=1e-13,
+                 tol_pff_cg=1e-13, tol_stag=1e-10, max_stag=400)
+    spec = dict(w=w, nsteps=2, lib=emu, ckpt=2)
+    rng = np.random.default_rng(1)
+    wc, wd = rng.standard_normal(shape), rng.standard_normal(shape)
+    wF = rng.standard_normal((3, 3) + shape)
+
+    def loss_of(lE, lG, lD):
+        c, F, d = coupled_steps(lE, lG, lD, spec)
+        return ((c * torch.from_numpy(wc)).sum() + (F * torch.from_numpy(wF)).sum()
+                + (d * torch.from_numpy(wd)).sum())
+    t = [torch.tensor(x, requires_grad=True) for x in logs]
+    L = loss_of(*t)
+    L.backward()
+    h = 1e-4
+    dirs = [0.3 * rng.standard_normal(shape) for _ in range(3)]
+    with torch.no_grad():
+        lp = loss_of(*[torch.tensor(x + h * dx) for x, dx in zip(logs, dirs)]).item()
+        lm = loss_of(*[torch.tensor(x - h * dx) for x, dx in zip(logs, dirs)]).item()
+    fd = (lp - lm) / (2 * h)
+    adj = sum(float((ti.grad.numpy() * dx).sum()) for ti, dx in zip(t, dirs))
+    assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
