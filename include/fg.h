@@ -286,6 +286,17 @@ int fg_adjoint(fg_ctx* ctx, int loss, const double* seed_c, const double* seed_F
                const double* seed_d, double* loss_value, double* grad_logE, double* grad_loggc,
                double* grad_logD, fg_adjoint_stats* st);
 
+/*
+ * Restart files: fg_save writes the evolving state of the context (c, F, d, H, the
+ * t-state of the last step, Fbar, the previous Fbar and the last dt) to a binary file;
+ * fg_load reads one into a context set up with the same grid, law and materials (the
+ * file holds no material data), which then steps as the saved one would.  Doubles in the
+ * machine's byte order.  Errors: FG_ERR_INVALID (file cannot be opened, written or read,
+ * is not a state file, or its grid or law differs), FG_ERR_CUDA.
+ */
+int fg_save(fg_ctx* ctx, const char* path);
+int fg_load(fg_ctx* ctx, const char* path);
+
 /* Releases the context, its tape and its device memory.  NULL is ignored. */
 void fg_destroy(fg_ctx* ctx);
 

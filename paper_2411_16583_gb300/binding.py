@@ -78,7 +78,7 @@ EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_re
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
            "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
-           "fg_tape_begin", "fg_adjoint",
+           "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load",
            "fg_kernel_launches", "fg_destroy", "fg_last_error"]
 
 _libs = {}
@@ -113,6 +113,8 @@ def load_library(path=LIB_PATH):
     lib.fg_solve_mech.argtypes = [C.c_void_p, dp, C.POINTER(Stats)]
     lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.fg_tape_begin.argtypes = [C.c_void_p, C.c_int]
+    lib.fg_save.argtypes = [C.c_void_p, C.c_char_p]
+    lib.fg_load.argtypes = [C.c_void_p, C.c_char_p]
     lib.fg_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, dp,
                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdjStats)]
     lib.fg_batch_setup.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
@@ -251,6 +253,14 @@ class Solver:
         it = C.c_int()
         self._check(self.lib.fg_adjoint_mech(self.ctx, _ptr(Wh), _ptr(g), C.byref(it)))
         return g, it.value
+
+    def save(self, path):
+        """Writes the evolving state to a restart file (fg_save)."""
+        self._check(self.lib.fg_save(self.ctx, os.fsencode(path)))
+
+    def load(self, path):
+        """Reads a restart file written for the same grid, law and materials (fg_load)."""
+        self._check(self.lib.fg_load(self.ctx, os.fsencode(path)))
 
     def tape(self, ckpt_every=1):
         """Starts recording the following steps for ``adjoint`` (checkpoint every k steps)."""

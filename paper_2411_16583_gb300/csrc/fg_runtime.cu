@@ -1927,6 +1927,74 @@ void fg_destroy(fg_ctx* ctx) {
   delete ctx;
 }
 
+// file layout: magic "FGST", version 1, nx ny nz law (int32), Fbar[9], Fbar_prev[9],
+// last_dt, stepped (as a double), then c F d H and c_t F_t d_t H_t (24 V doubles)
+static const char FG_MAGIC[4] = {'F', 'G', 'S', 'T'};
+
+int fg_save(fg_ctx* c, const char* path) {
+  FG_API_BEGIN
+  if (!c || !path) fail(FG_ERR_INVALID, "fg_save: null argument");
+  const long long V = c->V;
+  std::vector<double> buf(24 * V);
+  save_state(*c, buf.data());
+  dcopy(buf.data() + 12 * V, c->ct, V * sizeof(double), c->st);
+  dcopy(buf.data() + 13 * V, c->Ft, 9 * V * sizeof(double), c->st);
+  dcopy(buf.data() + 22 * V, c->dt, V * sizeof(double), c->st);
+  dcopy(buf.data() + 23 * V, c->Ht, V * sizeof(double), c->st);
+  dsync(c->st);
+  FILE* f = fopen(path, "wb");
+  if (!f) fail(FG_ERR_INVALID, std::string("fg_save: cannot open ") + path);
+  const int32_t hdr[5] = {1, c->nx, c->ny, c->nz, c->law};
+  double sc[20];
+  memcpy(sc, c->Fbar, 9 * sizeof(double));
+  memcpy(sc + 9, c->Fbar_prev, 9 * sizeof(double));
+  sc[18] = c->last_dt;
+  sc[19] = c->stepped ? 1.0 : 0.0;
+  bool ok = fwrite(FG_MAGIC, 1, 4, f) == 4 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            fwrite(sc, sizeof(sc), 1, f) == 1 &&
+            fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) fail(FG_ERR_INVALID, std::string("fg_save: write failed: ") + path);
+  FG_API_END
+}
+
+int fg_load(fg_ctx* c, const char* path) {
+  FG_API_BEGIN
+  if (!c || !path) fail(FG_ERR_INVALID, "fg_load: null argument");
+  const long long V = c->V;
+  FILE* f = fopen(path, "rb");
+  if (!f) fail(FG_ERR_INVALID, std::string("fg_load: cannot open ") + path);
+  char mg[4] = {};
+  int32_t hdr[5] = {};
+  double sc[20];
+  std::vector<double> buf(24 * V);
+  bool ok = fread(mg, 1, 4, f) == 4 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+            fread(sc, sizeof(sc), 1, f) == 1;
+  if (!ok || memcmp(mg, FG_MAGIC, 4) != 0 || hdr[0] != 1) {
+    fclose(f);
+    fail(FG_ERR_INVALID, std::string("fg_load: not a state file of this version: ") + path);
+  }
+  if (hdr[1] != c->nx || hdr[2] != c->ny || hdr[3] != c->nz || hdr[4] != c->law) {
+    fclose(f);
+    fail(FG_ERR_INVALID, "fg_load: the file's grid or law differs from the context's");
+  }
+  ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) fail(FG_ERR_INVALID, std::string("fg_load: truncated state file: ") + path);
+  load_state(*c, buf.data(), c->c, c->F, c->d, c->H);
+  dcopy(c->ct, buf.data() + 12 * V, V * sizeof(double), c->st);
+  dcopy(c->Ft, buf.data() + 13 * V, 9 * V * sizeof(double), c->st);
+  dcopy(c->dt, buf.data() + 22 * V, V * sizeof(double), c->st);
+  dcopy(c->Ht, buf.data() + 23 * V, V * sizeof(double), c->st);
+  refresh_heff(*c);
+  memcpy(c->Fbar, sc, 9 * sizeof(double));
+  memcpy(c->Fbar_prev, sc + 9, 9 * sizeof(double));
+  c->last_dt = sc[18];
+  c->stepped = sc[19] != 0.0;
+  dsync(c->st);
+  FG_API_END
+}
+
 int fg_tape_begin(fg_ctx* c, int ckpt_every) {
   FG_API_BEGIN
   if (!c || ckpt_every < 1) fail(FG_ERR_INVALID, "fg_tape_begin: bad argument");

@@ -83,3 +83,28 @@ def test_nan_input_is_reported(emu):
     st = sol.step(w.dt, check=False)
     assert st["status"] in (-5, -6)
     sol.close()
+
+
+def test_save_load_restarts_bit_identically(emu, tmp_path):
+    """A context restored from a restart file after one step takes the second step exactly
+    as the context that wrote it; a file for another grid is refused."""
+    w = S.disc2d(n=16, radius=6.0, band=3, nsteps=10)
+    a = B.from_workload(w, lib=emu)
+    a.step(w.dt)
+    path = str(tmp_path / "state.fg")
+    a.save(path)
+    b = B.from_workload(w, lib=emu)
+    b.load(path)
+    a.step(w.dt)
+    b.step(w.dt)
+    for f in (B.FIELD_C, B.FIELD_F, B.FIELD_D, B.FIELD_H):
+        np.testing.assert_array_equal(a.get(f), b.get(f))
+    np.testing.assert_array_equal(np.array(a.residual()), np.array(b.residual()))
+    w2 = S.disc2d(n=24, radius=6.0, band=3, nsteps=10)
+    c = B.from_workload(w2, lib=emu)
+    with pytest.raises(B.FgError, match="grid"):
+        c.load(path)
+    with pytest.raises(B.FgError, match="cannot open"):
+        c.load(str(tmp_path / "missing.fg"))
+    for s_ in (a, b, c):
+        s_.close()
