@@ -196,6 +196,78 @@ def _cores():
         return 1
 
 
+def cufft_comparator(sol, w, reps=10, device="cuda"):
+    """The FP32 Neo-Hookean mechanical operator y = G : F^-1[F[K : x]] of the stored state
+    assembled from torch element-wise kernels and torch.fft (cuFFT), unfused: the timed
+    comparator for the fused apply.  Returns (ms per apply, max |y - y_fused| / max |y|)."""
+    import numpy as np
+    import torch
+    from paper_2411_16583_gb300 import binding as B
+    dev = torch.device(device)
+    nz, ny, nx = w.shape
+    V = w.nvox
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, torch.float32)
+    F = f32(sol.get(B.FIELD_F).reshape(3, 3, V))
+    c = f32(sol.get(B.FIELD_C).ravel())
+    d = f32(sol.get(B.FIELD_D).ravel())
+    pid = w.phase_id.ravel()
+    tab = lambda attr: f32(np.array([getattr(p, attr) for p in w.phases])[pid])
+    E, nu, Om, c0 = tab("E"), tab("nu"), tab("Omega"), tab("c0")
+    if w.log_E is not None:
+        E = E * f32(np.exp(w.log_E.ravel()))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    a = (1 + Om * (c - c0)) ** (-1.0 / 3.0)
+    g = (1 - d) ** 2
+    Fe = (a * F).permute(2, 0, 1)                       # (V, 3, 3)
+    Bt = torch.linalg.inv(Fe).transpose(1, 2)           # F_e^-T
+    lnJ = torch.log(torch.linalg.det(Fe))
+    s1, s2, s3 = (g * a * a)[:, None, None], (mu - lam * lnJ)[:, None, None], lam[:, None, None]
+
+    def tangent(X):                                     # X (V, 3, 3): K : X
+        M = Bt @ X.transpose(1, 2) @ Bt
+        tr = (Bt * X).sum(dim=(1, 2))[:, None, None]
+        return s1 * (mu[:, None, None] * X + s2 * M + s3 * tr * Bt)
+
+    def freq(n, h):
+        k = torch.arange(n, device=dev, dtype=torch.float64)
+        q = 2 * np.pi * k / n
+        return (2.0 / h) * torch.sin(q / 2), torch.cos(q / 2)
+    (sx, cx), (sy, cy), (sz, cz) = freq(nx, w.h[0]), freq(ny, w.h[1]), freq(nz, w.h[2])
+    sx, cx = sx[: nx // 2 + 1], cx[: nx // 2 + 1]
+    cx[-1] = 0.0 if nx % 2 == 0 else cx[-1]
+    cy[ny // 2] = 0.0 if ny % 2 == 0 else cy[ny // 2]
+    cz[nz // 2] = 0.0 if nz % 2 == 0 else cz[nz // 2]
+    Z, Y, X_ = torch.meshgrid(torch.arange(nz, device=dev), torch.arange(ny, device=dev),
+                              torch.arange(nx // 2 + 1, device=dev), indexing="ij")
+    n = torch.stack([sx[X_] * cy[Y] * cz[Z], cx[X_] * sy[Y] * cz[Z], cx[X_] * cy[Y] * sz[Z]]).float()
+    n2 = (n * n).sum(0)
+    inv = torch.where(n2 > 0, 1.0 / n2, torch.zeros_like(n2))
+
+    def apply(x):                                       # x (9, V)
+        tau = tangent(x.reshape(3, 3, V).permute(2, 0, 1)).permute(1, 2, 0).reshape(3, 3, nz, ny, nx)
+        T = torch.fft.rfftn(tau, dim=(-3, -2, -1))
+        An = torch.einsum("imzyx,mzyx->izyx", T, n.to(T.dtype))
+        Y_ = torch.einsum("izyx,jzyx->ijzyx", An * inv, n.to(T.dtype))
+        return torch.fft.irfftn(Y_, s=(nz, ny, nx), dim=(-3, -2, -1)).reshape(9, V)
+    x = torch.randn(9, V, dtype=torch.float32, generator=torch.Generator().manual_seed(0)).to(dev)
+    yf = torch.empty_like(x)
+    sol.apply(B.OP_MECH, x, yf, prec=1)
+    y = apply(x)
+    diff = float((y - yf).abs().max() / yf.abs().max())
+    if dev.type != "cuda":
+        return None, diff
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    e0.record(cur)
+    for _ in range(reps):
+        y = apply(x)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, diff
+
+
 def main():
     a = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -271,8 +343,18 @@ def main():
         e2e = {"value": V * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * V * 8,
                "d2h_bytes_per_step": 11 * V * 8}
 
-    # fused matvec rates: FP32 operator of the mixed context
+    # fused matvec rates: FP32 operator of the mixed context, and the unfused cuFFT
+    # comparator of the same operator
     mech32_ms = sol.time_apply(B.OP_MECH, 1, 20)
+    comparator = None
+    if w.phases[0].law == B.FG_NEOHOOKE and rank == 0:
+        try:
+            cms, cdiff = cufft_comparator(sol, w)
+            comparator = {"kind": "torch element-wise + torch.fft (cuFFT), unfused, FP32",
+                          "ms_per_apply": cms, "voxel_applies_per_s": V / (cms * 1e-3),
+                          "max_rel_diff_vs_fused": cdiff}
+        except torch.cuda.OutOfMemoryError as e:  # noqa: F841
+            comparator = {"unavailable": "out of device memory"}
     sol.close()
     out = {}
     if a.fp64_steps > 0 and rank == 0:
@@ -327,7 +409,7 @@ def main():
                      "traffic": None},
         "kernels": sites,
         "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),
-                   "mech_fp32_ms": mech32_ms},
+                   "mech_fp32_ms": mech32_ms, "cufft_comparator": comparator},
         "step_stats": stats[-1],
         "autotuned_apply_ms": tuned_ms,
         "clocks": clk.summary(),
