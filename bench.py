@@ -59,6 +59,9 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--adjoint", action="store_true",
+                   help="time the coupled adjoint (128^3 ellipsoid with log fields, FP64, "
+                        "checkpoints every 5 steps) instead of the step benchmark")
     p.add_argument("--batch", type=int, default=0,
                    help="batched RVEs: N particles of seeded sizes {48,64,80,96}^3 (0: off)")
     return p.parse_args()
@@ -277,6 +280,8 @@ def main():
         return reference_arm(a, rank, world)
     if a.batch:
         return batch_mode(a)
+    if a.adjoint:
+        return adjoint_mode(a)
     import numpy as np
     import torch
     from paper_2411_16583_gb300 import binding as B
@@ -421,6 +426,41 @@ def main():
         line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": _cores(),
                                 "kind": "oracle", "sample": desc}
     print(json.dumps(line))
+
+
+def adjoint_mode(a):
+    """Forward steps with a tape, then the reverse pass for dGamma_E/dlog(E, g_c, D); both
+    timed with CUDA events on the context's stream (FP64 throughout)."""
+    import torch
+    from paper_2411_16583_gb300 import binding as B, synth as S
+    n = a.n if a.n != 256 else 128
+    w = S.with_log_fields(S.ellipsoid(n=n, axes=(50 * n / 128, 40 * n / 128, 35 * n / 128),
+                                      rough_std=1.5 * n / 128, rough_corr=4 * n / 128,
+                                      band=max(1, round(8 * n / 128)), nsteps=50), std=0.1)
+    stream = torch.cuda.current_stream()
+    sol = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream)
+    for _ in range(a.warmup):
+        sol.step(w.dt)
+    sol.tape(5)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(a.steps):
+        sol.step(w.dt)
+    e[1].record(stream)
+    val, g, st = sol.adjoint()
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1])
+    rev = e[1].elapsed_time(e[2])
+    print(json.dumps({"metric": "coupled adjoint: reverse-pass wall time per step", "value":
+                      rev / a.steps, "unit": "ms/step", "higher_is_better": False,
+                      "config": {"workload": f"rough ellipsoid {n}^3, per-voxel log E, log g_c, "
+                                 f"log D ~ N(0, 0.1^2), FP64, checkpoint every 5 steps",
+                                 "steps": a.steps, "warmup": a.warmup},
+                      "forward_ms_per_step": fwd / a.steps, "loss": val, "adjoint_stats": st,
+                      "grad_max": {k: float(abs(v).max()) for k, v in g.items()}}))
+    sol.close()
 
 
 def batch_mode(a):
