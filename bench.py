@@ -76,7 +76,7 @@ def _workload(n, seed, nz=0):
     axes = (100 * f, 80 * f, min(70 * f, 0.4 * nz) if nz else 70 * f)
     return S.ellipsoid(n=n, axes=axes, rough_std=3 * f, rough_corr=8 * f,
                        band=max(1, round(8 * f)), nsteps=100, seed=seed, c_perturb=0.02,
-                       shape=shape)
+                       shape=shape, phases=S.default_phases(buffer_E=S.BENCH_BUFFER_E))
 
 
 class Clocks:

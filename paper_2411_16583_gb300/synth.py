@@ -158,7 +158,14 @@ def ellipsoid(n=128, axes=(50.0, 40.0, 35.0), rough_std=1.5, rough_corr=4.0, ban
                    c_perturb=c_perturb, **kw)
 
 
+BENCH_BUFFER_E = 1e-2  # buffer stiffness of the benchmark particle, relative to the particle's
+
+
 def ellipsoid256(seed=0, nsteps=100, **kw):
+    """The 256^3 benchmark particle.  Its buffer is 100 times softer than the particle: with
+    1000 times, the particle's rigid rotations against the buffer lose their stiffness to
+    the compressive prestress after a few steps and the mechanical Newton stalls."""
+    kw.setdefault("phases", default_phases(buffer_E=BENCH_BUFFER_E))
     return ellipsoid(n=256, axes=(100.0, 80.0, 70.0), rough_std=3.0, rough_corr=8.0, band=8,
                      nsteps=nsteps, seed=seed, c_perturb=0.02, **kw)
 
