@@ -61,6 +61,21 @@ def test_invalid_arguments(emu):
     with pytest.raises(B.FgError) as e:  # initial concentration outside (0, 1)
         B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=np.full(w.shape, 1.2), lib=emu)
     assert e.value.code == -5
+    with pytest.raises(B.FgError, match="cg_indefinite") as e:  # modes 0, 1, 2 only
+        B.from_workload(w, lib=emu, cg_indefinite=3)
+    assert e.value.code == -1
+    with pytest.raises(B.FgError, match="no recorded steps") as e:  # adjoint without a tape
+        s_ = B.from_workload(w, lib=emu)
+        try:
+            s_.adjoint()
+        finally:
+            s_.close()
+    with pytest.raises(B.FgError, match="fg_tape_begin") as e:
+        s_ = B.from_workload(w, lib=emu)
+        try:
+            s_.tape(0)
+        finally:
+            s_.close()
     assert emu.fg_supported_size(64) == 1 and emu.fg_supported_size(18) == 0
 
 
