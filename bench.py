@@ -223,8 +223,14 @@ def cufft_comparator(sol, w, reps=10, device="cuda"):
     a = (1 + Om * (c - c0)) ** (-1.0 / 3.0)
     g = (1 - d) ** 2
     Fe = (a * F).permute(2, 0, 1)                       # (V, 3, 3)
-    Bt = torch.linalg.inv(Fe).transpose(1, 2)           # F_e^-T
-    lnJ = torch.log(torch.linalg.det(Fe))
+    # F_e^-T = cof(F_e) / det F_e, written out (element-wise kernels only)
+    f = [[Fe[:, i, j] for j in range(3)] for i in range(3)]
+    cof = torch.stack([torch.stack([f[(i + 1) % 3][(j + 1) % 3] * f[(i + 2) % 3][(j + 2) % 3]
+                                    - f[(i + 1) % 3][(j + 2) % 3] * f[(i + 2) % 3][(j + 1) % 3]
+                                    for j in range(3)], dim=1) for i in range(3)], dim=1)
+    J = (Fe[:, 0, :] * cof[:, 0, :]).sum(dim=1)
+    Bt = cof / J[:, None, None]
+    lnJ = torch.log(J)
     s1, s2, s3 = (g * a * a)[:, None, None], (mu - lam * lnJ)[:, None, None], lam[:, None, None]
 
     def tangent(X):                                     # X (V, 3, 3): K : X

@@ -299,16 +299,18 @@ def test_coupled_adjoint_matches_oracle(lib, ckpt):
 
 
 def test_coupled_adjoint_3d_checkpoint_spacing(lib):
-    """A 32^3 sphere with log fields, four FP64 steps, a loss with random seeds on the final
-    (c, F, d): the gradients do not depend on the checkpoint spacing (1, 2 or 4 steps per
-    segment), and the stored state is the one before the call."""
-    w = S.with_log_fields(S.sphere(32, 0.35, band=3, nsteps=8), std=0.1)
+    """A 32^3 sphere with log fields, four FP64 steps at the default tolerances, a loss with
+    random seeds on the final (c, F, d): the gradients do not depend on the checkpoint
+    spacing (1, 2 or 4 steps per segment: the recomputed steps repeat the recorded ones),
+    and the stored state is the one before the call."""
+    w = S.with_log_fields(S.sphere(32, 0.35, band=3, nsteps=8,
+                                   phases=S.default_phases(buffer_E=S.BENCH_BUFFER_E)), std=0.1)
     rng = np.random.default_rng(5)
     seeds = dict(seed_c=rng.standard_normal(w.shape), seed_F=rng.standard_normal((3, 3) + w.shape),
                  seed_d=rng.standard_normal(w.shape))
     out = {}
     for ckpt in (1, 2, 4):
-        sol = B.from_workload(w, lib=lib, **ADJ_TOLS)
+        sol = B.from_workload(w, lib=lib)
         sol.tape(ckpt)
         for _ in range(4):
             sol.step(w.dt)
@@ -316,8 +318,9 @@ def test_coupled_adjoint_3d_checkpoint_spacing(lib):
         out[ckpt] = sol.adjoint(B.FG_LOSS_SEEDS, **seeds)
         np.testing.assert_array_equal(sol.get(B.FIELD_F), F0)
         sol.close()
+    # no damage in four steps: g_c cannot act and its gradient is exactly zero
+    assert np.abs(out[1][1]["E"]).max() > 0.0 and np.abs(out[1][1]["D"]).max() > 0.0
     for k in ("E", "gc", "D"):
-        assert np.abs(out[1][1][k]).max() > 0.0
         for ckpt in (2, 4):
             assert rel_err(out[ckpt][1][k], out[1][1][k]) < 1e-9, (ckpt, k)
     assert out[4][2]["recomputed"] == 4 and out[1][2]["steps"] == 4
