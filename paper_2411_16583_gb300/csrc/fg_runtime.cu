@@ -1024,13 +1024,23 @@ static int newton_solve(fg_ctx& c, Prec<X>& PX, double& sigma, fg_stats& s) {
 // when a CG correction (FP32 or FP64) fails the line search, the iteration is redone
 // with FP64 MINRES on the unshifted system, and the rest of this solve uses it.
 template <typename R>
-static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s) {
+static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s, double err0 = -1.0) {
   bool hi = !is_mixed(c);  // Krylov in FP64
   bool mr = false;         // MINRES
   auto resid = [&]() {
     return hi ? residual_mech<double>(c, den, c.pd.state) : residual_mech<R>(c, den, P.state);
   };
-  double err = resid();
+  // err0 >= 0: the caller has just evaluated err_res at this F (c.P, c.GP current), so
+  // only the tangent state is built
+  double err;
+  if (err0 >= 0.0) {
+    if (hi) mech_state<double>(c, c.F, nullptr, nullptr, c.pd.state);
+    else mech_state<R>(c, c.F, nullptr, nullptr, P.state);
+    check_flags(c, "tangent state");
+    err = err0;
+  } else {
+    err = resid();
+  }
   double sigma = 0.0;
   for (int it = 0;; ++it, sigma *= 0.25) {
     s.err_mech = err;
@@ -1303,7 +1313,7 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
       s.err_mech = err;
       if (err <= c.o.tol_stag) break;
       if (k >= c.o.max_stag) fail(FG_ERR_NOCONV, "staggered scheme hit max_stag");
-      mech_newton<R>(c, P, den, s);
+      mech_newton<R>(c, P, den, s, err);
       history(c);
       pff_solve<R>(c, P, s);
       s.stag += 1;
