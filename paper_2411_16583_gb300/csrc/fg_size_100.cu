@@ -1,0 +1,13 @@
+// Pass kernels of transform length 100, both precisions.
+#include "fg_launch.cuh"
+
+namespace fg {
+namespace {
+struct RegisterSize100 {
+  RegisterSize100() {
+    register_size_ops_f(make_size_ops<float, 100>());
+    register_size_ops_d(make_size_ops<double, 100>());
+  }
+} register_size_100;
+}  // namespace
+}  // namespace fg

@@ -17,7 +17,7 @@ H3 = (1.0e-7, 1.1e-7, 0.9e-7)
 # grids spanning several tiles, ragged last tiles (rows not a multiple of the tile) in the
 # X, Y and Z passes, mixed radix (12 = 4 x 3, 24 = 8 x 3, 48, 80 = 16 x 5), plane strain
 SHAPES = [(8, 12, 16), (12, 24, 16), (1, 12, 16), (1, 64, 64), (16, 32, 64), (24, 48, 80),
-          (32, 32, 32)]
+          (32, 32, 32), (1, 100, 100), (100, 96, 80)]
 
 
 @pytest.fixture(scope="module")
