@@ -128,7 +128,9 @@ typedef struct fg_ctx fg_ctx;
  * caps 30 / 5000 / 50 / 50, no L2 chunking, cg_indefinite 2. */
 void fg_default_opts(fg_opts* o);
 
-/* 1 when the transform length n is compiled in, else 0. */
+/* 1 when the transform length n is compiled in, else 0.  The library is built with
+ * 1, 8, 12, 16, 24, 32, 48, 64, 80, 96, 100, 128, 256 and 512 (own Stockham FFT with
+ * radices 2, 4, 8, 16, 3 and 5; nx must be even). */
 int fg_supported_size(int n);
 
 /*
