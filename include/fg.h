@@ -242,6 +242,20 @@ int fg_batch_step(fg_batch* batch, double dt, const double Fbar[9], fg_stats* st
 void fg_batch_destroy(fg_batch* batch);
 
 /*
+ * Mixed macroscopic control (the paper's Sec. 3 allows prescribing macroscopic stress
+ * components instead of F-bar components).  Bit 3 i + j of mask marks component (i, j) as
+ * stress-controlled: the mean first Piola stress P-bar_ij is prescribed (Pbar[9],
+ * row-major) and the mean F-bar_ij becomes an unknown.  The projection keeps those
+ * components of the zero-frequency mode (the orthogonal projection onto compatible
+ * zero-mean fields plus uniform fields on the mask, so the Newton operator stays
+ * symmetric), and the residual is G P - M P-bar.  In fg_step, the Fbar argument's
+ * controlled components are only the starting guess; after a step the stored F-bar holds
+ * their solved mean.  mask = 0 restores full strain control.  fg_adjoint refuses contexts
+ * with a mask.  Errors: FG_ERR_INVALID (mask outside 0..511, Pbar NULL with a mask).
+ */
+int fg_set_stress_control(fg_ctx* ctx, int mask, const double Pbar[9]);
+
+/*
  * Discrete adjoint of recorded time steps (a hand-written reverse of Alg. 4; the paper's
  * forward equations Eqs. Chemresidualfc, mechanicalsolve, Hist, SigDrivingForce, PFFA
  * differentiated at each converged step).

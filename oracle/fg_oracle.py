@@ -143,6 +143,27 @@ def apply_G(T, h):
     return irfft3(project_G(rfft3(T), n), shape)
 
 
+def apply_G_mixed(T, prm):
+    """Projection of mixed macroscopic control: G * T plus, on the stress-controlled
+    components M, the mean of T (the zero-frequency mode kept instead of removed).  It is
+    the orthogonal projection onto compatible zero-mean fields plus uniform fields on M, so
+    the Newton operator stays symmetric; the mean of F on M is then an unknown, with the
+    mean stress on M prescribed (mixed strain/stress control of the macroscopic problem)."""
+    G = apply_G(T, prm.h)
+    if prm.stress_mask is None:
+        return G
+    mean = T.mean(axis=(2, 3, 4))
+    return G + (np.where(prm.stress_mask, mean, 0.0))[:, :, None, None, None]
+
+
+def stress_target(prm, shape):
+    """M P-bar*: the prescribed mean stress on the controlled components, as a field."""
+    if prm.stress_mask is None:
+        return 0.0
+    return np.broadcast_to(np.where(prm.stress_mask, prm.Pbar, 0.0)[:, :, None, None, None],
+                           (3, 3) + tuple(shape))
+
+
 # --------------------------------------------------------------------------------------
 # Tensor helpers (voxel-wise)
 # --------------------------------------------------------------------------------------
@@ -213,6 +234,8 @@ class Params:
     shape: tuple
     extra: dict = field(default_factory=dict)
     gcr: np.ndarray | None = None  # per-voxel g_c(x) / g_c (None: uniform g_c)
+    stress_mask: np.ndarray | None = None  # (3, 3) bool: components of P-bar prescribed
+    Pbar: np.ndarray | None = None         # (3, 3) prescribed mean stress on the mask
 
 
 def gc_ratio(prm):
@@ -526,8 +549,9 @@ def pcg(apply, precond, b, tol, maxit, x0):
 
 
 def mech_apply(F, c, d, prm, dF):
-    """One matrix-free operator application  F^-1[ G : F[K : dF] ]."""
-    return apply_G(tangent_apply(F, c, d, prm, dF), prm.h)
+    """One matrix-free operator application  F^-1[ G : F[K : dF] ] (G of mixed control
+    when stress components are prescribed)."""
+    return apply_G_mixed(tangent_apply(F, c, d, prm, dF), prm)
 
 
 def mech_residual(F, c, d, prm, Fbar):
@@ -535,10 +559,11 @@ def mech_residual(F, c, d, prm, Fbar):
 
     When the comparison stress has no incompatible part (a homogeneous medium) the
     denominator falls back to ||P(Fbar)||, then to 1."""
-    GP = apply_G(stress(F, c, d, prm), prm.h)
+    GP = apply_G_mixed(stress(F, c, d, prm), prm) - stress_target(prm, F.shape[2:])
     Fb = np.broadcast_to(np.asarray(Fbar, dtype=float).reshape(3, 3, 1, 1, 1), F.shape)
     Pb = stress(np.array(Fb), c, d, prm)
-    den = math.sqrt(dot(apply_G(Pb, prm.h), apply_G(Pb, prm.h)))
+    GPb = apply_G_mixed(Pb, prm) - stress_target(prm, F.shape[2:])
+    den = math.sqrt(dot(GPb, GPb))
     nPb = math.sqrt(dot(Pb, Pb))
     if den <= 1e-12 * nPb:
         den = nPb
@@ -780,6 +805,8 @@ class CoupledState:
             d = pff_solve(H, d, prm, tol.tol_pff_cg, tol.max_cg, stats)
             stag += 1
         stats["stag"] = stag
+        if prm.stress_mask is not None:  # the controlled components of F-bar were unknowns
+            Fbar_new = np.where(prm.stress_mask, F.mean(axis=(2, 3, 4)), Fbar_new)
         self.F, self.c, self.d, self.H, self.Fbar = F, c, d, H, Fbar_new
         return stats
 

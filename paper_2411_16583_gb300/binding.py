@@ -78,7 +78,7 @@ EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_re
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
            "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
-           "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load",
+           "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load", "fg_set_stress_control",
            "fg_kernel_launches", "fg_destroy", "fg_last_error"]
 
 _libs = {}
@@ -114,6 +114,7 @@ def load_library(path=LIB_PATH):
     lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.fg_tape_begin.argtypes = [C.c_void_p, C.c_int]
     lib.fg_save.argtypes = [C.c_void_p, C.c_char_p]
+    lib.fg_set_stress_control.argtypes = [C.c_void_p, C.c_int, dp]
     lib.fg_load.argtypes = [C.c_void_p, C.c_char_p]
     lib.fg_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, dp,
                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdjStats)]
@@ -253,6 +254,13 @@ class Solver:
         it = C.c_int()
         self._check(self.lib.fg_adjoint_mech(self.ctx, _ptr(Wh), _ptr(g), C.byref(it)))
         return g, it.value
+
+    def stress_control(self, mask, Pbar=None):
+        """Mixed macroscopic control: mask (3, 3) bool of stress-controlled components with
+        prescribed mean stress Pbar (3, 3); None or an all-False mask: strain control."""
+        m = 0 if mask is None else int(sum(1 << k for k, on in enumerate(np.asarray(mask).ravel()) if on))
+        Pb = _f64(np.zeros(9) if Pbar is None else Pbar).ravel()
+        self._check(self.lib.fg_set_stress_control(self.ctx, m, Pb.ctypes.data_as(C.POINTER(C.c_double))))
 
     def save(self, path):
         """Writes the evolving state to a restart file (fg_save)."""

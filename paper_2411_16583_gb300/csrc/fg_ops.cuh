@@ -9,7 +9,9 @@ namespace fg {
 
 // Compatibility projection (Eqs. mapping G, mechanicalsolve): A'_ij = n_j (A_im n_m)/|n|^2
 // with the rotated-scheme vector n_j = (2/h_j) sin(q_j/2) prod_{m!=j} cos(q_m/2); zero
-// where |n| = 0.  coef[0] = 1/V (inverse DFT scaling).
+// where |n| = 0, except that under mixed macroscopic control the zero-frequency mode keeps
+// the stress-controlled components (bit 3 i + j of the mask in coef[1]).
+// coef[0] = 1/V (inverse DFT scaling).
 template <typename R>
 struct ZProject {
   using C = cplx<R>;
@@ -20,6 +22,12 @@ struct ZProject {
     const R n2 = a.rs[2][kz] * a.rc[0][kx] * a.rc[1][ky];
     const R nn = n0 * n0 + n1 * n1 + n2 * n2;
     const R s = nn > (R)0 ? a.coef[0] / nn : (R)0;
+    const int mask = (int)a.coef[1];
+    if (mask != 0 && kx == 0 && ky == 0 && kz == 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[k] = ((mask >> k) & 1) ? cscale(v[k], a.coef[0]) : cmk<C>((R)0, (R)0);
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       C t = cadd(cadd(cscale(v[3 * i], n0), cscale(v[3 * i + 1], n1)), cscale(v[3 * i + 2], n2));

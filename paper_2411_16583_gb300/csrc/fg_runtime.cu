@@ -185,6 +185,8 @@ struct fg_ctx {
   int xi_percomp = 1;                // fused CG update: one component per block
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
+  int smask = 0;              // mixed control: stress-controlled components (bit 3 i + j)
+  double Pbar[9] = {0};       // their prescribed mean first Piola stress
   double* mr[6] = {};         // MINRES work vectors (9 V doubles each), allocated on first use
   fg::Tape* tape = nullptr;   // recorded steps for fg_adjoint
 };
@@ -454,7 +456,7 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
     ProfScope ps(c, SITE_XF);
     (c.law == FG_SVK ? P.ox->xf_tangent_svk : P.ox->xf_tangent)(a, c.st);
   }
-  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
   static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
   yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
   a = pbase(c, P, done);
@@ -474,7 +476,7 @@ static int op_gres(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
   a.rin = x;
   a.cout = P.S1;
   P.ox->xf_copy9(a, c.st);
-  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
   yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr);
   a = pbase(c, P, done);
   a.tw = P.twx;
@@ -722,7 +724,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
                 (double)(indef >= 0 ? indef : c.o.cg_indefinite == 1));
   const int* done = &ks->done;
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
-  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
   int chunk = 4;
   long long launched = 0;
   while (true) {
@@ -869,13 +871,29 @@ static double mixed_tol(const fg_ctx& c, double tol) {
 }
 
 // ||G*P(Fbar)|| with the fallbacks ||P(Fbar)||, then 1
+// |G P - M P-bar*|^2 into c.GP from c.P: the equilibrium residual; under mixed control
+// G keeps the mean of the stress-controlled components M and their prescribed mean
+// stress P-bar* is subtracted
+static double gres_residual(fg_ctx& c) {
+  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
+  if (!c.smask) {
+    fin<FStore>(c, KS_MISC, nb, nullptr);
+    read_ks(c);
+    return c.ks_host[KS_MISC].aux;
+  }
+  VArgs v = vbase(c, 9 * c.V);
+  v.in[0] = c.GP;
+  v.out[0] = c.GP;
+  for (int k = 0; k < 9; ++k) v.s[k] = ((c.smask >> k) & 1) ? -c.Pbar[k] : 0.0;
+  launch_vec<KShiftF>(v, c.st);
+  return reduce_sum(c, c.GP, 9 * c.V, true);
+}
+
 static double residual_den(fg_ctx& c) {
   mech_state<double>(c, nullptr, c.Fbar, c.P, nullptr);
-  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
-  fin<FStore>(c, KS_MISC, nb, nullptr);
-  read_ks(c);
+  const double g2 = gres_residual(c);
   check_flags(c, "residual");
-  const double g = sqrt(c.ks_host[KS_MISC].aux);
+  const double g = sqrt(g2);
   const double p = sqrt(reduce_sum(c, c.P, 9 * c.V, true));
   double den = g;
   if (den <= 1e-12 * p) den = p;
@@ -888,11 +906,9 @@ static double residual_den(fg_ctx& c) {
 template <typename R>
 static double residual_mech(fg_ctx& c, double den, R* state) {
   mech_state<R>(c, c.F, nullptr, c.P, state);
-  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
-  fin<FStore>(c, KS_MISC, nb, nullptr);
-  read_ks(c);
+  const double g2 = gres_residual(c);
   check_flags(c, "residual");
-  return sqrt(c.ks_host[KS_MISC].aux) / den;
+  return sqrt(g2) / den;
 }
 
 static double dotd(fg_ctx& c, const double* x, const double* y, long long n) {
@@ -1330,6 +1346,9 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
     throw;
   }
   memcpy(c.Fbar_prev, Fbar_old, sizeof(Fbar_old));
+  if (c.smask)  // the stress-controlled components of F-bar were unknowns: their mean
+    for (int k = 0; k < 9; ++k)
+      if ((c.smask >> k) & 1) c.Fbar[k] = reduce_sum(c, c.F + (long long)k * V, V, false) / (double)V;
   c.last_dt = dt;
   c.stepped = true;
   dsync(c.st);
@@ -2005,6 +2024,14 @@ int fg_load(fg_ctx* c, const char* path) {
   FG_API_END
 }
 
+int fg_set_stress_control(fg_ctx* c, int mask, const double Pbar[9]) {
+  FG_API_BEGIN
+  if (!c || mask < 0 || mask > 511 || (mask && !Pbar)) fail(FG_ERR_INVALID, "fg_set_stress_control: bad argument");
+  c->smask = mask;
+  for (int k = 0; k < 9; ++k) c->Pbar[k] = mask ? Pbar[k] : 0.0;
+  FG_API_END
+}
+
 int fg_tape_begin(fg_ctx* c, int ckpt_every) {
   FG_API_BEGIN
   if (!c || ckpt_every < 1) fail(FG_ERR_INVALID, "fg_tape_begin: bad argument");
@@ -2021,6 +2048,7 @@ int fg_adjoint(fg_ctx* c, int loss, const double* seed_c, const double* seed_F, 
   if (!c) fail(FG_ERR_INVALID, "fg_adjoint: null context");
   if (!c->tape || c->tape->dts.empty()) fail(FG_ERR_INVALID, "fg_adjoint: no recorded steps (fg_tape_begin, fg_step)");
   if (loss != FG_LOSS_CRACK_ENERGY && loss != FG_LOSS_SEEDS) fail(FG_ERR_INVALID, "fg_adjoint: loss");
+  if (c->smask) fail(FG_ERR_INVALID, "fg_adjoint: mixed stress control is not differentiated");
   fg_adjoint_stats as;
   memset(&as, 0, sizeof(as));
   double v = is_mixed(*c)

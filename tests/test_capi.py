@@ -76,6 +76,18 @@ def test_invalid_arguments(emu):
             s_.tape(0)
         finally:
             s_.close()
+    s_ = B.from_workload(w, lib=emu)
+    try:
+        with pytest.raises(B.FgError, match="fg_set_stress_control"):
+            s_._check(emu.fg_set_stress_control(s_.ctx, 512, None))
+        s_.stress_control(np.eye(3, dtype=bool), np.zeros((3, 3)))
+        s_.step(w.dt)
+        s_.tape(1)
+        s_.step(w.dt)
+        with pytest.raises(B.FgError, match="mixed stress control"):
+            s_.adjoint()
+    finally:
+        s_.close()
     assert emu.fg_supported_size(64) == 1 and emu.fg_supported_size(18) == 0
 
 

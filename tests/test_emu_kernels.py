@@ -260,3 +260,27 @@ def test_emulated_bimaterial_diffusion_100(emu):
     # the step runs along y; the slow phase (x >= 50) keeps more of its spread
     assert c[0, :, 80].std() > c[0, :, 10].std()
     sol.close()
+
+
+def test_emulated_mixed_control_step_matches_oracle(emu):
+    """One coupled step of a swelling particle in a buffer under mixed macroscopic control
+    (F11 prescribed at 1.01, every other mean stress zero) against the oracle: fields and the
+    solved mean deformation gradient."""
+    w = S.disc2d(n=16, radius=6.0, band=3, nsteps=10)
+    prm = oracle_params(w)
+    mask = np.ones((3, 3), dtype=bool)
+    mask[0, 0] = False
+    prm.stress_mask, prm.Pbar = mask, np.zeros((3, 3))
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_stag=1e-11)  # compare beyond the stop
+    ref = O.CoupledState(prm, w.c_init, w.cdot_B, O.Tolerances(**tols))
+    Fbar = np.diag([1.01, 1.0, 1.0])
+    ref.step(w.dt, Fbar)
+    sol = B.from_workload(w, lib=emu, **tols)
+    sol.stress_control(mask, np.zeros((3, 3)))
+    sol.step(w.dt, Fbar)
+    F = sol.get(B.FIELD_F)
+    assert rel_err(F, ref.F) < 1e-9
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
+    np.testing.assert_allclose(F.mean(axis=(2, 3, 4)), ref.Fbar, atol=1e-12)
+    assert abs(ref.Fbar[1, 1] - 1.0) > 1e-4  # the lateral mean strain was solved for
+    sol.close()

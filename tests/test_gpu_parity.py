@@ -324,3 +324,27 @@ def test_coupled_adjoint_3d_checkpoint_spacing(lib):
         for ckpt in (2, 4):
             assert rel_err(out[ckpt][1][k], out[1][1][k]) < 1e-9, (ckpt, k)
     assert out[4][2]["recomputed"] == 4 and out[1][2]["steps"] == 4
+
+
+def test_mixed_control_step_matches_oracle(lib):
+    """Two coupled FP64 steps of a swelling disc under mixed macroscopic control (F11
+    prescribed, every other mean stress zero) against the oracle, including the solved
+    mean deformation gradient."""
+    w = S.disc2d(n=32, radius=11.0, band=3, nsteps=10)
+    prm = oracle_params(w)
+    mask = np.ones((3, 3), dtype=bool)
+    mask[0, 0] = False
+    prm.stress_mask, prm.Pbar = mask, np.zeros((3, 3))
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_stag=1e-11)
+    ref = O.CoupledState(prm, w.c_init, w.cdot_B, O.Tolerances(**tols))
+    sol = B.from_workload(w, lib=lib, **tols)
+    sol.stress_control(mask, np.zeros((3, 3)))
+    for k in range(2):
+        Fbar = np.diag([1.0 + 0.005 * (k + 1), 1.0, 1.0])
+        ref.step(w.dt, Fbar)
+        sol.step(w.dt, Fbar)
+    F = sol.get(B.FIELD_F)
+    assert rel_err(F, ref.F) < 1e-9
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
+    np.testing.assert_allclose(F.mean(axis=(2, 3, 4)), ref.Fbar, atol=1e-12)
+    sol.close()

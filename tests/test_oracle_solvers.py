@@ -387,3 +387,44 @@ def test_mech_adjoint_matches_central_differences():
         lm[v] -= h
         fd = (np.sum(W * solve(lp)[0]) - np.sum(W * solve(lm)[0])) / (2 * h)
         assert abs(fd - g[v]) <= 1e-6 * np.abs(g).max() + 1e-7 * abs(fd)
+
+
+def test_mixed_control_projection_and_uniaxial_stress():
+    """Mixed macroscopic control.  The projection with stress-controlled components M is
+    idempotent and self-adjoint and keeps the mean on M only.  A homogeneous Neo-Hookean
+    block with F11 = 1.02 prescribed and every other mean stress zero reaches the uniaxial
+    state F = diag(1.02, l, l), l found by bisection on P22(diag(1.02, l, l)) = 0 of the
+    law itself, and its mean stress vanishes on M."""
+    shape = (2, 3, 4)
+    phases = [O.Phase(E=10e9, nu=0.3, Omega=0.0, c0=0.01), O.Phase(E=3e9, nu=0.2, Omega=0.0)]
+    rng = np.random.default_rng(4)
+    prm = O.make_params(phases, (rng.random(shape) < 0.5).astype(int), H, gc=1.0, lc=2e-7)
+    mask = np.ones((3, 3), dtype=bool)
+    mask[0, 0] = False
+    prm.stress_mask, prm.Pbar = mask, np.zeros((3, 3))
+    A = rng.standard_normal((3, 3) + shape)
+    Bf = rng.standard_normal((3, 3) + shape)
+    GA = O.apply_G_mixed(A, prm)
+    np.testing.assert_allclose(O.apply_G_mixed(GA, prm), GA, atol=1e-13 * np.abs(GA).max())
+    assert abs(O.dot(GA, Bf) - O.dot(A, O.apply_G_mixed(Bf, prm))) < 1e-12 * abs(O.dot(GA, Bf))
+    np.testing.assert_allclose(GA.mean(axis=(2, 3, 4)), np.where(mask, A.mean(axis=(2, 3, 4)), 0.0),
+                               atol=1e-14)
+    hom = O.make_params(phases[:1], np.zeros(shape, dtype=int), H, gc=1.0, lc=2e-7)
+    hom.stress_mask, hom.Pbar = mask, np.zeros((3, 3))
+    F = identity(shape)
+    F[0, 0] = 1.02
+    c, d = np.full(shape, 0.01), np.zeros(shape)
+    F, err = O.mech_newton(F, c, d, hom, np.diag([1.02, 1.0, 1.0]), 1e-12, 1e-13, 20, 500)
+    assert err <= 1e-12
+
+    def p22(l):
+        Fe = np.diag([1.02, l, l]).reshape(3, 3, 1, 1, 1)
+        one = O.make_params(phases[:1], np.zeros((1, 1, 1), dtype=int), H, gc=1.0, lc=2e-7)
+        return O.P0(Fe, one)[1, 1, 0, 0, 0]
+    lo, hi = 0.95, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (lo, mid) if p22(lo) * p22(mid) <= 0 else (mid, hi)
+    np.testing.assert_allclose(F[:, :, 0, 0, 0], np.diag([1.02, lo, lo]), atol=1e-12)
+    P = O.stress(F, c, d, hom).mean(axis=(2, 3, 4))
+    assert np.abs(np.where(mask, P, 0.0)).max() < 1e-6 * abs(P[0, 0])
