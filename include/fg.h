@@ -102,6 +102,11 @@ typedef struct {
                          1 = take it (the Galerkin iterate exists while <p, A p> != 0),
                          0 = stop there and keep the iterate (truncated CG).
                          <p, A p> = 0 or a non-finite value always stops a solve */
+  int chem_full_jacobian; /* 0 (default): the chemistry Newton of Alg. 3 with the Jacobian
+                         of the ideal part mu_c' only; 1: also the elastic part
+                         d(mu_e/RT)/dc (same root; converges where mu_e reaches several RT,
+                         e.g. Omega = 1.3 with E = 15 GPa).  FG_ERR_NUMERIC where the full
+                         dmu~/dc <= 0 */
 } fg_opts;
 
 typedef struct {

@@ -715,16 +715,33 @@ def chem_apply(y, m, Kc, dt, prm):
     return y / m + dt * chem_L(y, Kc, prm)
 
 
-def chem_solve(c_t, F, d_t, dt, cdot_B, prm, tol_chem, tol_cg, max_newton, max_cg, stats=None):
+def chem_jacobian_elastic(c, F, d, prm):
+    """d(mu_e/RT)/dc at fixed F, d: (1-d)^2 Omega^2/(3 c_max J_c^2 RT) (q + (K0[F_e]:F_e + q)/3),
+    q = P0(F_e) : F_e (the derivative of Eq. mue in c)."""
+    a = swelling_a(c, prm)
+    Jc = swelling_J(c, prm)
+    Fe = a * F
+    q = ddot(P0(Fe, prm), Fe)
+    kf = ddot(dP0(Fe, Fe, prm), Fe)
+    return (1.0 - d) ** 2 * prm.Omega ** 2 / (3.0 * prm.cmax * Jc ** 2 * prm.RT) * (q + (kf + q) / 3.0)
+
+
+def chem_solve(c_t, F, d_t, dt, cdot_B, prm, tol_chem, tol_cg, max_newton, max_cg, stats=None,
+               full_jacobian=False):
     """Alg. 3: Newton-CG from c^0 = c_t until ||dc|| / ||c_t|| < tol_chem.  A correction
     that would take c out of (0, 1), where mu_c = RT log(c/(1-c)) is undefined, is halved
-    (at most 10 times) until the update stays inside."""
+    (at most 10 times) until the update stays inside.  full_jacobian adds the elastic part
+    of dmu~/dc to the Jacobian, which the paper's Newton leaves out (same root)."""
     Kc = chem_conductivity(F, c_t, d_t, prm)
     c = c_t.copy()
     nct = math.sqrt(dot(c_t, c_t))
     for k in range(max_newton):
         f = chem_residual(c, c_t, F, d_t, Kc, dt, cdot_B, prm)
         m = 1.0 / (c * (1.0 - c))
+        if full_jacobian:  # the elastic part of dmu~/dc as well (Alg. 3 keeps mu_c' only)
+            m = m + chem_jacobian_elastic(c, F, d_t, prm)
+            if not np.all(m > 0.0):
+                raise FloatingPointError("chemistry Jacobian not positive (dmu~/dc <= 0)")
         y, it = cg(lambda v: chem_apply(v, m, Kc, dt, prm), -f, tol_cg, max_cg)
         dc = y / m
         for _ in range(11):
@@ -761,6 +778,7 @@ class Tolerances:
     max_chem_newton: int = 50
     max_stag: int = 50
     cg_indefinite: int = 2
+    chem_full_jacobian: bool = False
 
 
 class CoupledState:
@@ -788,7 +806,7 @@ class CoupledState:
         F_t, c_t, d_t, H_t = self.F, self.c, self.d, self.H
         F = F_t + dFbar  # F_{t+dt} = Fbar_{t+dt} + F~_t
         c = chem_solve(c_t, F, d_t, dt, self.cdot_B, prm, tol.tol_chem, tol.tol_chem_cg,
-                       tol.max_chem_newton, tol.max_cg, stats)
+                       tol.max_chem_newton, tol.max_cg, stats, tol.chem_full_jacobian)
         d = d_t.copy()
         H = H_t.copy()
         stag = 0

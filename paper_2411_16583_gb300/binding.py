@@ -48,7 +48,7 @@ class Opts(C.Structure):
                 ("tol_pff_cg", C.c_double), ("tol_stag", C.c_double), ("cg_forcing", C.c_double),
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
                 ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double),
-                ("cg_indefinite", C.c_int)]
+                ("cg_indefinite", C.c_int), ("chem_full_jacobian", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -470,6 +470,40 @@ struct KCrackSeed : VecOp<double> {
   }
 };
 
+// 1/m of the chemistry Newton with the full Jacobian m = 1/(c (1 - c)) + d(mu_e/RT)/dc,
+// out0 (R), at (c, F~, d_t); in: c, F~, d_t, lam, mu, Om, c0 ; s0 = 1/RT, s1 = 1/c_max.
+// Flags ST_NUMERIC where m <= 0.
+template <typename R, int LAW>
+struct KChemFullM : VecOp<double> {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>&, const Pre&) {
+    const long long V = a.V;
+    const double c = ((const double*)a.in[0])[v];
+    double m = 1.0 / (c * (1.0 - c));
+    double lam, mu, Om, c0;
+    load_mat(a, 3, v, lam, mu, Om, c0);
+    if (Om != 0.0) {
+      double F[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = ((const double*)a.in[1])[k * V + v];
+      ElasticPoint P;
+      if (!elastic_point<LAW>(F, c, ((const double*)a.in[2])[v], lam, mu, Om, c0, P)) {
+        atomicOr(a.flags, ST_DOMAIN);
+        return;
+      }
+      double KFe[9];
+      k0_apply<LAW>(P, P.Fe, KFe);
+      double kf = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) kf += KFe[k] * P.Fe[k];
+      const double q = P.P0Fe;
+      m += P.g * Om * Om / (3.0 * P.Jc * P.Jc) * a.s[1] * (q + (kf + q) / 3.0) * a.s[0];
+    }
+    if (!(m > 0.0)) atomicOr(a.flags, ST_NUMERIC);
+    ((R*)a.out[0])[v] = (R)(1.0 / m);
+  }
+};
+
 // <in0, in1> (FP64)
 struct KDot : VecOp<double> {
   static constexpr bool RED = true;

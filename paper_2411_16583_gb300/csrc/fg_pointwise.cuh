@@ -428,14 +428,16 @@ struct KChemPrep : VecOp<double> {
   }
 };
 
-// c = c_i + s0 dc with dc = y c_i (1 - c_i) (y = m dc); accumulates |s0 dc|^2.
-// in0 = y (R), in1 = c_i; out0 = c
+// c = c_i + s0 dc with dc = y / m (y = m dc), 1/m = c_i (1 - c_i) or, with the full
+// Jacobian, the stored in2 = 1/m (R); accumulates |s0 dc|^2.
+// in0 = y (R), in1 = c_i, in2 = 1/m (R, may be null); out0 = c
 template <typename R>
 struct KChemUpdate : VecOp<double> {
   static constexpr bool RED = true;
   FG_DEV static void apply(const VArgs& a, long long v, Acc<AccReal>& acc, const Pre&) {
     const double ci = ((const double*)a.in[1])[v];
-    const double dc = a.s[0] * (double)((const R*)a.in[0])[v] * ci * (1.0 - ci);
+    const double im = a.in[2] ? (double)((const R*)a.in[2])[v] : ci * (1.0 - ci);
+    const double dc = a.s[0] * (double)((const R*)a.in[0])[v] * im;
     const double cn = ci + dc;
     ((double*)a.out[0])[v] = cn;
     if (!(cn > 0.0 && cn < 1.0)) atomicOr(a.flags, ST_DOMAIN);

@@ -1252,6 +1252,21 @@ static void chem_prep(fg_ctx& c, Prec<R>& P, double dt, const double* F) {
   v.s[2] = 1.0 / c.o.cmax;
   if (c.law == FG_SVK) launch_vec<KChemPrep<R, LAW_SVK_>>(v, c.st);
   else launch_vec<KChemPrep<R, LAW_NH_>>(v, c.st);
+  if (c.o.chem_full_jacobian) {  // 1/m with the elastic part of dmu~/dc as well
+    VArgs u = vbase(c, c.V);
+    u.in[0] = c.c;
+    u.in[1] = F;
+    u.in[2] = c.dt;
+    u.in[3] = c.lam;
+    u.in[4] = c.mu_;
+    u.in[5] = c.Om;
+    u.in[6] = c.c0;
+    u.out[0] = P.w;
+    u.s[0] = 1.0 / c.o.RT;
+    u.s[1] = 1.0 / c.o.cmax;
+    if (c.law == FG_SVK) launch_vec<KChemFullM<R, LAW_SVK_>>(u, c.st);
+    else launch_vec<KChemFullM<R, LAW_NH_>>(u, c.st);
+  }
 }
 
 template <typename R>
@@ -1280,6 +1295,7 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
       VArgs v = vbase(c, c.V);
       v.in[0] = P.x;
       v.in[1] = c.base;
+      v.in[2] = c.o.chem_full_jacobian ? P.w : nullptr;
       v.out[0] = c.c;
       v.s[0] = lam;
       launch_vec<KChemUpdate<R>>(v, c.st);
@@ -2087,6 +2103,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (o.precision != FG_FP64 && o.precision != FG_MIXED) fail(FG_ERR_INVALID, "fg_setup: precision");
   if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
   if (o.cg_indefinite < 0 || o.cg_indefinite > 2) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
+  if (o.chem_full_jacobian != 0 && o.chem_full_jacobian != 1) fail(FG_ERR_INVALID, "fg_setup: chem_full_jacobian");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;

@@ -23,6 +23,8 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
 * ``spheres``   64 RVEs with edge N in {48, 64, 80, 96} and sphere radius
   U(0.30, 0.45) N.
 * ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
+* ``gumbel_disc`` 512^2 Saint-Venant-Kirchhoff disc with Weibull-type random stiffness and
+  the paper's Omega = 1.3 (Sec. 5.1).
 """
 from __future__ import annotations
 
@@ -188,24 +190,26 @@ def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=
 
 
 def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16e-6 / 512,
-                E=15e9, vol_change=0.10):
+                E=15e9, Omega=1.3):
     """2D circular Saint-Venant-Kirchhoff particle with Weibull-type random stiffness
     (Sec. 5.1, Eq. Gumbell): E_i = E log(1/(1 - w_i))^(1/m), w_i ~ U(0, 1), m = 3, carried
-    as the per-voxel log-stiffness log_E = log(log(1/(1 - w_i)))/m.  The paper also draws
-    a random sigma_max per voxel with the same law; the C ABI takes sigma_max per phase,
-    so this workload keeps it uniform.  The paper's Omega = 1.3 is not used: with
-    E = 15 GPa the elastic chemical potential reaches several RT and the Newton of Alg. 3,
-    whose Jacobian keeps only the ideal-solution part, stops converging (the oracle fails
-    the same way), so the swelling is the 10 % volume change of the other workloads."""
+    as the per-voxel log-stiffness log_E = log(log(1/(1 - w_i)))/m, and the paper's
+    swelling Omega = 1.3.  The paper also draws a random sigma_max per voxel with the same
+    law; the C ABI takes sigma_max per phase, so this workload keeps it uniform.  With
+    E = 15 GPa and Omega = 1.3 the elastic chemical potential reaches several RT, where the
+    Newton of Alg. 3 (Jacobian of the ideal part only) stops converging; the workload
+    therefore runs the chemistry Newton with the full Jacobian (chem_full_jacobian)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (1, n, n)
     x, y, _ = _grid_coords(shape)
     particle = (x * x + y * y) <= (0.5 * diameter_frac * n) ** 2
-    phases = default_phases(E=E, law=LAW_SVK, vol_change=vol_change, buffer_E=1e-5)
+    c0 = 0.01
+    phases = default_phases(E=E, c0=c0, law=LAW_SVK, vol_change=Omega * (1.0 - c0), buffer_E=1e-5)
     w = _finish("gumbel_disc", shape, (h, h, h), particle, band, nsteps, 1.0, rng, phases=phases)
     om = rng.uniform(size=shape)
     log_E = np.log(np.log(1.0 / (1.0 - om))) / m
     w.log_E = np.where(particle, log_E, 0.0)
+    w.tol = dict(w.tol, chem_full_jacobian=1)
     return w
 
 

@@ -284,3 +284,19 @@ def test_emulated_mixed_control_step_matches_oracle(emu):
     np.testing.assert_allclose(F.mean(axis=(2, 3, 4)), ref.Fbar, atol=1e-12)
     assert abs(ref.Fbar[1, 1] - 1.0) > 1e-4  # the lateral mean strain was solved for
     sol.close()
+
+
+def test_emulated_full_chemistry_jacobian_matches_oracle(emu):
+    """The chemistry Newton with the full Jacobian (chem_full_jacobian) on a 32 x 32 version
+    of the Omega = 1.3 Saint-Venant-Kirchhoff Gumbel disc: one coupled step against the
+    oracle's."""
+    w = S.gumbel_disc(n=32, band=2)
+    prm = oracle_params(w)
+    ref = O.CoupledState(prm, w.c_init, w.cdot_B, O.Tolerances(**w.tol))
+    st_ref = ref.step(w.dt, np.eye(3))
+    sol = B.from_workload(w, lib=emu)
+    st = sol.step(w.dt)
+    assert st["newton_chem"] == st_ref["newton_chem"]
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-9
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-8
+    sol.close()
