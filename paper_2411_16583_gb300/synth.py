@@ -23,6 +23,7 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
 * ``spheres``   64 RVEs with edge N in {48, 64, 80, 96} and sphere radius
   U(0.30, 0.45) N.
 * ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
+* ``multi_particle`` several non-overlapping rough ellipsoids in one RVE.
 * ``gumbel_disc`` 512^2 Saint-Venant-Kirchhoff disc with Weibull-type random stiffness and
   the paper's Omega = 1.3 (Sec. 5.1).
 """
@@ -158,6 +159,34 @@ def ellipsoid(n=128, axes=(50.0, 40.0, 35.0), rough_std=1.5, rough_corr=4.0, ban
     particle = (rho - 1.0) * min(axes) <= eta
     return _finish("ellipsoid", shape, (h, h, h), particle, band, nsteps, 1.0, rng,
                    c_perturb=c_perturb, **kw)
+
+
+def multi_particle(n=128, count=4, rmin=0.12, rmax=0.2, rough_std=1.0, rough_corr=3.0, band=4,
+                   nsteps=50, seed=0, h=0.1e-6, **kw):
+    """Several rough ellipsoidal particles in one periodic RVE (a piece of electrode, as in
+    the paper's outlook): semi-axes drawn from U(rmin, rmax) n, centres placed by rejection
+    so that no two particles overlap (periodic distance), each with its own influx band."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (n, n, n)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    eta = _rough_field(rng, shape, rough_std, rough_corr) if rough_std > 0 else 0.0
+    particle = np.zeros(shape, dtype=bool)
+    placed = []
+    tries = 0
+    while len(placed) < count:
+        tries += 1
+        if tries > 1000:
+            raise ValueError("multi_particle: could not place the particles")
+        ax = rng.uniform(rmin, rmax, size=3) * n
+        ctr = rng.uniform(0, n, size=3)
+        if any(np.linalg.norm(((ctr - c2 + n / 2) % n) - n / 2) < ax.max() + a2.max() + band
+               for c2, a2 in placed):
+            continue
+        placed.append((ctr, ax))
+        d = [((q - c + n / 2) % n) - n / 2 for q, c in zip((x, y, z), ctr)]
+        rho = np.sqrt((d[0] / ax[0]) ** 2 + (d[1] / ax[1]) ** 2 + (d[2] / ax[2]) ** 2)
+        particle |= (rho - 1.0) * ax.min() <= eta
+    return _finish("multi_particle", shape, (h, h, h), particle, band, nsteps, 1.0, rng, **kw)
 
 
 BENCH_BUFFER_E = 1e-2  # buffer stiffness of the benchmark particle, relative to the particle's
