@@ -2,15 +2,28 @@
 // dispatches through (one table per transform length N and precision).
 #pragma once
 #include <atomic>
+#include <type_traits>
 #include <vector>
 #include <cstring>
 #include "fg_ops.cuh"
 
 namespace fg {
 
+// Resident blocks per SM a kernel asks the compiler to fit (K::MINB when present): it caps
+// the registers per thread at 65536 / (MINB NT), so that occupancy is not limited by
+// registers before shared memory.
+template <class K, class = void>
+struct MinBlocks {
+  static constexpr int value = 1;
+};
+template <class K>
+struct MinBlocks<K, std::void_t<decltype(K::MINB)>> {
+  static constexpr int value = K::MINB;
+};
+
 #ifndef FG_EMU
 template <class K, class A>
-__global__ void __launch_bounds__(K::NT) pass_kernel(A a) {
+__global__ void __launch_bounds__(K::NT, MinBlocks<K>::value) pass_kernel(A a) {
   extern __shared__ __align__(16) char smem[];
   typename K::Locals L;
   K::body(a, Dim3{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z},
@@ -40,6 +53,9 @@ int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
 #else
   static const bool configured = [sm]() {  // once per kernel, thread-safe
     cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (MinBlocks<K>::value > 1)  // room for MINB blocks' shared memory
+      cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
     return true;
   }();
   (void)configured;

@@ -196,8 +196,16 @@ struct XInv {
     C v[TF::VMAX];
     Acc<R> acc;
   };
-  static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
+  static constexpr size_t SMEM = (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double);
+  static size_t smem_bytes() { return SMEM; }
   static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
+  // blocks per SM the shared memory (227 KB usable, 1 KB reserved per block) and the
+  // threads (2048) allow, at most 4: the inverse pass is latency-bound on its loads
+  // (long-scoreboard stalls), so residency matters more than registers
+  static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 1024));
+  static constexpr int MINB_THR = 2048 / NT;
+  static constexpr int MINB_RAW = MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR;
+  static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 4 ? 4 : MINB_RAW);
 
   template <class Loc>
   FG_DEV static void body(const PassArgs<R>& a0, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
