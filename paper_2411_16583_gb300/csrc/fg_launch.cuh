@@ -52,10 +52,10 @@ int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
       }
 #else
   static const bool configured = [sm]() {  // once per kernel, thread-safe
+    // no carveout preference: the driver sizes the L1/shared split per kernel (a maximum-
+    // shared preference on the inverse passes left the following passes with a small L1
+    // and slowed them by 15-25%)
     cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (MinBlocks<K>::value > 1)  // room for MINB blocks' shared memory
-      cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
     return true;
   }();
   (void)configured;

@@ -200,8 +200,9 @@ struct XInv {
   static size_t smem_bytes() { return SMEM; }
   static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
   // blocks per SM the shared memory (227 KB usable, 1 KB reserved per block) and the
-  // threads (2048) allow, at most 4: the inverse pass is latency-bound on its loads
-  // (long-scoreboard stalls), so residency matters more than registers
+  // threads (2048) allow, at most 4, declared to the compiler so that registers do not cap
+  // residency below it: the inverse pass is latency-bound on its loads (long-scoreboard
+  // stalls)
   static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 1024));
   static constexpr int MINB_THR = 2048 / NT;
   static constexpr int MINB_RAW = MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR;
