@@ -22,8 +22,18 @@ struct MinBlocks<K, std::void_t<decltype(K::MINB)>> {
 };
 
 #ifndef FG_EMU
+// Kernels without K::MINB keep the plain bound on the block size: an explicit minimum of
+// one block lets the compiler spend more registers and halved the residency of the
+// forward and Y/Z passes.
 template <class K, class A>
-__global__ void __launch_bounds__(K::NT, MinBlocks<K>::value) pass_kernel(A a) {
+__global__ void __launch_bounds__(K::NT) pass_kernel(A a) {
+  extern __shared__ __align__(16) char smem[];
+  typename K::Locals L;
+  K::body(a, Dim3{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z},
+          Dim3{(int)gridDim.x, (int)gridDim.y, (int)gridDim.z}, smem, &L);
+}
+template <class K, class A>
+__global__ void __launch_bounds__(K::NT, MinBlocks<K>::value) pass_kernel_mb(A a) {
   extern __shared__ __align__(16) char smem[];
   typename K::Locals L;
   K::body(a, Dim3{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z},
@@ -51,15 +61,19 @@ int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
         K::body(a, Dim3{x, y, z}, grid, smem.data(), Ls.data());
       }
 #else
+  constexpr bool MB = MinBlocks<K>::value > 1;
   static const bool configured = [sm]() {  // once per kernel, thread-safe
-    // no carveout preference: the driver sizes the L1/shared split per kernel (a maximum-
-    // shared preference on the inverse passes left the following passes with a small L1
-    // and slowed them by 15-25%)
-    cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if constexpr (MB)
+      cudaFuncSetAttribute(pass_kernel_mb<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    else
+      cudaFuncSetAttribute(pass_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     return true;
   }();
   (void)configured;
-  pass_kernel<K, A><<<dim3(grid.x, grid.y, grid.z), K::NT, sm, st>>>(a);
+  if constexpr (MB)
+    pass_kernel_mb<K, A><<<dim3(grid.x, grid.y, grid.z), K::NT, sm, st>>>(a);
+  else
+    pass_kernel<K, A><<<dim3(grid.x, grid.y, grid.z), K::NT, sm, st>>>(a);
 #endif
   return grid.x * grid.y * grid.z;
 }
