@@ -141,9 +141,9 @@ def _peaks():
 
 # Per-step operator counts used to express the oracle's per-operator times in the
 # metric's unit when no GPU step is available (the --impl reference arm): the counts of
-# the first coupled steps of this workload (FP64 path, whose Krylov iterations follow the
-# oracle's), rounded.
-DEFAULT_STEP_PROFILE = {"cg_mech": 2400, "newton_mech": 3, "stag": 1, "cg_chem": 450,
+# the first coupled step of this workload on the FP64 path, whose Krylov iterations follow
+# the oracle's (measured on a GB300 with the buffer at 1e-2 of the particle's stiffness).
+DEFAULT_STEP_PROFILE = {"cg_mech": 549, "newton_mech": 3, "stag": 1, "cg_chem": 746,
                         "newton_chem": 8, "cg_pff": 0}
 
 
