@@ -31,6 +31,12 @@ UNIT = "voxel-steps/s"
 # Algorithmic bytes per voxel of each profiled launch site of the FP32 mechanical CG
 # iteration (9-component fields, 4-byte reals; the half spectrum holds (nx/2+1)/nx of a
 # real field as complex numbers, so a 9-component spectrum is 72 (nx/2+1)/nx B/voxel).
+# DRAM bytes per voxel that ncu measured per launch of the fused CG X passes
+# (profiles/x_passes_traffic_256x256x64.md; x rows of 256): valid for these kernels as they
+# are, at nx = 256
+MEASURED_TRAFFIC_B_PER_VOXEL = {"xi": 203.6, "xf": 181.2}
+
+
 def site_bytes(nx):
     spec = 72.0 * (nx // 2 + 1) / nx
     return {0: 36 + 36 + 48 + 36 + spec,   # X-fwd: read r, p, tangent state; write p, spectrum
@@ -45,6 +51,14 @@ SITE_NAMES = {0: "mech X-fwd: p = r + beta p, tangent, <p,Kp> (pass_kernel<XFwd<
               2: "mech Z + projection (pass_kernel<ZPassD<float,N,ZProject>>)",
               3: "mech Y-inv (pass_kernel<YPassD<float,N,true>>)",
               4: "mech X-inv: r -= alpha q, x += alpha p, |r|^2 (pass_kernel<XInv<float,N,ECgUpdate1,true>> per component, or ECgUpdate)"}
+
+
+def _traffic(site, nx, voxels_per_launch):
+    """Measured DRAM bytes per launch of the dominant site (None without a capture)."""
+    key = {4: "xi", 0: "xf"}.get(site)
+    if key is None or nx != 256:
+        return None
+    return MEASURED_TRAFFIC_B_PER_VOXEL[key] * voxels_per_launch
 
 
 def _args():
@@ -417,7 +431,7 @@ def main():
                      "peak_source": src,
                      "alg_bytes_per_launch": sb[dom] * V * vol_dom / n_dom,
                      "avg_launch_us": avg_dom * 1e6,
-                     "traffic": None},
+                     "traffic": _traffic(dom, w.shape[2], V * vol_dom / n_dom)},
         "kernels": sites,
         "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),
                    "mech_fp32_ms": mech32_ms, "cufft_comparator": comparator},
