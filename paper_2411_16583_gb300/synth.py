@@ -214,7 +214,8 @@ def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=
     rng = np.random.Generator(np.random.PCG64(seed))
     ns = rng.choice(np.array(sizes), size=count)
     rs = rng.uniform(rmin, rmax, size=count)
-    return [sphere(int(n), float(r), nsteps=nsteps, seed=seed + 1 + i)
+    return [sphere(int(n), float(r), nsteps=nsteps, seed=seed + 1 + i,
+                   phases=default_phases(buffer_E=BENCH_BUFFER_E))
             for i, (n, r) in enumerate(zip(ns, rs))]
 
 
