@@ -456,7 +456,9 @@ def adjoint_mode(a):
     n = a.n if a.n != 256 else 128
     w = S.with_log_fields(S.ellipsoid(n=n, axes=(50 * n / 128, 40 * n / 128, 35 * n / 128),
                                       rough_std=1.5 * n / 128, rough_corr=4 * n / 128,
-                                      band=max(1, round(8 * n / 128)), nsteps=50), std=0.1)
+                                      band=max(1, round(8 * n / 128)), nsteps=50,
+                                      phases=S.default_phases(buffer_E=S.BENCH_BUFFER_E)),
+                          std=0.1)
     stream = torch.cuda.current_stream()
     sol = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream)
     for _ in range(a.warmup):
