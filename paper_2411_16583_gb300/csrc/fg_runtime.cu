@@ -185,6 +185,13 @@ struct fg_ctx {
   int xi_percomp = 1;                // fused CG update: one component per block
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
+#ifndef FG_EMU
+  // CUDA graphs of 16 fused mechanical CG iterations, [FP32, FP64][without, with the
+  // re-projection at the end], and the kernels each holds
+  cudaGraphExec_t cg_graph[2][2] = {};
+  long long cg_graph_kernels[2][2] = {};
+  bool graphs_off = false;
+#endif
   int smask = 0;              // mixed control: stress-controlled components (bit 3 i + j)
   double Pbar[9] = {0};       // their prescribed mean first Piola stress
   double* mr[6] = {};         // MINRES work vectors (9 V doubles each), allocated on first use
@@ -725,53 +732,101 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
   const int* done = &ks->done;
   const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
   const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
-  int chunk = 4;
   long long launched = 0;
+  // one fused iteration; the re-projection every 32 iterations
+  auto iteration = [&]() {
+    PassArgs<R> a = pbase(c, P, done);
+    a.tw = P.twx;
+    a.rin = P.r;
+    a.rout = P.p;
+    a.aux[0] = P.state;
+    a.dscal = sc;
+    a.coef[1] = (R)sigma;
+    a.cout = P.S1;
+    int nb;
+    {
+      ProfScope ps(c, SITE_XF);
+      nb = (c.law == FG_SVK ? P.ox->xf_cgtangent_svk : P.ox->xf_cgtangent)(a, c.st);
+    }
+    fin<FAlpha>(c, slot, nb, done);
+    {
+      static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
+      yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
+    }
+    a = pbase(c, P, done);
+    a.tw = P.twx;
+    a.cin = P.S1;
+    a.rout = P.r;
+    a.rout2 = P.x;
+    a.aux[0] = P.p;
+    a.dscal = sc;
+    a.coef[1] = (R)sigma;
+    {
+      ProfScope ps(c, SITE_XI);
+      nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
+    }
+    fin<FBetaCg>(c, slot, nb, done);
+    snap_iterate(c, P, n, ks);
+    if (++launched % 32 == 0) {
+      // every CG vector is compatible in exact arithmetic; re-project r and p so that
+      // roundoff in modes G does not see cannot build up and corrupt <p, K p>
+      nb = op_gres(c, P, P.r, P.r, done);
+      fin<FSetResidual>(c, slot, nb, done);
+      op_gres(c, P, P.p, P.p, done);
+    }
+  };
+  // chunks of 4, 12, then 16 iterations between host checks (iterations after convergence
+  // exit at once on the device flag): from the third chunk on every chunk starts at a
+  // multiple of 16 and either ends with the re-projection or has none, so it is replayed
+  // from one of two CUDA graphs on streams that can be captured
   while (true) {
-    for (int j = 0; j < chunk; ++j) {
-      PassArgs<R> a = pbase(c, P, done);
-      a.tw = P.twx;
-      a.rin = P.r;
-      a.rout = P.p;
-      a.aux[0] = P.state;
-      a.dscal = sc;
-      a.coef[1] = (R)sigma;
-      a.cout = P.S1;
-      int nb;
-      {
-        ProfScope ps(c, SITE_XF);
-        nb = (c.law == FG_SVK ? P.ox->xf_cgtangent_svk : P.ox->xf_cgtangent)(a, c.st);
+    const int cnt = launched == 0 ? 4 : (launched == 4 ? 12 : 16);
+    bool ran = false;
+#ifndef FG_EMU
+    // graphs from iteration 32 on: every kernel of a chunk, the re-projection included, has
+    // run once directly before it is captured
+    if (cnt == 16 && launched >= 32 && sigma == 0.0 && !c.prof_mask && !c.graphs_off &&
+        c.st != nullptr) {
+      const int pi = sizeof(R) == 8 ? 1 : 0, var = (launched + 16) % 32 == 0 ? 1 : 0;
+      cudaGraphExec_t& ex = c.cg_graph[pi][var];
+      if (!ex) {  // capture once per context (the kernels read every scalar from the device)
+        const long long k0 = launch_counter().load();
+        const long long l0 = launched;
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          for (int j = 0; j < cnt; ++j) iteration();
+          ok = cudaStreamEndCapture(c.st, &g) == cudaSuccess && g != nullptr;
+        }
+        launched = l0;                                   // captured, nothing ran
+        const long long captured = launch_counter().load() - k0;
+        launch_counter() -= captured;
+        if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (ok) {
+          c.cg_graph_kernels[pi][var] = captured;
+        } else {  // not capturable here: direct launches from now on
+          ex = nullptr;
+          c.graphs_off = true;
+          cudaGetLastError();
+        }
       }
-      fin<FAlpha>(c, slot, nb, done);
-      {
-        static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
-        yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
-      }
-      a = pbase(c, P, done);
-      a.tw = P.twx;
-      a.cin = P.S1;
-      a.rout = P.r;
-      a.rout2 = P.x;
-      a.aux[0] = P.p;
-      a.dscal = sc;
-      a.coef[1] = (R)sigma;
-      {
-        ProfScope ps(c, SITE_XI);
-        nb = (c.xi_percomp ? P.ox->xi_cgupdate_pc : P.ox->xi_cgupdate)(a, c.st);
-      }
-      fin<FBetaCg>(c, slot, nb, done);
-      snap_iterate(c, P, n, ks);
-      if (++launched % 32 == 0) {
-        // every CG vector is compatible in exact arithmetic; re-project r and p so that
-        // roundoff in modes G does not see cannot build up and corrupt <p, K p>
-        nb = op_gres(c, P, P.r, P.r, done);
-        fin<FSetResidual>(c, slot, nb, done);
-        op_gres(c, P, P.p, P.p, done);
+      if (ex) {
+        if (cudaGraphLaunch(ex, c.st) == cudaSuccess) {
+          launch_counter() += c.cg_graph_kernels[pi][var];
+          launched += cnt;
+          ran = true;
+        } else {
+          c.graphs_off = true;
+          cudaGetLastError();
+        }
       }
     }
+#endif
+    if (!ran)
+      for (int j = 0; j < cnt; ++j) iteration();
     read_ks(c);
     if (c.ks_host[slot].done) break;
-    if (chunk < 16) chunk *= 2;
   }
   const KScal& k = c.ks_host[slot];
   if (st) st->cg_negcurv += k.negc;
@@ -1389,6 +1444,20 @@ static void load_state(fg_ctx& c, const double* buf, double* cc, double* F, doub
   dcopy(H, buf + 11 * V, V * sizeof(double), c.st);
 }
 
+// forgets the captured CG graphs (they bake in the stress mask and the kernel choices)
+static void drop_graphs(fg_ctx& c) {
+#ifndef FG_EMU
+  for (auto& row : c.cg_graph)
+    for (auto& ex : row)
+      if (ex) {
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+      }
+#else
+  (void)c;
+#endif
+}
+
 static void free_tape(fg_ctx& c) {
   if (!c.tape) return;
   for (double* p : c.tape->ckpt) dfree(p);
@@ -1968,6 +2037,11 @@ void fg_destroy(fg_ctx* ctx) {
     for (cudaEvent_t e : v) cudaEventDestroy(e);
 #endif
   free_tape(*ctx);
+#ifndef FG_EMU
+  for (auto& row : ctx->cg_graph)
+    for (auto& ex : row)
+      if (ex) cudaGraphExecDestroy(ex);
+#endif
   free_all(*ctx);
   delete ctx;
 }
@@ -2045,6 +2119,7 @@ int fg_set_stress_control(fg_ctx* c, int mask, const double Pbar[9]) {
   if (!c || mask < 0 || mask > 511 || (mask && !Pbar)) fail(FG_ERR_INVALID, "fg_set_stress_control: bad argument");
   c->smask = mask;
   for (int k = 0; k < 9; ++k) c->Pbar[k] = mask ? Pbar[k] : 0.0;
+  drop_graphs(*c);
   FG_API_END
 }
 
@@ -2555,6 +2630,7 @@ int fg_adjoint_mech(fg_ctx* c, const double* W, double* grad_logE, int* iters) {
 int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   FG_API_BEGIN
   if (!c) fail(FG_ERR_INVALID, "fg_autotune: null context");
+  drop_graphs(*c);
 #ifdef FG_EMU
   if (ms_per_iteration) *ms_per_iteration = 0.0;
 #else

@@ -348,3 +348,22 @@ def test_mixed_control_step_matches_oracle(lib):
     assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
     np.testing.assert_allclose(F.mean(axis=(2, 3, 4)), ref.Fbar, atol=1e-12)
     sol.close()
+
+
+def test_cg_graph_replay_is_bitwise_identical(lib):
+    """The mechanical CG replays chunks of 16 iterations from captured CUDA graphs on streams
+    that can be captured: two steps of the 64^3 benchmark recipe on a side stream equal, bit
+    for bit, the same steps on the legacy default stream (where nothing is captured)."""
+    import bench
+    w = bench._workload(64, 0)
+    side = torch.cuda.Stream()
+    a = B.from_workload(w, precision=B.FG_MIXED, stream=side.cuda_stream, lib=lib)
+    b = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
+    for _ in range(2):
+        sa = a.step(w.dt)
+        sb = b.step(w.dt)
+        assert sa["cg_mech"] == sb["cg_mech"] and sa["cg_mech"] > 48
+    for f in (B.FIELD_F, B.FIELD_C, B.FIELD_D):
+        np.testing.assert_array_equal(a.get(f), b.get(f))
+    a.close()
+    b.close()
