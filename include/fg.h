@@ -119,6 +119,9 @@ typedef struct {
   int newton_shifted; /* mechanical Newton systems solved again with a larger shift */
   int newton_minres;  /* mechanical solves that fell back to FP64 MINRES after a CG
                          correction failed to lower the FP64 residual */
+  int cg_graph_replays; /* 16-iteration chunks of the mechanical CG replayed from captured
+                         CUDA graphs (contexts on a stream other than the legacy default
+                         stream, profiling off, no shift) */
   double err_mech;    /* final err_res */
   double err_chem;    /* final ||dc|| / ||c_t|| */
   double mass;        /* sum of c after the step */

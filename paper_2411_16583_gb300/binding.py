@@ -56,6 +56,7 @@ class Stats(C.Structure):
                 ("cg_mech", C.c_int), ("cg_pff", C.c_int), ("stag", C.c_int),
                 ("inner_refine", C.c_int), ("cg_truncated", C.c_int), ("newton_damped", C.c_int),
                 ("cg_negcurv", C.c_int), ("newton_shifted", C.c_int), ("newton_minres", C.c_int),
+                ("cg_graph_replays", C.c_int),
                 ("err_mech", C.c_double), ("err_chem", C.c_double),
                 ("mass", C.c_double), ("mass_err", C.c_double), ("status", C.c_int)]
 

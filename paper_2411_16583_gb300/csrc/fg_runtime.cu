@@ -816,6 +816,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
           launch_counter() += c.cg_graph_kernels[pi][var];
           launched += cnt;
           ran = true;
+          if (st) st->cg_graph_replays += 1;
         } else {
           c.graphs_off = true;
           cudaGetLastError();

@@ -359,10 +359,14 @@ def test_cg_graph_replay_is_bitwise_identical(lib):
     side = torch.cuda.Stream()
     a = B.from_workload(w, precision=B.FG_MIXED, stream=side.cuda_stream, lib=lib)
     b = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
+    replays = 0
     for _ in range(2):
         sa = a.step(w.dt)
         sb = b.step(w.dt)
         assert sa["cg_mech"] == sb["cg_mech"] and sa["cg_mech"] > 48
+        assert sb["cg_graph_replays"] == 0
+        replays += sa["cg_graph_replays"]
+    assert replays > 0
     for f in (B.FIELD_F, B.FIELD_C, B.FIELD_D):
         np.testing.assert_array_equal(a.get(f), b.get(f))
     a.close()
