@@ -15,7 +15,7 @@ the paper:
   1/V, real-to-half-complex along x (Sec. 3.2, "Discrete Fourier Transform");
 * no blocking, fusion or reordering beyond the paper's algorithms.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
 
 * swelling  F_c = J_c^{1/3} I with J_c = 1 + Omega (c - c0)  (Eq. Fc, shifted so the
   material is stress free at its reference concentration c0);
