@@ -315,3 +315,32 @@ def test_emulated_multi_particle_step_matches_oracle(emu):
     assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-9
     assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-10
     sol.close()
+
+
+def test_emulated_coupled_adjoint_svk_matches_oracle(emu):
+    """The coupled adjoint with the Saint-Venant-Kirchhoff law (its tangent and cofactor
+    branches of the reverse step) against the oracle's, on the damaging 12 x 12 disc."""
+    from oracle import fg_oracle_adjoint as A
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, _, phases, pid = _disc(n=12, smax=21e6)
+    ph = [O.Phase(law=O.LAW_SVK, E=p.E, nu=p.nu, Omega=p.Omega, c0=p.c0, D=p.D,
+                  sigma_max=p.sigma_max) for p in phases]
+    prm = O.make_params(ph, pid, (1e-7,) * 3, gc=1.0, lc=2e-7, log_E=logs[0], log_D=logs[2],
+                        log_gc=logs[1])
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_chem=1e-12, tol_chem_cg=1e-13,
+                tol_pff_cg=1e-13, tol_stag=1e-10, max_stag=400)
+    val, g = A.crack_energy_gradient(prm, np.full(shape, 0.01), src, [1.0, 1.0],
+                                     [np.eye(3)] * 2, O.Tolerances(**tols))
+    assert val > 0.0
+    sol = B.Solver(shape, (1e-7,) * 3, ph, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], lib=emu, gc=1.0, lc=2e-7,
+                   **tols)
+    sol.tape(2)
+    for _ in range(2):
+        sol.step(1.0)
+    v2, g2, st = sol.adjoint()
+    assert st["gmres"] >= 1
+    assert abs(v2 - val) < 1e-8 * val
+    for k in ("E", "gc", "D"):
+        assert rel_err(g2[k], g[k]) < 1e-9, k
+    sol.close()

@@ -371,3 +371,34 @@ def test_cg_graph_replay_is_bitwise_identical(lib):
         np.testing.assert_array_equal(a.get(f), b.get(f))
     a.close()
     b.close()
+
+
+def test_coupled_steps_autograd_gpu(lib):
+    """torch autograd through CoupledSteps on the GPU: a directional derivative of a loss on
+    the final (c, F, d) agrees with central differences of the forward (damaging disc)."""
+    from paper_2411_16583_gb300.autograd import coupled_steps
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, _, phases, pid = _disc(n=12, smax=21e6)
+    w = S.Workload(name="disc12", shape=shape, h=(1e-7,) * 3, phases=phases,
+                   phase_id=pid.astype(np.uint8), cdot_B=src, c_init=np.full(shape, 0.01),
+                   gc=1.0, lc=2e-7, dt=1.0, nsteps=2)
+    w.tol = dict(ADJ_TOLS)
+    spec = dict(w=w, nsteps=2, lib=lib, ckpt=1)
+    rng = np.random.default_rng(1)
+    wc, wd = rng.standard_normal(shape), rng.standard_normal(shape)
+    wF = rng.standard_normal((3, 3) + shape)
+
+    def loss_of(lE, lG, lD):
+        c, F, d = coupled_steps(lE, lG, lD, spec)
+        return ((c * torch.from_numpy(wc)).sum() + (F * torch.from_numpy(wF)).sum()
+                + (d * torch.from_numpy(wd)).sum())
+    t = [torch.tensor(x, requires_grad=True) for x in logs]
+    loss_of(*t).backward()
+    h = 1e-4
+    dirs = [0.3 * rng.standard_normal(shape) for _ in range(3)]
+    with torch.no_grad():
+        lp = loss_of(*[torch.tensor(x + h * dx) for x, dx in zip(logs, dirs)]).item()
+        lm = loss_of(*[torch.tensor(x - h * dx) for x, dx in zip(logs, dirs)]).item()
+    fd = (lp - lm) / (2 * h)
+    adj = sum(float((ti.grad.numpy() * dx).sum()) for ti, dx in zip(t, dirs))
+    assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
