@@ -1229,21 +1229,25 @@ static void hbar_from_sum(fg_ctx& c) {
 }
 
 template <typename R>
-static void pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
+// Alg. 2 for d.  Returns whether d changed: with H = 0 the solution is d = 0 (the
+// right-hand side 2H vanishes), which leaves an already zero d as it is.
+static bool pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
+  const double hh = reduce_sum(c, c.Heff, c.V, true);
+  if (hh == 0.0) {
+    if (reduce_sum(c, c.d, c.V, true) == 0.0) return false;
+    dzero(c.d, c.V * sizeof(double), c.st);
+    return true;
+  }
   if (!is_mixed(c)) {
     to_prec<double>(c, c.Heff, c.pd.b, c.V, 2.0);
     dcopy(c.pd.x, c.d, c.V * sizeof(double), c.st);
     s.cg_pff += pcg_pff<double>(c, c.pd, c.Heff, c.o.tol_pff_cg, c.o.max_cg);
     dcopy(c.d, c.pd.x, c.V * sizeof(double), c.st);
-    return;
+    return true;
   }
   // mixed: FP64 residual b - A d, FP32 PCG corrections
   to_prec<R>(c, c.Heff, P.Hr, c.V, 1.0);
-  const double bb = 4.0 * reduce_sum(c, c.Heff, c.V, true);
-  if (bb == 0.0) {
-    dzero(c.d, c.V * sizeof(double), c.st);
-    return;
-  }
+  const double bb = 4.0 * hh;
   Prec<double>& D = c.pd;
   for (int it = 0;; ++it) {
     op_pff(c, D, c.d, D.q, c.Heff, nullptr);  // q = A d in FP64
@@ -1275,6 +1279,7 @@ static void pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
     u.out[0] = c.d;
     launch_vec<KAddTo<R>>(u, c.st);
   }
+  return true;
 }
 
 template <typename R>
@@ -1395,16 +1400,24 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
     const double mass = reduce_sum(c, c.c, V, false);
     s.mass = mass;
     s.mass_err = (mass - (mass_t + dt * src)) / (mass != 0.0 ? mass : 1.0);
+    // when the phase-field solve leaves d as it was (no damage yet), F, c and d are the
+    // state of the Newton's last err_res, with the same denominator: it is reused
+    bool fresh = false;
+    double den = 0.0, err = 0.0;
     for (int k = 0;; ++k) {
-      const double den = residual_den(c);
-      const double err = residual_mech<double>(c, den, nullptr);
+      if (!fresh) {
+        den = residual_den(c);
+        err = residual_mech<double>(c, den, nullptr);
+      }
       s.err_mech = err;
       if (err <= c.o.tol_stag) break;
       if (k >= c.o.max_stag) fail(FG_ERR_NOCONV, "staggered scheme hit max_stag");
       mech_newton<R>(c, P, den, s, err);
       history(c);
-      pff_solve<R>(c, P, s);
+      const bool dchanged = pff_solve<R>(c, P, s);
       s.stag += 1;
+      fresh = !dchanged;
+      if (fresh) err = s.err_mech;
     }
   } catch (Fail&) {
     // restore the t-state
