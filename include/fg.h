@@ -155,13 +155,18 @@ int fg_supported_size(int n);
  *                           H = max(H_t, g_c(x)/(2 l_c) D_f), and the phase-field equation
  *                           g_c(x) (d/l_c - l_c lap d) = 2 (1 - d) H is solved divided by
  *                           g_c(x)/g_c, i.e. Eq. PFFA with H replaced by H g_c/g_c(x)
+ *   log_smax[V]             optional per-voxel log-scale of the strength, sigma_max(x) =
+ *                           phases[id].sigma_max exp(log_smax) in the driving force of
+ *                           Eq. SigDrivingForce (Sec. 5.1 draws it per voxel from the
+ *                           law of Eq. Gumbell; NULL: the phase value).  It is a fixed
+ *                           input: fg_adjoint returns no gradient with respect to it
  * Initial state F = I, d = 0, H = 0 (Alg. 4).  Allocates all device memory.
  * Errors: FG_ERR_INVALID (sizes, ids, law), FG_ERR_OOM, FG_ERR_CUDA.
  */
 int fg_setup(fg_ctx** out, const fg_grid* grid, const fg_phase* phases, int nphases,
              const uint8_t* phase_id, const double* cdot_B, const double* c_init,
              const double* log_E, const double* log_D, const double* log_gc,
-             const fg_opts* opts);
+             const double* log_smax, const fg_opts* opts);
 
 /*
  * One time step of Alg. 4 from the stored state (F_t, c_t, d_t, H_t) to t + dt with the

@@ -250,9 +250,10 @@ def lame(E, nu):
 
 
 def make_params(phases, phase_id, h, gc, lc, RT=8.314462618 * 298.15, cmax=3.0e4,
-                log_E=None, log_D=None, log_gc=None):
+                log_E=None, log_D=None, log_gc=None, log_smax=None):
     """Gather per-phase constants onto the voxel grid (optionally times exp(log-field):
-    stiffness E, diffusivity D and toughness g_c(x) = g_c exp(log_gc))."""
+    stiffness E, diffusivity D, toughness g_c(x) = g_c exp(log_gc) and strength
+    sigma_max(x) = sigma_max exp(log_smax), the per-voxel threshold of Sec. 5.1)."""
     phase_id = np.asarray(phase_id)
     laws = {p.law for p in phases}
     if len(laws) != 1:
@@ -265,8 +266,11 @@ def make_params(phases, phase_id, h, gc, lc, RT=8.314462618 * 298.15, cmax=3.0e4
     if log_D is not None:
         D = D * np.exp(log_D)
     lam, mu = lame(E, tab("nu"))
+    smax = tab("sigma_max")
+    if log_smax is not None:
+        smax = smax * np.exp(log_smax)
     return Params(law=phases[0].law, lam=lam, mu=mu, Omega=tab("Omega"), c0=tab("c0"), D=D,
-                  sigma_max=tab("sigma_max"), gc=float(gc), lc=float(lc), RT=float(RT),
+                  sigma_max=smax, gc=float(gc), lc=float(lc), RT=float(RT),
                   cmax=float(cmax), h=tuple(float(x) for x in h), shape=phase_id.shape,
                   gcr=None if log_gc is None else np.exp(np.asarray(log_gc, dtype=float)))
 

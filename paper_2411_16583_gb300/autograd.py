@@ -3,7 +3,8 @@
 MechEquilibrium: F(log E) of the mechanical equilibrium (Alg. 1) at fixed (c, d);
   backward solves G K G lambda = G dL/dF (fg_adjoint_mech), dL/dlogE = -lambda : P.
 CoupledSteps: the final state (c, F, d) after n staggered steps (Alg. 4) as a function of
-  the per-voxel log E, log g_c, log D; backward runs the recorded steps in reverse
+  the per-voxel log E, log g_c, log D (a per-voxel strength of the workload is a fixed
+  input); backward runs the recorded steps in reverse
   (fg_tape_begin / fg_adjoint with the seeds dL/d(c, F, d)).
 Everything runs in the CUDA library; this module only moves arguments.
 """
@@ -48,7 +49,8 @@ class CoupledSteps(torch.autograd.Function):
         w = spec["w"]
         np_ = lambda t: t.detach().double().cpu().numpy()
         sol = B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=w.c_init,
-                       log_E=np_(logE), log_gc=np_(loggc), log_D=np_(logD), lib=spec.get("lib"),
+                       log_E=np_(logE), log_gc=np_(loggc), log_D=np_(logD),
+                       log_smax=w.log_smax, lib=spec.get("lib"),
                        precision=spec.get("precision", B.FG_FP64), gc=w.gc, lc=w.lc, RT=w.RT,
                        cmax=w.cmax, **{**w.tol, **spec.get("opts", {})})
         sol.tape(spec.get("ckpt", 1))

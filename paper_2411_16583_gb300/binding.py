@@ -99,7 +99,7 @@ def load_library(path=LIB_PATH):
     lib.fg_supported_size.argtypes = [C.c_int]
     lib.fg_setup.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(Phase), C.c_int,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                             C.c_void_p, C.POINTER(Opts)]
+                             C.c_void_p, C.c_void_p, C.POINTER(Opts)]
     lib.fg_step.argtypes = [C.c_void_p, C.c_double, dp, C.POINTER(Stats)]
     lib.fg_residual.argtypes = [C.c_void_p, dp, dp, dp]
     lib.fg_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, dp]
@@ -158,7 +158,8 @@ class Solver:
     """One periodic RVE: owns an ``fg_ctx``.  Host arrays are numpy, (nz, ny, nx)."""
 
     def __init__(self, shape, h, phases, phase_id, cdot_B, c_init=None, log_E=None, log_D=None,
-                 log_gc=None, opts=None, precision=FG_FP64, stream=None, lib=None, **opt_kw):
+                 log_gc=None, log_smax=None, opts=None, precision=FG_FP64, stream=None, lib=None,
+                 **opt_kw):
         self.lib = lib or load_library()
         nz, ny, nx = shape
         self.shape = tuple(shape)
@@ -176,7 +177,7 @@ class Solver:
         self.opts = o
         self._keep = [np.ascontiguousarray(phase_id, dtype=np.uint8).ravel(), _f64(cdot_B).ravel()]
         opt_arrays = []
-        for a in (c_init, log_E, log_D, log_gc):
+        for a in (c_init, log_E, log_D, log_gc, log_smax):
             opt_arrays.append(None if a is None else _f64(a).ravel())
         self._keep += opt_arrays
         ctx = C.c_void_p()
@@ -337,6 +338,7 @@ def from_workload(w, precision=FG_FP64, lib=None, stream=None, **opt_kw):
     kw = dict(w.tol)
     kw.update(opt_kw)
     return Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=w.c_init, log_E=w.log_E,
-                  log_D=w.log_D, log_gc=w.log_gc, precision=precision, lib=lib, stream=stream,
+                  log_D=w.log_D, log_gc=w.log_gc, log_smax=w.log_smax, precision=precision,
+                  lib=lib, stream=stream,
                   gc=w.gc, lc=w.lc,
                   RT=w.RT, cmax=w.cmax, **kw)

@@ -2167,7 +2167,7 @@ int fg_adjoint(fg_ctx* c, int loss, const double* seed_c, const double* seed_F, 
 int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases,
              const uint8_t* phase_id, const double* cdot_B, const double* c_init,
              const double* log_E, const double* log_D, const double* log_gc,
-             const fg_opts* opts) {
+             const double* log_smax, const fg_opts* opts) {
   FG_API_BEGIN
   if (!out || !g || !phases || nphases <= 0 || nphases > 255 || !phase_id || !cdot_B)
     fail(FG_ERR_INVALID, "fg_setup: null argument or bad phase count");
@@ -2224,7 +2224,8 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
       Om[v] = p.Omega;
       c0[v] = p.c0;
       D[v] = p.D * (log_D ? exp(log_D[v]) : 1.0);
-      sm[v] = p.sigma_max;
+      sm[v] = p.sigma_max * (log_smax ? exp(log_smax[v]) : 1.0);
+      if (!(sm[v] > 0.0 && sm[v] < INFINITY)) fail(FG_ERR_INVALID, "fg_setup: sigma_max(x) not finite and > 0");
       cin[v] = c_init ? c_init[v] : p.c0;
       if (!(cin[v] > 0.0 && cin[v] < 1.0)) fail(FG_ERR_DOMAIN, "fg_setup: initial c outside (0,1)");
     }

@@ -25,7 +25,7 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
 * ``ellipsoid`` 128^3 with per-voxel log E, log g_c, log D ~ N(0, 0.1^2).
 * ``multi_particle`` several non-overlapping rough ellipsoids in one RVE.
 * ``gumbel_disc`` 512^2 Saint-Venant-Kirchhoff disc with Weibull-type random stiffness and
-  the paper's Omega = 1.3 (Sec. 5.1).
+  strength and the paper's Omega = 1.3 (Sec. 5.1).
 """
 from __future__ import annotations
 
@@ -67,6 +67,7 @@ class Workload:
     log_E: np.ndarray | None = None
     log_gc: np.ndarray | None = None
     log_D: np.ndarray | None = None
+    log_smax: np.ndarray | None = None
     RT: float = 8.314462618 * 298.15
     cmax: float = 3.0e4
     tol: dict = field(default_factory=lambda: dict(
@@ -219,26 +220,35 @@ def sphere_batch(count=64, sizes=(48, 64, 80, 96), rmin=0.30, rmax=0.45, nsteps=
             for i, (n, r) in enumerate(zip(ns, rs))]
 
 
+def gumbel_log_scale(rng, shape, m=3.0):
+    """Per-voxel log-scale of a property drawn with the law of Eq. Gumbell,
+    X_i = X log(1/(1 - w_i))^(1/m) with w_i ~ U(0, 1): returns log(X_i / X)."""
+    om = rng.uniform(size=shape)
+    return np.log(np.log(1.0 / (1.0 - om))) / m
+
+
 def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16e-6 / 512,
-                E=15e9, Omega=1.3):
+                E=15e9, Omega=1.3, sigma_max=100e6, random_strength=True):
     """2D circular Saint-Venant-Kirchhoff particle with Weibull-type random stiffness
     (Sec. 5.1, Eq. Gumbell): E_i = E log(1/(1 - w_i))^(1/m), w_i ~ U(0, 1), m = 3, carried
     as the per-voxel log-stiffness log_E = log(log(1/(1 - w_i)))/m, and the paper's
-    swelling Omega = 1.3.  The paper also draws a random sigma_max per voxel with the same
-    law; the C ABI takes sigma_max per phase, so this workload keeps it uniform.  With
-    E = 15 GPa and Omega = 1.3 the elastic chemical potential reaches several RT, where the
-    Newton of Alg. 3 (Jacobian of the ideal part only) stops converging; the workload
-    therefore runs the chemistry Newton with the full Jacobian (chem_full_jacobian)."""
+    swelling Omega = 1.3.  The strength sigma_max (100 MPa in the text of Sec. 5.1) is
+    drawn per voxel from the same law with its own w_i (log_smax; random_strength=False
+    keeps it uniform).  With E = 15 GPa and Omega = 1.3 the elastic chemical potential
+    reaches several RT, where the Newton of Alg. 3 (Jacobian of the ideal part only) stops
+    converging; the workload therefore runs the chemistry Newton with the full Jacobian
+    (chem_full_jacobian)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (1, n, n)
     x, y, _ = _grid_coords(shape)
     particle = (x * x + y * y) <= (0.5 * diameter_frac * n) ** 2
     c0 = 0.01
-    phases = default_phases(E=E, c0=c0, law=LAW_SVK, vol_change=Omega * (1.0 - c0), buffer_E=1e-5)
+    phases = default_phases(E=E, c0=c0, law=LAW_SVK, vol_change=Omega * (1.0 - c0), buffer_E=1e-5,
+                            sigma_max=sigma_max)
     w = _finish("gumbel_disc", shape, (h, h, h), particle, band, nsteps, 1.0, rng, phases=phases)
-    om = rng.uniform(size=shape)
-    log_E = np.log(np.log(1.0 / (1.0 - om))) / m
-    w.log_E = np.where(particle, log_E, 0.0)
+    w.log_E = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
+    if random_strength:
+        w.log_smax = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
     w.tol = dict(w.tol, chem_full_jacobian=1)
     return w
 

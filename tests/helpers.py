@@ -17,7 +17,7 @@ def oracle_params(w_or_phases, phase_id=None, h=None, gc=1.0, lc=2e-7, RT=8.3144
         w = w_or_phases
         return O.make_params([O.Phase(**vars(p)) for p in w.phases], w.phase_id, w.h, gc=w.gc,
                              lc=w.lc, RT=w.RT, cmax=w.cmax, log_E=w.log_E, log_D=w.log_D,
-                             log_gc=w.log_gc)
+                             log_gc=w.log_gc, log_smax=w.log_smax)
     return O.make_params([O.Phase(**vars(p)) for p in w_or_phases], phase_id, h, gc=gc, lc=lc,
                          RT=RT, cmax=cmax)
 

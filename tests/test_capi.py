@@ -61,6 +61,11 @@ def test_invalid_arguments(emu):
     with pytest.raises(B.FgError) as e:  # initial concentration outside (0, 1)
         B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=np.full(w.shape, 1.2), lib=emu)
     assert e.value.code == -5
+    bad_smax = np.zeros(w.shape)
+    bad_smax.flat[3] = np.inf  # sigma_max(x) = sigma_max exp(log_smax) must stay finite
+    with pytest.raises(B.FgError, match="sigma_max") as e:
+        B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, log_smax=bad_smax, lib=emu)
+    assert e.value.code == -1
     with pytest.raises(B.FgError, match="cg_indefinite") as e:  # modes 0, 1, 2 only
         B.from_workload(w, lib=emu, cg_indefinite=3)
     assert e.value.code == -1

@@ -166,6 +166,53 @@ def test_emulated_damage_with_log_fields_matches_oracle(emu):
     sol.close()
 
 
+def test_emulated_per_voxel_strength_matches_oracle(emu):
+    """Two steps of the disc with per-voxel log E, log D, log g_c and a Gumbel-distributed
+    strength sigma_max(x) (Sec. 5.1): damage starts at the weak voxels in the first step;
+    F, c, H and d against the oracle."""
+    from tests.test_oracle_adjoint import _strength_disc
+    shape, logs, ls, src, prm, phases, pid = _strength_disc()
+    tols = dict(tol_newton=1e-12, tol_stag=1e-10, max_stag=400)
+    ref = O.CoupledState(prm, np.full(shape, 0.01), src, O.Tolerances(**tols))
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], log_smax=ls, lib=emu, gc=1.0,
+                   lc=2e-7, **tols)
+    ref.step(1.0, np.eye(3))
+    sol.step(1.0)
+    assert ref.d.max() > 0.01  # damaging already
+    ref.step(1.0, np.eye(3))
+    sol.step(1.0)
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-8
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-8
+    assert rel_err(sol.get(B.FIELD_H), ref.H) < 1e-8
+    assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < 1e-8
+    sol.close()
+
+
+def test_emulated_adjoint_with_per_voxel_strength_matches_oracle(emu):
+    """dGamma_E/dlog(E, g_c, D) of the CUDA reverse pass with a per-voxel strength (a fixed
+    input) against the oracle's adjoint, two damaging steps."""
+    from oracle import fg_oracle_adjoint as A
+    from tests.test_oracle_adjoint import _strength_disc
+    shape, logs, ls, src, prm, phases, pid = _strength_disc()
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_chem=1e-12, tol_chem_cg=1e-13,
+                tol_pff_cg=1e-13, tol_stag=1e-10, max_stag=400)
+    val, g = A.crack_energy_gradient(prm, np.full(shape, 0.01), src, [1.0, 1.0],
+                                     [np.eye(3)] * 2, O.Tolerances(**tols))
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], log_smax=ls, lib=emu, gc=1.0,
+                   lc=2e-7, **tols)
+    sol.tape(1)
+    for _ in range(2):
+        sol.step(1.0)
+    v2, g2, _ = sol.adjoint()
+    assert abs(v2 - val) < 1e-8 * val
+    assert np.abs(g["gc"]).max() > 0.0
+    for k in ("E", "gc", "D"):
+        assert rel_err(g2[k], g[k]) < 1e-9, k
+    sol.close()
+
+
 @pytest.mark.parametrize("ckpt", [1, 2])
 def test_emulated_coupled_adjoint_matches_oracle(emu, ckpt):
     """dGamma_E/dlog(E, g_c, D) of the CUDA reverse pass (tape, recompute from

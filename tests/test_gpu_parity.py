@@ -247,6 +247,28 @@ def test_mixed_vs_fp64_gpu_perturbed_particle(lib):
     b.close()
 
 
+def test_per_voxel_strength_matches_oracle(lib):
+    """Per-voxel strength sigma_max(x) drawn with the law of Eq. Gumbell (Sec. 5.1), with
+    per-voxel log E, log D and log g_c: two FP64 steps on the device, damaging from the
+    first, against the oracle (F, c, H, d)."""
+    from tests.test_oracle_adjoint import _strength_disc
+    shape, logs, ls, src, prm, phases, pid = _strength_disc()
+    tols = dict(tol_newton=1e-12, tol_stag=1e-10, max_stag=400)
+    ref = O.CoupledState(prm, np.full(shape, 0.01), src, O.Tolerances(**tols))
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], log_smax=ls, lib=lib, gc=1.0,
+                   lc=2e-7, **tols)
+    for _ in range(2):
+        ref.step(1.0, np.eye(3))
+        sol.step(1.0)
+    assert ref.d.max() > 0.5
+    assert rel_err(sol.get(B.FIELD_F), ref.F) < 1e-8
+    assert rel_err(sol.get(B.FIELD_C), ref.c) < 1e-8
+    assert rel_err(sol.get(B.FIELD_H), ref.H) < 1e-8
+    assert np.abs(sol.get(B.FIELD_D) - ref.d).max() < 1e-8
+    sol.close()
+
+
 def test_gumbel_svk_disc_step(lib):
     """The paper's 2D example type (Sec. 5.1): a 512^2 Saint-Venant-Kirchhoff disc with
     Weibull-distributed stiffness; one mixed step, then the oracle's residuals of the

@@ -7,6 +7,7 @@ import pytest
 
 from oracle import fg_oracle as O
 from oracle import fg_oracle_adjoint as A
+from paper_2411_16583_gb300 import synth as S
 
 H = (1e-7, 1e-7, 1e-7)
 SHAPE = (2, 3, 4)
@@ -17,12 +18,12 @@ def _phases(law, smax):
             O.Phase(law=law, E=3e9, nu=0.33, Omega=0.1, c0=0.05, D=2e-14, sigma_max=smax)]
 
 
-def _params(law, shape=SHAPE, smax=20e6, seed=0, log_E=None):
+def _params(law, shape=SHAPE, smax=20e6, seed=0, log_E=None, log_smax=None):
     """Two random phases with a random log g_c field; the same seed gives the same maps."""
     rng = np.random.default_rng(seed)
     pid = (rng.random(shape) < 0.5).astype(int)
     return O.make_params(_phases(law, smax), pid, H, gc=1.3, lc=2e-7, log_E=log_E,
-                         log_gc=0.1 * rng.standard_normal(shape))
+                         log_gc=0.1 * rng.standard_normal(shape), log_smax=log_smax)
 
 
 def _state(shape=SHAPE, seed=1, amp=0.04):
@@ -62,11 +63,14 @@ def test_stress_and_chemical_potential_derivatives(law):
     np.testing.assert_allclose(mue, (1.0 - d) ** 2 * O.mu_elastic(F, c, 0.0 * d, prm), rtol=1e-13)
 
 
+@pytest.mark.parametrize("per_voxel_strength", [False, True])
 @pytest.mark.parametrize("law", [O.LAW_NEOHOOKE, O.LAW_SVK])
-def test_driving_force_derivatives(law):
+def test_driving_force_derivatives(law, per_voxel_strength):
     """psi = g_c(x)/(2 l_c) D_f and its derivatives in F, c and log E, on voxels away from
-    the Macaulay kink of D_f (the threshold is low enough that most voxels are damaging)."""
-    prm = _params(law, smax=60e6)
+    the Macaulay kink of D_f (the threshold is low enough that most voxels are damaging),
+    with a uniform or a per-voxel strength sigma_max(x)."""
+    ls = 0.3 * np.random.default_rng(21).standard_normal(SHAPE) if per_voxel_strength else None
+    prm = _params(law, smax=60e6, log_smax=ls)
     F, c, _ = _state(amp=0.06)
     psi, Z, psi_c, psi_E = A.psi_terms(F, c, prm)
     np.testing.assert_allclose(psi, prm.gc * O.gc_ratio(prm) / (2 * prm.lc) *
@@ -84,7 +88,7 @@ def test_driving_force_derivatives(law):
     np.testing.assert_allclose(psi_c[safe], fdc[safe], rtol=1e-5, atol=1e-6 * np.abs(psi).max())
 
     def psi_at(logE):
-        return A.psi_terms(F, c, _params(law, smax=60e6, log_E=logE))[0]
+        return A.psi_terms(F, c, _params(law, smax=60e6, log_E=logE, log_smax=ls))[0]
     z = np.zeros(SHAPE)
     fdE = (psi_at(z + h) - psi_at(z - h)) / (2 * h)
     np.testing.assert_allclose(psi_E[safe], fdE[safe], rtol=1e-5, atol=1e-6 * np.abs(psi).max())
@@ -173,6 +177,16 @@ def _disc(n=10, smax=17e6, seed=3):
     def prm_of(lE, lG, lD):
         return O.make_params(phases, pid, H, gc=1.0, lc=2e-7, log_E=lE, log_D=lD, log_gc=lG)
     return shape, logs, src, tol, prm_of, phases, pid
+
+
+def _strength_disc(n=12, smax=40e6, seed=17):
+    """The damaging disc with a per-voxel strength drawn inside the particle with the law
+    of Eq. Gumbell (m = 3), as Sec. 5.1 does: its weakest voxel damages in the first step."""
+    shape, logs, src, _, _, phases, pid = _disc(n=n, smax=smax)
+    ls = np.where(pid == 0, S.gumbel_log_scale(np.random.default_rng(seed), shape), 0.0)
+    prm = O.make_params(phases, pid, (1e-7,) * 3, gc=1.0, lc=2e-7, log_E=logs[0], log_D=logs[2],
+                        log_gc=logs[1], log_smax=ls)
+    return shape, logs, ls, src, prm, phases, pid
 
 
 @pytest.mark.slow

@@ -153,3 +153,30 @@ def test_principal_stress_driving_force():
     sy = np.maximum(sigma[1, 1], 0) / prm.sigma_max
     sz = np.maximum(sigma[2, 2], 0) / prm.sigma_max
     np.testing.assert_allclose(Df, np.maximum(sx ** 2 + sy ** 2 + sz ** 2 - 1, 0), rtol=1e-12, atol=1e-14)
+
+
+def test_per_voxel_strength_driving_force():
+    """Per-voxel strength sigma_max(x) = sigma_max exp(log_smax) (Sec. 5.1 draws it per
+    voxel): under a homogeneous uniaxial stretch the Cauchy stress is diagonal and the
+    same everywhere, so D_f at each voxel is the closed form of Eq. SigDrivingForce with
+    that voxel's own threshold."""
+    phases = [O.Phase(law=O.LAW_SVK, E=15e9, nu=0.3, Omega=0.0, c0=0.01, sigma_max=100e6)]
+    pid = np.zeros(SHAPE, dtype=int)
+    log_smax = RNG.uniform(-1.5, 0.5, SHAPE)
+    prm = O.make_params(phases, pid, (1e-7,) * 3, gc=1.0, lc=2e-7, log_smax=log_smax)
+    np.testing.assert_allclose(prm.sigma_max, 100e6 * np.exp(log_smax), rtol=1e-15)
+    l = 1.004
+    F = np.zeros((3, 3) + SHAPE)
+    F[0, 0], F[1, 1], F[2, 2] = l, 1.0, 1.0
+    c = np.full(SHAPE, 0.01)
+    # SVK: E = (l^2 - 1)/2 e1 e1, S = lam tr E I + 2 G E, sigma = F S F^T / J
+    lam, G = O.lame(15e9, 0.3)
+    e = 0.5 * (l * l - 1.0)
+    sx = (lam * e + 2.0 * G * e) * l * l / l
+    sy = lam * e / l
+    thr = 100e6 * np.exp(log_smax)
+    ref = np.maximum((sx / thr) ** 2 + 2.0 * (sy / thr) ** 2 - 1.0, 0.0)
+    assert (ref > 0).any() and (ref == 0).any()  # both sides of the threshold
+    np.testing.assert_allclose(O.driving_force(F, c, prm), ref, rtol=1e-12, atol=1e-15)
+    H = O.history_update(np.zeros(SHAPE), F, c, prm)
+    np.testing.assert_allclose(H, ref / (2.0 * 2e-7), rtol=1e-12)
