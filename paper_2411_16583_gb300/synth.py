@@ -227,7 +227,7 @@ def gumbel_log_scale(rng, shape, m=3.0):
     return np.log(np.log(1.0 / (1.0 - om))) / m
 
 
-def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16e-6 / 512,
+def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=200, seed=0, m=3.0, h=16e-6 / 512,
                 E=15e9, Omega=1.3, sigma_max=100e6, random_strength=True):
     """2D circular Saint-Venant-Kirchhoff particle with Weibull-type random stiffness
     (Sec. 5.1, Eq. Gumbell): E_i = E log(1/(1 - w_i))^(1/m), w_i ~ U(0, 1), m = 3, carried
@@ -237,7 +237,10 @@ def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16
     keeps it uniform).  With E = 15 GPa and Omega = 1.3 the elastic chemical potential
     reaches several RT, where the Newton of Alg. 3 (Jacobian of the ideal part only) stops
     converging; the workload therefore runs the chemistry Newton with the full Jacobian
-    (chem_full_jacobian)."""
+    (chem_full_jacobian).  The influx fills the particle to a mean c of 0.5 over nsteps
+    steps.  The default of 200 keeps the first step free of damage, as in Sec. 5.1: at
+    512^2 with 20 steps the first step already cracked most of the particle and needed
+    341 staggered iterations, so the staggered cap is raised to 400 (max_stag)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (1, n, n)
     x, y, _ = _grid_coords(shape)
@@ -249,7 +252,7 @@ def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=20, seed=0, m=3.0, h=16
     w.log_E = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
     if random_strength:
         w.log_smax = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
-    w.tol = dict(w.tol, chem_full_jacobian=1)
+    w.tol = dict(w.tol, chem_full_jacobian=1, max_stag=400)
     return w
 
 

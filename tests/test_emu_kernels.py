@@ -337,7 +337,7 @@ def test_emulated_full_chemistry_jacobian_matches_oracle(emu):
     """The chemistry Newton with the full Jacobian (chem_full_jacobian) on a 32 x 32 version
     of the Omega = 1.3 Saint-Venant-Kirchhoff Gumbel disc: one coupled step against the
     oracle's."""
-    w = S.gumbel_disc(n=32, band=2)
+    w = S.gumbel_disc(n=32, band=2, nsteps=20)
     prm = oracle_params(w)
     ref = O.CoupledState(prm, w.c_init, w.cdot_B, O.Tolerances(**w.tol))
     st_ref = ref.step(w.dt, np.eye(3))

@@ -271,13 +271,15 @@ def test_per_voxel_strength_matches_oracle(lib):
 
 def test_gumbel_svk_disc_step(lib):
     """The paper's 2D example type (Sec. 5.1): a 512^2 Saint-Venant-Kirchhoff disc with
-    Weibull-distributed stiffness and a uniform strength; one mixed step, then the oracle's
-    residuals of the GPU's fields.  (The per-voxel strength has its own parity test.)"""
-    w = S.gumbel_disc(random_strength=False)
+    Weibull-distributed stiffness and strength; two mixed steps, the second one damaging
+    at the weakest voxels, then the oracle's residuals of the GPU's fields."""
+    w = S.gumbel_disc()
     sol = B.from_workload(w, precision=B.FG_MIXED, lib=lib)
-    st = sol.step(w.dt)
-    assert st["status"] == 0
+    for _ in range(2):
+        st = sol.step(w.dt)
+        assert st["status"] == 0
     F, c, d = sol.get(B.FIELD_F), sol.get(B.FIELD_C), sol.get(B.FIELD_D)
+    assert st["stag"] > 1 and d.max() > 1e-3
     prm = oracle_params(w)
     _, err = O.mech_residual(F, c, d, prm, np.eye(3))
     assert err <= 2 * w.tol["tol_stag"]
