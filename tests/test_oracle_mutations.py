@@ -97,3 +97,23 @@ def test_adjoint_sign_is_caught(monkeypatch):
     monkeypatch.setattr(O, "mech_adjoint", lambda *a, **k: -good(*a, **k))
     with pytest.raises(AssertionError):
         TS.test_mech_adjoint_matches_central_differences()
+
+
+def test_strength_scale_inverted_is_caught(monkeypatch):
+    good = O.make_params
+
+    def bad(*a, log_smax=None, **kw):  # sigma_max exp(-log_smax) instead of exp(+log_smax)
+        return good(*a, log_smax=None if log_smax is None else -log_smax, **kw)
+    monkeypatch.setattr(O, "make_params", bad)
+    with pytest.raises(AssertionError):
+        TC.test_per_voxel_strength_driving_force()
+
+
+def test_strength_ignored_in_driving_force_is_caught(monkeypatch):
+    def bad(F, c, prm):  # the phase's mean strength instead of the voxel's own
+        s = O.principal_stresses(O.cauchy_undegraded(F, c, prm))
+        t = np.maximum(s, 0.0) / prm.sigma_max.mean()
+        return np.maximum(np.sum(t * t, axis=0) - 1.0, 0.0)
+    monkeypatch.setattr(O, "driving_force", bad)
+    with pytest.raises(AssertionError):
+        TC.test_per_voxel_strength_driving_force()
