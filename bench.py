@@ -31,9 +31,9 @@ UNIT = "voxel-steps/s"
 # Algorithmic bytes per voxel of each profiled launch site of the FP32 mechanical CG
 # iteration (9-component fields, 4-byte reals; the half spectrum holds (nx/2+1)/nx of a
 # real field as complex numbers, so a 9-component spectrum is 72 (nx/2+1)/nx B/voxel).
-# DRAM bytes per voxel that ncu measured per launch of the fused CG X passes
-# (profiles/x_passes_traffic_256x256x64.md; x rows of 256): valid for these kernels as they
-# are, at nx = 256
+# DRAM bytes per voxel that ncu measured per launch of the fused CG X passes (dram bytes
+# read + written on a 256 x 256 x 64 grid, divided by its voxels; x rows of 256): valid for
+# these kernels as they are, at nx = 256
 MEASURED_TRAFFIC_B_PER_VOXEL = {"xi": 203.6, "xf": 181.2}
 
 
@@ -59,6 +59,22 @@ def _traffic(site, nx, voxels_per_launch):
     if key is None or nx != 256:
         return None
     return MEASURED_TRAFFIC_B_PER_VOXEL[key] * voxels_per_launch
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the slowest rank sets the job's time); x itself when
+    there is one rank (dist None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(voxels_per_rank, world, seconds_per_step):
+    """Whole-job voxel-steps/s: every rank advances its own RVE by one step."""
+    return voxels_per_rank * world / seconds_per_step
 
 
 def _args():
@@ -340,10 +356,7 @@ def main():
     prof = {s: sol.profile_read(s) for s in range(5)}
     for s in range(5):
         sol.profile(s, False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end through the same public calls with host buffers: each step copies the
     # state (F, c, d, H) in from pinned host memory and the new (F, c, d) back out
@@ -364,8 +377,9 @@ def main():
             for f, buf in ((B.FIELD_F, hF), (B.FIELD_C, hs[0]), (B.FIELD_D, hs[1])):
                 sol._check(lib.fg_get_field(sol.ctx, f, B._ptr(buf), 0))
         barrier()
-        e2e_s = (time.perf_counter() - t0) / a.steps
-        e2e = {"value": V * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * V * 8,
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / a.steps, dist, "cuda")
+        e2e = {"value": job_throughput(V, world, e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": 12 * V * 8,
                "d2h_bytes_per_step": 11 * V * 8}
 
     # fused matvec rates: FP32 operator of the mixed context, and the unfused cuFFT
@@ -410,7 +424,7 @@ def main():
     ach = sb[dom] * V * vol_dom / (t_dom * 1e-3) / 1e9
     line = {
         "metric": METRIC,
-        "value": V * world / (ms * 1e-3),
+        "value": job_throughput(V, world, ms * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": a.steps,
