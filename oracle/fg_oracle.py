@@ -26,7 +26,10 @@ Readings of points the paper leaves open:
 * the history is H = max(H_t, g_c/(2 l_c) D_f) with D_f from the undegraded Cauchy
   stress (Eqs. Hist, SigDrivingForce);
 * the chemical Newton Jacobian keeps only the ideal-solution part of mu (Eq.
-  Chemderfc) and is solved in the symmetric variable y = m dc, m = 1/(c(1-c)).
+  Chemderfc) and is solved in the symmetric variable y = m dc, m = 1/(c(1-c)); an
+  option adds the elastic part d(mu_e/RT)/dc (same root);
+* toughness and strength may vary per voxel, g_c(x) = g_c exp(log_gc) and
+  sigma_max(x) = sigma_max exp(log_smax) (Sec. 5.1 draws the strength per voxel).
 
 Parity status: every function below is pinned by ``tests/test_oracle_*.py``
 except the composition of a whole coupled step (Alg. 4), which is pinned only
