@@ -817,10 +817,14 @@ class CoupledState:
         d = d_t.copy()
         H = H_t.copy()
         stag = 0
+        # Alg. 4 evaluates err_res inside the body of its loop, so the body (mechanics,
+        # history, phase field) runs at least once per step, also when the step starts in
+        # equilibrium (an affine load of a homogeneous medium); the loop then ends once the
+        # state (F, c, d) it left is in equilibrium
         while True:
             _, err = mech_residual(F, c, d, prm, Fbar_new)
             stats.setdefault("err_stag", []).append(err)
-            if err <= tol.tol_stag:
+            if err <= tol.tol_stag and stag > 0:
                 break
             if stag >= tol.max_stag:
                 raise RuntimeError("staggered scheme did not converge")

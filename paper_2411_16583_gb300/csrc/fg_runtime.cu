@@ -1103,7 +1103,11 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s, double e
     return hi ? residual_mech<double>(c, den, c.pd.state) : residual_mech<R>(c, den, P.state);
   };
   // err0 >= 0: the caller has just evaluated err_res at this F (c.P, c.GP current), so
-  // only the tangent state is built
+  // only the tangent state is built, and nothing when F is converged already
+  if (err0 >= 0.0 && err0 <= c.o.tol_newton) {
+    s.err_mech = err0;
+    return;
+  }
   double err;
   if (err0 >= 0.0) {
     if (hi) mech_state<double>(c, c.F, nullptr, nullptr, c.pd.state);
@@ -1400,8 +1404,10 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
     const double mass = reduce_sum(c, c.c, V, false);
     s.mass = mass;
     s.mass_err = (mass - (mass_t + dt * src)) / (mass != 0.0 ? mass : 1.0);
-    // when the phase-field solve leaves d as it was (no damage yet), F, c and d are the
-    // state of the Newton's last err_res, with the same denominator: it is reused
+    // Alg. 4: the body (mechanics, history, phase field) runs at least once, also from a
+    // state already in equilibrium, and the loop ends when the state it left is.  When the
+    // phase-field solve leaves d as it was (no damage yet), F, c and d are the state of the
+    // Newton's last err_res, with the same denominator: it is reused
     bool fresh = false;
     double den = 0.0, err = 0.0;
     for (int k = 0;; ++k) {
@@ -1410,7 +1416,7 @@ static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_s
         err = residual_mech<double>(c, den, nullptr);
       }
       s.err_mech = err;
-      if (err <= c.o.tol_stag) break;
+      if (k > 0 && err <= c.o.tol_stag) break;
       if (k >= c.o.max_stag) fail(FG_ERR_NOCONV, "staggered scheme hit max_stag");
       mech_newton<R>(c, P, den, s, err);
       history(c);

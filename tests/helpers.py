@@ -27,3 +27,19 @@ def rel_err(a, b):
     b = np.asarray(b, dtype=float)
     den = np.abs(b).max()
     return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def homogeneous_stretch_damage(E, nu, smax, gc, lc, l):
+    """History and phase field of a homogeneous compressible Neo-Hookean medium (no
+    swelling) under F = diag(l, 1, 1): the Cauchy stress is diagonal, sigma_xx =
+    (G (l^2 - 1) + lam ln l)/l and sigma_yy = sigma_zz = lam ln l / l, so D_f =
+    sum (<sigma_i>/sigma_max)^2 - 1 (Eq. SigDrivingForce), H = g_c/(2 l_c) <D_f>, and the
+    uniform solution of Eq. PFFA is d = 2H/(g_c/l_c + 2H).  Returns (H, d)."""
+    import math
+    lam, G = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    sx = (G * (l * l - 1.0) + lam * math.log(l)) / l
+    sy = lam * math.log(l) / l
+    Df = max((max(sx, 0.0) / smax) ** 2 + 2.0 * (max(sy, 0.0) / smax) ** 2 - 1.0, 0.0)
+    Hx = gc / (2.0 * lc) * Df
+    return Hx, 2.0 * Hx / (gc / lc + 2.0 * Hx)
+

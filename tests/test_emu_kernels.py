@@ -10,7 +10,8 @@ import pytest
 
 from oracle import fg_oracle as O
 from paper_2411_16583_gb300 import binding as B, build, synth as S
-from tests.helpers import TOL_APPLY_FP32, TOL_APPLY_FP64, oracle_params, rel_err
+from tests.helpers import (TOL_APPLY_FP32, TOL_APPLY_FP64, homogeneous_stretch_damage,
+                           oracle_params, rel_err)
 
 H3 = (1.0e-7, 1.1e-7, 0.9e-7)
 
@@ -391,3 +392,31 @@ def test_emulated_coupled_adjoint_svk_matches_oracle(emu):
     for k in ("E", "gc", "D"):
         assert rel_err(g2[k], g[k]) < 1e-9, k
     sol.close()
+
+
+@pytest.mark.parametrize("shape", [(8, 12, 16), (1, 12, 16), (1, 1, 16)])
+@pytest.mark.parametrize("prec", [B.FG_FP64, B.FG_MIXED])
+def test_emulated_homogeneous_bar_damages_in_closed_form(emu, shape, prec):
+    """Degenerate case of Alg. 4 on 3-D, plane and single-line grids: a homogeneous medium
+    without swelling or influx, stretched by F-bar = diag(l, 1, 1) in two steps.  F stays
+    F-bar exactly, c is unchanged, no Newton iteration is needed, and the step's single
+    staggered pass gives the closed-form H and d (below the threshold at the first
+    stretch, damaged at the second)."""
+    E, nu, smax, gc, lc = 10e9, 0.3, 50e6, 1.0, 2e-7
+    ph = [S.PhaseSpec(E=E, nu=nu, Omega=0.0, c0=0.01, D=1e-14, sigma_max=smax)]
+    sol = B.Solver(shape, (1e-7,) * 3, ph, np.zeros(shape, np.uint8), np.zeros(shape),
+                   c_init=np.full(shape, 0.2), lib=emu, precision=prec, gc=gc, lc=lc)
+    for l, damaged in ((1.002, False), (1.012, True)):
+        Fbar = np.diag([l, 1.0, 1.0])
+        st = sol.step(1.0, Fbar)
+        Hx, dx = homogeneous_stretch_damage(E, nu, smax, gc, lc, l)
+        assert (Hx > 0.0) == damaged
+        assert st["stag"] == 1 and st["newton_mech"] == 0
+        F = sol.get(B.FIELD_F)
+        Fx = np.broadcast_to(Fbar.reshape(3, 3, 1, 1, 1), (3, 3) + shape)
+        np.testing.assert_allclose(F, Fx, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(sol.get(B.FIELD_C), 0.2, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(sol.get(B.FIELD_H), Hx, rtol=1e-12)
+        np.testing.assert_allclose(sol.get(B.FIELD_D), dx, rtol=1e-9, atol=1e-15)
+    sol.close()
+

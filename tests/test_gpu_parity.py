@@ -8,7 +8,8 @@ torch = pytest.importorskip("torch")
 
 from oracle import fg_oracle as O
 from paper_2411_16583_gb300 import binding as B, synth as S
-from tests.helpers import TOL_APPLY_FP32, TOL_APPLY_FP64, TOL_STEP_FP64, oracle_params, rel_err
+from tests.helpers import (TOL_APPLY_FP32, TOL_APPLY_FP64, TOL_STEP_FP64,
+                           homogeneous_stretch_damage, oracle_params, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -426,3 +427,30 @@ def test_coupled_steps_autograd_gpu(lib):
     fd = (lp - lm) / (2 * h)
     adj = sum(float((ti.grad.numpy() * dx).sum()) for ti, dx in zip(t, dirs))
     assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
+
+
+@pytest.mark.parametrize("shape", [(32, 48, 64), (1, 64, 64)])
+@pytest.mark.parametrize("prec", [B.FG_FP64, B.FG_MIXED])
+def test_homogeneous_bar_damages_in_closed_form(lib, shape, prec):
+    """Degenerate case of Alg. 4 on the device: a homogeneous medium without swelling or
+    influx, stretched by F-bar = diag(l, 1, 1) in two steps, keeps F = F-bar and c, needs
+    no Newton iteration, and its single staggered pass gives the closed-form H and d
+    (undamaged at the first stretch, damaged at the second)."""
+    E, nu, smax, gc, lc = 10e9, 0.3, 50e6, 1.0, 2e-7
+    ph = [S.PhaseSpec(E=E, nu=nu, Omega=0.0, c0=0.01, D=1e-14, sigma_max=smax)]
+    sol = B.Solver(shape, (1e-7,) * 3, ph, np.zeros(shape, np.uint8), np.zeros(shape),
+                   c_init=np.full(shape, 0.2), lib=lib, precision=prec, gc=gc, lc=lc)
+    for l, damaged in ((1.002, False), (1.012, True)):
+        Fbar = np.diag([l, 1.0, 1.0])
+        st = sol.step(1.0, Fbar)
+        Hx, dx = homogeneous_stretch_damage(E, nu, smax, gc, lc, l)
+        assert (Hx > 0.0) == damaged
+        assert st["stag"] == 1 and st["newton_mech"] == 0
+        F = sol.get(B.FIELD_F)
+        Fx = np.broadcast_to(Fbar.reshape(3, 3, 1, 1, 1), (3, 3) + shape)
+        np.testing.assert_allclose(F, Fx, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(sol.get(B.FIELD_C), 0.2, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(sol.get(B.FIELD_H), Hx, rtol=1e-12)
+        np.testing.assert_allclose(sol.get(B.FIELD_D), dx, rtol=1e-9, atol=1e-15)
+    sol.close()
+

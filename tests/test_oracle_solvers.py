@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import fg_oracle as O
+from tests.helpers import homogeneous_stretch_damage
 
 RNG = np.random.default_rng(7)
 H = (1e-7, 1e-7, 1e-7)
@@ -239,6 +240,32 @@ def test_chem_mass_balance_with_source():
 # ---------------------------------------------------------------- coupled step (Alg. 4)
 
 @pytest.mark.slow
+def test_homogeneous_bar_under_stretch_damages_in_closed_form():
+    """A homogeneous Neo-Hookean medium (no swelling, no influx) under a macroscopic
+    stretch F-bar = diag(l, 1, 1), loaded in two steps of Alg. 4.  The mechanics stays
+    uniform, F = F-bar, and each step's body (mechanics, history, phase field) runs once:
+    the Cauchy stress is diagonal with sigma_xx = (G (l^2 - 1) + lam ln l)/l and
+    sigma_yy = sigma_zz = lam ln l / l, so D_f = sum (<sigma_i>/sigma_max)^2 - 1,
+    H = g_c/(2 l_c) D_f (Eq. SigDrivingForce) and, with uniform H, Eq. PFFA gives
+    d = 2H/(g_c/l_c + 2H).  The first stretch stays below the threshold (d = 0)."""
+    shape = (2, 4, 4)
+    E, nu, smax, gc, lc = 10e9, 0.3, 50e6, 1.0, 2e-7
+    prm = O.make_params([O.Phase(E=E, nu=nu, Omega=0.0, c0=0.01, sigma_max=smax)],
+                        np.zeros(shape, dtype=int), H, gc=gc, lc=lc)
+    st = O.CoupledState(prm, np.full(shape, 0.2), np.zeros(shape))
+    for l, damaged in ((1.002, False), (1.012, True)):
+        Fbar = np.diag([l, 1.0, 1.0])
+        stats = st.step(1.0, Fbar)
+        Hx, dx = homogeneous_stretch_damage(E, nu, smax, gc, lc, l)
+        assert (Hx > 0.0) == damaged
+        assert stats["stag"] == 1
+        np.testing.assert_allclose(st.F, np.broadcast_to(Fbar.reshape(3, 3, 1, 1, 1),
+                                                         (3, 3) + shape), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(st.H, Hx, rtol=1e-12)
+        np.testing.assert_allclose(st.d, dx, rtol=1e-9, atol=1e-15)
+        np.testing.assert_array_equal(st.c, 0.2)
+
+
 def test_coupled_steps_invariants():
     shape = (1, 16, 16)
     y, x = np.meshgrid(np.arange(16) - 7.5, np.arange(16) - 7.5, indexing="ij")
