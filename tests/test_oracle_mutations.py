@@ -117,3 +117,26 @@ def test_strength_ignored_in_driving_force_is_caught(monkeypatch):
     monkeypatch.setattr(O, "driving_force", bad)
     with pytest.raises(AssertionError):
         TC.test_per_voxel_strength_driving_force()
+
+
+def test_history_not_updated_is_caught(monkeypatch):
+    from tests import test_oracle_solvers as TSO
+
+    def bad(H_t, F, c, prm):  # the step keeps the last converged history
+        return H_t.copy()
+    monkeypatch.setattr(O, "history_update", bad)
+    with pytest.raises(AssertionError):
+        TSO.test_homogeneous_bar_under_stretch_damages_in_closed_form()
+
+
+def test_staggered_body_skipped_at_equilibrium_is_caught(monkeypatch):
+    from tests import test_oracle_solvers as TSO
+    good = O.pff_solve
+    calls = {"n": 0}
+
+    def bad(H, d0, prm, tol, maxit, stats=None):  # phase field never solved after the first
+        calls["n"] += 1
+        return d0.copy() if calls["n"] > 1 else good(H, d0, prm, tol, maxit, stats)
+    monkeypatch.setattr(O, "pff_solve", bad)
+    with pytest.raises(AssertionError):
+        TSO.test_homogeneous_bar_under_stretch_damages_in_closed_form()
