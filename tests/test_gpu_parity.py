@@ -454,3 +454,25 @@ def test_homogeneous_bar_damages_in_closed_form(lib, shape, prec):
         np.testing.assert_allclose(sol.get(B.FIELD_D), dx, rtol=1e-9, atol=1e-15)
     sol.close()
 
+def test_mixed_precision_damage_and_crack_energy(lib):
+    """The mixed FP32/FP64 form against the FP64 oracle through three damaging steps of
+    the disc with a Gumbel-distributed strength (damage from the first step, d up to 0.93):
+    max relative error in F and c <= 1e-7, max |delta d| <= 1e-6 and the fracture energy
+    Gamma_E (Eq. crack) of the final d within 1e-6 relative."""
+    from tests.test_oracle_adjoint import _strength_disc
+    shape, logs, ls, src, prm, phases, pid = _strength_disc()
+    ref = O.CoupledState(prm, np.full(shape, 0.01), src, O.Tolerances(max_stag=400))
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], log_smax=ls, lib=lib,
+                   precision=B.FG_MIXED, gc=1.0, lc=2e-7, max_stag=400)
+    for _ in range(3):
+        ref.step(1.0, np.eye(3))
+        sol.step(1.0)
+    d = sol.get(B.FIELD_D)
+    assert ref.d.max() > 0.5
+    assert rel_err(sol.get(B.FIELD_F), ref.F) <= 1e-7
+    assert rel_err(sol.get(B.FIELD_C), ref.c) <= 1e-7
+    assert np.abs(d - ref.d).max() <= 1e-6
+    g_ref = O.crack_energy(ref.d, prm)
+    assert abs(O.crack_energy(d, prm) - g_ref) <= 1e-6 * g_ref
+    sol.close()
