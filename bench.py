@@ -455,7 +455,10 @@ def main():
     }
     line.update(out)
     if not a.no_cpu_baseline:
-        prof_counts = {k: stats[-1][k] for k in DEFAULT_STEP_PROFILE}
+        # the oracle is an FP64 method: its step takes the FP64 form's operator counts (of
+        # this run when it timed an FP64 step, else those recorded at 256^3)
+        counts = out.get("fp64_step_stats") or DEFAULT_STEP_PROFILE
+        prof_counts = {k: counts[k] for k in DEFAULT_STEP_PROFILE}
         secs, desc = oracle_step_seconds(w, a.cpu_seconds, prof_counts)
         line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": _cores(),
                                 "kind": "oracle", "sample": desc}
