@@ -23,6 +23,9 @@
  *     calls return after that work has completed unless stated otherwise.
  *   - Functions return FG_OK (0) or a negative FG_ERR_* code, and never throw;
  *     fg_last_error() gives the calling thread's last message.
+ *   - With the environment variable FG_VERBOSE set, the mechanical Newton solver
+ *     prints one line per iteration (residual, CG iterations, damping, shifts) to
+ *     stderr; nothing else reads the environment.
  */
 #ifndef FG_H
 #define FG_H
