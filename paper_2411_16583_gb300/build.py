@@ -98,7 +98,7 @@ def build_gpu(jobs=None, verbose=False):
     with ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(obj, _sources()))
     cudart = os.path.join(_cuda_home(nvcc), "lib64")
-    _run([nvcc, "-shared", "-o", out] + objs + ARCH + ["-L", cudart, "-lcudart"])
+    _run([nvcc, "-shared", "-o", out] + objs + ARCH + ["-L", cudart, "-lcudart", "-ldl"])
     with open(stamp_file, "w") as f:
         f.write(stamp)
     return out

@@ -17,6 +17,9 @@
 #include "fg_pointwise.cuh"
 #include "fg_adjoint.cuh"
 #include "../../include/fg.h"
+#ifndef FG_EMU
+#include <nvtx3/nvToolsExt.h>
+#endif
 
 namespace fg {
 
@@ -51,6 +54,20 @@ static bool verbose() {
   return v;
 }
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+// NVTX range over one solve phase (step, chemistry, mechanics, history, phase field,
+// adjoint), for profilers that filter or group launches by range; without a tool attached
+// the calls do nothing
+struct Range {
+#ifndef FG_EMU
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+#else
+  explicit Range(const char*) {}
+#endif
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 struct Fail {
   int code;
@@ -1097,6 +1114,7 @@ static int newton_solve(fg_ctx& c, Prec<X>& PX, double& sigma, fg_stats& s) {
 // with FP64 MINRES on the unshifted system, and the rest of this solve uses it.
 template <typename R>
 static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s, double err0 = -1.0) {
+  Range range("mech_newton");
   bool hi = !is_mixed(c);  // Krylov in FP64
   bool mr = false;         // MINRES
   auto resid = [&]() {
@@ -1196,6 +1214,7 @@ struct FScaleAux {
 
 // H = max(H_t, g_c/(2 l_c) D_f(F, c)); Hbar = mean H to the device scalar
 static void history(fg_ctx& c) {
+  Range range("history");
   VArgs v = vbase(c, c.V);
   v.in[0] = c.F;
   v.in[1] = c.c;
@@ -1236,6 +1255,7 @@ template <typename R>
 // Alg. 2 for d.  Returns whether d changed: with H = 0 the solution is d = 0 (the
 // right-hand side 2H vanishes), which leaves an already zero d as it is.
 static bool pff_solve(fg_ctx& c, Prec<R>& P, fg_stats& s) {
+  Range range("pff_solve");
   const double hh = reduce_sum(c, c.Heff, c.V, true);
   if (hh == 0.0) {
     if (reduce_sum(c, c.d, c.V, true) == 0.0) return false;
@@ -1336,6 +1356,7 @@ static void chem_prep(fg_ctx& c, Prec<R>& P, double dt, const double* F) {
 
 template <typename R>
 static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
+  Range range("chem_solve");
   chem_cond<R>(c, P, c.F, c.ct, c.dt);
   if (is_mixed(c)) chem_cond<double>(c, c.pd, c.F, c.ct, c.dt);
   dcopy(c.c, c.ct, c.V * sizeof(double), c.st);
@@ -1380,6 +1401,7 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
 
 template <typename R>
 static void step_impl(fg_ctx& c, Prec<R>& P, double dt, const double* Fbar, fg_stats& s) {
+  Range range("fg_step");
   const long long V = c.V;
   // t-state
   dcopy(c.Ft, c.F, 9 * V * sizeof(double), c.st);
@@ -1851,6 +1873,7 @@ static double crack_loss(fg_ctx& c, AdjWork& W, double* S) {
 template <typename R>
 static double adjoint_impl(fg_ctx& c, Prec<R>& P, int loss, const double* sc, const double* sF,
                            const double* sd, double* gE, double* gG, double* gD, fg_adjoint_stats* as) {
+  Range range("fg_adjoint");
   Tape& T = *c.tape;
   const long long V = c.V;
   const int nsteps = (int)T.dts.size();
