@@ -19,6 +19,9 @@
 #include "../../include/fg.h"
 #ifndef FG_EMU
 #include <nvtx3/nvToolsExt.h>
+#else
+#include <sys/mman.h>
+#include <unistd.h>
 #endif
 
 namespace fg {
@@ -81,18 +84,62 @@ static void fail(int code, const std::string& msg) {
 // ------------------------------------------------------------------ device memory
 
 #ifdef FG_EMU
+// Emulated device memory is guarded: every buffer lies between two inaccessible pages and
+// ends at the upper one (its start rounded down to 16 bytes), so a kernel that indexes
+// past the end of a buffer, or far before its start, faults in the host tests instead of
+// touching a neighbouring buffer.  FG_EMU_GUARD=start puts the start on the lower guard
+// page instead, which catches any index below zero.
+struct GuardedBlock {
+  char* base;
+  size_t len;
+};
+static std::mutex& guard_mutex() {
+  static std::mutex m;
+  return m;
+}
+static std::map<void*, GuardedBlock>& guard_blocks() {
+  static std::map<void*, GuardedBlock> m;
+  return m;
+}
 static void* dalloc(size_t n) {
-  void* p = calloc(n ? n : 1, 1);
-  if (!p) fail(FG_ERR_OOM, "host allocation failed");
+  static const bool at_start = [] {
+    const char* e = getenv("FG_EMU_GUARD");
+    return e && strcmp(e, "start") == 0;
+  }();
+  const size_t pg = (size_t)sysconf(_SC_PAGESIZE);
+  const size_t m = n ? n : 1;
+  const size_t body = (m + pg - 1) / pg * pg;
+  const size_t len = body + 2 * pg;
+  void* b = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (b == MAP_FAILED) fail(FG_ERR_OOM, "host allocation failed");
+  char* base = (char*)b;
+  if (mprotect(base, pg, PROT_NONE) != 0 || mprotect(base + pg + body, pg, PROT_NONE) != 0) {
+    munmap(b, len);
+    fail(FG_ERR_OOM, "guard page setup failed");
+  }
+  char* p = at_start ? base + pg : base + pg + ((body - m) & ~(size_t)15);
+  std::lock_guard<std::mutex> lk(guard_mutex());
+  guard_blocks()[p] = GuardedBlock{base, len};
   return p;
 }
-static void dfree(void* p) { free(p); }
+static void dfree(void* p) {
+  if (!p) return;
+  GuardedBlock g{nullptr, 0};
+  {
+    std::lock_guard<std::mutex> lk(guard_mutex());
+    auto it = guard_blocks().find(p);
+    if (it == guard_blocks().end()) return;
+    g = it->second;
+    guard_blocks().erase(it);
+  }
+  munmap(g.base, g.len);
+}
 static void dcopy(void* d, const void* s, size_t n, cudaStream_t) { memcpy(d, s, n); }
 static void dzero(void* d, size_t n, cudaStream_t) { memset(d, 0, n); }
 static void dsync(cudaStream_t) {}
 static void ccheck(const char*) {}
 static void* hpinned(size_t n) { return dalloc(n); }
-static void hfree(void* p) { free(p); }
+static void hfree(void* p) { dfree(p); }
 #else
 static void ccheck(const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -2815,5 +2862,18 @@ int fg_time_apply(fg_ctx* c, int op, int prec, int n, double* ms) {
 #endif
   FG_API_END
 }
+
+#ifdef FG_EMU
+// Test hook of the host emulation only (not part of the C ABI): writes one byte at
+// `offset` from the start of a fresh guarded 64-byte buffer and frees it.  An offset
+// outside [0, 64) must fault (past the end by default; below zero under
+// FG_EMU_GUARD=start), which the tests observe in a child process.
+int fg_emu_guard_probe(long long offset) {
+  volatile char* p = (volatile char*)fg::dalloc(64);
+  p[offset] = 1;
+  fg::dfree((void*)p);
+  return 0;
+}
+#endif
 
 }  // extern "C"

@@ -140,3 +140,39 @@ def test_save_load_restarts_bit_identically(emu, tmp_path):
         c.load(str(tmp_path / "missing.fg"))
     for s_ in (a, b, c):
         s_.close()
+
+
+@pytest.mark.parametrize("mode,offset,faults", [
+    ("end", 0, False), ("end", 63, False), ("end", 64, True),
+    ("start", 0, False), ("start", 63, False), ("start", -1, True)])
+def test_emulated_memory_guards_fault_out_of_bounds(mode, offset, faults):
+    """The host emulation places every emulated device buffer against an inaccessible page,
+    so the emulated kernels of the other tests run bounds-checked: a write one byte past
+    the end (or, with FG_EMU_GUARD=start, one byte before the start) of a buffer faults.
+    Checked in a child process on the CPU."""
+    import signal
+    import subprocess
+    import sys
+    path = build.build_emu()
+    code = ("import ctypes, sys; lib = ctypes.CDLL(sys.argv[1]); "
+            "lib.fg_emu_guard_probe.argtypes = [ctypes.c_longlong]; "
+            "sys.exit(lib.fg_emu_guard_probe(int(sys.argv[2])))")
+    env = dict(os.environ, FG_EMU_GUARD=mode)
+    r = subprocess.run([sys.executable, "-c", code, path, str(offset)], env=env,
+                       capture_output=True, timeout=120)
+    assert r.returncode == (-signal.SIGSEGV if faults else 0), r.stderr.decode()[-500:]
+
+
+def test_emulated_kernels_in_bounds_below_start():
+    """The emulated operators, coupled steps, batch and mechanical adjoint rerun with every
+    buffer starting on its guard page (FG_EMU_GUARD=start): no kernel indexes below zero.
+    (The default placement, guard after the end, covers the whole emulated suite.)"""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FG_EMU_GUARD="start")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_emu_kernels.py", "-q",
+                        "-p", "no:cacheprovider", "-k",
+                        "operators or coupled_step_matches or batch or homogeneous or mech_adjoint"],
+                       cwd=root, env=env, capture_output=True, timeout=900)
+    assert r.returncode == 0, r.stdout.decode()[-2000:]
