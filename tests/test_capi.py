@@ -176,3 +176,22 @@ def test_emulated_kernels_in_bounds_below_start():
                         "operators or coupled_step_matches or batch or homogeneous or mech_adjoint"],
                        cwd=root, env=env, capture_output=True, timeout=900)
     assert r.returncode == 0, r.stdout.decode()[-2000:]
+
+
+@pytest.mark.parametrize("prec", [B.FG_FP64, B.FG_MIXED])
+def test_inverting_load_reports_domain_and_keeps_state(emu, prec):
+    """A macroscopic load with det F-bar < 0 puts every voxel outside the domain of the
+    law: the step returns FG_ERR_DOMAIN, the stored state (F, c, d, H) is exactly the one
+    before the step, and the next valid step runs."""
+    w = S.disc2d()
+    sol = B.from_workload(w, lib=emu, precision=prec)
+    sol.step(w.dt)
+    fields = (B.FIELD_F, B.FIELD_C, B.FIELD_D, B.FIELD_H)
+    before = [sol.get(f).copy() for f in fields]
+    with pytest.raises(B.FgError) as e:
+        sol.step(w.dt, np.diag([-1.0, 1.0, 1.0]))
+    assert e.value.code == -5
+    for f, b in zip(fields, before):
+        np.testing.assert_array_equal(sol.get(f), b)
+    assert sol.step(w.dt)["status"] == 0
+    sol.close()
