@@ -189,6 +189,60 @@ def crack_energy_seed(d, prm):
     return float(np.sum(dens)), seed, dens
 
 
+def displacement_multiplier(prm):
+    """m_j(k) = -i exp(-i sum_m q_m/2) n_j / |n|^2, and 0 where |n| = 0: the least-squares
+    inverse of the rotated-scheme gradient of a field at the voxel corners, whose DFT
+    symbol is i n_j exp(i sum_m q_m/2) (Sec. 3.2, rotated scheme; n of
+    fg_oracle.rotated_frequencies).  Shape (3, nz, ny, nx//2+1)."""
+    shape = prm.shape
+    n = O.rotated_frequencies(shape, prm.h)
+    (_, _, sz, cz), (_, _, sy, cy), (_, _, sx, cx) = O._axes(shape)
+    if shape[0] == 1:  # plane strain: q_z = 0
+        sz, cz = np.zeros_like(sz), np.ones_like(cz)
+    e = ((cx - 1j * sx)[None, None, :] * (cy - 1j * sy)[None, :, None]
+         * (cz - 1j * sz)[:, None, None])
+    nn = np.sum(n * n, axis=0)
+    inv = np.divide(1.0, nn, out=np.zeros_like(nn), where=nn > 0.0)
+    return -1j * e[None] * n * inv[None]
+
+
+def corner_nodes(prm):
+    """Positions x_j = i_j h_j of the voxel corners (3, nz, ny, nx); corner i is the lower
+    corner of voxel i."""
+    nz, ny, nx = prm.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.stack([x * prm.h[0], y * prm.h[1], z * prm.h[2]]).astype(float)
+
+
+def corner_displacement(F, Fbar, prm):
+    """Displacement at the voxel corners, u = (Fbar - I) x + u~, from the split F =
+    Fbar + grad u~ (Eq. Fsplit): u~ periodic with zero mean, and its rotated-scheme
+    gradient equal to F - mean(F) in least squares (exactly, for a compatible F, up to the
+    scheme's null modes)."""
+    m = displacement_multiplier(prm)
+    Uh = np.einsum("j...,ij...->i...", m, O.rfft3(F))
+    u = O.irfft3(Uh, prm.shape)
+    A = np.asarray(Fbar, dtype=float).reshape(3, 3) - np.eye(3)
+    return u + np.einsum("ij,j...->i...", A, corner_nodes(prm))
+
+
+def corner_displacement_adjoint(r, prm):
+    """Transpose of F -> u~ of corner_displacement: sum_i <u~_i, r_i> = sum_ij <F_ij, g_ij>
+    for g = irfft3(conj(m_j) rfft3(r_i)) (unnormalised forward DFT, 1/V inverse)."""
+    m = displacement_multiplier(prm)
+    G = np.conj(m)[None] * O.rfft3(r)[:, None]
+    return O.irfft3(G, prm.shape)
+
+
+def displacement_mismatch(F, Fbar, u_obs, w, prm):
+    """L = 1/2 sum_corners w |u - u_obs|^2 h^3 with u = corner_displacement(F, Fbar) and
+    its seed dL/dF (3, 3, ...).  Returns (L, seed_F)."""
+    h3 = prm.h[0] * prm.h[1] * prm.h[2]
+    diff = corner_displacement(F, Fbar, prm) - u_obs
+    r = w[None] * diff * h3
+    return 0.5 * float(np.sum(w[None] * diff * diff)) * h3, corner_displacement_adjoint(r, prm)
+
+
 def step_adjoint(prm, s_in, s_out, dt, seeds, tol, stats=None):
     """Reverse of one converged step.  seeds = dict(c, F, d, H) of dL/d(outputs); returns
     (dict(c, F, d, H) of dL/d(inputs), dict(E, gc, D) of dL/dlog-parameters)."""

@@ -272,3 +272,74 @@ def test_crack_energy_gradient_matches_central_differences():
             lm[idx][v] -= h
             fd = (loss(lp) - loss(lm)) / (2 * h)
             assert abs(g[name][v] - fd) <= 2e-5 * abs(g[name]).max(), (name, v, g[name][v], fd)
+
+
+# ------------------------------------------------- displacement-mismatch loss (Eq. Fsplit)
+
+def _grid_params(shape, h=(0.7e-7, 1.3e-7, 0.9e-7)):
+    return O.make_params([O.Phase()], np.zeros(shape, dtype=int), h, gc=1.0, lc=2e-7)
+
+
+@pytest.mark.parametrize("shape", [(5, 7, 9), (1, 7, 9), (3, 5, 5)])
+def test_corner_displacement_inverts_the_corner_stencil(shape):
+    """On odd grids the rotated scheme has no null mode besides k = 0, so a periodic
+    corner field u of zero mean, turned into F = Fbar + grad u by the real-space 2x2x2
+    stencil, is recovered exactly, together with the affine part (Fbar - I) x."""
+    from tests.test_oracle_spectral import corner_gradient
+    prm = _grid_params(shape)
+    rng = np.random.default_rng(31)
+    u = rng.standard_normal((3,) + shape) * 1e-9
+    if shape[0] == 1:
+        u[2] = 0.0  # plane strain: no out-of-plane displacement
+    u -= u.mean(axis=(1, 2, 3), keepdims=True)
+    Fbar = np.eye(3) + 0.01 * rng.standard_normal((3, 3))
+    if shape[0] == 1:
+        Fbar[2, :2] = Fbar[:2, 2] = 0.0
+    F = Fbar.reshape(3, 3, 1, 1, 1) + corner_gradient(u, prm.h)
+    got = A.corner_displacement(F, Fbar, prm)
+    ref = u + np.einsum("ij,j...->i...", Fbar - np.eye(3), A.corner_nodes(prm))
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_corner_displacement_on_even_grids_reproduces_compatible_fields():
+    """With Nyquist planes the scheme has null modes, which carry no strain: the
+    reconstructed u~ then differs from u by them, but its stencil gradient is F - Fbar."""
+    from tests.test_oracle_spectral import corner_gradient
+    shape = (4, 6, 8)
+    prm = _grid_params(shape)
+    u = np.random.default_rng(32).standard_normal((3,) + shape) * 1e-9
+    F = np.eye(3).reshape(3, 3, 1, 1, 1) + corner_gradient(u, prm.h)
+    got = A.corner_displacement(F, np.eye(3), prm)
+    np.testing.assert_allclose(corner_gradient(got, prm.h), F - np.eye(3).reshape(3, 3, 1, 1, 1),
+                               rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(4, 6, 8), (1, 8, 6), (5, 7, 9)])
+def test_corner_displacement_transpose(shape):
+    """<u~(F), r> = <F, D^T r> for random F and r (dot-product test of the adjoint map)."""
+    prm = _grid_params(shape)
+    rng = np.random.default_rng(33)
+    F = rng.standard_normal((3, 3) + shape)
+    r = rng.standard_normal((3,) + shape)
+    lhs = np.sum(A.corner_displacement(F, np.eye(3), prm) * r)
+    rhs = np.sum(F * A.corner_displacement_adjoint(r, prm))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.sqrt(np.sum(r * r) * np.sum(F * F)))
+
+
+def test_displacement_mismatch_seed_is_its_derivative():
+    """dL/dF of L = 1/2 sum w |u - u_obs|^2 h^3 against central differences along a
+    random direction (L is quadratic in F, so the difference is exact up to rounding)."""
+    shape = (3, 4, 6)
+    prm = _grid_params(shape)
+    rng = np.random.default_rng(34)
+    F = np.eye(3).reshape(3, 3, 1, 1, 1) + 0.01 * rng.standard_normal((3, 3) + shape)
+    Fbar = np.diag([1.01, 1.0, 0.995])
+    u_obs = 1e-9 * rng.standard_normal((3,) + shape)
+    w = rng.uniform(0.0, 1.0, shape)
+    L, g = A.displacement_mismatch(F, Fbar, u_obs, w, prm)
+    dF = rng.standard_normal(F.shape)
+    h = 1e-4
+    fd = (A.displacement_mismatch(F + h * dF, Fbar, u_obs, w, prm)[0]
+          - A.displacement_mismatch(F - h * dF, Fbar, u_obs, w, prm)[0]) / (2 * h)
+    assert L > 0.0
+    np.testing.assert_allclose(np.sum(g * dF), fd, rtol=1e-8)

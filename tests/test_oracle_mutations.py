@@ -140,3 +140,17 @@ def test_staggered_body_skipped_at_equilibrium_is_caught(monkeypatch):
     monkeypatch.setattr(O, "pff_solve", bad)
     with pytest.raises(AssertionError):
         TSO.test_homogeneous_bar_under_stretch_damages_in_closed_form()
+
+
+def test_displacement_without_corner_phase_is_caught(monkeypatch):
+    from oracle import fg_oracle_adjoint as A
+    from tests import test_oracle_adjoint as TA
+
+    def bad(prm):  # drops exp(-i sum q/2): u placed at the voxel centres, not the corners
+        n = O.rotated_frequencies(prm.shape, prm.h)
+        nn = np.sum(n * n, axis=0)
+        inv = np.divide(1.0, nn, out=np.zeros_like(nn), where=nn > 0.0)
+        return -1j * n * inv[None]
+    monkeypatch.setattr(A, "displacement_multiplier", bad)
+    with pytest.raises(AssertionError):
+        TA.test_corner_displacement_inverts_the_corner_stencil((5, 7, 9))
