@@ -319,6 +319,26 @@ int fg_adjoint(fg_ctx* ctx, int loss, const double* seed_c, const double* seed_F
                double* grad_logD, fg_adjoint_stats* st);
 
 /*
+ * Displacement at the voxel corners, for losses on displacements (e.g. a mismatch with
+ * measured displacements) in the adjoint.  From the split F = Fbar + grad u~ of Eq. Fsplit:
+ *   u = (Fbar - I) x + u~,  x_j = i_j h_j the position of corner i (the lower corner of
+ *   voxel i), u~ periodic with zero mean and its rotated-scheme gradient (Sec. 3.2) equal
+ *   to F - mean(F) in least squares: exactly, for a compatible F, up to the scheme's null
+ *   modes (several axes at their Nyquist frequency), which carry no strain.
+ *   F[9 V], Fbar[9]  deformation gradient (component (i, j) at (3 i + j) V) and its mean,
+ *                    row-major; both NULL: the context's current state
+ *   u[3 V]           output, component i at i V
+ * fg_displacement_adjoint applies the transpose of F -> u~: g[9 V] = (du~/dF)^T r for
+ * r[3 V].  With r = dL/du of a loss L on the displacement, g is dL/dF at fixed Fbar, the
+ * seed_F of fg_adjoint with FG_LOSS_SEEDS.
+ * Pointers may be host or device memory (on_device is informational); the work runs in
+ * FP64 in either precision mode.  Errors: FG_ERR_INVALID (null argument, or only one of F
+ * and Fbar given), FG_ERR_OOM, FG_ERR_CUDA.
+ */
+int fg_displacement(fg_ctx* ctx, const double* F, const double* Fbar, double* u, int on_device);
+int fg_displacement_adjoint(fg_ctx* ctx, const double* r, double* g, int on_device);
+
+/*
  * Restart files: fg_save writes the evolving state of the context (c, F, d, H, the
  * t-state of the last step, Fbar, the previous Fbar and the last dt) to a binary file;
  * fg_load reads one into a context set up with the same grid, law and materials (the

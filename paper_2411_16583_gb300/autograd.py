@@ -2,6 +2,9 @@
 
 MechEquilibrium: F(log E) of the mechanical equilibrium (Alg. 1) at fixed (c, d);
   backward solves G K G lambda = G dL/dF (fg_adjoint_mech), dL/dlogE = -lambda : P.
+Displacement: the displacement at the voxel corners as a function of F (Eq. Fsplit;
+  fg_displacement), backward by the transpose (fg_displacement_adjoint); with
+  CoupledSteps it gives the gradient of a displacement-mismatch loss.
 CoupledSteps: the final state (c, F, d) after n staggered steps (Alg. 4) as a function of
   the per-voxel log E, log g_c, log D (a per-voxel strength of the workload is a fixed
   input); backward runs the recorded steps in reverse
@@ -74,3 +77,33 @@ class CoupledSteps(torch.autograd.Function):
 
 def coupled_steps(logE, loggc, logD, spec):
     return CoupledSteps.apply(logE, loggc, logD, spec)
+
+
+class Displacement(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, F, Fbar, sol):
+        """F (3, 3, nz, ny, nx) -> u (3, nz, ny, nx) at the voxel corners, u = (Fbar - I) x
+        + u~ with grad u~ = F - Fbar; Fbar (3, 3) is a fixed input.  sol is any
+        ``binding.Solver`` on the same grid (only its transforms are used)."""
+        u = sol.displacement(F.detach().double().cpu().numpy(), np.asarray(Fbar, dtype=float))
+        ctx.sol = sol
+        return torch.from_numpy(u).to(F.device)
+
+    @staticmethod
+    def backward(ctx, gu):
+        g = ctx.sol.displacement_adjoint(gu.detach().double().contiguous().cpu().numpy())
+        return torch.from_numpy(g).to(gu.device), None, None
+
+
+def displacement(F, Fbar, sol):
+    return Displacement.apply(F, Fbar, sol)
+
+
+def displacement_mismatch(F, Fbar, u_obs, w, sol):
+    """L = 1/2 sum over the corners of w |u - u_obs|^2 h^3, u = displacement(F, Fbar, sol);
+    u_obs (3, nz, ny, nx) and w (nz, ny, nx) are tensors."""
+    u = displacement(F, Fbar, sol)
+    h3 = sol.h[0] * sol.h[1] * sol.h[2]
+    diff = u - u_obs
+    return 0.5 * h3 * (w * diff * diff).sum()
+

@@ -80,7 +80,8 @@ EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_re
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
            "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
            "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load", "fg_set_stress_control",
-           "fg_kernel_launches", "fg_destroy", "fg_last_error"]
+           "fg_displacement", "fg_displacement_adjoint", "fg_kernel_launches", "fg_destroy",
+           "fg_last_error"]
 
 _libs = {}
 
@@ -114,6 +115,8 @@ def load_library(path=LIB_PATH):
     lib.fg_solve_mech.argtypes = [C.c_void_p, dp, C.POINTER(Stats)]
     lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.fg_tape_begin.argtypes = [C.c_void_p, C.c_int]
+    lib.fg_displacement.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    lib.fg_displacement_adjoint.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     lib.fg_save.argtypes = [C.c_void_p, C.c_char_p]
     lib.fg_set_stress_control.argtypes = [C.c_void_p, C.c_int, dp]
     lib.fg_load.argtypes = [C.c_void_p, C.c_char_p]
@@ -163,6 +166,7 @@ class Solver:
         self.lib = lib or load_library()
         nz, ny, nx = shape
         self.shape = tuple(shape)
+        self.h = tuple(float(x) for x in h)
         self.V = nx * ny * nz
         g = Grid(nx, ny, nz, *[float(x) for x in h])
         ph = (Phase * len(phases))()
@@ -288,6 +292,26 @@ class Solver:
                                         C.byref(val), _ptr(g["E"]), _ptr(g["gc"]), _ptr(g["D"]),
                                         C.byref(st)))
         return val.value, g, st.as_dict()
+
+    def displacement(self, F=None, Fbar=None):
+        """Displacement (3, nz, ny, nx) at the voxel corners of F and Fbar (both None: the
+        current state): (Fbar - I) x + u~ with grad u~ = F - Fbar (fg_displacement)."""
+        if (F is None) != (Fbar is None):
+            raise ValueError("F and Fbar are given together")
+        u = np.empty((3,) + self.shape)
+        Fa = None if F is None else _f64(F).ravel()
+        Fb = None if Fbar is None else _f64(Fbar).ravel()
+        self._check(self.lib.fg_displacement(self.ctx, None if Fa is None else _ptr(Fa),
+                                             None if Fb is None else _ptr(Fb), _ptr(u), 0))
+        return u
+
+    def displacement_adjoint(self, r):
+        """(du~/dF)^T r for r (3, nz, ny, nx): a (3, 3, nz, ny, nx) field
+        (fg_displacement_adjoint)."""
+        ra = _f64(r).ravel()
+        g = np.empty((3, 3) + self.shape)
+        self._check(self.lib.fg_displacement_adjoint(self.ctx, _ptr(ra), _ptr(g), 0))
+        return g
 
     def autotune(self):
         ms = C.c_double()

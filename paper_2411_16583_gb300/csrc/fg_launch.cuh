@@ -91,6 +91,8 @@ struct SizeOps {
       xi_chemrhs, xi_cgupdate, xi_cgupdate_pc;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
+  // FP64 only (null in the FP32 table): displacement at the corners and its transpose
+  PassFn<R> xi_store9, z_disp, z_dispT;
 };
 
 template <class K, typename R>
@@ -137,6 +139,7 @@ SizeOps<R> make_size_ops() {
     s.xi_chemflux = run_x<XInv<R, N, EChemFlux<R>>, R>;
     s.xi_chemop = run_x<XInv<R, N, EChemOp<R>>, R>;
     s.xi_chemrhs = run_x<XInv<R, N, EChemRhs<R>>, R>;
+    if constexpr (std::is_same<R, double>::value) s.xi_store9 = run_x<XInv<R, N, EStore<R, 9>>, R>;
   }
   if constexpr (Square<N>::OK) {  // register-direct two-stage passes
     s.yf = run_y<YPassD<R, N, false>, R>;
@@ -146,6 +149,10 @@ SizeOps<R> make_size_ops() {
     s.z_prec = run_z<ZPassD<R, N, ZPrecond<R>>, R>;
     s.z_grad = run_z<ZPassD<R, N, ZGrad<R>>, R>;
     s.z_div = run_z<ZPassD<R, N, ZDiv<R>>, R>;
+    if constexpr (std::is_same<R, double>::value) {
+      s.z_disp = run_z<ZPassD<R, N, ZDisp<R>>, R>;
+      s.z_dispT = run_z<ZPassD<R, N, ZDispT<R>>, R>;
+    }
   } else {
     s.yf = run_y<YPass<R, N, false>, R>;
     s.yi = run_y<YPass<R, N, true>, R>;
@@ -154,6 +161,10 @@ SizeOps<R> make_size_ops() {
     s.z_prec = run_z<ZPass<R, N, ZPrecond<R>>, R>;
     s.z_grad = run_z<ZPass<R, N, ZGrad<R>>, R>;
     s.z_div = run_z<ZPass<R, N, ZDiv<R>>, R>;
+    if constexpr (std::is_same<R, double>::value) {
+      s.z_disp = run_z<ZPass<R, N, ZDisp<R>>, R>;
+      s.z_dispT = run_z<ZPass<R, N, ZDispT<R>>, R>;
+    }
   }
   return s;
 }

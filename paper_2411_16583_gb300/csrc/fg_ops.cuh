@@ -87,6 +87,65 @@ struct ZDiv {
   }
 };
 
+// Displacement at the voxel corners from the split F = Fbar + grad u (Eq. Fsplit).  The
+// rotated-scheme gradient of a corner field has the symbol i n_j e^{i sum_m q_m/2}, so the
+// least-squares inverse multiplies F_ij^ by m_j = -i e^{-i sum q/2} n_j / |n|^2 (0 where
+// |n| = 0).  disp_symbol returns n and w = -i e^{-i sum q/2} coef[0] / |n|^2; the half
+// angle th_j = q_j/2 has cos th_j = rc_j and sin th_j = rs_j h_j / 2 = rs_j coef[1 + j].
+template <typename R>
+FG_DEV void disp_symbol(const PassArgs<R>& a, int kx, int ky, int kz, R* n, cplx<R>& w) {
+  using C = cplx<R>;
+  const R cx = a.rc[0][kx], cy = a.rc[1][ky], cz = a.rc[2][kz];
+  const R sx = a.rs[0][kx], sy = a.rs[1][ky], sz = a.rs[2][kz];
+  n[0] = sx * cy * cz;
+  n[1] = sy * cx * cz;
+  n[2] = sz * cx * cy;
+  const R nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  const R s = nn > (R)0 ? a.coef[0] / nn : (R)0;
+  const C e = cmul(cmul(cmk<C>(cx, -sx * a.coef[1]), cmk<C>(cy, -sy * a.coef[2])),
+                   cmk<C>(cz, -sz * a.coef[3]));
+  w = cmk<C>(e.y * s, -e.x * s);  // -i e s
+}
+
+// u_i^ = sum_j m_j F_ij^ / V: nine components in, three out.
+template <typename R>
+struct ZDisp {
+  using C = cplx<R>;
+  static constexpr int CIN = 9, COUT = 3;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
+    R n[3];
+    C w;
+    disp_symbol(a, kx, ky, kz, n, w);
+    C t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      t[i] = cmul(w, cadd(cadd(cscale(v[3 * i], n[0]), cscale(v[3 * i + 1], n[1])),
+                          cscale(v[3 * i + 2], n[2])));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = t[i];
+  }
+};
+
+// Transpose of ZDisp: G_ij^ = conj(m_j) r_i^ / V, three components in, nine out.
+template <typename R>
+struct ZDispT {
+  using C = cplx<R>;
+  static constexpr int CIN = 3, COUT = 9;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, C* v, R zs) {
+    R n[3];
+    C w;
+    disp_symbol(a, kx, ky, kz, n, w);
+    const C wc = cmk<C>(w.x, -w.y);
+    C r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r[i] = cmul(wc, v[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v[3 * i + j] = cscale(r[i], n[j]);
+  }
+};
+
 // ================================================================== X-fwd prologues
 
 template <typename R, int NC>

@@ -539,6 +539,18 @@ struct KShiftF : VecOp<double> {
   }
 };
 
+// u += B_0 i_x + B_1 i_y + B_2 i_z at the corner of every voxel i (x fastest), the affine
+// part (Fbar - I) x of one displacement component with B_j = (Fbar - I)_kj h_j.
+// s[0..2] = B, s[3] = nx, s[4] = ny; out0 = u (V)
+struct KAddAffine : VecOp<double> {
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const VArgs& a, long long i, Acc<AccReal>&, const Pre&) {
+    const long long nx = (long long)a.s[3], ny = (long long)a.s[4];
+    const long long t = i / nx, ix = i - t * nx, iz = t / ny, iy = t - iz * ny;
+    ((double*)a.out[0])[i] += a.s[0] * (double)ix + a.s[1] * (double)iy + a.s[2] * (double)iz;
+  }
+};
+
 // ---------------------------------------------------------------- Krylov vectors
 
 // CG start from x = 0: x = 0, r = b, p = b (in0 = b, out0 = x, out1 = r, out2 = p); sum b^2

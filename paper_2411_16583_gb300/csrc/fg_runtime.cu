@@ -1587,6 +1587,72 @@ static void divadj(fg_ctx& c, const double* f, double* out) {
   P.ox->xi_store1(a, c.st);
 }
 
+// Displacement at the voxel corners (Eq. Fsplit), FP64: u~ (3 V) of F (9 V) by the
+// least-squares inverse of the rotated gradient, and its transpose (9 V) of r (3 V).
+static void disp_coef(const fg_ctx& c, double* zc) {
+  zc[0] = 1.0 / (double)c.V;
+  for (int j = 0; j < 3; ++j) zc[1 + j] = 0.5 * c.h[j];
+}
+
+static void disp_fluct(fg_ctx& c, const double* F, double* u) {
+  Prec<double>& P = c.pd;
+  PassArgs<double> a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.rin = F;
+  a.cout = P.S1;
+  P.ox->xf_copy9(a, c.st);
+  double zc[4];
+  disp_coef(c, zc);
+  yzy(c, P, nullptr, 9, P.oz->z_disp, 3, zc, nullptr);
+  a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = u;
+  P.ox->xi_store3(a, c.st);
+}
+
+static void disp_fluct_adj(fg_ctx& c, const double* r, double* g) {
+  Prec<double>& P = c.pd;
+  PassArgs<double> a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.rin = r;
+  a.cout = P.S1;
+  P.ox->xf_copy3(a, c.st);
+  double zc[4];
+  disp_coef(c, zc);
+  yzy(c, P, nullptr, 3, P.oz->z_dispT, 9, zc, nullptr);
+  a = pbase(c, P, nullptr);
+  a.tw = P.twx;
+  a.cin = P.S1;
+  a.rout = g;
+  P.ox->xi_store9(a, c.st);
+}
+
+// adds (Fbar - I) x at the corners to u (3 V)
+static void disp_affine(fg_ctx& c, const double* Fbar, double* u) {
+  for (int i = 0; i < 3; ++i) {
+    VArgs v = vbase(c, c.V);
+    v.out[0] = u + (long long)i * c.V;
+    for (int j = 0; j < 3; ++j) v.s[j] = (Fbar[3 * i + j] - (i == j ? 1.0 : 0.0)) * c.h[j];
+    v.s[3] = (double)c.nx;
+    v.s[4] = (double)c.ny;
+    launch_vec<KAddAffine>(v, c.st);
+  }
+}
+
+// device buffers of one API call, freed on every exit path
+struct Scratch {
+  std::vector<void*> p;
+  double* get(long long n) {
+    p.push_back(nullptr);
+    p.back() = dalloc((size_t)n * sizeof(double));
+    return (double*)p.back();
+  }
+  ~Scratch() {
+    for (void* q : p) dfree(q);
+  }
+};
+
 static void axpy64(fg_ctx& c, double* out, const double* x, double s, const double* y, long long n) {
   VArgs v = vbase(c, n);  // out = x + s y
   v.in[0] = x;
@@ -2504,6 +2570,42 @@ int fg_get_field(fg_ctx* c, int field, void* dst, int on_device) {
   }
   (void)on_device;
   dcopy(dst, src, n * sizeof(double), c->st);
+  dsync(c->st);
+  FG_API_END
+}
+
+int fg_displacement(fg_ctx* c, const double* F, const double* Fbar, double* u, int on_device) {
+  FG_API_BEGIN
+  if (!c || !u || (F == nullptr) != (Fbar == nullptr))
+    fail(FG_ERR_INVALID, "fg_displacement: null argument (F and Fbar are given together)");
+  (void)on_device;  // host and device pointers are both copied through device scratch
+  const long long V = c->V;
+  Scratch s;
+  const double* Fd = c->F;
+  if (F) {
+    double* t = s.get(9 * V);
+    dcopy(t, F, 9 * V * sizeof(double), c->st);
+    Fd = t;
+  }
+  double* ud = s.get(3 * V);
+  disp_fluct(*c, Fd, ud);
+  disp_affine(*c, Fbar ? Fbar : c->Fbar, ud);
+  dcopy(u, ud, 3 * V * sizeof(double), c->st);
+  dsync(c->st);
+  FG_API_END
+}
+
+int fg_displacement_adjoint(fg_ctx* c, const double* r, double* g, int on_device) {
+  FG_API_BEGIN
+  if (!c || !r || !g) fail(FG_ERR_INVALID, "fg_displacement_adjoint: null argument");
+  (void)on_device;
+  const long long V = c->V;
+  Scratch s;
+  double* rd = s.get(3 * V);
+  double* gd = s.get(9 * V);
+  dcopy(rd, r, 3 * V * sizeof(double), c->st);
+  disp_fluct_adj(*c, rd, gd);
+  dcopy(g, gd, 9 * V * sizeof(double), c->st);
   dsync(c->st);
   FG_API_END
 }

@@ -442,3 +442,64 @@ def test_emulated_mixed_precision_damage_and_crack_energy(emu):
     g_ref = O.crack_energy(ref.d, prm)
     assert abs(O.crack_energy(d, prm) - g_ref) <= 1e-6 * g_ref
     sol.close()
+
+
+@pytest.mark.parametrize("shape", [(8, 12, 16), (1, 12, 16), (12, 8, 8), (1, 1, 16)])
+def test_emulated_displacement_matches_oracle(emu, shape):
+    """Displacement at the voxel corners from F and Fbar (Eq. Fsplit) and its transpose,
+    against the oracle, on 3-D, plane and single-line grids; also the context's own state."""
+    from oracle import fg_oracle_adjoint as A
+    rng = np.random.default_rng(5)
+    ph = S.default_phases()
+    pid = S.random_phase_map(shape, 1)
+    h = (1.0e-7, 1.1e-7, 0.9e-7)
+    sol = B.Solver(shape, h, ph, pid, np.zeros(shape), lib=emu)
+    prm = oracle_params(ph, pid, h)
+    F = np.eye(3).reshape(3, 3, 1, 1, 1) + 0.02 * rng.standard_normal((3, 3) + shape)
+    Fbar = np.eye(3) + 0.01 * rng.standard_normal((3, 3))
+    assert rel_err(sol.displacement(F, Fbar), A.corner_displacement(F, Fbar, prm)) < 1e-13
+    r = rng.standard_normal((3,) + shape)
+    assert rel_err(sol.displacement_adjoint(r), A.corner_displacement_adjoint(r, prm)) < 1e-13
+    np.testing.assert_array_equal(sol.displacement(), 0.0)  # F = Fbar = I initially
+    sol.close()
+
+
+def test_emulated_displacement_mismatch_gradient_matches_oracle(emu):
+    """d/dlog(E, g_c, D) of a displacement-mismatch loss after two steps of the disc with a
+    Gumbel-distributed strength (damaging from the first step, d up to 0.82), through torch
+    autograd (CoupledSteps, then Displacement), against the oracle's adjoint seeded with
+    the oracle's dL/dF of the same loss; errors on the common scale of the gradients."""
+    import torch
+    from oracle import fg_oracle_adjoint as A
+    from paper_2411_16583_gb300.autograd import coupled_steps, displacement_mismatch
+    from tests.test_oracle_adjoint import _strength_disc
+    shape, logs, ls, src, prm, phases, pid = _strength_disc()
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_chem=1e-12, tol_chem_cg=1e-13,
+                tol_pff_cg=1e-13, tol_stag=1e-10, max_stag=400)
+    w = S.Workload(name="strength_disc12", shape=shape, h=(1e-7,) * 3, phases=phases,
+                   phase_id=pid.astype(np.uint8), cdot_B=src, c_init=np.full(shape, 0.01),
+                   gc=1.0, lc=2e-7, dt=1.0, nsteps=2, log_smax=ls)
+    w.tol = tols
+    rng = np.random.default_rng(8)
+    u_obs = 1e-10 * rng.standard_normal((3,) + shape)
+    wt = rng.uniform(0.0, 1.0, shape)
+    geo = B.Solver(shape, w.h, phases, pid, np.zeros(shape), lib=emu)
+    t = [torch.tensor(x, requires_grad=True) for x in logs]
+    c, F, d = coupled_steps(*t, dict(w=w, nsteps=2, lib=emu, ckpt=1))
+    L = displacement_mismatch(F, np.eye(3), torch.from_numpy(u_obs), torch.from_numpy(wt), geo)
+    L.backward()
+    tol = O.Tolerances(**tols)
+    traj = A.forward(prm, np.full(shape, 0.01), src, [1.0, 1.0], [np.eye(3)] * 2, tol)
+    Lr, seedF = A.displacement_mismatch(traj[-1].F, np.eye(3), u_obs, wt, prm)
+    z = np.zeros(shape)
+    g, _ = A.adjoint(prm, traj, [1.0, 1.0], dict(c=z, F=seedF, d=z, H=z), tol)
+    assert traj[-1].d.max() > 0.5
+    assert abs(L.item() - Lr) <= 1e-8 * Lr
+    scale = max(np.abs(g[k]).max() for k in g)
+    # with H = g_c(x)/(2 l_c) D_f the toughness cancels from the phase-field equation, so
+    # (c, F, d) and any loss on them do not depend on g_c: that gradient is rounding noise
+    assert np.abs(g["gc"]).max() < 1e-12 * scale
+    assert np.abs(t[1].grad.numpy()).max() < 1e-12 * scale
+    for k, ti in ((("E", t[0]), ("D", t[2]))):
+        assert np.abs(ti.grad.numpy() - g[k]).max() < 1e-8 * scale, k
+    geo.close()
