@@ -52,12 +52,13 @@ LAW_NEOHOOKE = 1
 
 
 def rfft3(a):
-    """Forward DFT over the last three axes (z, y, x), unnormalised, half spectrum in x."""
+    """Forward DFT over the last three axes (z, y, x), unnormalised, half spectrum in x
+    (Sec. 3.2, discrete Fourier transform; numpy's FFT as the library primitive)."""
     return np.fft.rfftn(a, axes=(-3, -2, -1))
 
 
 def irfft3(A, shape):
-    """Inverse of :func:`rfft3` (scaled by 1/V); ``shape`` = (nz, ny, nx)."""
+    """Inverse of :func:`rfft3` (scaled by 1/V; Sec. 3.2); ``shape`` = (nz, ny, nx)."""
     return np.fft.irfftn(A, s=shape, axes=(-3, -2, -1))
 
 
@@ -123,7 +124,8 @@ def fd_frequencies(shape, h):
 
 
 def fd_laplacian_symbol(shape, h):
-    """|xi|^2 = sum_j 4 sin^2(q_j/2)/h_j^2 : symbol of minus the 7-point Laplacian."""
+    """|xi|^2 = sum_j 4 sin^2(q_j/2)/h_j^2 : symbol of minus the 7-point Laplacian, the xi.xi
+    of Eqs. PFFA and PFFprecond under the forward-difference scheme."""
     xi = fd_frequencies(shape, h)
     return np.sum(np.abs(xi) ** 2, axis=0)
 
@@ -140,7 +142,8 @@ def project_G(A, n):
 
 
 def apply_G(T, h):
-    """Real-space G * T for a real tensor field T (3,3,nz,ny,nx): F^-1[G : F[T]]."""
+    """Real-space G * T for a real tensor field T (3,3,nz,ny,nx): F^-1[G : F[T]]
+    (Eqs. mapping G, mechanicalsolve)."""
     shape = T.shape[-3:]
     n = rotated_frequencies(shape, h)
     return irfft3(project_G(rfft3(T), n), shape)
@@ -160,7 +163,8 @@ def apply_G_mixed(T, prm):
 
 
 def stress_target(prm, shape):
-    """M P-bar*: the prescribed mean stress on the controlled components, as a field."""
+    """M P-bar*: the prescribed mean stress on the controlled components, as a field
+    (Sec. 3.1, macroscopic stress conditions)."""
     if prm.stress_mask is None:
         return 0.0
     return np.broadcast_to(np.where(prm.stress_mask, prm.Pbar, 0.0)[:, :, None, None, None],
@@ -221,7 +225,8 @@ class Phase:
 
 @dataclass
 class Params:
-    """Per-voxel material arrays (nz, ny, nx) plus the global constants."""
+    """Per-voxel material arrays (nz, ny, nx) plus the global constants (Sec. 2 material
+    parameters; the tables of Secs. 4.3 and 5.1)."""
     law: int
     lam: np.ndarray
     mu: np.ndarray
@@ -242,11 +247,13 @@ class Params:
 
 
 def gc_ratio(prm):
-    """g_c(x) / g_c per voxel (ones for a uniform toughness)."""
+    """g_c(x) / g_c per voxel (ones for a uniform toughness; the paper's g_c of Eq. PFF is
+    uniform)."""
     return np.ones(prm.shape) if prm.gcr is None else prm.gcr
 
 
 def lame(E, nu):
+    """Lame constants of Young's modulus and Poisson's ratio (Sec. 2.1)."""
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return lam, mu
@@ -284,17 +291,18 @@ def make_params(phases, phase_id, h, gc, lc, RT=8.314462618 * 298.15, cmax=3.0e4
 
 
 def swelling_J(c, prm):
-    """J_c = det F_c = 1 + Omega (c - c0)."""
+    """J_c = det F_c = 1 + Omega (c - c0)  (Eq. Fc, shifted to the reference c0)."""
     return 1.0 + prm.Omega * (c - prm.c0)
 
 
 def swelling_a(c, prm):
-    """a = J_c^{-1/3}, so that F_e = F F_c^{-1} = a F."""
+    """a = J_c^{-1/3}, so that F_e = F F_c^{-1} = a F  (Eq. F=Fe+Fc)."""
     return swelling_J(c, prm) ** (-1.0 / 3.0)
 
 
 def psi0(Fe, prm):
-    """Pristine elastic energy density of F_e."""
+    """Pristine elastic energy density of F_e (Eqs. Ee, psie0 for Saint-Venant-Kirchhoff;
+    the compressible Neo-Hookean form for that law)."""
     if prm.law == LAW_SVK:  # Eq. psie0 with E_e = (F_e^T F_e - I)/2  (Eq. Ee)
         E = 0.5 * (tmul(tT(Fe), Fe) - _I(Fe))
         trE = E[0, 0] + E[1, 1] + E[2, 2]
@@ -305,7 +313,7 @@ def psi0(Fe, prm):
 
 
 def P0(Fe, prm):
-    """d psi0 / d F_e."""
+    """d psi0 / d F_e, the pristine stress of Eq. pristine."""
     if prm.law == LAW_SVK:  # Eq. pristine: F_e S,  S = lam tr(E) I + 2 G E
         E = 0.5 * (tmul(tT(Fe), Fe) - _I(Fe))
         trE = E[0, 0] + E[1, 1] + E[2, 2]
@@ -317,7 +325,8 @@ def P0(Fe, prm):
 
 
 def dP0(Fe, dFe, prm):
-    """Directional derivative d P0(F_e)[dF_e]."""
+    """Directional derivative d P0(F_e)[dF_e] of Eq. pristine (the tangent of Eq.
+    mechanicalsolve)."""
     if prm.law == LAW_SVK:
         E = 0.5 * (tmul(tT(Fe), Fe) - _I(Fe))
         trE = E[0, 0] + E[1, 1] + E[2, 2]
@@ -346,7 +355,7 @@ def stress(F, c, d, prm):
 
 
 def tangent_apply(F, c, d, prm, dF):
-    """K : dF with K = dP/dF = (1-d)^2 a^2 dP0/dF_e (a F)."""
+    """K : dF with K = dP/dF = (1-d)^2 a^2 dP0/dF_e (a F)  (Eqs. Pderivada, mechanicalsolve)."""
     a = swelling_a(c, prm)
     return (1.0 - d) ** 2 * a * dP0(a * F, a * dF, prm)
 
@@ -367,7 +376,8 @@ def mu_elastic(F, c, d, prm):
 
 
 def cauchy_undegraded(F, c, prm):
-    """sigma = J^{-1} P~ F^T with the undegraded stress P~ = a P0(a F)."""
+    """sigma = J^{-1} P~ F^T with the undegraded stress P~ = a P0(a F), the stress whose
+    principal values enter Eq. SigDrivingForce."""
     a = swelling_a(c, prm)
     Pu = a * P0(a * F, prm)
     s = tmul(Pu, tT(F)) / tdet(F)
@@ -375,21 +385,23 @@ def cauchy_undegraded(F, c, prm):
 
 
 def principal_stresses(sig):
-    """Eigenvalues of the symmetric 3x3 stress at every voxel (numpy eigvalsh)."""
+    """Eigenvalues of the symmetric 3x3 stress at every voxel (numpy eigvalsh), the
+    principal stresses of Eq. SigDrivingForce."""
     M = np.moveaxis(np.moveaxis(sig, 0, -1), 0, -1)
     w = np.linalg.eigvalsh(M)
     return np.moveaxis(w, -1, 0)
 
 
 def driving_force(F, c, prm):
-    """D_f = < sum_i (<sigma_i>/sigma_max)^2 - 1 >, <.> the positive part."""
+    """D_f = < sum_i (<sigma_i>/sigma_max)^2 - 1 >, <.> the positive part
+    (Eq. SigDrivingForce)."""
     s = principal_stresses(cauchy_undegraded(F, c, prm))
     t = np.maximum(s, 0.0) / prm.sigma_max
     return np.maximum(np.sum(t * t, axis=0) - 1.0, 0.0)
 
 
 def history_update(H_t, F, c, prm):
-    """H = max(H_t, g_c(x)/(2 l_c) D_f)."""
+    """H = max(H_t, g_c(x)/(2 l_c) D_f)  (Eq. Hist)."""
     return np.maximum(H_t, prm.gc * gc_ratio(prm) / (2.0 * prm.lc) * driving_force(F, c, prm))
 
 
@@ -403,7 +415,8 @@ def dot(a, b):
 
 
 def cg(apply, b, tol, maxit, x0=None, stats=None, indefinite=True, info=None):
-    """Textbook conjugate gradients; stops when ||r|| <= tol ||b||.  Returns (x, iters).
+    """Textbook conjugate gradients (the linear solver of Algs. 1 and 3); stops when
+    ||r|| <= tol ||b||.  Returns (x, iters).
 
     Near a prestressed equilibrium the mechanical tangent of a particle in a soft buffer
     is not always positive definite.  With indefinite=True a direction of negative
@@ -527,7 +540,7 @@ def minres(apply, b, tol, maxit, stats=None):
 
 
 def pcg(apply, precond, b, tol, maxit, x0):
-    """Preconditioned conjugate gradients from x0; stops when ||r|| <= tol ||b||."""
+    """Preconditioned conjugate gradients from x0 (Alg. 2); stops when ||r|| <= tol ||b||."""
     bn = math.sqrt(dot(b, b))
     if bn == 0.0:
         return np.zeros_like(b), 0
@@ -556,13 +569,13 @@ def pcg(apply, precond, b, tol, maxit, x0):
 
 
 def mech_apply(F, c, d, prm, dF):
-    """One matrix-free operator application  F^-1[ G : F[K : dF] ] (G of mixed control
-    when stress components are prescribed)."""
+    """One matrix-free operator application  F^-1[ G : F[K : dF] ] (Eq. mechanicalsolve;
+    G of mixed control when stress components are prescribed)."""
     return apply_G_mixed(tangent_apply(F, c, d, prm, dF), prm)
 
 
 def mech_residual(F, c, d, prm, Fbar):
-    """Returns (G*P(F), err_res) with err_res = ||G*P(F)|| / ||G*P(Fbar)||.
+    """Returns (G*P(F), err_res) with err_res = ||G*P(F)|| / ||G*P(Fbar)|| (Eq. mechresiduum).
 
     When the comparison stress has no incompatible part (a homogeneous medium) the
     denominator falls back to ||P(Fbar)||, then to 1."""
@@ -655,13 +668,13 @@ def mech_adjoint(F, c, d, prm, W, tol_cg, max_cg):
 
 
 def pff_apply(dd, H, prm):
-    """A(d) = [g_c/l_c + 2H] d + F^-1{ g_c l_c |xi|^2 d^ }."""
+    """A(d) = [g_c/l_c + 2H] d + F^-1{ g_c l_c |xi|^2 d^ }  (Eq. PFFA)."""
     lap = fd_laplacian_symbol(prm.shape, prm.h)
     return (prm.gc / prm.lc + 2.0 * H) * dd + irfft3(prm.gc * prm.lc * lap * rfft3(dd), prm.shape)
 
 
 def pff_precond(r, Hbar, prm):
-    """P(r) = F^-1{ r^ / (g_c/l_c + 2 Hbar + g_c l_c |xi|^2) }."""
+    """P(r) = F^-1{ r^ / (g_c/l_c + 2 Hbar + g_c l_c |xi|^2) }  (Eq. PFFprecond)."""
     lap = fd_laplacian_symbol(prm.shape, prm.h)
     return irfft3(rfft3(r) / (prm.gc / prm.lc + 2.0 * Hbar + prm.gc * prm.lc * lap), prm.shape)
 
@@ -698,7 +711,8 @@ def chem_conductivity(F_t, c_t, d_t, prm):
 
 def chem_L(u, Kc, prm):
     """L u = grad_f^H (K_c grad_f u): minus the discrete divergence of K_c grad u, with
-    forward differences for the gradient and their adjoint for the divergence."""
+    forward differences for the gradient and their adjoint for the divergence (Eq.
+    ChemresidualFourier_A)."""
     xi = fd_frequencies(prm.shape, prm.h)
     U = rfft3(u)
     g = irfft3(xi * U[None], prm.shape)  # (3, ...) forward-difference gradient
