@@ -444,16 +444,18 @@ def test_emulated_mixed_precision_damage_and_crack_energy(emu):
     sol.close()
 
 
-@pytest.mark.parametrize("shape", [(8, 12, 16), (1, 12, 16), (12, 8, 8), (1, 1, 16)])
-def test_emulated_displacement_matches_oracle(emu, shape):
+@pytest.mark.parametrize("shape,prec", [((8, 12, 16), B.FG_FP64), ((1, 12, 16), B.FG_FP64),
+                                        ((12, 8, 8), B.FG_MIXED), ((1, 1, 16), B.FG_MIXED)])
+def test_emulated_displacement_matches_oracle(emu, shape, prec):
     """Displacement at the voxel corners from F and Fbar (Eq. Fsplit) and its transpose,
-    against the oracle, on 3-D, plane and single-line grids; also the context's own state."""
+    against the oracle, on 3-D, plane and single-line grids of FP64 and mixed contexts
+    (the transforms are FP64 in both); also the context's own state."""
     from oracle import fg_oracle_adjoint as A
     rng = np.random.default_rng(5)
     ph = S.default_phases()
     pid = S.random_phase_map(shape, 1)
     h = (1.0e-7, 1.1e-7, 0.9e-7)
-    sol = B.Solver(shape, h, ph, pid, np.zeros(shape), lib=emu)
+    sol = B.Solver(shape, h, ph, pid, np.zeros(shape), lib=emu, precision=prec)
     prm = oracle_params(ph, pid, h)
     F = np.eye(3).reshape(3, 3, 1, 1, 1) + 0.02 * rng.standard_normal((3, 3) + shape)
     Fbar = np.eye(3) + 0.01 * rng.standard_normal((3, 3))
