@@ -22,9 +22,11 @@ def emu():
 
 
 # (64, 16, 16), (256, 8, 8), (8, 256, 8): the register-direct Y and Z passes (64 = 8 x 8,
-# 256 = 16 x 16), including ragged row tiles
+# 256 = 16 x 16), including ragged row tiles; (1, 8, 256): the X passes at the benchmark's
+# row length
 @pytest.mark.parametrize("shape", [(8, 12, 16), (1, 16, 24), (12, 8, 8), (64, 16, 16),
-                                   (256, 8, 8), (8, 256, 8), (1, 64, 16), (1, 100, 100)])
+                                   (256, 8, 8), (8, 256, 8), (1, 64, 16), (1, 100, 100),
+                                   (1, 8, 256)])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
 def test_emulated_operators_match_oracle(emu, shape, prec, law):
