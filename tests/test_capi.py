@@ -61,6 +61,16 @@ def test_invalid_arguments(emu):
     with pytest.raises(B.FgError) as e:  # initial concentration outside (0, 1)
         B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=np.full(w.shape, 1.2), lib=emu)
     assert e.value.code == -5
+    s_ = B.from_workload(w, lib=emu)
+    try:  # F and Fbar of fg_displacement come together
+        u = np.empty((3,) + w.shape)
+        F = np.zeros((9,) + w.shape)
+        for call in (lambda: emu.fg_displacement(s_.ctx, B._ptr(F), None, B._ptr(u), 0),
+                     lambda: emu.fg_displacement(s_.ctx, None, B._ptr(np.eye(3)), B._ptr(u), 0)):
+            with pytest.raises(B.FgError, match="fg_displacement"):
+                s_._check(call())
+    finally:
+        s_.close()
     bad_smax = np.zeros(w.shape)
     bad_smax.flat[3] = np.inf  # sigma_max(x) = sigma_max exp(log_smax) must stay finite
     with pytest.raises(B.FgError, match="sigma_max") as e:
