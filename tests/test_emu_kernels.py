@@ -507,3 +507,37 @@ def test_emulated_displacement_mismatch_gradient_matches_oracle(emu):
     for k, ti in ((("E", t[0]), ("D", t[2]))):
         assert np.abs(ti.grad.numpy() - g[k]).max() < 1e-8 * scale, k
     geo.close()
+
+
+@pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
+def test_emulated_krylov_operators_are_symmetric(emu, law):
+    """The CUDA operators the conjugate-gradient solves apply are symmetric in FP64,
+    independently of the oracle: G K G on compatible fields (made compatible by the
+    library's own FP64 projection), the phase-field operator and its preconditioner, and
+    the chemistry Newton operator."""
+    shape = (8, 12, 16)
+    pid = S.random_phase_map(shape, 3)
+    phases = S.default_phases(law=law)
+    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu)
+    F, c, d = S.random_state(shape, seed=6)
+    Hh = np.random.default_rng(7).uniform(0, 1e6, shape)
+    for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d), (B.FIELD_H, Hh)):
+        sol.set(f, v)
+    rng = np.random.default_rng(9)
+
+    def op(o, v, dt=1.0):
+        out = np.zeros_like(v)
+        sol.apply(o, np.ascontiguousarray(v), out, 0, dt=dt)
+        return out
+
+    def sym(o, a, b, dt=1.0):
+        lhs, rhs = float(np.sum(op(o, a, dt) * b)), float(np.sum(a * op(o, b, dt)))
+        return abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    x = op(B.OP_GRES, rng.standard_normal((9,) + shape))
+    y = op(B.OP_GRES, rng.standard_normal((9,) + shape))
+    assert sym(B.OP_MECH, x, y) < 1e-12
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    assert sym(B.OP_PFF, a, b) < 1e-12
+    assert sym(B.OP_PFF_PREC, a, b) < 1e-12
+    assert sym(B.OP_CHEM, a, b, dt=0.7) < 1e-12
+    sol.close()

@@ -455,3 +455,31 @@ def test_mixed_control_projection_and_uniaxial_stress():
     np.testing.assert_allclose(F[:, :, 0, 0, 0], np.diag([1.02, lo, lo]), atol=1e-12)
     P = O.stress(F, c, d, hom).mean(axis=(2, 3, 4))
     assert np.abs(np.where(mask, P, 0.0)).max() < 1e-6 * abs(P[0, 0])
+
+
+@pytest.mark.parametrize("law", [O.LAW_NEOHOOKE, O.LAW_SVK])
+def test_krylov_operators_are_symmetric(law):
+    """The operators the conjugate-gradient solves of Algs. 1-3 apply are symmetric:
+    G K G on compatible fields (K has major symmetry, G is an orthogonal projection), the
+    phase-field operator of Eq. PFFA and its preconditioner (Eq. PFFprecond), and the
+    chemistry Newton operator y/m + dt L y (Eq. Chemderfc in y = m dc)."""
+    shape = (3, 4, 6)
+    pid = RNG.integers(0, 2, size=shape)
+    prm = two_phase(shape, pid, law=law)
+    rng = np.random.default_rng(41)
+    F = identity(shape) + 0.04 * rng.standard_normal((3, 3) + shape)
+    c = rng.uniform(0.05, 0.6, shape)
+    d = rng.uniform(0.0, 0.5, shape)
+    x = O.apply_G(rng.standard_normal((3, 3) + shape), prm.h)
+    y = O.apply_G(rng.standard_normal((3, 3) + shape), prm.h)
+
+    def sym(A, a, b):
+        lhs, rhs = O.dot(A(a), b), O.dot(a, A(b))
+        return abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    assert sym(lambda v: O.mech_apply(F, c, d, prm, v), x, y) < 1e-12
+    H = rng.uniform(0.0, 1e6, shape)
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    assert sym(lambda v: O.pff_apply(v, H, prm), a, b) < 1e-12
+    assert sym(lambda v: O.pff_precond(v, H.mean(), prm), a, b) < 1e-12
+    Kc = O.chem_conductivity(F, c, d, prm)
+    assert sym(lambda v: O.chem_apply(v, 1.0 / (c * (1.0 - c)), Kc, 0.7, prm), a, b) < 1e-12
