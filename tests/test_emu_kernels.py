@@ -541,3 +541,25 @@ def test_emulated_krylov_operators_are_symmetric(emu, law):
     assert sym(B.OP_PFF_PREC, a, b) < 1e-12
     assert sym(B.OP_CHEM, a, b, dt=0.7) < 1e-12
     sol.close()
+
+
+def test_emulated_damage_does_not_depend_on_the_toughness(emu):
+    """The CUDA path keeps the toughness cancellation of the oracle: two damaging steps of
+    the 12 x 12 disc with different per-voxel g_c fields give the same (c, F, d) up to the
+    solver tolerances and the same H / g_c(x)."""
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, _, phases, pid = _disc(n=12, smax=21e6)
+    tols = dict(tol_newton=1e-12, tol_stag=1e-10, max_stag=400)
+    out = []
+    for lg in (logs[1], np.zeros(shape), 0.5 * np.random.default_rng(4).standard_normal(shape)):
+        sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                       log_E=logs[0], log_gc=lg, log_D=logs[2], lib=emu, gc=1.0, lc=2e-7, **tols)
+        for _ in range(2):
+            sol.step(1.0)
+        out.append((sol.get(B.FIELD_C), sol.get(B.FIELD_F), sol.get(B.FIELD_D),
+                    sol.get(B.FIELD_H) / np.exp(lg)))
+        sol.close()
+    assert out[0][2].max() > 0.01
+    for o in out[1:]:
+        for a, b, t in zip(o, out[0], (1e-14, 1e-12, 1e-9, 1e-9)):
+            assert np.abs(a - b).max() <= t * np.abs(b).max()

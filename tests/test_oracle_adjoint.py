@@ -343,3 +343,22 @@ def test_displacement_mismatch_seed_is_its_derivative():
           - A.displacement_mismatch(F - h * dF, Fbar, u_obs, w, prm)[0]) / (2 * h)
     assert L > 0.0
     np.testing.assert_allclose(np.sum(g * dF), fd, rtol=1e-8)
+
+
+def test_damage_does_not_depend_on_the_toughness():
+    """With H = g_c(x)/(2 l_c) D_f (Eq. Hist) and the phase-field equation solved divided by
+    g_c(x)/g_c, the toughness cancels: two damaging steps with different per-voxel g_c
+    fields give the same (c, F, d) up to the solver tolerances, and the same H / g_c(x).
+    This is why the toughness gradient of any loss on (c, F, d) vanishes."""
+    shape, logs, src, _, prm_of, phases, pid = _disc(n=10, smax=17e6)
+    tol = O.Tolerances(tol_newton=1e-12, tol_stag=1e-10, max_stag=400)
+    out = []
+    for lg in (logs[1], np.zeros(shape), 0.5 * np.random.default_rng(4).standard_normal(shape)):
+        st = O.CoupledState(prm_of(logs[0], lg, logs[2]), np.full(shape, 0.01), src, tol)
+        for _ in range(2):
+            st.step(1.0, np.eye(3))
+        out.append((st.c, st.F, st.d, st.H / np.exp(lg)))
+    assert out[0][2].max() > 0.01
+    for o in out[1:]:
+        for a, b, t in zip(o, out[0], (1e-14, 1e-12, 1e-10, 1e-10)):
+            assert np.abs(a - b).max() <= t * np.abs(b).max()

@@ -154,3 +154,16 @@ def test_displacement_without_corner_phase_is_caught(monkeypatch):
     monkeypatch.setattr(A, "displacement_multiplier", bad)
     with pytest.raises(AssertionError):
         TA.test_corner_displacement_inverts_the_corner_stencil((5, 7, 9))
+
+
+def test_phase_field_without_toughness_division_is_caught(monkeypatch):
+    from tests import test_oracle_adjoint as TA
+
+    def bad(H, d0, prm, tol, maxit, stats=None):  # H instead of H g_c / g_c(x)
+        Hbar = float(np.mean(H))
+        d, it = O.pcg(lambda x: O.pff_apply(x, H, prm), lambda r: O.pff_precond(r, Hbar, prm),
+                      2.0 * H, tol, maxit, d0)
+        return d
+    monkeypatch.setattr(O, "pff_solve", bad)
+    with pytest.raises(AssertionError):
+        TA.test_damage_does_not_depend_on_the_toughness()
