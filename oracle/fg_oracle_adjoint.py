@@ -160,11 +160,16 @@ def gmres(apply, b, tol, maxit):
 
 
 class Snapshot:
-    """State after a step: c, F, d, H and the macroscopic Fbar it was solved for."""
+    """State after a step: c, F, d, H, the macroscopic Fbar it stores (under mixed control
+    the mean of F on the stress-controlled components) and Fcmd, the Fbar the step was
+    called with (equal to Fbar without mixed control)."""
 
-    def __init__(self, c, F, d, H, Fbar):
+    def __init__(self, c, F, d, H, Fbar, Fcmd=None):
         self.c, self.F, self.d, self.H = c.copy(), F.copy(), d.copy(), H.copy()
         self.Fbar = np.array(Fbar, dtype=float).reshape(3, 3)
+        self.Fcmd = self.Fbar.copy() if Fcmd is None else np.array(Fcmd, dtype=float).reshape(3, 3)
+        # a state left by a step stores mean(F) on the stress-controlled components as Fbar
+        self.mean_controlled = Fcmd is not None
 
 
 def forward(prm, c_init, cdot_B, dts, Fbars, tol):
@@ -173,7 +178,7 @@ def forward(prm, c_init, cdot_B, dts, Fbars, tol):
     traj = [Snapshot(st.c, st.F, st.d, st.H, st.Fbar)]
     for dt, Fb in zip(dts, Fbars):
         st.step(dt, Fb)
-        traj.append(Snapshot(st.c, st.F, st.d, st.H, st.Fbar))
+        traj.append(Snapshot(st.c, st.F, st.d, st.H, st.Fbar, Fb))
     return traj
 
 
@@ -257,8 +262,8 @@ def step_adjoint(prm, s_in, s_out, dt, seeds, tol, stats=None):
     chi = (psi > H_t).astype(float)
     Pd = stress_dd(F, c, d, prm)
 
-    def solve_M(rhs):
-        lam, it = O.cg(lambda x: O.mech_apply(F, c, d, prm, x), O.apply_G(rhs, prm.h),
+    def solve_M(rhs):  # G K G lambda = G rhs, G the projection of mixed control if any
+        lam, it = O.cg(lambda x: O.mech_apply(F, c, d, prm, x), O.apply_G_mixed(rhs, prm),
                        tol.tol_cg, tol.max_cg)
         if stats is not None:
             stats["cg_mech"] = stats.get("cg_mech", 0) + it
@@ -300,8 +305,10 @@ def step_adjoint(prm, s_in, s_out, dt, seeds, tol, stats=None):
     sH_t = (1.0 - chi) * lamH
     gc_tot = seeds["c"] - O.ddot(stress_dc(F, c, d, prm), lamM) + chi * lamH * psi_c
 
-    # ---- chemistry: (I + dt M L)^T lam = gc_tot, M = dmu~/dc
-    Ft = F_t + (s_out.Fbar - s_in.Fbar).reshape(3, 3, 1, 1, 1)
+    # ---- chemistry: (I + dt M L)^T lam = gc_tot, M = dmu~/dc.  The chemistry sees
+    # F~ = F_t + Fcmd - Fbar_t; under mixed control Fbar_t is mean(F_t) on the controlled
+    # components, so there dF~/dF_t = I - mean and the seed of F_t loses its mean
+    Ft = F_t + (s_out.Fcmd - s_in.Fbar).reshape(3, 3, 1, 1, 1)
     K = O.chem_conductivity(Ft, c_t, d_t, prm)
     mue, mue_F, mue_c = mu_elastic_derivs(Ft, c, d_t, prm)
     m = 1.0 / (c * (1.0 - c)) + mue_c / prm.RT
@@ -321,6 +328,9 @@ def step_adjoint(prm, s_in, s_out, dt, seeds, tol, stats=None):
     sc_t = lamC - dt * (1.0 - 2.0 * c_t) / (c_t * (1.0 - c_t)) * s
     sd_t = -dt * dphi / phi * s + dt * Ll * 2.0 * mue / ((1.0 - d_t) * prm.RT)
     sF_t = -dt * conductivity_form_dF(Ft, c_t, d_t, gl, gm, prm) - dt * Ll * mue_F / prm.RT
+    if prm.stress_mask is not None and s_in.mean_controlled:
+        M = np.asarray(prm.stress_mask, dtype=bool)
+        sF_t[M] -= sF_t[M].mean(axis=(1, 2, 3), keepdims=True)
     gD = -dt * s
     gE = gE - dt * Ll * mue / prm.RT
     return dict(c=sc_t, F=sF_t, d=sd_t, H=sH_t), dict(E=gE, gc=gG, D=gD)

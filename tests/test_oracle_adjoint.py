@@ -362,3 +362,42 @@ def test_damage_does_not_depend_on_the_toughness():
     for o in out[1:]:
         for a, b, t in zip(o, out[0], (1e-14, 1e-12, 1e-10, 1e-10)):
             assert np.abs(a - b).max() <= t * np.abs(b).max()
+
+
+@pytest.mark.slow
+def test_adjoint_under_mixed_control_matches_central_differences():
+    """Two damaging steps with F_xx under stress control (P-bar*_xx = 0, R28): the gradient
+    of a random linear loss on the final (c, F, d) against central differences of the whole
+    forward run.  Under mixed control the stored Fbar_t is mean(F_t) on the controlled
+    component, which the next step's chemistry sees through F~ = F_t + Fcmd - Fbar_t; the
+    adjoint that drops this mean dependence misses the E gradient by about 1e-4."""
+    shape, logs, src, tol, prm_of, _, _ = _disc(n=10)
+    mask = np.zeros((3, 3), dtype=bool)
+    mask[0, 0] = True
+
+    def prm_m(*ls):
+        p = prm_of(*ls)
+        p.stress_mask, p.Pbar = mask, np.zeros((3, 3))
+        return p
+    rng = np.random.default_rng(12)
+    wc, wF, wd = (rng.standard_normal(shape), rng.standard_normal((3, 3) + shape),
+                  rng.standard_normal(shape))
+
+    def loss(p):
+        traj = A.forward(p, np.full(shape, 0.01), src, [1.0, 1.0], [np.eye(3)] * 2, tol)
+        s = traj[-1]
+        return float(np.sum(wc * s.c) + np.sum(wF * s.F) + np.sum(wd * s.d)), traj
+    L, traj = loss(prm_m(*logs))
+    assert traj[-1].d.max() > 0.05 and abs(traj[-1].Fbar[0, 0] - 1.0) > 1e-4
+    z = np.zeros(shape)
+    g, _ = A.adjoint(prm_m(*logs), traj, [1.0, 1.0], dict(c=wc, F=wF, d=wd, H=z), tol)
+    assert np.abs(g["gc"]).max() < 1e-12 * np.abs(g["E"]).max()  # R26: no g_c dependence
+    h = 1e-6
+    for name, idx, rtol in (("E", 0, 2e-6), ("D", 2, 5e-6)):
+        v = np.unravel_index(np.argmax(np.abs(g[name])), shape)
+        lp = [x.copy() for x in logs]
+        lm = [x.copy() for x in logs]
+        lp[idx][v] += h
+        lm[idx][v] -= h
+        fd = (loss(prm_m(*lp))[0] - loss(prm_m(*lm))[0]) / (2 * h)
+        assert abs(g[name][v] - fd) <= rtol * abs(g[name]).max(), (name, v, g[name][v], fd)
