@@ -266,8 +266,10 @@ void fg_batch_destroy(fg_batch* batch);
  * zero-mean fields plus uniform fields on the mask, so the Newton operator stays
  * symmetric), and the residual is G P - M P-bar.  In fg_step, the Fbar argument's
  * controlled components are only the starting guess; after a step the stored F-bar holds
- * their solved mean.  mask = 0 restores full strain control.  fg_adjoint refuses contexts
- * with a mask.  Errors: FG_ERR_INVALID (mask outside 0..511, Pbar NULL with a mask).
+ * their solved mean.  mask = 0 restores full strain control.  fg_adjoint differentiates
+ * steps under a mask as well; the mask cannot change while the tape holds recorded steps.
+ * Errors: FG_ERR_INVALID (mask outside 0..511, Pbar NULL with a mask, steps recorded on
+ * the tape).
  */
 int fg_set_stress_control(fg_ctx* ctx, int mask, const double Pbar[9]);
 

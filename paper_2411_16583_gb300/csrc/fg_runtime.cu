@@ -2058,11 +2058,30 @@ static double adjoint_impl(fg_ctx& c, Prec<R>& P, int loss, const double* sc, co
         const int j = k - k0;
         load_state(c, snap[j + 1], c.c, c.F, c.d, c.H);
         load_state(c, snap[j], c.ct, c.Ft, c.dt, c.Ht);
+        // the chemistry of step k saw F~ = F_t + Fcmd_k - Fbar_t.  Under mixed control a
+        // step stores Fbar_t = mean(F_t) on the stress-controlled components, which makes
+        // F~ depend on that mean for every step after the first of the tape
+        const bool mean_ctl = c.smask != 0 && k > 0;
         double dFb[9];
-        for (int q = 0; q < 9; ++q) dFb[q] = snap_fb[j + 1][q] - snap_fb[j][q];
+        for (int q = 0; q < 9; ++q) {
+          double fbt = snap_fb[j][q];
+          if (mean_ctl && ((c.smask >> q) & 1))
+            fbt = reduce_sum(c, c.Ft + (long long)q * V, V, false) / (double)V;
+          dFb[q] = snap_fb[j + 1][q] - fbt;
+        }
         dzero(Sin, 12 * V * sizeof(double), c.st);
         if (c.law == FG_SVK) adj_step<LAW_SVK_>(c, W, Sout, Sin, T.dts[k], dFb, as);
         else adj_step<LAW_NH_>(c, W, Sout, Sin, T.dts[k], dFb, as);
+        if (mean_ctl)  // dF~/dF_t = I - mean on the controlled components
+          for (int q = 0; q < 9; ++q)
+            if ((c.smask >> q) & 1) {
+              double* sq = Sin + V + (long long)q * V;  // component q of the F seed
+              VArgs v = vbase(c, V);
+              v.in[0] = sq;
+              v.out[0] = sq;
+              v.s[0] = -reduce_sum(c, sq, V, false) / (double)V;
+              launch_vec<KShiftF>(v, c.st);
+            }
         std::swap(Sout, Sin);
       }
     }
@@ -2273,6 +2292,8 @@ int fg_load(fg_ctx* c, const char* path) {
 int fg_set_stress_control(fg_ctx* c, int mask, const double Pbar[9]) {
   FG_API_BEGIN
   if (!c || mask < 0 || mask > 511 || (mask && !Pbar)) fail(FG_ERR_INVALID, "fg_set_stress_control: bad argument");
+  if (c->tape && !c->tape->dts.empty())  // the reverse pass applies one mask to every step
+    fail(FG_ERR_INVALID, "fg_set_stress_control: steps are recorded on the tape");
   c->smask = mask;
   for (int k = 0; k < 9; ++k) c->Pbar[k] = mask ? Pbar[k] : 0.0;
   drop_graphs(*c);
@@ -2295,7 +2316,6 @@ int fg_adjoint(fg_ctx* c, int loss, const double* seed_c, const double* seed_F, 
   if (!c) fail(FG_ERR_INVALID, "fg_adjoint: null context");
   if (!c->tape || c->tape->dts.empty()) fail(FG_ERR_INVALID, "fg_adjoint: no recorded steps (fg_tape_begin, fg_step)");
   if (loss != FG_LOSS_CRACK_ENERGY && loss != FG_LOSS_SEEDS) fail(FG_ERR_INVALID, "fg_adjoint: loss");
-  if (c->smask) fail(FG_ERR_INVALID, "fg_adjoint: mixed stress control is not differentiated");
   fg_adjoint_stats as;
   memset(&as, 0, sizeof(as));
   double v = is_mixed(*c)

@@ -99,8 +99,8 @@ def test_invalid_arguments(emu):
         s_.step(w.dt)
         s_.tape(1)
         s_.step(w.dt)
-        with pytest.raises(B.FgError, match="mixed stress control"):
-            s_.adjoint()
+        _, _, st = s_.adjoint()  # the adjoint covers mixed control too
+        assert st["steps"] == 1
     finally:
         s_.close()
     assert emu.fg_supported_size(64) == 1 and emu.fg_supported_size(18) == 0

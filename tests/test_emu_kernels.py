@@ -563,3 +563,43 @@ def test_emulated_damage_does_not_depend_on_the_toughness(emu):
     for o in out[1:]:
         for a, b, t in zip(o, out[0], (1e-14, 1e-12, 1e-9, 1e-9)):
             assert np.abs(a - b).max() <= t * np.abs(b).max()
+
+
+@pytest.mark.parametrize("ckpt", [1, 2])
+def test_emulated_adjoint_under_mixed_control_matches_oracle(emu, ckpt):
+    """Reverse pass of two damaging steps with F_xx under stress control (P-bar*_xx = 0):
+    the gradient of a seeded loss on the final (c, F, d) against the oracle's adjoint, with
+    checkpoints every 1 and 2 steps (F-bar_t from a checkpoint or from mean(F_t))."""
+    from oracle import fg_oracle_adjoint as A
+    from tests.test_oracle_adjoint import _disc
+    shape, logs, src, _, prm_of, phases, pid = _disc(n=12, smax=21e6)
+    mask = np.zeros((3, 3), dtype=bool)
+    mask[0, 0] = True
+    prm = prm_of(*logs)
+    prm.stress_mask, prm.Pbar = mask, np.zeros((3, 3))
+    tols = dict(tol_newton=1e-12, tol_cg=1e-13, tol_chem=1e-12, tol_chem_cg=1e-13,
+                tol_pff_cg=1e-13, tol_stag=1e-10, max_stag=400)
+    tol = O.Tolerances(**tols)
+    traj = A.forward(prm, np.full(shape, 0.01), src, [1.0, 1.0], [np.eye(3)] * 2, tol)
+    rng = np.random.default_rng(12)
+    wc, wF, wd = (rng.standard_normal(shape), rng.standard_normal((3, 3) + shape),
+                  rng.standard_normal(shape))
+    g, _ = A.adjoint(prm, traj, [1.0, 1.0], dict(c=wc, F=wF, d=wd, H=np.zeros(shape)), tol)
+    sol = B.Solver(shape, (1e-7,) * 3, phases, pid, src, c_init=np.full(shape, 0.01),
+                   log_E=logs[0], log_gc=logs[1], log_D=logs[2], lib=emu, gc=1.0, lc=2e-7,
+                   **tols)
+    sol.stress_control(mask, np.zeros((3, 3)))
+    sol.tape(ckpt)
+    for _ in range(2):
+        sol.step(1.0)
+    assert traj[-1].d.max() > 0.01 and abs(traj[-1].Fbar[0, 0] - 1.0) > 1e-4
+    assert rel_err(sol.get(B.FIELD_F), traj[-1].F) < 1e-9
+    _, g2, st = sol.adjoint(B.FG_LOSS_SEEDS, seed_c=wc, seed_F=wF, seed_d=wd)
+    assert st["steps"] == 2
+    scale = max(np.abs(g[k]).max() for k in g)
+    for k in ("E", "D"):
+        assert np.abs(g2[k] - g[k]).max() < 1e-8 * scale, k
+    assert np.abs(g2["gc"]).max() < 1e-12 * scale
+    with pytest.raises(B.FgError, match="recorded"):  # one mask for the whole tape
+        sol.stress_control(np.zeros((3, 3), dtype=bool), np.zeros((3, 3)))
+    sol.close()
