@@ -167,3 +167,50 @@ def test_phase_field_without_toughness_division_is_caught(monkeypatch):
     monkeypatch.setattr(O, "pff_solve", bad)
     with pytest.raises(AssertionError):
         TA.test_damage_does_not_depend_on_the_toughness()
+
+
+def test_conductivity_with_left_cauchy_green_is_caught(monkeypatch):
+    def bad(F_t, c_t, d_t, prm):  # b^{-1} = F^{-T} F^{-1} in place of C^{-1}
+        binv = O.tinv(O.tmul(F_t, O.tT(F_t)))
+        return prm.D * O.mobility_phi(d_t) * c_t * (1.0 - c_t) * binv
+    monkeypatch.setattr(O, "chem_conductivity", bad)
+    with pytest.raises(AssertionError):
+        TS.test_chem_mode_decay_under_shear_follows_inverse_right_cauchy_green(1, 0)
+    with pytest.raises(AssertionError):
+        TS.test_chem_step_under_shear_equals_isotropic_step_with_scaled_diffusivity()
+
+
+def test_conductivity_with_C_not_inverse_is_caught(monkeypatch):
+    def bad(F_t, c_t, d_t, prm):  # C in place of C^{-1}
+        C = O.tmul(O.tT(F_t), F_t)
+        return prm.D * O.mobility_phi(d_t) * c_t * (1.0 - c_t) * C
+    monkeypatch.setattr(O, "chem_conductivity", bad)
+    with pytest.raises(AssertionError):
+        TS.test_chem_mode_decay_under_shear_follows_inverse_right_cauchy_green(1, 0)
+
+
+def test_mobility_linear_damage_term_is_caught(monkeypatch):
+    # 0.1 d in place of 0.1 d^2: phi(0) is unchanged, so only a damaged pin sees it
+    monkeypatch.setattr(O, "mobility_phi", lambda d: 0.9 * (1.0 - d) ** 2 + 0.1 * d)
+    TS.test_chem_single_mode_decay()  # undamaged pin cannot tell
+    with pytest.raises(AssertionError):
+        TS.test_chem_mode_decay_with_uniform_damage_follows_mobility(0.25)
+
+
+def test_crack_energy_length_scale_factor_is_caught(monkeypatch):
+    def bad(d, prm, gc_field=None):  # l_c in place of l_c/2 on the gradient term
+        xi = O.fd_frequencies(prm.shape, prm.h)
+        g = O.irfft3(xi * O.rfft3(d)[None], prm.shape)
+        dens = prm.gc * (d * d / (2.0 * prm.lc) + prm.lc * np.sum(g * g, axis=0))
+        return float(np.sum(dens) * prm.h[0] * prm.h[1] * prm.h[2])
+    monkeypatch.setattr(O, "crack_energy", bad)
+    with pytest.raises(AssertionError):
+        TS.test_crack_energy_closed_form()
+
+
+def test_crack_energy_without_voxel_volume_is_caught(monkeypatch):
+    good = O.crack_energy
+    monkeypatch.setattr(O, "crack_energy",
+                        lambda d, prm, gc_field=None: good(d, prm, gc_field) / prm.h[2] * prm.h[0])
+    with pytest.raises(AssertionError):
+        TS.test_crack_energy_closed_form()

@@ -202,6 +202,112 @@ def test_chem_single_mode_decay():
     np.testing.assert_allclose(c.mean(), c_t.mean(), rtol=1e-14)
 
 
+def _mode_amplitude(c, kx, ky=0):
+    """Amplitude a of c = mean + a cos(q . x) from the DFT coefficient of the mode."""
+    n_y, n_x = c.shape[-2], c.shape[-1]
+    return 2.0 * np.abs(np.fft.fft2(c[0])[ky, kx]) / (n_x * n_y)
+
+
+def _chem_plane_setup(n, amp, kx, ky, D=1e-14):
+    shape = (1, n, n)
+    L = 1.0e-6
+    h = (L / n, L / n, L / n)
+    prm = O.make_params([O.Phase(Omega=0.0, D=D)], np.zeros(shape, dtype=int), h, gc=1.0,
+                        lc=2e-7)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    c_t = 0.3 + amp * np.cos(2 * np.pi * (kx * x + ky * y) / n)
+    return prm, c_t.reshape(shape), h
+
+
+@pytest.mark.parametrize("kx,ky", [(1, 0), (0, 1), (1, 2)])
+def test_chem_mode_decay_under_shear_follows_inverse_right_cauchy_green(kx, ky):
+    """Eq. Jmassflowexpression: the referential mobility carries C^{-1} = (F^T F)^{-1}, the
+    pull-back of an isotropic spatial mobility.  Under a uniform simple shear
+    F = I + g e_x (x) e_y, a small Fourier mode with forward-difference symbol xi decays per
+    backward-Euler step by 1/(1 + 0.9 D dt xi^H C^{-1} xi), C^{-1} = [[1 + g^2, -g], [-g, 1]]
+    in the (x, y) block.  The mode along x sees 1 + g^2 (b^{-1} = F^{-T} F^{-1} would give 1,
+    C itself 1), the mode along y sees 1 (b^{-1}: 1 + g^2, C: 1 + g^2), the oblique mode
+    the off-diagonal -g."""
+    n, amp, g, dt = 16, 1e-6, 0.3, 0.5
+    prm, c_t, h = _chem_plane_setup(n, amp, kx, ky)
+    F = identity(c_t.shape)
+    F[0, 1] = g
+    c = O.chem_solve(c_t, F, np.zeros_like(c_t), dt, np.zeros_like(c_t), prm, 1e-13, 1e-14,
+                     30, 400)
+    q = (2 * np.pi * kx / n, 2 * np.pi * ky / n)
+    xi = np.array([(np.exp(1j * q[0]) - 1) / h[0], (np.exp(1j * q[1]) - 1) / h[1]])
+    Cinv = np.array([[1 + g * g, -g], [-g, 1.0]])
+    s = float(np.real(np.conj(xi) @ Cinv @ xi))
+    fac = 1.0 / (1.0 + 0.9 * 1e-14 * dt * s)
+    assert abs(_mode_amplitude(c, kx, ky) / amp - fac) < 1e-5
+    np.testing.assert_allclose(c.mean(), c_t.mean(), rtol=1e-14)
+
+
+@pytest.mark.parametrize("d0", [0.25, 0.6])
+def test_chem_mode_decay_with_uniform_damage_follows_mobility(d0):
+    """Eq. mobility: with a uniform phase field d the mobility factor is
+    phi(d) = 0.9 (1 - d)^2 + 0.1 d^2, so the mode decays per step by
+    1/(1 + phi(d) D dt |xi|^2) (phi(0.25) = 0.5125, phi(0.6) = 0.18)."""
+    n, amp, dt = 16, 1e-6, 0.5
+    prm, c_t, k, h = _chem_mode_setup(n, amp)
+    F = identity(c_t.shape)
+    d_t = np.full_like(c_t, d0)
+    c = O.chem_solve(c_t, F, d_t, dt, np.zeros_like(c_t), prm, 1e-13, 1e-14, 30, 200)
+    phi = {0.25: 0.5125, 0.6: 0.18}[d0]
+    xi2 = 4 * math.sin(math.pi / n) ** 2 / h[0] ** 2
+    fac = 1.0 / (1.0 + phi * 1e-14 * dt * xi2)
+    amp_new = 2 * np.abs(np.fft.rfft(c.ravel())[1]) / n
+    assert abs(amp_new / amp - fac) < 1e-5
+
+
+def test_chem_step_under_shear_equals_isotropic_step_with_scaled_diffusivity():
+    """Nonlinear, non-uniform case: for c_t and d_t varying along x only, the x-x entry of
+    C^{-1} is the only one the divergence sees, so a step under the simple shear
+    F = I + g e_x (x) e_y equals, to solver tolerance, the step at F = I with D (1 + g^2),
+    at any concentration profile (Eq. Jmassflowexpression; the whole nonlinear Newton of
+    Alg. 3, no linearisation)."""
+    n, g, dt = 24, 0.4, 2.0
+    shape = (1, 1, n)
+    rng = np.random.default_rng(11)
+    c_t = rng.uniform(0.05, 0.7, shape)
+    d_t = rng.uniform(0.0, 0.8, shape)
+    src = np.where(rng.uniform(size=shape) < 0.3, 0.02, 0.0)
+    h = (1e-7, 1e-7, 1e-7)
+    pid = np.zeros(shape, dtype=int)
+    prm = O.make_params([O.Phase(Omega=0.0, D=1e-14)], pid, h, gc=1.0, lc=2e-7)
+    prm_iso = O.make_params([O.Phase(Omega=0.0, D=1e-14 * (1 + g * g))], pid, h, gc=1.0,
+                            lc=2e-7)
+    F = identity(shape)
+    F[0, 1] = g
+    c_shear = O.chem_solve(c_t, F, d_t, dt, src, prm, 1e-13, 1e-14, 50, 500)
+    c_iso = O.chem_solve(c_t, identity(shape), d_t, dt, src, prm_iso, 1e-13, 1e-14, 50, 500)
+    assert np.abs(c_shear - c_t).max() > 1e-3  # the step moves c
+    np.testing.assert_allclose(c_shear, c_iso, rtol=0, atol=1e-12)
+
+
+def test_crack_energy_closed_form():
+    """Eq. crack, Gamma = sum_voxels g_c (d^2/(2 l_c) + l_c/2 |grad_f d|^2) h_x h_y h_z.  For
+    d = d0 + a cos(2 pi k y / n_y) the voxel sums are V (d0^2 + a^2/2) and
+    V a^2/2 |xi_y|^2 with |xi_y|^2 = 4 sin^2(pi k / n_y)/h_y^2, so
+    Gamma = g_c h_x h_y h_z V [(d0^2 + a^2/2)/(2 l_c) + l_c a^2 |xi_y|^2 / 4]; uniform d (a = 0)
+    gives g_c d0^2/(2 l_c) V h_x h_y h_z."""
+    shape = (3, 8, 4)
+    h = (0.9e-7, 1.1e-7, 1.3e-7)
+    lc, gc = 2.5e-7, 1.7
+    prm = O.make_params([O.Phase()], np.zeros(shape, dtype=int), h, gc=gc, lc=lc)
+    V = np.prod(shape)
+    hv = h[0] * h[1] * h[2]
+    d0 = 0.3
+    np.testing.assert_allclose(O.crack_energy(np.full(shape, d0), prm),
+                               gc * d0 * d0 / (2 * lc) * V * hv, rtol=1e-13)
+    a, k = 0.2, 3
+    y = np.arange(shape[1]).reshape(1, -1, 1)
+    d = d0 + a * np.cos(2 * np.pi * k * y / shape[1]) * np.ones(shape)
+    xi2 = 4 * math.sin(math.pi * k / shape[1]) ** 2 / h[1] ** 2
+    ref = gc * hv * V * ((d0 * d0 + a * a / 2) / (2 * lc) + lc * a * a * xi2 / 4)
+    np.testing.assert_allclose(O.crack_energy(d, prm), ref, rtol=1e-12)
+
+
 def test_chem_mode_converges_to_continuum_decay():
     """Refining h and dt together, the decay approaches exp(-0.9 D k^2 t) (first order
     in dt)."""
