@@ -202,7 +202,8 @@ int fg_apply(fg_ctx* ctx, int op, int prec, const void* x, void* y, double dt, d
 int fg_get_field(fg_ctx* ctx, int field, void* dst, int on_device);
 
 /* Overwrites a stored field (C, F, D or H) from host or device memory, for tests and
- * restarts.  The step's t-state is the stored state. */
+ * restarts.  The step's t-state is the stored state.  Refused (FG_ERR_INVALID) while the
+ * tape holds recorded steps (fg_tape_begin), whose trajectory fg_adjoint recomputes. */
 int fg_set_field(fg_ctx* ctx, int field, const void* src, int on_device);
 
 /* Runs n applications of op back to back on the stream between two CUDA events and
@@ -342,11 +343,13 @@ int fg_displacement_adjoint(fg_ctx* ctx, const double* r, double* g, int on_devi
 
 /*
  * Restart files: fg_save writes the evolving state of the context (c, F, d, H, the
- * t-state of the last step, Fbar, the previous Fbar and the last dt) to a binary file;
- * fg_load reads one into a context set up with the same grid, law and materials (the
- * file holds no material data), which then steps as the saved one would.  Doubles in the
- * machine's byte order.  Errors: FG_ERR_INVALID (file cannot be opened, written or read,
- * is not a state file, or its grid or law differs), FG_ERR_CUDA.
+ * t-state of the last step, Fbar, the previous Fbar, the last dt, and the mixed-control
+ * mask and prescribed Pbar of fg_set_stress_control) to a binary file; fg_load reads one
+ * into a context set up with the same grid, law and materials (the file holds no
+ * material data), which then steps as the saved one would.  Doubles in the machine's byte
+ * order.  fg_load is refused while the tape holds recorded steps.  Errors: FG_ERR_INVALID
+ * (file cannot be opened, written or read, is not a state file, its grid or law differs,
+ * or the tape holds steps), FG_ERR_CUDA.
  */
 int fg_save(fg_ctx* ctx, const char* path);
 int fg_load(fg_ctx* ctx, const char* path);
@@ -356,7 +359,8 @@ void fg_destroy(fg_ctx* ctx);
 
 /*
  * fg_mech_apply_noalloc -- the FP32 mechanical operator application of fg_apply
- * (FG_OP_MECH, prec 1), for callers that cannot allocate GPU memory.  The paper has no
+ * (FG_OP_MECH, prec 1) of a context under full strain control (the projection G, no
+ * stress-control mask), for callers that cannot allocate GPU memory.  The paper has no
  * counterpart: this is a deployment variant.  It suits code that may only hand over
  * pointers, e.g. a plug-in running inside a host framework that owns all device memory
  * through its own pool, or a service whose device-memory budget is fixed after start-up,

@@ -2221,8 +2221,9 @@ void fg_destroy(fg_ctx* ctx) {
   delete ctx;
 }
 
-// file layout: magic "FGST", version 1, nx ny nz law (int32), Fbar[9], Fbar_prev[9],
-// last_dt, stepped (as a double), then c F d H and c_t F_t d_t H_t (24 V doubles)
+// file layout: magic "FGST", version 2, nx ny nz law smask (int32), Fbar[9], Fbar_prev[9],
+// last_dt, stepped (as a double), Pbar[9], then c F d H and c_t F_t d_t H_t (24 V doubles).
+// Version 1 files (no smask, no Pbar) still load and leave the stress control as it is.
 static const char FG_MAGIC[4] = {'F', 'G', 'S', 'T'};
 
 int fg_save(fg_ctx* c, const char* path) {
@@ -2238,12 +2239,13 @@ int fg_save(fg_ctx* c, const char* path) {
   dsync(c->st);
   FILE* f = fopen(path, "wb");
   if (!f) fail(FG_ERR_INVALID, std::string("fg_save: cannot open ") + path);
-  const int32_t hdr[5] = {1, c->nx, c->ny, c->nz, c->law};
-  double sc[20];
+  const int32_t hdr[6] = {2, c->nx, c->ny, c->nz, c->law, c->smask};
+  double sc[29];
   memcpy(sc, c->Fbar, 9 * sizeof(double));
   memcpy(sc + 9, c->Fbar_prev, 9 * sizeof(double));
   sc[18] = c->last_dt;
   sc[19] = c->stepped ? 1.0 : 0.0;
+  memcpy(sc + 20, c->Pbar, 9 * sizeof(double));
   bool ok = fwrite(FG_MAGIC, 1, 4, f) == 4 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
             fwrite(sc, sizeof(sc), 1, f) == 1 &&
             fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
@@ -2255,18 +2257,23 @@ int fg_save(fg_ctx* c, const char* path) {
 int fg_load(fg_ctx* c, const char* path) {
   FG_API_BEGIN
   if (!c || !path) fail(FG_ERR_INVALID, "fg_load: null argument");
+  if (c->tape && !c->tape->dts.empty())  // the reverse pass recomputes the taped trajectory
+    fail(FG_ERR_INVALID, "fg_load: steps are recorded on the tape");
   const long long V = c->V;
   FILE* f = fopen(path, "rb");
   if (!f) fail(FG_ERR_INVALID, std::string("fg_load: cannot open ") + path);
   char mg[4] = {};
-  int32_t hdr[5] = {};
-  double sc[20];
+  int32_t hdr[6] = {};
+  double sc[29] = {};
   std::vector<double> buf(24 * V);
-  bool ok = fread(mg, 1, 4, f) == 4 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
-            fread(sc, sizeof(sc), 1, f) == 1;
-  if (!ok || memcmp(mg, FG_MAGIC, 4) != 0 || hdr[0] != 1) {
+  bool ok = fread(mg, 1, 4, f) == 4 && fread(hdr, sizeof(int32_t), 5, f) == 5;
+  const int version = ok ? hdr[0] : 0;
+  if (ok && version == 2) ok = fread(hdr + 5, sizeof(int32_t), 1, f) == 1;
+  if (ok) ok = fread(sc, sizeof(double), version == 2 ? 29 : 20, f) == (version == 2 ? 29u : 20u);
+  if (!ok || memcmp(mg, FG_MAGIC, 4) != 0 || (version != 1 && version != 2) ||
+      (version == 2 && (hdr[5] < 0 || hdr[5] > 511))) {
     fclose(f);
-    fail(FG_ERR_INVALID, std::string("fg_load: not a state file of this version: ") + path);
+    fail(FG_ERR_INVALID, std::string("fg_load: not a state file of a known version: ") + path);
   }
   if (hdr[1] != c->nx || hdr[2] != c->ny || hdr[3] != c->nz || hdr[4] != c->law) {
     fclose(f);
@@ -2285,6 +2292,11 @@ int fg_load(fg_ctx* c, const char* path) {
   memcpy(c->Fbar_prev, sc + 9, 9 * sizeof(double));
   c->last_dt = sc[18];
   c->stepped = sc[19] != 0.0;
+  if (version == 2 && (hdr[5] != c->smask || memcmp(c->Pbar, sc + 20, 9 * sizeof(double)) != 0)) {
+    c->smask = hdr[5];
+    for (int k = 0; k < 9; ++k) c->Pbar[k] = c->smask ? sc[20 + k] : 0.0;
+    drop_graphs(*c);
+  }
   dsync(c->st);
   FG_API_END
 }
@@ -2633,6 +2645,8 @@ int fg_displacement_adjoint(fg_ctx* c, const double* r, double* g, int on_device
 int fg_set_field(fg_ctx* c, int field, const void* src, int on_device) {
   FG_API_BEGIN
   if (!c || !src) fail(FG_ERR_INVALID, "fg_set_field: null argument");
+  if (c->tape && !c->tape->dts.empty())  // the reverse pass recomputes the taped trajectory
+    fail(FG_ERR_INVALID, "fg_set_field: steps are recorded on the tape");
   double* dst = nullptr;
   double* dst_t = nullptr;
   long long n = c->V;

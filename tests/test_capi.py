@@ -152,6 +152,60 @@ def test_save_load_restarts_bit_identically(emu, tmp_path):
         s_.close()
 
 
+def test_state_writes_are_refused_while_the_tape_holds_steps(emu, tmp_path):
+    """fg_adjoint recomputes the recorded trajectory from its checkpoints, so fg_set_field
+    and fg_load, which would make the stored state jump between two recorded steps, are
+    refused while the tape holds steps; a new tape (fg_tape_begin) allows them again."""
+    w = _disc()
+    s_ = B.from_workload(w, lib=emu)
+    try:
+        s_.step(w.dt)
+        path = str(tmp_path / "state.fg")
+        s_.save(path)
+        s_.tape(1)
+        s_.step(w.dt)
+        c = s_.get(B.FIELD_C)
+        with pytest.raises(B.FgError, match="fg_set_field: steps are recorded") as e:
+            s_.set(B.FIELD_C, c * 0.5)
+        assert e.value.code == -1
+        with pytest.raises(B.FgError, match="fg_load: steps are recorded") as e:
+            s_.load(path)
+        assert e.value.code == -1
+        np.testing.assert_array_equal(s_.get(B.FIELD_C), c)  # nothing was written
+        s_.adjoint()
+        s_.tape(1)  # an empty tape
+        s_.load(path)
+        s_.set(B.FIELD_C, c)
+    finally:
+        s_.close()
+
+
+def test_save_load_keeps_mixed_stress_control(emu, tmp_path):
+    """The restart file carries the stress-control mask and the prescribed mean stress, so a
+    context restored after a mixed-control step steps on as the one that wrote it."""
+    w = _disc()
+    mask = np.zeros((3, 3), dtype=bool)
+    mask[1, 1] = True
+    Pbar = np.zeros((3, 3))
+    a = B.from_workload(w, lib=emu)
+    a.stress_control(mask, Pbar)
+    a.step(w.dt)
+    path = str(tmp_path / "mixed.fg")
+    a.save(path)
+    b = B.from_workload(w, lib=emu)  # full strain control until the file is read
+    b.load(path)
+    a.step(w.dt)
+    b.step(w.dt)
+    for f in (B.FIELD_C, B.FIELD_F, B.FIELD_D, B.FIELD_H):
+        np.testing.assert_array_equal(a.get(f), b.get(f))
+    c = B.from_workload(w, lib=emu)
+    c.step(w.dt)
+    c.step(w.dt)
+    assert np.abs(c.get(B.FIELD_F) - a.get(B.FIELD_F)).max() > 1e-9  # the mask matters
+    for s_ in (a, b, c):
+        s_.close()
+
+
 @pytest.mark.parametrize("mode,offset,faults", [
     ("end", 0, False), ("end", 63, False), ("end", 64, True),
     ("start", 0, False), ("start", 63, False), ("start", -1, True)])
