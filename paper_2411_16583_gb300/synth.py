@@ -26,6 +26,8 @@ Workloads (sizes in voxels, voxel size h = 0.1 um unless stated):
 * ``multi_particle`` several non-overlapping rough ellipsoids in one RVE.
 * ``gumbel_disc`` 512^2 Saint-Venant-Kirchhoff disc with Weibull-type random stiffness and
   strength and the paper's Omega = 1.3 (Sec. 5.1).
+* ``plate``     64x64x1 Saint-Venant-Kirchhoff plate of Sec. 4.3 with a stronger influx
+  at one corner.
 """
 from __future__ import annotations
 
@@ -252,6 +254,38 @@ def gumbel_disc(n=512, diameter_frac=0.8, band=6, nsteps=200, seed=0, m=3.0, h=1
     w.log_E = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
     if random_strength:
         w.log_smax = np.where(particle, gumbel_log_scale(rng, shape, m), 0.0)
+    w.tol = dict(w.tol, chem_full_jacobian=1, max_stag=400)
+    return w
+
+
+def plate(n=64, plate_frac=0.75, nsteps=20, corner_ratio=1.5, corner_frac=0.25, seed=0):
+    """The chemo-mechanical fracture plate of Sec. 4.3 (Table tab:4.3_properties): a square
+    Saint-Venant-Kirchhoff plate, E = 15 GPa, nu = 0.3, sigma_max = 50 MPa, Omega = 1.3,
+    g_c = 2 J/m^2, l_c = 2 voxels, D = 1e-15 m^2/s, in a buffer 1e-5 times as stiff and as
+    diffusive, on an n x n x 1 grid of side 8 um (h = 0.125 um for n = 64, so that l_c is
+    the table's 0.25 um).  The influx enters through a band one voxel wide along the plate's
+    edges (dL = 1 voxel); the band voxels within corner_frac of the edge length of the
+    (+x, +y) corner take corner_ratio times the edge rate (the table's 3e-4 against
+    2e-4), which breaks the plate's symmetry so that the crack starts there.  The plate
+    occupies the central plate_frac of each in-plane axis (the buffer's size is only drawn
+    in the paper).  The edge rate fills the plate to a mean c of 0.5 over nsteps steps of
+    dt = h^2/D (Fourier number 1); like the Sec. 5.1 disc with Omega = 1.3, the chemistry
+    Newton runs with the full Jacobian."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (1, n, n)
+    h = 8e-6 / n
+    x, y, _ = _grid_coords(shape)
+    half = 0.5 * plate_frac * n
+    particle = (np.abs(x) < half) & (np.abs(y) < half)
+    c0 = 0.01
+    D = 1e-15
+    phases = default_phases(E=15e9, nu=0.3, c0=c0, D=D, sigma_max=50e6, law=LAW_SVK,
+                            vol_change=1.3 * (1.0 - c0), buffer_E=1e-5, buffer_D=1e-5)
+    dt = h * h / D
+    w = _finish("plate", shape, (h, h, h), particle, 1, nsteps, dt, rng, phases=phases,
+                gc=2.0)
+    corner = (x > half - 2.0 * corner_frac * half) & (y > half - 2.0 * corner_frac * half)
+    w.cdot_B = np.where(corner, corner_ratio * w.cdot_B, w.cdot_B)
     w.tol = dict(w.tol, chem_full_jacobian=1, max_stag=400)
     return w
 

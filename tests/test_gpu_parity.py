@@ -18,7 +18,10 @@ H3 = (1.0e-7, 1.1e-7, 0.9e-7)
 # grids spanning several tiles, ragged last tiles (rows not a multiple of the tile) in the
 # X, Y and Z passes, mixed radix (12 = 4 x 3, 24 = 8 x 3, 48, 80 = 16 x 5), plane strain
 SHAPES = [(8, 12, 16), (12, 24, 16), (1, 12, 16), (1, 64, 64), (16, 32, 64), (24, 48, 80),
-          (32, 32, 32), (1, 100, 100), (100, 96, 80)]
+          (32, 32, 32), (1, 100, 100), (100, 96, 80),
+          # the transform lengths of the 128^3 particle (two-stage 128 = 16 x 8 in every
+          # pass) and of the 512^2 disc (512 = 16 x 16 x 2)
+          (16, 128, 128), (128, 16, 24), (1, 512, 512), (8, 16, 512)]
 
 
 @pytest.fixture(scope="module")
@@ -83,15 +86,38 @@ def test_operator_parity(lib, shape, law, l2f, prec):
     sol.close()
 
 
-def test_operator_parity_full_size_fp32(lib):
-    """The FP32 mechanical operator at the benchmark size (256^3), element by element."""
+@pytest.mark.parametrize("prec", [1, 0])
+def test_operator_parity_full_size(lib, prec):
+    """Every operator at the benchmark size (256^3, where the Y and Z passes take their
+    register-direct two-stage form), element by element against the oracle: mechanics,
+    phase field and its preconditioner, chemistry, and in FP64 the residual projection."""
     shape = (256, 256, 256)
-    sol, prm, F, c, d, _ = _solver(lib, shape, B.FG_MIXED, seed=11)
-    x = torch.from_numpy(S.random_tensor_field(shape, 7)).to("cuda", torch.float32)
+    sol, prm, F, c, d, Hh = _solver(lib, shape, B.FG_MIXED if prec else B.FG_FP64, seed=11)
+    tdt = torch.float32 if prec else torch.float64
+    tol = TOL_APPLY_FP32 if prec else TOL_APPLY_FP64
+    x = torch.from_numpy(S.random_tensor_field(shape, 7)).to("cuda", tdt)
     y = torch.empty_like(x)
-    sol.apply(B.OP_MECH, x, y, 1)
-    ref = O.mech_apply(F, c, d, prm, x.double().cpu().numpy().reshape(F.shape))
-    assert rel_err(y.cpu().numpy().reshape(ref.shape), ref) < TOL_APPLY_FP32
+    xn = x.double().cpu().numpy().reshape(F.shape)
+    sol.apply(B.OP_MECH, x, y, prec)
+    ref = O.mech_apply(F, c, d, prm, xn)
+    assert rel_err(y.cpu().numpy().reshape(ref.shape), ref) < tol
+    del ref
+    if prec == 0:
+        sol.apply(B.OP_GRES, x, y, 0)
+        assert rel_err(y.cpu().numpy().reshape(F.shape), O.apply_G(xn, prm.h)) < tol
+    del x, y, xn
+    x1 = torch.from_numpy(S.random_tensor_field(shape, 8, ncomp=1)[0]).to("cuda", tdt)
+    y1 = torch.empty_like(x1)
+    xn1 = x1.double().cpu().numpy()
+    sol.apply(B.OP_PFF, x1, y1, prec)
+    assert rel_err(y1.cpu().numpy(), O.pff_apply(xn1, Hh, prm)) < tol
+    sol.apply(B.OP_PFF_PREC, x1, y1, prec)
+    assert rel_err(y1.cpu().numpy(), O.pff_precond(xn1, Hh.mean(), prm)) < tol
+    dt = 0.7
+    sol.apply(B.OP_CHEM, x1, y1, prec, dt=dt)
+    Kc = O.chem_conductivity(F, c, d, prm)
+    ref = O.chem_apply(xn1, 1.0 / (c * (1 - c)), Kc, dt, prm)
+    assert rel_err(y1.cpu().numpy(), ref) < tol
     sol.close()
 
 

@@ -1,7 +1,8 @@
 """fg_mech_apply_noalloc: the operator application for callers that cannot allocate GPU
 memory (their device memory belongs to a host framework's pool or a fixed budget).  It
 keeps all scratch in one static device array.  Checked against fg_apply (FG_OP_MECH,
-FP32) on two calls in a row with different inputs, and for its size limit.  This file is
+FP32) and against the CPU oracle's operator on two calls in a row with different inputs,
+and for its size limit.  This file is
 collected last so that a run stopping at the first failure has run every other test."""
 import ctypes as C
 
@@ -10,8 +11,9 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import fg_oracle as O
 from paper_2411_16583_gb300 import binding as B, synth as S
-from tests.helpers import TOL_APPLY_FP32, rel_err
+from tests.helpers import TOL_APPLY_FP32, oracle_params, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +35,7 @@ def test_noalloc_apply_matches_fg_apply_twice():
     F, c, d = S.random_state(SHAPE, seed=4)
     for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d)):
         sol.set(f, v)
+    prm = oracle_params(phases, pid, H)
     E = np.array([p.E for p in phases])[pid]
     nu = np.array([p.nu for p in phases])[pid]
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
@@ -55,6 +58,9 @@ def test_noalloc_apply_matches_fg_apply_twice():
         assert rc == 0, lib.fg_last_error()
         assert rel_err(y.cpu().numpy(), y_ref.cpu().numpy()) < TOL_APPLY_FP32
         assert abs(dot.value - dot_ref) <= TOL_APPLY_FP32 * abs(dot_ref)
+        Fo = F.reshape((3, 3) + SHAPE)
+        ref = O.mech_apply(Fo, c, d, prm, x.double().cpu().numpy().reshape(Fo.shape))
+        assert rel_err(y.cpu().numpy().reshape(ref.shape), ref) < TOL_APPLY_FP32
     sol.close()
 
 
