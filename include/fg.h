@@ -296,10 +296,10 @@ int fg_set_stress_control(fg_ctx* ctx, int mask, const double Pbar[9]);
  *               h^3 of the final phase field (Eq. crack); the seeds are ignored.
  *               FG_LOSS_SEEDS: L with dL/dc, dL/dF, dL/dd of the final state given in
  *               seed_c (V), seed_F (9 V, component (i, j) at (3 i + j) V), seed_d (V),
- *               host arrays, NULL meaning zero.
+ *               host or device arrays, NULL meaning zero.
  *   loss_value  (may be NULL) Gamma_E, or 0 for FG_LOSS_SEEDS
- *   grad_*      (host, V doubles each, may be NULL) dL/dlog E, dL/dlog g_c, dL/dlog D per
- *               voxel (log g_c as in fg_setup's log_gc)
+ *   grad_*      (host or device, V doubles each, may be NULL) dL/dlog E, dL/dlog g_c,
+ *               dL/dlog D per voxel (log g_c as in fg_setup's log_gc)
  * On return the stored state is the one at the call and the tape is kept.  Errors:
  * FG_ERR_INVALID (no recorded step, bad loss), FG_ERR_NOCONV (an adjoint solve hit its
  * cap), FG_ERR_NUMERIC (dmu~/dc <= 0 somewhere: the chemistry Jacobian is not positive),

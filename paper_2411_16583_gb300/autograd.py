@@ -9,7 +9,10 @@ CoupledSteps: the final state (c, F, d) after n staggered steps (Alg. 4) as a fu
   the per-voxel log E, log g_c, log D (a per-voxel strength of the workload is a fixed
   input); backward runs the recorded steps in reverse
   (fg_tape_begin / fg_adjoint with the seeds dL/d(c, F, d)).
-Everything runs in the CUDA library; this module only moves arguments.
+Everything runs in the CUDA library; this module only moves arguments.  Outputs, seeds
+and gradients of tensors on a CUDA device stay on the device (the library reads and writes
+device pointers); only the set-up inputs of a context (the per-voxel log fields) are read
+from host memory, as fg_setup takes them.
 """
 from __future__ import annotations
 
@@ -17,6 +20,25 @@ import numpy as np
 import torch
 
 from . import binding as B
+
+
+def _field(sol, field, device):
+    """A stored field as a tensor on `device` (copied device to device on a GPU)."""
+    if device.type == "cuda":
+        return sol.get(field, device=device)
+    return torch.from_numpy(sol.get(field))
+
+
+def _pass(t):
+    """A tensor argument for the library: the CUDA tensor itself, else a host array."""
+    if t is None:
+        return None
+    t = t.detach()
+    return t.double().contiguous() if t.is_cuda else t.double().contiguous().numpy()
+
+
+def _back(g, device):
+    return g if torch.is_tensor(g) else torch.from_numpy(g).to(device)
 
 
 class MechEquilibrium(torch.autograd.Function):
@@ -29,15 +51,15 @@ class MechEquilibrium(torch.autograd.Function):
         sol.set(B.FIELD_C, spec["c"])
         sol.set(B.FIELD_D, spec["d"])
         sol.solve_mech(spec.get("Fbar"))
-        F = torch.from_numpy(sol.get(B.FIELD_F)).to(logE.device)
+        F = _field(sol, B.FIELD_F, logE.device)
         ctx.sol = sol
         return F
 
     @staticmethod
     def backward(ctx, gF):
-        g, _ = ctx.sol.adjoint_mech(gF.detach().double().contiguous().cpu().numpy())
+        g, _ = ctx.sol.adjoint_mech(_pass(gF))
         ctx.sol.close()
-        return torch.from_numpy(g).to(gF.device), None
+        return _back(g, gF.device), None
 
 
 def mech_equilibrium(logE, spec):
@@ -61,18 +83,16 @@ class CoupledSteps(torch.autograd.Function):
             sol.step(w.dt)
         ctx.sol = sol
         dev = logE.device
-        return (torch.from_numpy(sol.get(B.FIELD_C)).to(dev),
-                torch.from_numpy(sol.get(B.FIELD_F)).to(dev),
-                torch.from_numpy(sol.get(B.FIELD_D)).to(dev))
+        return (_field(sol, B.FIELD_C, dev), _field(sol, B.FIELD_F, dev),
+                _field(sol, B.FIELD_D, dev))
 
     @staticmethod
     def backward(ctx, gc, gF, gd):
-        np_ = lambda t: None if t is None else t.detach().double().contiguous().cpu().numpy()
-        _, g, _ = ctx.sol.adjoint(B.FG_LOSS_SEEDS, seed_c=np_(gc), seed_F=np_(gF), seed_d=np_(gd))
+        _, g, _ = ctx.sol.adjoint(B.FG_LOSS_SEEDS, seed_c=_pass(gc), seed_F=_pass(gF),
+                                  seed_d=_pass(gd))
         ctx.sol.close()
         dev = (gc if gc is not None else gF if gF is not None else gd).device
-        return (torch.from_numpy(g["E"]).to(dev), torch.from_numpy(g["gc"]).to(dev),
-                torch.from_numpy(g["D"]).to(dev), None)
+        return _back(g["E"], dev), _back(g["gc"], dev), _back(g["D"], dev), None
 
 
 def coupled_steps(logE, loggc, logD, spec):
@@ -85,14 +105,14 @@ class Displacement(torch.autograd.Function):
         """F (3, 3, nz, ny, nx) -> u (3, nz, ny, nx) at the voxel corners, u = (Fbar - I) x
         + u~ with grad u~ = F - Fbar; Fbar (3, 3) is a fixed input.  sol is any
         ``binding.Solver`` on the same grid (only its transforms are used)."""
-        u = sol.displacement(F.detach().double().cpu().numpy(), np.asarray(Fbar, dtype=float))
+        u = sol.displacement(_pass(F), np.asarray(Fbar, dtype=float))
         ctx.sol = sol
-        return torch.from_numpy(u).to(F.device)
+        return _back(u, F.device)
 
     @staticmethod
     def backward(ctx, gu):
-        g = ctx.sol.displacement_adjoint(gu.detach().double().contiguous().cpu().numpy())
-        return torch.from_numpy(g).to(gu.device), None, None
+        g = ctx.sol.displacement_adjoint(_pass(gu))
+        return _back(g, gu.device), None, None
 
 
 def displacement(F, Fbar, sol):

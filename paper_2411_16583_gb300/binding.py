@@ -157,6 +157,33 @@ def _f64(a, shape=None):
     return a if shape is None else a.reshape(shape)
 
 
+def _on_device(a):
+    """True for a CUDA torch tensor (passed to the library as a device pointer)."""
+    return hasattr(a, "data_ptr") and bool(getattr(a, "is_cuda", False))
+
+
+def _dev64(a):
+    """A CUDA tensor as the library expects it: float64, contiguous."""
+    import torch
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        a = a.to(torch.float64).contiguous()
+    return a
+
+
+def _arg64(a):
+    """Host numpy float64 copy, or the CUDA tensor itself (float64, contiguous)."""
+    return _dev64(a) if _on_device(a) else _f64(a).ravel()
+
+
+def _out64(shape, like):
+    """An output buffer of float64: a CUDA tensor on like's device when like is one, else
+    a numpy array."""
+    if like is not None and _on_device(like):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=like.device)
+    return np.empty(shape)
+
+
 class Solver:
     """One periodic RVE: owns an ``fg_ctx``.  Host arrays are numpy, (nz, ny, nx)."""
 
@@ -220,15 +247,24 @@ class Solver:
         self._check(self.lib.fg_residual(self.ctx, C.byref(em), C.byref(ec), C.byref(ms)))
         return em.value, ec.value, ms.value
 
-    def get(self, field):
+    def get(self, field, device=None):
+        """A field as a numpy array, or (device given, e.g. "cuda") as a CUDA tensor copied
+        on the device."""
         n = 9 if field in (FIELD_F, FIELD_P) else 1
-        out = np.empty((n,) + self.shape if n == 9 else self.shape)
+        shp = (3, 3) + self.shape if n == 9 else self.shape
+        if device is not None:
+            import torch
+            out = torch.empty(shp, dtype=torch.float64, device=device)
+            self._check(self.lib.fg_get_field(self.ctx, field, _ptr(out), 1))
+            return out
+        out = np.empty(shp)
         self._check(self.lib.fg_get_field(self.ctx, field, _ptr(out), 0))
-        return out.reshape((3, 3) + self.shape) if n == 9 else out
+        return out
 
     def set(self, field, value):
-        v = _f64(value).ravel()
-        self._check(self.lib.fg_set_field(self.ctx, field, _ptr(v), 0))
+        """Overwrites a stored field from a host array or a CUDA tensor."""
+        v = _arg64(value)
+        self._check(self.lib.fg_set_field(self.ctx, field, _ptr(v), int(_on_device(v))))
 
     def apply(self, op, x, y, prec=0, dt=1.0):
         """y = op(x) on device buffers (torch tensors); returns <x, y>."""
@@ -254,9 +290,10 @@ class Solver:
         return st.as_dict()
 
     def adjoint_mech(self, W):
-        """dL/dlogE for a loss with dL/dF = W (host array (3, 3, ...) or device tensor)."""
-        Wh = W if hasattr(W, "data_ptr") else _f64(W).ravel()
-        g = np.empty(self.shape)
+        """dL/dlogE for a loss with dL/dF = W (host array (3, 3, ...) or CUDA tensor; the
+        gradient comes back the same way)."""
+        Wh = _arg64(W)
+        g = _out64(self.shape, Wh)
         it = C.c_int()
         self._check(self.lib.fg_adjoint_mech(self.ctx, _ptr(Wh), _ptr(g), C.byref(it)))
         return g, it.value
@@ -283,8 +320,9 @@ class Solver:
     def adjoint(self, loss=FG_LOSS_CRACK_ENERGY, seed_c=None, seed_F=None, seed_d=None):
         """Reverse of the recorded steps: returns (loss value, dict(E, gc, D) of per-voxel
         dL/dlog E, dL/dlog g_c, dL/dlog D, statistics)."""
-        seeds = [None if a is None else _f64(a).ravel() for a in (seed_c, seed_F, seed_d)]
-        g = {k: np.empty(self.shape) for k in ("E", "gc", "D")}
+        seeds = [None if a is None else _arg64(a) for a in (seed_c, seed_F, seed_d)]
+        like = next((a for a in seeds if a is not None), None)
+        g = {k: _out64(self.shape, like) for k in ("E", "gc", "D")}
         val = C.c_double()
         st = AdjStats()
         self._check(self.lib.fg_adjoint(self.ctx, int(loss),
@@ -298,19 +336,21 @@ class Solver:
         current state): (Fbar - I) x + u~ with grad u~ = F - Fbar (fg_displacement)."""
         if (F is None) != (Fbar is None):
             raise ValueError("F and Fbar are given together")
-        u = np.empty((3,) + self.shape)
-        Fa = None if F is None else _f64(F).ravel()
+        Fa = None if F is None else _arg64(F)
         Fb = None if Fbar is None else _f64(Fbar).ravel()
+        u = _out64((3,) + self.shape, Fa)
         self._check(self.lib.fg_displacement(self.ctx, None if Fa is None else _ptr(Fa),
-                                             None if Fb is None else _ptr(Fb), _ptr(u), 0))
+                                             None if Fb is None else _ptr(Fb), _ptr(u),
+                                             int(_on_device(u))))
         return u
 
     def displacement_adjoint(self, r):
         """(du~/dF)^T r for r (3, nz, ny, nx): a (3, 3, nz, ny, nx) field
         (fg_displacement_adjoint)."""
-        ra = _f64(r).ravel()
-        g = np.empty((3, 3) + self.shape)
-        self._check(self.lib.fg_displacement_adjoint(self.ctx, _ptr(ra), _ptr(g), 0))
+        ra = _arg64(r)
+        g = _out64((3, 3) + self.shape, ra)
+        self._check(self.lib.fg_displacement_adjoint(self.ctx, _ptr(ra), _ptr(g),
+                                                     int(_on_device(g))))
         return g
 
     def autotune(self):

@@ -104,6 +104,27 @@ def build_gpu(jobs=None, verbose=False):
     return out
 
 
+def build_comparator():
+    """Compile libfg_cufft.so, the cuFFT-based comparator of the mechanical operator that
+    bench.py times beside the fused path (csrc/comparator/, linked with cuFFT; only its
+    fgc_* functions are exported).  Returns its path."""
+    nvcc = _nvcc()
+    os.makedirs(LIBDIR, exist_ok=True)
+    out = os.path.join(LIBDIR, "libfg_cufft.so")
+    src = os.path.join(CSRC, "comparator", "fg_cufft_cmp.cu")
+    flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+             "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE, "-shared"] + ARCH
+    stamp = _digest([src] + _headers(), flags)
+    stamp_file = out + ".stamp"
+    if os.path.exists(out) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:
+        return out
+    lib = os.path.join(_cuda_home(nvcc), "lib64")
+    _run([nvcc, src, "-o", out] + flags + ["-L", lib, "-lcufft", "-lcudart"])
+    with open(stamp_file, "w") as f:
+        f.write(stamp)
+    return out
+
+
 def build_emu(jobs=None):
     """Compile the host-emulation library libfg_emu.so (test fixture); returns its path."""
     nvcc = _nvcc()
