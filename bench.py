@@ -37,6 +37,29 @@ UNIT = "voxel-steps/s"
 MEASURED_TRAFFIC_B_PER_VOXEL = {"xi": 203.6, "xf": 181.2}
 
 
+# SURVEY's algorithmic minimum of one FP32 mechanical operator application, per voxel:
+# read x (9 x 4 B) and the state (F 9 x 4 B, c, d, phase), write y (9 x 4 B)
+MECH_ALG_B_PER_VOXEL = 116.0
+# DRAM bytes per voxel that ncu measured over the five kernels of one FP32 mechanical
+# operator application (fg_time_apply) on a 256 x 256 x 64 grid (x rows of 256), summed over
+# the kernels and divided by the voxels; None until captured for the kernels as they are
+MEASURED_APPLY_TRAFFIC_B_PER_VOXEL = None
+
+
+def APPLY_SCHEDULED_B_PER_VOXEL(nx):
+    """Bytes per voxel the five passes of one FP32 operator application schedule: X-fwd reads
+    x and the packed 12-real state and writes the half spectrum, Y-fwd, Z and Y-inv read and
+    write it, X-inv reads it and writes y (its <x, y> reads x once more)."""
+    spec = 72.0 * (nx // 2 + 1) / nx
+    return (36 + 48 + spec) + 3 * (2 * spec) + (spec + 36 + 36)
+
+
+def _apply_traffic(nx, V):
+    if MEASURED_APPLY_TRAFFIC_B_PER_VOXEL is None or nx != 256:
+        return None
+    return MEASURED_APPLY_TRAFFIC_B_PER_VOXEL * V
+
+
 def site_bytes(nx):
     spec = 72.0 * (nx // 2 + 1) / nx
     return {0: 36 + 36 + 48 + 36 + spec,   # X-fwd: read r, p, tangent state; write p, spectrum
@@ -77,6 +100,14 @@ def job_throughput(voxels_per_rank, world, seconds_per_step):
     return voxels_per_rank * world / seconds_per_step
 
 
+# untimed steps before the warm-up: the timed window (after 5 warm-up steps, 20 timed) then
+# covers steps 51-70 of the 100-step schedule, whose step times sit at the median of steps
+# 11-100 (measured on a GB300: 987 ms, rising from 850 ms at step 11 to 1140 ms at step
+# 100 as the Krylov counts grow).  The particle does not crack within the 100 steps (max d
+# stays 0), so the phase-field solve is timed on the damaging Sec. 5.1 disc instead
+START_STEPS = 45
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -85,7 +116,22 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=256, help="grid edge of the particle workload")
     p.add_argument("--nz", type=int, default=0, help="override the z extent (profiling cases)")
-    p.add_argument("--fp64-steps", type=int, default=1, help="FP64 comparison steps (0: skip)")
+    p.add_argument("--start", type=int, default=START_STEPS,
+                   help="untimed steps before the warm-up (the timed window's position in the "
+                        "100-step schedule)")
+    p.add_argument("--site-steps", type=int, default=2,
+                   help="steps of the separate per-kernel profiling pass")
+    p.add_argument("--fp64-steps", type=int, default=1,
+                   help="FP64 comparison from the window's first state (0: skip)")
+    p.add_argument("--adjoint-steps", type=int, default=2,
+                   help="taped steps of the 128^3 adjoint timing added to the line (0: skip)")
+    p.add_argument("--batch-rves", type=int, default=64,
+                   help="RVEs of the batch timing added to the line (0: skip)")
+    p.add_argument("--damage-steps", type=int, default=3,
+                   help="damaging steps of the 512^2 Sec. 5.1 disc timed for the line (0: skip)")
+    p.add_argument("--profile-apply", type=int, default=0,
+                   help="only run this many FP32 mechanical operator applications on the "
+                        "workload (a small case for ncu captures) and print their time")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -229,82 +275,137 @@ def _cores():
         return 1
 
 
-def cufft_comparator(sol, w, reps=10, device="cuda"):
-    """The FP32 Neo-Hookean mechanical operator y = G : F^-1[F[K : x]] of the stored state
-    assembled from torch element-wise kernels and torch.fft (cuFFT), unfused: the timed
-    comparator for the fused apply.  Returns (ms per apply, max |y - y_fused| / max |y|)."""
+def cufft_comparator(sol, w, device="cuda", reps=10):
+    """The same FP32 mechanical operator built from cuFFT's batched 3D real transforms over
+    the nine components and two separate element-wise kernels (tangent, projection),
+    libfg_cufft.so: the timed library comparator of the fused apply.  Returns (ms per
+    apply, max |y - y_fused| / max |y_fused|)."""
+    import ctypes as C
     import numpy as np
     import torch
-    from paper_2411_16583_gb300 import binding as B
-    dev = torch.device(device)
-    nz, ny, nx = w.shape
+    from paper_2411_16583_gb300 import binding as B, build
+    lib = C.CDLL(build.build_comparator())
+    lib.fgc_last_error.restype = C.c_char_p
     V = w.nvox
-    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, torch.float32)
-    F = f32(sol.get(B.FIELD_F).reshape(3, 3, V))
-    c = f32(sol.get(B.FIELD_C).ravel())
-    d = f32(sol.get(B.FIELD_D).ravel())
+    nz, ny, nx = w.shape
     pid = w.phase_id.ravel()
-    tab = lambda attr: f32(np.array([getattr(p, attr) for p in w.phases])[pid])
-    E, nu, Om, c0 = tab("E"), tab("nu"), tab("Omega"), tab("c0")
-    if w.log_E is not None:
-        E = E * f32(np.exp(w.log_E.ravel()))
+    tab = lambda attr: np.array([getattr(p, attr) for p in w.phases])[pid]
+    E = tab("E") * (np.exp(w.log_E.ravel()) if w.log_E is not None else 1.0)
+    nu = tab("nu")
     lam = E * nu / ((1 + nu) * (1 - 2 * nu))
     mu = E / (2 * (1 + nu))
-    a = (1 + Om * (c - c0)) ** (-1.0 / 3.0)
-    g = (1 - d) ** 2
-    Fe = (a * F).permute(2, 0, 1)                       # (V, 3, 3)
-    # F_e^-T = cof(F_e) / det F_e, written out (element-wise kernels only)
-    f = [[Fe[:, i, j] for j in range(3)] for i in range(3)]
-    cof = torch.stack([torch.stack([f[(i + 1) % 3][(j + 1) % 3] * f[(i + 2) % 3][(j + 2) % 3]
-                                    - f[(i + 1) % 3][(j + 2) % 3] * f[(i + 2) % 3][(j + 1) % 3]
-                                    for j in range(3)], dim=1) for i in range(3)], dim=1)
-    J = (Fe[:, 0, :] * cof[:, 0, :]).sum(dim=1)
-    Bt = cof / J[:, None, None]
-    lnJ = torch.log(J)
-    s1, s2, s3 = (g * a * a)[:, None, None], (mu - lam * lnJ)[:, None, None], lam[:, None, None]
-
-    def tangent(X):                                     # X (V, 3, 3): K : X
-        M = Bt @ X.transpose(1, 2) @ Bt
-        tr = (Bt * X).sum(dim=(1, 2))[:, None, None]
-        return s1 * (mu[:, None, None] * X + s2 * M + s3 * tr * Bt)
-
-    def freq(n, h):
-        k = torch.arange(n, device=dev, dtype=torch.float64)
-        q = 2 * np.pi * k / n
-        return (2.0 / h) * torch.sin(q / 2), torch.cos(q / 2)
-    (sx, cx), (sy, cy), (sz, cz) = freq(nx, w.h[0]), freq(ny, w.h[1]), freq(nz, w.h[2])
-    sx, cx = sx[: nx // 2 + 1], cx[: nx // 2 + 1]
-    cx[-1] = 0.0 if nx % 2 == 0 else cx[-1]
-    cy[ny // 2] = 0.0 if ny % 2 == 0 else cy[ny // 2]
-    cz[nz // 2] = 0.0 if nz % 2 == 0 else cz[nz // 2]
-    Z, Y, X_ = torch.meshgrid(torch.arange(nz, device=dev), torch.arange(ny, device=dev),
-                              torch.arange(nx // 2 + 1, device=dev), indexing="ij")
-    n = torch.stack([sx[X_] * cy[Y] * cz[Z], cx[X_] * sy[Y] * cz[Z], cx[X_] * cy[Y] * sz[Z]]).float()
-    n2 = (n * n).sum(0)
-    inv = torch.where(n2 > 0, 1.0 / n2, torch.zeros_like(n2))
-
-    def apply(x):                                       # x (9, V)
-        tau = tangent(x.reshape(3, 3, V).permute(2, 0, 1)).permute(1, 2, 0).reshape(3, 3, nz, ny, nx)
-        T = torch.fft.rfftn(tau, dim=(-3, -2, -1))
-        An = torch.einsum("imzyx,mzyx->izyx", T, n.to(T.dtype))
-        Y_ = torch.einsum("izyx,jzyx->ijzyx", An * inv, n.to(T.dtype))
-        return torch.fft.irfftn(Y_, s=(nz, ny, nx), dim=(-3, -2, -1)).reshape(9, V)
-    x = torch.randn(9, V, dtype=torch.float32, generator=torch.Generator().manual_seed(0)).to(dev)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+    F = sol.get(B.FIELD_F, device=device)
+    c = sol.get(B.FIELD_C, device=device)
+    d = sol.get(B.FIELD_D, device=device)
+    L, M, Om, c0 = dev(lam), dev(mu), dev(tab("Omega")), dev(tab("c0"))
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(9 * V, dtype=torch.float32, generator=g).to(device)
+    y = torch.empty_like(x)
     yf = torch.empty_like(x)
     sol.apply(B.OP_MECH, x, yf, prec=1)
-    y = apply(x)
+    ms = C.c_float()
+    torch.cuda.synchronize()
+    P = lambda t: C.c_void_p(t.data_ptr())
+    rc = lib.fgc_mech_apply(nx, ny, nz, C.c_double(w.h[0]), C.c_double(w.h[1]),
+                            C.c_double(w.h[2]), P(F), P(c), P(d), P(L), P(M), P(Om), P(c0),
+                            P(x), P(y), reps, C.byref(ms),
+                            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError(lib.fgc_last_error().decode())
     diff = float((y - yf).abs().max() / yf.abs().max())
-    if dev.type != "cuda":
-        return None, diff
-    torch.cuda.synchronize()
+    return float(ms.value), diff
+
+
+def crack_energy(d, w):
+    """Fracture energy sum g_c (d^2/(2 l_c) + l_c/2 |grad_f d|^2) h^3 (Eq. crack) of a CUDA
+    tensor d (nz, ny, nx), forward differences with periodic wrap; a reported figure."""
+    import torch
+    g2 = torch.zeros_like(d)
+    for axis, h in ((2, w.h[0]), (1, w.h[1]), (0, w.h[2])):
+        if d.shape[axis] > 1:
+            g2 += ((torch.roll(d, -1, axis) - d) / h) ** 2
+    dens = w.gc * (d * d / (2 * w.lc) + 0.5 * w.lc * g2)
+    return float(dens.sum()) * w.h[0] * w.h[1] * w.h[2]
+
+
+def _state(sol):
+    """Device copies of the evolving state (F, c, d, H)."""
+    from paper_2411_16583_gb300 import binding as B
+    return {f: sol.get(f, device="cuda") for f in (B.FIELD_F, B.FIELD_C, B.FIELD_D, B.FIELD_H)}
+
+
+def _restore(sol, st):
+    for f, t in st.items():
+        sol.set(f, t)
+
+
+def _timed_step(sol, w, stream):
+    """One coupled step timed with CUDA events on the context's stream: (ms, stats)."""
+    import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    cur = torch.cuda.current_stream()
-    e0.record(cur)
-    for _ in range(reps):
-        y = apply(x)
-    e1.record(cur)
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps, diff
+    e0.record(stream)
+    st = sol.step(w.dt)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), st
+
+
+def fp64_split(w, sol, state0, stream):
+    """From one saved state of the mixed run: a mixed step, an FP64 step at the FP64
+    form's Krylov tolerance and an FP64 step at the mixed form's inner (forcing) tolerance.
+    Reports the three times and Krylov counts, and the mixed step's per-field error against
+    the FP64 step (max |dF| / max |F|, the same for c, max |dd|, and the fracture energy's
+    relative error)."""
+    from paper_2411_16583_gb300 import binding as B
+    out = {}
+    _restore(sol, state0)
+    ms_m, st_m = _timed_step(sol, w, stream)
+    mixed = _state(sol)
+    forcing = sol.opts.cg_forcing
+    runs = {"fp64": {}, "fp64_at_forcing": {"tol_cg": forcing, "tol_chem_cg": forcing}}
+    ref = None
+    for name, kw in runs.items():
+        s64 = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream, **kw)
+        _restore(s64, state0)
+        ms, st = _timed_step(s64, w, stream)
+        out[name] = {"ms": ms, "stats": st}
+        if name == "fp64":
+            ref = _state(s64)
+        s64.close()
+    out["mixed"] = {"ms": ms_m, "stats": st_m}
+    rel = lambda a, b: float((a - b).abs().max() / b.abs().max())
+    gm, gr = crack_energy(mixed[B.FIELD_D], w), crack_energy(ref[B.FIELD_D], w)
+    out["mixed_vs_fp64_error"] = {
+        "F_max_rel": rel(mixed[B.FIELD_F], ref[B.FIELD_F]),
+        "c_max_rel": rel(mixed[B.FIELD_C], ref[B.FIELD_C]),
+        "d_max_abs": float((mixed[B.FIELD_D] - ref[B.FIELD_D]).abs().max()),
+        "crack_energy_rel": abs(gm - gr) / gr if gr > 0 else None,
+        "crack_energy_fp64": gr,
+        "bars": {"F_max_rel": 1e-7, "c_max_rel": 1e-7, "d_max_abs": 1e-6, "crack_energy_rel": 1e-6}}
+    out["precision_speedup"] = out["fp64_at_forcing"]["ms"] / ms_m
+    out["krylov_speedup"] = out["fp64"]["ms"] / out["fp64_at_forcing"]["ms"]
+    return out
+
+
+def _oracle_worker(args):
+    n, budget, counts = args
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    w = _workload(n, 0)
+    return oracle_step_seconds(w, budget, counts)[0]
+
+
+def oracle_all_cores(n, budget_s, counts):
+    """The oracle's operator sample on every host core at once: one process per core (spawn,
+    one BLAS thread each), each timing the same sample on its own copy of the n^3 fields
+    with the given per-step operator counts.  Returns (voxel-steps/s of all processes
+    together, processes)."""
+    import multiprocessing as mp
+    procs = max(1, os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        secs = pool.map(_oracle_worker, [(n, budget_s, counts)] * procs)
+    return sum(n ** 3 / s for s in secs), procs
 
 
 def main():
@@ -315,48 +416,78 @@ def main():
     if a.impl == "reference":
         return reference_arm(a, rank, world)
     if a.batch:
-        return batch_mode(a)
+        print(json.dumps(batch_mode(a.batch, a.steps, a.warmup)))
+        return
     if a.adjoint:
-        return adjoint_mode(a)
-    import numpy as np
+        print(json.dumps(adjoint_mode(a.n if a.n != 256 else 128, a.steps, a.warmup)))
+        return
+    if a.profile_apply:
+        print(json.dumps(profile_apply(a)))
+        return
     import torch
-    from paper_2411_16583_gb300 import binding as B
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()  # a capturable stream: the CG's CUDA graphs replay on it
+    with torch.cuda.stream(stream):
+        line = run_ours(a, rank, world, local, dist, stream)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_ours(a, rank, world, local, dist, stream):
+    import torch
+    from paper_2411_16583_gb300 import binding as B
     w = _workload(a.n, seed=rank, nz=a.nz)
-    stream = torch.cuda.current_stream()
     sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
     V = w.nvox
     tuned_ms = sol.autotune()
+    for _ in range(a.start):  # advance to the measured window (untimed)
+        sol.step(w.dt)
     for _ in range(a.warmup):
         sol.step(w.dt)
+    state0 = _state(sol) if (a.fp64_steps > 0 and rank == 0) else None
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for s in range(5):
-        sol.profile(s, True)
-    stats = []
+    stats, step_ms = [], []
     with Clocks(local) as clk:
         barrier()
         l0 = B.kernel_launches()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(a.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+        ev[0].record(stream)
+        for k in range(a.steps):
             stats.append(sol.step(w.dt))
-        e1.record(stream)
+            ev[k + 1].record(stream)
         barrier()
         launches = B.kernel_launches() - l0
-    ms = e0.elapsed_time(e1) / a.steps
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(a.steps)]
+    ms = max_over_ranks(ev[0].elapsed_time(ev[-1]) / a.steps, dist, "cuda")
+    d_end = sol.get(B.FIELD_D, device="cuda")
+    window = {"first_step": a.start + a.warmup + 1, "last_step": a.start + a.warmup + a.steps,
+              "median_step_ms": statistics.median(step_ms), "min_step_ms": min(step_ms),
+              "max_step_ms": max(step_ms),
+              "steps_with_phase_field_cg": sum(1 for s in stats if s["cg_pff"] > 0),
+              "damaged_voxels_at_end": int((d_end > 1e-3).sum()), "d_max_at_end": float(d_end.max()),
+              "cg_graph_replays": sum(s["cg_graph_replays"] for s in stats),
+              "totals": {k: sum(s[k] for s in stats) for k in
+                         ("newton_chem", "newton_mech", "cg_chem", "cg_mech", "cg_pff", "stag")}}
+    del d_end
+
+    # per-site kernel times of the mechanical CG in a separate pass (CUDA events around
+    # every launch of a site; graphs do not replay while a site is profiled)
+    for s in range(5):
+        sol.profile(s, True)
+    for _ in range(a.site_steps):
+        sol.step(w.dt)
     prof = {s: sol.profile_read(s) for s in range(5)}
     for s in range(5):
         sol.profile(s, False)
-    ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end through the same public calls with host buffers: each step copies the
     # state (F, c, d, H) in from pinned host memory and the new (F, c, d) back out
@@ -382,33 +513,41 @@ def main():
                "h2d_bytes_per_step": 12 * V * 8,
                "d2h_bytes_per_step": 11 * V * 8}
 
-    # fused matvec rates: FP32 operator of the mixed context, and the unfused cuFFT
-    # comparator of the same operator
-    mech32_ms = sol.time_apply(B.OP_MECH, 1, 20)
-    comparator = None
-    if w.phases[0].law == B.FG_NEOHOOKE and rank == 0:
+    # fused matvec rates (SURVEY's measurement: 50 applies after 5 warm-ups, CUDA events):
+    # the FP32 operators of the mixed context, and the cuFFT comparator of the mechanical one
+    sol.time_apply(B.OP_MECH, 1, 5)
+    mech32_ms = sol.time_apply(B.OP_MECH, 1, 50)
+    matvec = {"mech_fp32_ms": mech32_ms, "mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3)}
+    for name, op, prec in (("pff_fp32", B.OP_PFF, 1), ("pff_prec_fp32", B.OP_PFF_PREC, 1),
+                           ("chem_fp32", B.OP_CHEM, 1), ("gres_fp64", B.OP_GRES, 0)):
+        t = sol.time_apply(op, prec, 20)
+        matvec[name + "_ms"] = t
+        matvec[name + "_voxel_applies_per_s"] = V / (t * 1e-3)
+    if rank == 0:
         try:
             cms, cdiff = cufft_comparator(sol, w)
-            comparator = {"kind": "torch element-wise + torch.fft (cuFFT), unfused, FP32",
-                          "ms_per_apply": cms, "voxel_applies_per_s": V / (cms * 1e-3),
-                          "max_rel_diff_vs_fused": cdiff}
-        except torch.cuda.OutOfMemoryError as e:  # noqa: F841
-            comparator = {"unavailable": "out of device memory"}
-    sol.close()
+            matvec["cufft_comparator"] = {
+                "kind": "cuFFT batched 3D R2C/C2R over the nine components (cufftPlanMany) + "
+                        "separate tangent and projection kernels, FP32",
+                "ms_per_apply": cms, "voxel_applies_per_s": V / (cms * 1e-3),
+                "max_rel_diff_vs_fused": cdiff, "fused_speedup": cms / mech32_ms}
+        except Exception as e:  # noqa: BLE001
+            matvec["cufft_comparator"] = {"unavailable": str(e)[:200]}
     out = {}
-    if a.fp64_steps > 0 and rank == 0:
-        sol64 = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream)
-        mech64_ms = sol64.time_apply(B.OP_MECH, 0, 5)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s64 = [sol64.step(w.dt) for _ in range(a.fp64_steps)]
-        torch.cuda.synchronize()
-        out["fp64_step_ms"] = (time.perf_counter() - t0) * 1e3 / a.fp64_steps
-        out["fp64_step_stats"] = s64[-1]
-        out["mech_fp64_voxel_applies_per_s"] = V / (mech64_ms * 1e-3)
-        sol64.close()
+    if state0 is not None:
+        out["fp64_split"] = fp64_split(w, sol, state0, stream)
+        out["fp64_step_ms"] = out["fp64_split"]["fp64"]["ms"]
+        del state0
+    sol.close()
     if rank != 0:
-        return
+        return None
+    if a.fp64_steps > 0:
+        s64 = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream)
+        s64.time_apply(B.OP_MECH, 0, 2)
+        t64 = s64.time_apply(B.OP_MECH, 0, 10)
+        matvec["mech_fp64_ms"] = t64
+        matvec["mech_fp64_voxel_applies_per_s"] = V / (t64 * 1e-3)
+        s64.close()
     peaks, src = _peaks()
     sb = site_bytes(w.shape[2])
     sites = {}
@@ -417,11 +556,11 @@ def main():
             sites[SITE_NAMES[s]] = {"launches": n, "total_ms": t, "volumes": vol,
                                     "us_per_volume": t * 1e3 / vol,
                                     "alg_bytes_per_voxel": sb[s],
-                                    "gbs": sb[s] * V * vol / (t * 1e-3) / 1e9}
-    dom = max((s for s in prof if prof[s][0]), key=lambda s: prof[s][1])
-    n_dom, t_dom, vol_dom = prof[dom]
-    avg_dom = t_dom / n_dom * 1e-3           # seconds per launch
-    ach = sb[dom] * V * vol_dom / (t_dom * 1e-3) / 1e9
+                                    "gbs": sb[s] * V * vol / (t * 1e-3) / 1e9,
+                                    "frac_of_peak": sb[s] * V * vol / (t * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    # the roofline of SURVEY's measurement: one fused mechanical operator application (five
+    # pass kernels) moves at least 116 B per voxel (read x and the state, write y)
+    ach = MECH_ALG_B_PER_VOXEL * V / (mech32_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC,
         "value": job_throughput(V, world, ms * 1e-3),
@@ -435,43 +574,116 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"rough ellipsoid particle {a.n}^3 (coupled step, mixed "
-                               f"FP32 Krylov / FP64 Newton, tol 1e-9)",
-                   "voxels": V, "l2": "inputs larger than L2 (no flush)"},
+        "config": {"workload": f"rough ellipsoid particle {a.n}^3 (coupled step of Alg. 4, mixed "
+                               f"FP32 Krylov / FP64 Newton, tol 1e-9); buffer E x 1e-2 of the "
+                               f"particle's; smooth Gaussian concentration field of std 0.02 "
+                               f"around c = 0.07 inside the particle, whose stress-free c0 is "
+                               f"0.07; 100-step influx schedule, timed steps "
+                               f"{window['first_step']}-{window['last_step']} after "
+                               f"{a.start} untimed steps and {a.warmup} warm-up steps",
+                   "voxels": V, "l2": "inputs larger than L2 (no flush)",
+                   "stream": "non-default (CUDA-graph replays on), profiling off"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": SITE_NAMES[dom], "achieved": ach,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-                     "peak_source": src,
-                     "alg_bytes_per_launch": sb[dom] * V * vol_dom / n_dom,
-                     "avg_launch_us": avg_dom * 1e6,
-                     "traffic": _traffic(dom, w.shape[2], V * vol_dom / n_dom)},
+        "roofline": {"bound": "hbm",
+                     "kernel": "fused FP32 mechanical operator application (five pass kernels: "
+                               "X-fwd tangent + R2C, Y-fwd, Z + projection, Y-inv, C2R X-inv)",
+                     "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                     "alg_bytes_per_launch": MECH_ALG_B_PER_VOXEL * V,
+                     "avg_launch_us": mech32_ms * 1e3,
+                     "traffic": _apply_traffic(w.shape[2], V),
+                     "scheduled_bytes_per_voxel": APPLY_SCHEDULED_B_PER_VOXEL(w.shape[2])},
+        "window": window,
         "kernels": sites,
-        "matvec": {"mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3),
-                   "mech_fp32_ms": mech32_ms, "cufft_comparator": comparator},
+        "matvec": matvec,
         "step_stats": stats[-1],
         "autotuned_apply_ms": tuned_ms,
         "clocks": clk.summary(),
     }
     line.update(out)
+    if a.adjoint_steps > 0:
+        try:
+            line["adjoint"] = adjoint_mode(128, a.adjoint_steps, 1)
+        except Exception as e:  # noqa: BLE001
+            line["adjoint"] = {"unavailable": str(e)[:200]}
+    if a.damage_steps > 0:
+        try:
+            line["damaging"] = damaging_window(a.damage_steps)
+        except Exception as e:  # noqa: BLE001
+            line["damaging"] = {"unavailable": str(e)[:200]}
+    if a.batch_rves > 0:
+        try:
+            line["batch"] = batch_mode(a.batch_rves, 2, 1)
+        except Exception as e:  # noqa: BLE001
+            line["batch"] = {"unavailable": str(e)[:200]}
     if not a.no_cpu_baseline:
         # the oracle is an FP64 method: its step takes the FP64 form's operator counts (of
         # this run when it timed an FP64 step, else those recorded at 256^3)
-        counts = out.get("fp64_step_stats") or DEFAULT_STEP_PROFILE
+        counts = out.get("fp64_split", {}).get("fp64", {}).get("stats") or DEFAULT_STEP_PROFILE
         prof_counts = {k: counts[k] for k in DEFAULT_STEP_PROFILE}
         secs, desc = oracle_step_seconds(w, a.cpu_seconds, prof_counts)
-        line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": _cores(),
+        line["cpu_baseline"] = {"value": V / secs, "unit": UNIT, "cores": 1,
                                 "kind": "oracle", "sample": desc}
-    print(json.dumps(line))
+        try:
+            allv, procs = oracle_all_cores(128, a.cpu_seconds / 2, prof_counts)
+            line["cpu_baseline_all_cores"] = {
+                "value": allv, "unit": UNIT, "cores": procs,
+                "kind": "oracle",
+                "sample": f"{procs} processes, each timing the oracle's operator sample on "
+                          f"128^3 fields with the recorded 256^3 step counts; voxel-steps/s "
+                          f"summed over the processes"}
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline_all_cores"] = {"unavailable": str(e)[:200]}
+    return line
 
 
-def adjoint_mode(a):
-    """Forward steps with a tape, then the reverse pass for dL/dlog(E, g_c, D) of a loss
-    with random seeds on the final state; both timed with CUDA events on the context's
-    stream (FP64 throughout)."""
+def profile_apply(a):
+    """n FP32 mechanical operator applications (fg_time_apply) on the workload's state after
+    set-up: the command that ncu captures of the five pass kernels run."""
+    import torch
+    from paper_2411_16583_gb300 import binding as B
+    w = _workload(a.n, 0, nz=a.nz)
+    stream = torch.cuda.Stream()
+    sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
+    ms = sol.time_apply(B.OP_MECH, 1, a.profile_apply)
+    sol.close()
+    return {"mode": "profile-apply", "shape": list(w.shape), "applies": a.profile_apply,
+            "ms_per_apply": ms}
+
+
+def damaging_window(steps):
+    """The Sec. 5.1 disc (512^2 Saint-Venant-Kirchhoff, Gumbel-distributed stiffness and
+    strength, Omega = 1.3, 200-step schedule), mixed precision on a side stream: its first
+    step is undamaged, the next `steps` crack, so they time the phase-field solves (Alg. 2)
+    and the staggered iterations (Alg. 4).  Returns per-step times and counts."""
     import torch
     from paper_2411_16583_gb300 import binding as B, synth as S
-    n = a.n if a.n != 256 else 128
+    w = S.gumbel_disc()
+    stream = torch.cuda.current_stream()
+    sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
+    sol.step(w.dt)
+    rows = []
+    for k in range(steps):
+        ms, st = _timed_step(sol, w, stream)
+        d = sol.get(B.FIELD_D, device="cuda")
+        rows.append({"step": k + 2, "ms": ms, "stag": st["stag"], "cg_pff": st["cg_pff"],
+                     "cg_mech": st["cg_mech"], "cg_chem": st["cg_chem"],
+                     "damaged_voxels": int((d > 1e-3).sum()), "d_max": float(d.max())})
+    sol.close()
+    return {"workload": "Sec. 5.1 disc 512^2 x 1 (Saint-Venant-Kirchhoff, Gumbel stiffness and "
+                        "strength, Omega = 1.3, full chemistry Jacobian, 200-step schedule), "
+                        "mixed precision", "voxels": w.nvox, "steps": rows,
+            "ms_per_step": sum(r["ms"] for r in rows) / len(rows)}
+
+
+def adjoint_mode(n, steps, warmup):
+    """Forward steps with a tape, then the reverse pass for dL/dlog(E, g_c, D) of a loss
+    with random seeds on the final state; both timed with CUDA events on the context's
+    stream (FP64 throughout).  Returns a dict."""
+    import numpy as np
+    import torch
+    from paper_2411_16583_gb300 import binding as B, synth as S
     w = S.with_log_fields(S.ellipsoid(n=n, axes=(50 * n / 128, 40 * n / 128, 35 * n / 128),
                                       rough_std=1.5 * n / 128, rough_corr=4 * n / 128,
                                       band=max(1, round(8 * n / 128)), nsteps=50,
@@ -479,79 +691,82 @@ def adjoint_mode(a):
                           std=0.1)
     stream = torch.cuda.current_stream()
     sol = B.from_workload(w, precision=B.FG_FP64, stream=stream.cuda_stream)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         sol.step(w.dt)
     sol.tape(5)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     e[0].record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         sol.step(w.dt)
     e[1].record(stream)
     # a loss with seeded random dL/d(c, F, d) on the final state: every adjoint solve
     # runs (the fracture energy is zero until damage starts)
-    import numpy as np
     rng = np.random.default_rng(0)
-    val, g, st = sol.adjoint(B.FG_LOSS_SEEDS, seed_c=rng.standard_normal(w.shape),
-                             seed_F=rng.standard_normal((3, 3) + w.shape),
-                             seed_d=rng.standard_normal(w.shape))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    val, g, st = sol.adjoint(B.FG_LOSS_SEEDS, seed_c=dev(rng.standard_normal(w.shape)),
+                             seed_F=dev(rng.standard_normal((3, 3) + w.shape)),
+                             seed_d=dev(rng.standard_normal(w.shape)))
     e[2].record(stream)
     torch.cuda.synchronize()
     fwd = e[0].elapsed_time(e[1])
     rev = e[1].elapsed_time(e[2])
-    print(json.dumps({"metric": "coupled adjoint: reverse-pass wall time per step", "value":
-                      rev / a.steps, "unit": "ms/step", "higher_is_better": False,
-                      "config": {"workload": f"rough ellipsoid {n}^3, per-voxel log E, log g_c, "
-                                 f"log D ~ N(0, 0.1^2), FP64, checkpoint every 5 steps, "
-                                 f"loss with random seeds on the final (c, F, d)",
-                                 "steps": a.steps, "warmup": a.warmup},
-                      "forward_ms_per_step": fwd / a.steps, "loss": val, "adjoint_stats": st,
-                      "grad_max": {k: float(abs(v).max()) for k, v in g.items()}}))
     sol.close()
+    return {"metric": "coupled adjoint: reverse-pass wall time per step", "value": rev / steps,
+            "unit": "ms/step", "higher_is_better": False,
+            "config": {"workload": f"rough ellipsoid {n}^3, per-voxel log E, log g_c, "
+                                   f"log D ~ N(0, 0.1^2), FP64, checkpoint every 5 steps, "
+                                   f"loss with random seeds on the final (c, F, d)",
+                       "steps": steps, "warmup": warmup},
+            "forward_ms_per_step": fwd / steps, "reverse_over_forward": rev / fwd,
+            "adjoint_stats": st, "grad_max": {k: float(v.abs().max()) for k, v in g.items()}}
 
 
-def batch_mode(a):
+def batch_mode(count, steps, warmup):
     """Many independent particle RVEs of uneven size: one batched coupled step (members
     on their own streams, driven concurrently) against the same members stepped one by
-    one.  Reports aggregate voxel-steps/s of both."""
+    one.  Returns aggregate voxel-steps/s of both."""
     import torch
     from paper_2411_16583_gb300 import binding as B, synth as S
-    ws = S.sphere_batch(count=a.batch, nsteps=20, seed=0)
+    ws = S.sphere_batch(count=count, nsteps=20, seed=0)
     V = sum(w.nvox for w in ws)
     mk = lambda: [B.from_workload(w, precision=B.FG_MIXED) for w in ws]
     seq = mk()
     for s_, w in zip(seq, ws):
         s_.autotune()
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         for s_, w in zip(seq, ws):
             s_.step(w.dt)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(a.steps):
+    for _ in range(steps):
         for s_, w in zip(seq, ws):
             s_.step(w.dt)
     torch.cuda.synchronize()
-    t_seq = (time.perf_counter() - t0) / a.steps
+    t_seq = (time.perf_counter() - t0) / steps
     for s_ in seq:
         s_.close()
     mem = mk()
     for s_ in mem:
         s_.autotune()
     batch = B.Batch(mem)
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         batch.step(1.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(a.steps):
+    for _ in range(steps):
         st = batch.step(1.0)
     torch.cuda.synchronize()
-    t_b = (time.perf_counter() - t0) / a.steps
+    t_b = (time.perf_counter() - t0) / steps
     batch.close()
-    print(json.dumps({"mode": "batch", "rves": len(ws), "voxels": V,
-                      "sizes": sorted({w.shape[0] for w in ws}),
-                      "batched_voxel_steps_per_s": V / t_b, "sequential_voxel_steps_per_s": V / t_seq,
-                      "batched_ms_per_step": t_b * 1e3, "sequential_ms_per_step": t_seq * 1e3,
-                      "speedup": t_seq / t_b, "cg_mech_total": sum(x["cg_mech"] for x in st)}))
+    for s_ in mem:
+        s_.close()
+    return {"mode": "batch", "rves": len(ws), "voxels": V, "steps": steps, "warmup": warmup,
+            "sizes": sorted({w.shape[0] for w in ws}),
+            "batched_voxel_steps_per_s": V / t_b, "sequential_voxel_steps_per_s": V / t_seq,
+            "batched_ms_per_step": t_b * 1e3, "sequential_ms_per_step": t_seq * 1e3,
+            "speedup": t_seq / t_b, "cg_mech_total": sum(x["cg_mech"] for x in st),
+            "cg_graph_replays": sum(x["cg_graph_replays"] for x in st)}
 
 
 def reference_arm(a, rank, world):
