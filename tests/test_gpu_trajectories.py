@@ -1,0 +1,85 @@
+"""GPU trajectories against stored oracle runs: the coupled steps of Alg. 4 on the paper's
+workload types, run to their first damaging steps on the device and compared, at every
+recorded step, with the CPU oracle's fields at a fixed sample of voxels (a seeded random
+set plus the most damaged voxels) and with its whole-field summaries (total concentration,
+fracture energy of Eq. crack, damaged voxels).  The oracle runs take minutes to hours on one
+core, so ``tests/golden/make_oracle_trajectories.py`` (which calls only the oracle) wrote
+them to ``tests/golden/<case>.npz``.
+
+FP64 bars: the GPU FP64 path within 1e-10 of the oracle in F and c (relative to the field's
+largest magnitude in the sample) and 1e-8 in d and H, whose damaging solves amplify
+round-off at the crack front.  Mixed FP32/FP64 bars: 1e-7 in F and c, 1e-6 in d, and the
+fracture energy within 1e-6 relative."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2411_16583_gb300 import binding as B
+from tests.golden.make_oracle_trajectories import workload
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+BARS = {B.FG_FP64: dict(F=1e-10, c=1e-10, d=1e-8, H=1e-8, energy=1e-8),
+        B.FG_MIXED: dict(F=1e-7, c=1e-7, d=1e-6, H=1e-6, energy=1e-6)}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    assert torch.cuda.is_available()
+    return B.load_library()
+
+
+def _crack_energy(d, w):
+    """Eq. crack of a host field, forward differences with periodic wrap (independent of the
+    oracle module, which wrote the stored value)."""
+    g2 = np.zeros_like(d)
+    for axis, h in ((2, w.h[0]), (1, w.h[1]), (0, w.h[2])):
+        if d.shape[axis] > 1:
+            g2 += ((np.roll(d, -1, axis) - d) / h) ** 2
+    return float(np.sum(w.gc * (d * d / (2 * w.lc) + 0.5 * w.lc * g2))) * w.h[0] * w.h[1] * w.h[2]
+
+
+def _compare(case, precision, lib):
+    ref = np.load(os.path.join(HERE, f"{case}.npz"))
+    w = workload(case)
+    sol = B.from_workload(w, precision=precision, lib=lib)
+    steps = [int(k) for k in ref["steps"]]
+    bars = BARS[precision]
+    report = {}
+    for k in range(1, max(steps) + 1):
+        st = sol.step(w.dt)
+        assert st["status"] == 0
+        if k not in steps:
+            continue
+        idx = ref[f"idx_s{k}"]
+        F = sol.get(B.FIELD_F).reshape(9, -1)[:, idx]
+        c, d, H = (sol.get(f).ravel()[idx] for f in (B.FIELD_C, B.FIELD_D, B.FIELD_H))
+        err = {}
+        for name, got, want in (("F", F, ref[f"F_s{k}"]), ("c", c, ref[f"c_s{k}"])):
+            err[name] = float(np.abs(got - want).max() / np.abs(want).max())
+        for name, got, want in (("d", d, ref[f"d_s{k}"]), ("H", H, ref[f"H_s{k}"])):
+            scale = max(np.abs(want).max(), 1.0 if name == "d" else 1e-30)
+            err[name] = float(np.abs(got - want).max() / scale)
+        mass, energy, dmax, ndam, _ = ref[f"scal_s{k}"]
+        dfull = sol.get(B.FIELD_D)
+        e = _crack_energy(dfull, w)
+        err["energy"] = abs(e - energy) / energy if energy > 0 else abs(e)
+        report[k] = err
+        assert abs(sol.get(B.FIELD_C).sum() - mass) <= 1e-11 * mass, (k, "mass")
+        assert abs(int((dfull > 1e-3).sum()) - ndam) <= max(2, 0.01 * ndam), (k, "damaged")
+        for name, bar in bars.items():
+            assert err[name] <= bar, (case, k, name, err)
+    sol.close()
+    return report
+
+
+@pytest.mark.parametrize("precision", [B.FG_FP64, B.FG_MIXED])
+def test_plate_trajectory_matches_oracle(lib, precision):
+    """The Sec. 4.3 plate (64 x 64 x 1, Saint-Venant-Kirchhoff, Omega = 1.3, a stronger
+    influx at one corner): steps 1-5, the plate cracks in step 3."""
+    _compare("plate", precision, lib)
