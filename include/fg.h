@@ -110,6 +110,10 @@ typedef struct {
                          d(mu_e/RT)/dc (same root; converges where mu_e reaches several RT,
                          e.g. Omega = 1.3 with E = 15 GPa).  FG_ERR_NUMERIC where the full
                          dmu~/dc <= 0 */
+  int l2_prefetch;    /* 1: the X passes hand the real-space rows each block reads to the
+                         bulk-copy unit as L2 prefetches (cp.async.bulk.prefetch.L2) before
+                         they start; 0 (default): plain loads.  fg_autotune overrides it with
+                         the faster choice */
 } fg_opts;
 
 typedef struct {
@@ -225,11 +229,16 @@ int fg_solve_mech(fg_ctx* ctx, const double Fbar[9], fg_stats* st);
 int fg_adjoint_mech(fg_ctx* ctx, const double* W, double* grad_logE, int* iters);
 
 /* Autotuner: times the run-time selectable schedule of the mechanical operator on this
- * context's grid (how many kx planes the Y-Z-Y passes take per L2-sized chunk, and a
- * one-component-per-block or nine-component X-inv CG update) and keeps the fastest.
- * ms_per_iteration (may be NULL) receives the best operator time.  Allocates two
- * temporary 9 V vectors. */
+ * context's grid (how many kx planes the Y-Z-Y passes take per L2-sized chunk, L2 prefetch
+ * of the X passes on or off, and a one-component-per-block or nine-component X-inv CG
+ * update) and keeps the fastest.  ms_per_iteration (may be NULL) receives the best
+ * operator time.  Allocates two temporary 9 V vectors.
+ * fg_autotune_report returns the choices in force, choice[3] = {kx planes per chunk of
+ * the Krylov precision, X-inv update one component per block (1) or nine (0), L2 prefetch
+ * (1) or not (0)}, and (xinv_ms, may be NULL) the autotuner's X-inv update times
+ * [prefetch off, nine; off, one; on, nine; on, one] in ms (zeros before fg_autotune). */
 int fg_autotune(fg_ctx* ctx, double* ms_per_iteration);
+int fg_autotune_report(fg_ctx* ctx, int choice[3], double xinv_ms[4]);
 
 /* Launch-site profiling.  While a site is enabled, every launch at that site is
  * bracketed by two CUDA events on the context stream (at most 32768 launches are recorded

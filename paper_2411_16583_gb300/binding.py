@@ -48,7 +48,8 @@ class Opts(C.Structure):
                 ("tol_pff_cg", C.c_double), ("tol_stag", C.c_double), ("cg_forcing", C.c_double),
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
                 ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double),
-                ("cg_indefinite", C.c_int), ("chem_full_jacobian", C.c_int)]
+                ("cg_indefinite", C.c_int), ("chem_full_jacobian", C.c_int),
+                ("l2_prefetch", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -78,7 +79,7 @@ FG_LOSS_SEEDS = 1
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
-           "fg_batch_destroy", "fg_autotune", "fg_solve_mech", "fg_adjoint_mech",
+           "fg_batch_destroy", "fg_autotune", "fg_autotune_report", "fg_solve_mech", "fg_adjoint_mech",
            "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load", "fg_set_stress_control",
            "fg_displacement", "fg_displacement_adjoint", "fg_kernel_launches", "fg_destroy",
            "fg_last_error"]
@@ -112,6 +113,7 @@ def load_library(path=LIB_PATH):
     lib.fg_mech_apply_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double] + [C.c_void_p] * 9 + [dp, C.c_void_p]
     lib.fg_autotune.argtypes = [C.c_void_p, dp]
+    lib.fg_autotune_report.argtypes = [C.c_void_p, C.POINTER(C.c_int), dp]
     lib.fg_solve_mech.argtypes = [C.c_void_p, dp, C.POINTER(Stats)]
     lib.fg_adjoint_mech.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
     lib.fg_tape_begin.argtypes = [C.c_void_p, C.c_int]
@@ -357,6 +359,16 @@ class Solver:
         ms = C.c_double()
         self._check(self.lib.fg_autotune(self.ctx, C.byref(ms)))
         return ms.value
+
+    def autotune_report(self):
+        """Choices in force (kx planes per chunk, one-component X-inv update, L2 prefetch)
+        and the autotuner's X-inv update times [prefetch off/on][nine/one component]."""
+        ch = (C.c_int * 3)()
+        ms = (C.c_double * 4)()
+        self._check(self.lib.fg_autotune_report(self.ctx, ch, ms))
+        return {"kx_chunk": ch[0], "xinv_per_component": ch[1], "l2_prefetch": ch[2],
+                "xinv_ms": {"nine": ms[0], "one": ms[1], "nine_prefetch": ms[2],
+                            "one_prefetch": ms[3]}}
 
     def time_apply(self, op, prec, n):
         ms = C.c_double()

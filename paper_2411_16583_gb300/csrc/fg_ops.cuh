@@ -152,6 +152,9 @@ template <typename R, int NC>
 struct PCopy {
   static constexpr int COUT = NC;
   static constexpr bool RED = false;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = NC, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 0, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) out[c] = a.rin[c * a.V + v];
@@ -218,6 +221,9 @@ template <typename R>
 struct PTangentSVK {
   static constexpr int COUT = 9;
   static constexpr bool RED = false;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 9, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 18, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
     R p[9];
 #pragma unroll
@@ -230,6 +236,9 @@ template <typename R>
 struct PCgTangentSVK {
   static constexpr int COUT = 9;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 9, PF_ROUT = 9, PF_ROUT2 = 0,
+                       PF_AUX0 = 18, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>& acc, const R* sc) {
     const R beta = sc[1];
     const R* __restrict__ r = a.rin;
@@ -251,6 +260,9 @@ template <typename R>
 struct PTangentNH {
   static constexpr int COUT = 9;
   static constexpr bool RED = false;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 9, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 12, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>&, const R*) {
     R p[9], B[9];
 #pragma unroll
@@ -272,6 +284,9 @@ template <typename R>
 struct PCgTangentNH {
   static constexpr int COUT = 9;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 9, PF_ROUT = 9, PF_ROUT2 = 0,
+                       PF_AUX0 = 12, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>& acc, const R* sc) {
     const R beta = sc[1];
     const R* __restrict__ r = a.rin;
@@ -303,6 +318,9 @@ template <typename R>
 struct ECgUpdate1 {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 9, PF_ROUT2 = 9,
+                       PF_AUX0 = 9, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R al = sc[0];
     R* __restrict__ r = a.rout;
@@ -323,6 +341,9 @@ template <typename R>
 struct ECgUpdate {
   static constexpr int CIN = 9;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 9, PF_ROUT2 = 9,
+                       PF_AUX0 = 9, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R al = sc[0];
     const R sig = a.coef[1];
@@ -353,6 +374,9 @@ template <typename R, int NC>
 struct EStoreDot {
   static constexpr int CIN = NC;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = NC, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -381,6 +405,9 @@ template <typename R>
 struct EPff {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 1, PF_AUX1 = 1;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R p = a.aux[0][v];
     const R y = (a.coef[0] + (R)2 * a.aux[1][v]) * p + val[0];
@@ -394,6 +421,9 @@ template <typename R>
 struct EChemFlux {
   static constexpr int CIN = 3;
   static constexpr bool RED = false;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 6, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* g, Acc<R>&, const R*) {
     const R* K = a.aux[0];
     const long long V = a.V;
@@ -411,6 +441,9 @@ template <typename R>
 struct EChemOp {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 1, PF_AUX1 = 1;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R y = a.aux[0][v];
     const R o = a.aux[1][v] * y + a.coef[0] * val[0];
@@ -426,6 +459,9 @@ template <typename R>
 struct EChemRhs {
   static constexpr int CIN = 1;
   static constexpr bool RED = true;
+  // components read per field (rin, rout, rout2, aux0, aux1), for the L2 prefetch
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
+                       PF_AUX0 = 1, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
     const R o = -(a.aux[0][v] + a.coef[0] * val[0]);
     a.rout[v] = o;

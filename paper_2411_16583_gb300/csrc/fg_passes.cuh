@@ -13,6 +13,7 @@
 // one complex row (a + i b) and separated with the Hermitian symmetry of real data.
 // The forward transform is unnormalised; the 1/V of the inverse is applied in the Z pass.
 #pragma once
+#include <type_traits>
 #include "fg_fft.cuh"
 
 namespace fg {
@@ -40,7 +41,63 @@ struct PassArgs {
   const int* done;      // early exit when *done != 0 (converged Krylov loop)
   int ncomp;            // components (Y passes)
   int row_lo, row_hi;   // Y and Z passes: rows [row_lo, row_hi) only (row_hi = 0: all)
+  int l2pf;             // X passes: prefetch the block's real-space rows into L2 first
 };
+
+// ------------------------------------------------------------------ L2 bulk prefetch
+// cp.async.bulk.prefetch.L2 hands a contiguous range to the bulk-copy (TMA) unit, which
+// brings it into L2 while the block goes on: the X passes issue it at their start for the
+// real-space rows their prologue or epilogue reads, so those loads hit L2 instead of
+// waiting on DRAM.  A hint only (no completion to wait for); ranges must start and end on
+// 16-byte boundaries, and misaligned ones are skipped.  In the host emulation the range's
+// first and last bytes are read instead, so the bounds-checked buffers catch a range that
+// leaves its buffer.
+FG_DEV void l2_prefetch(const void* p, long long bytes) {
+  if (!p || bytes < 16) return;
+  const unsigned long long u = (unsigned long long)p;
+  if (u & 15) return;
+  bytes &= ~15LL;
+#ifdef FG_EMU
+  volatile const char* c = (const char*)p;
+  (void)c[0];
+  (void)c[bytes - 1];
+#else
+  for (long long o = 0; o < bytes; o += (1LL << 20)) {
+    const unsigned n = (unsigned)(bytes - o < (1LL << 20) ? bytes - o : (1LL << 20));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char*)p + o), "r"(n)
+                 : "memory");
+  }
+#endif
+}
+
+// Components of each real-space field an X-pass functor reads (0: none); functors that
+// declare none are not prefetched.
+template <class Op, class = void>
+struct PfCounts {
+  static constexpr int rin = 0, rout = 0, rout2 = 0, aux0 = 0, aux1 = 0;
+};
+template <class Op>
+struct PfCounts<Op, std::void_t<decltype(Op::PF_AUX0)>> {
+  static constexpr int rin = Op::PF_RIN, rout = Op::PF_ROUT, rout2 = Op::PF_ROUT2,
+                       aux0 = Op::PF_AUX0, aux1 = Op::PF_AUX1;
+};
+
+// rows [e0, e0 + ne) (element offsets within a component) of `comps` components V apart
+template <typename T>
+FG_DEV void prefetch_rows(const T* p, int comps, long long V, long long e0, long long ne) {
+  for (int c = 0; c < comps; ++c) l2_prefetch(p + c * V + e0, ne * (long long)sizeof(T));
+}
+
+template <class Op, typename R>
+FG_DEV void prefetch_op_rows(const PassArgs<R>& a, long long e0, long long ne, int percomp) {
+  using P = PfCounts<Op>;
+  const int k = percomp;
+  prefetch_rows(a.rin, k ? (P::rin ? 1 : 0) : P::rin, a.V, e0, ne);
+  prefetch_rows(a.rout, k ? (P::rout ? 1 : 0) : P::rout, a.V, e0, ne);
+  prefetch_rows(a.rout2, k ? (P::rout2 ? 1 : 0) : P::rout2, a.V, e0, ne);
+  prefetch_rows(a.aux[0], k ? (P::aux0 ? 1 : 0) : P::aux0, a.V, e0, ne);
+  prefetch_rows(a.aux[1], k ? (P::aux1 ? 1 : 0) : P::aux1, a.V, e0, ne);
+}
 
 // ------------------------------------------------------------------ tile sizing
 
@@ -126,6 +183,7 @@ struct XFwd {
     const int row0 = bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     FG_PHASE(NT)
+    if (a.l2pf && tid == 0) prefetch_op_rows<Op>(a, (long long)row0 * N, (long long)nr * N, 0);
     L.acc.zero();
     // device scalars of the fused Krylov updates, converted once per thread
     const R sc[2] = {a.dscal ? (R)a.dscal[0] : (R)0, a.dscal ? (R)a.dscal[1] : (R)0};
@@ -227,6 +285,8 @@ struct XInv {
     const int row0 = bid.x * ROWS;
     const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
     FG_PHASE(NT)
+    if (a.l2pf && tid == 0)
+      prefetch_op_rows<Op>(a, (long long)row0 * N, (long long)nr * N, PERCOMP ? 1 : 0);
     L.acc.zero();
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
     constexpr int H = N / 2 + 1;

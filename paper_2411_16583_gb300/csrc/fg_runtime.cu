@@ -247,6 +247,8 @@ struct fg_ctx {
   int prof_used[8] = {0};
   int kx_chunk[2] = {1, 1};          // kx planes per Y-Z-Y chunk (FP32, FP64)
   int xi_percomp = 1;                // fused CG update: one component per block
+  int l2pf = 0;                      // X passes prefetch their real-space rows into L2
+  double tune_ms[4] = {0, 0, 0, 0};  // autotuner: X-inv update times [prefetch][per comp]
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
 #ifndef FG_EMU
@@ -463,6 +465,7 @@ static PassArgs<R> pbase(fg_ctx& c, Prec<R>& P, const int* done) {
   }
   a.partials = c.partials;
   a.done = done;
+  a.l2pf = c.l2pf;
   return a;
 }
 
@@ -2193,6 +2196,7 @@ void fg_default_opts(fg_opts* o) {
   o->max_stag = 50;
   o->cuda_stream = nullptr;
   o->cg_indefinite = 2;
+  o->l2_prefetch = 0;
 }
 
 int fg_supported_size(int n) {
@@ -2367,6 +2371,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (!(o.gc > 0 && o.lc > 0 && o.RT > 0 && o.cmax > 0)) fail(FG_ERR_INVALID, "fg_setup: gc, lc, RT, cmax");
   if (o.cg_indefinite < 0 || o.cg_indefinite > 2) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
   if (o.chem_full_jacobian != 0 && o.chem_full_jacobian != 1) fail(FG_ERR_INVALID, "fg_setup: chem_full_jacobian");
+  if (o.l2_prefetch != 0 && o.l2_prefetch != 1) fail(FG_ERR_INVALID, "fg_setup: l2_prefetch");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;
@@ -2383,6 +2388,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     c->h[1] = g->hy;
     c->h[2] = g->hz;
     c->o = o;
+    c->l2pf = o.l2_prefetch;
     c->st = (cudaStream_t)o.cuda_stream;
     const long long V = c->V;
     // per-voxel material on the host
@@ -2893,21 +2899,26 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
     return (double)t / reps;
   };
   double best = 1e300;
-  int best_ch = c->kx_chunk[k];
-  for (int ch : chunks) {
-    c->kx_chunk[k] = ch;
-    const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
-                           : time_it([&] { op_mech(*c, c->pd, (const double*)x, (double*)y, nullptr); }, 3);
-    if (t < best) {
-      best = t;
-      best_ch = ch;
+  int best_ch = c->kx_chunk[k], best_pf = c->l2pf;
+  for (int pf = 0; pf < 2; ++pf)
+    for (int ch : chunks) {
+      c->kx_chunk[k] = ch;
+      c->l2pf = pf;
+      const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
+                             : time_it([&] { op_mech(*c, c->pd, (const double*)x, (double*)y, nullptr); }, 3);
+      if (t < best) {
+        best = t;
+        best_ch = ch;
+        best_pf = pf;
+      }
     }
-  }
   c->kx_chunk[k] = best_ch;
+  c->l2pf = best_pf;
   // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
   double* zero = (double*)dalloc(4 * sizeof(double));
   dzero(zero, 4 * sizeof(double), c->st);
-  double tv[2];
+  double tv[2][2];
+  for (int pf = 0; pf < 2; ++pf)
   for (int pc = 0; pc < 2; ++pc) {
     auto run = [&]() {
       if (mixed) {
@@ -2918,6 +2929,7 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
         a.rout2 = (float*)x;
         a.aux[0] = (const float*)x;
         a.dscal = zero;
+        a.l2pf = pf;
         (pc ? c->pf.ox->xi_cgupdate_pc : c->pf.ox->xi_cgupdate)(a, c->st);
       } else {
         PassArgs<double> a = pbase(*c, c->pd, nullptr);
@@ -2927,12 +2939,18 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
         a.rout2 = (double*)x;
         a.aux[0] = (const double*)x;
         a.dscal = zero;
+        a.l2pf = pf;
         (pc ? c->pd.ox->xi_cgupdate_pc : c->pd.ox->xi_cgupdate)(a, c->st);
       }
     };
-    tv[pc] = time_it(run, 5);
+    tv[pf][pc] = time_it(run, 5);
   }
-  c->xi_percomp = tv[1] <= tv[0] ? 1 : 0;
+  // the update form with the context's prefetch choice (made on the whole operator)
+  c->xi_percomp = tv[c->l2pf][1] <= tv[c->l2pf][0] ? 1 : 0;
+  c->tune_ms[0] = tv[0][0];
+  c->tune_ms[1] = tv[0][1];
+  c->tune_ms[2] = tv[1][0];
+  c->tune_ms[3] = tv[1][1];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   dsync(c->st);
@@ -2942,6 +2960,17 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   ccheck("fg_autotune");
   if (ms_per_iteration) *ms_per_iteration = best;
 #endif
+  FG_API_END
+}
+
+int fg_autotune_report(fg_ctx* c, int choice[3], double xinv_ms[4]) {
+  FG_API_BEGIN
+  if (!c || !choice) fail(FG_ERR_INVALID, "fg_autotune_report: bad argument");
+  choice[0] = c->kx_chunk[is_mixed(*c) ? 0 : 1];
+  choice[1] = c->xi_percomp;
+  choice[2] = c->l2pf;
+  if (xinv_ms)
+    for (int k = 0; k < 4; ++k) xinv_ms[k] = c->tune_ms[k];
   FG_API_END
 }
 
