@@ -363,6 +363,12 @@ def fp64_split(w, sol, state0, stream):
     ms_m, st_m = _timed_step(sol, w, stream)
     mixed = _state(sol)
     forcing = sol.opts.cg_forcing
+    # the mixed form with its residual transforms in FP64 arithmetic instead of float-float
+    m64 = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream, residual_ff=0)
+    _restore(m64, state0)
+    ms_m64, st_m64 = _timed_step(m64, w, stream)
+    mixed64 = _state(m64)
+    m64.close()
     runs = {"fp64": {}, "fp64_at_forcing": {"tol_cg": forcing, "tol_chem_cg": forcing}}
     ref = None
     for name, kw in runs.items():
@@ -373,8 +379,13 @@ def fp64_split(w, sol, state0, stream):
         if name == "fp64":
             ref = _state(s64)
         s64.close()
-    out["mixed"] = {"ms": ms_m, "stats": st_m}
+    out["mixed"] = {"ms": ms_m, "stats": st_m,
+                    "residual_transforms": "float-float" if sol.opts.residual_ff else "FP64"}
+    out["mixed_fp64_residuals"] = {"ms": ms_m64, "stats": st_m64}
     rel = lambda a, b: float((a - b).abs().max() / b.abs().max())
+    out["mixed_fp64_residuals"]["vs_fp64_error"] = {
+        "F_max_rel": rel(mixed64[B.FIELD_F], ref[B.FIELD_F]),
+        "c_max_rel": rel(mixed64[B.FIELD_C], ref[B.FIELD_C])}
     gm, gr = crack_energy(mixed[B.FIELD_D], w), crack_energy(ref[B.FIELD_D], w)
     out["mixed_vs_fp64_error"] = {
         "F_max_rel": rel(mixed[B.FIELD_F], ref[B.FIELD_F]),
@@ -520,7 +531,8 @@ def run_ours(a, rank, world, local, dist, stream):
     mech32_ms = sol.time_apply(B.OP_MECH, 1, 50)
     matvec = {"mech_fp32_ms": mech32_ms, "mech_fp32_voxel_applies_per_s": V / (mech32_ms * 1e-3)}
     for name, op, prec in (("pff_fp32", B.OP_PFF, 1), ("pff_prec_fp32", B.OP_PFF_PREC, 1),
-                           ("chem_fp32", B.OP_CHEM, 1), ("gres_fp64", B.OP_GRES, 0)):
+                           ("chem_fp32", B.OP_CHEM, 1), ("gres_fp64", B.OP_GRES, 0),
+                           ("gres_float_float", B.OP_GRES, 2)):
         t = sol.time_apply(op, prec, 20)
         matvec[name + "_ms"] = t
         matvec[name + "_voxel_applies_per_s"] = V / (t * 1e-3)

@@ -114,6 +114,13 @@ typedef struct {
                          bulk-copy unit as L2 prefetches (cp.async.bulk.prefetch.L2) before
                          they start; 0 (default): plain loads.  fg_autotune overrides it with
                          the faster choice */
+  int residual_ff;    /* mixed mode only: 1 (default): the residual transforms that stay in
+                         FP64 storage (the equilibrium residual G*P of Eq. mechresiduum and its
+                         norm, the FP64 projection of each Newton correction, and the Fick
+                         residual of Eq. Chemresidualfc) run their FFTs in float-float
+                         arithmetic (pairs of FP32, about 48 significant bits, error-free
+                         TwoSum/TwoProduct) on the FP32 pipes; 0: in FP64 arithmetic.  The
+                         fields, updates, norms and sums stay FP64 either way */
 } fg_opts;
 
 typedef struct {
@@ -193,7 +200,8 @@ int fg_residual(fg_ctx* ctx, double* err_mech, double* err_chem, double* mass_su
 
 /*
  * One operator application y = op(x) at the stored state, for tests and benchmarks.
- *   op         FG_OP_*;  prec: 0 = FP64 (x, y double), 1 = FP32 (x, y float)
+ *   op         FG_OP_*;  prec: 0 = FP64 (x, y double), 1 = FP32 (x, y float), 2 = FG_OP_GRES
+ *              with float-float transforms (x, y double; mixed context with residual_ff)
  *   x, y       device pointers, 9 V (MECH, GRES) or V (others) elements
  *   dt         time step of FG_OP_CHEM (ignored otherwise)
  *   dot        if not NULL receives <x, y> accumulated in FP64
@@ -211,7 +219,8 @@ int fg_get_field(fg_ctx* ctx, int field, void* dst, int on_device);
 int fg_set_field(fg_ctx* ctx, int field, const void* src, int on_device);
 
 /* Runs n applications of op back to back on the stream between two CUDA events and
- * reports the mean time per application in ms (no synchronisation inside). */
+ * reports the mean time per application in ms (no synchronisation inside); prec as in
+ * fg_apply. */
 int fg_time_apply(fg_ctx* ctx, int op, int prec, int n, double* ms_per_apply);
 
 /* Mechanical equilibrium alone (Alg. 1) at the stored c and d: the stored F is shifted by

@@ -49,7 +49,7 @@ class Opts(C.Structure):
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
                 ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double),
                 ("cg_indefinite", C.c_int), ("chem_full_jacobian", C.c_int),
-                ("l2_prefetch", C.c_int)]
+                ("l2_prefetch", C.c_int), ("residual_ff", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -77,11 +77,88 @@ template <> struct Acc<float> {
   FG_HD double value() const { return (double)s + (double)c; }
 };
 
+// ------------------------------------------------------------------ float-float reals
+// A real carried as the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2: about
+// 48 significant bits from FP32 instructions alone (GB300 issues FP64 at a small fraction
+// of its FP32 rate).  Sums use Knuth's error-free TwoSum and products the FMA form of
+// Dekker's TwoProduct, renormalised as in the double-double algorithms of Dekker (1971)
+// and Hida, Li and Bailey (2001); the quotient is one Newton correction of the float
+// quotient.  The residual transforms of the mixed-precision mode run on it: stored in
+// FP64, transformed in float-float.  FP32 addition and multiplication are IEEE in both
+// builds; only explicit fmaf contracts.
+
+struct ff {
+  float hi, lo;
+  FG_HD constexpr ff() : hi(0.f), lo(0.f) {}
+  FG_HD constexpr ff(float h, float l) : hi(h), lo(l) {}
+  // split of a double: hi its nearest float, lo the nearest float of the remainder
+  FG_HD constexpr ff(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  FG_HD constexpr ff(int x) : hi((float)x), lo(0.f) {}
+  FG_HD explicit operator double() const { return (double)hi + (double)lo; }
+  FG_HD explicit operator int() const { return (int)hi; }
+};
+
+FG_HD ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return ff(s, (a - (s - bb)) + (b - bb));
+}
+FG_HD ff ff_quick_two_sum(float a, float b) {  // |a| >= |b| (or a = 0)
+  const float s = a + b;
+  return ff(s, b - (s - a));
+}
+FG_HD ff operator+(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  const ff t = ff_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = ff_quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return ff_quick_two_sum(s.hi, s.lo);
+}
+FG_HD ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+FG_HD ff operator-(ff a, ff b) { return a + (-b); }
+FG_HD ff operator*(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_quick_two_sum(p, e);
+}
+FG_HD ff operator/(ff a, ff b) {
+  const float q1 = a.hi / b.hi;
+  const ff r = a - ff(q1, 0.f) * b;
+  const float q2 = r.hi / b.hi;
+  return ff_quick_two_sum(q1, q2);
+}
+FG_HD ff& operator+=(ff& a, ff b) { return a = a + b; }
+FG_HD ff& operator-=(ff& a, ff b) { return a = a - b; }
+FG_HD ff& operator*=(ff& a, ff b) { return a = a * b; }
+FG_HD bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+FG_HD bool operator<(ff a, ff b) { return b > a; }
+
+struct ffc {  // complex float-float
+  ff x, y;
+};
+
+// the type real-space fields of a precision are stored in: float-float transforms read
+// and write FP64 fields
+template <typename R> struct io_type { using type = R; };
+template <> struct io_type<ff> { using type = double; };
+template <typename R> using io_t = typename io_type<R>::type;
+
+template <> struct Acc<ff> {  // float-float passes accumulate their FP64 outputs in FP64
+  double s;
+  FG_HD void zero() { s = 0.0; }
+  FG_HD void add(double x) { s += x; }
+  FG_HD double value() const { return s; }
+};
+
 // ------------------------------------------------------------------ complex arithmetic
 
 template <typename R> struct ctype;
 template <> struct ctype<float> { using type = float2; };
 template <> struct ctype<double> { using type = double2; };
+template <> struct ctype<ff> { using type = ffc; };
 template <typename R> using cplx = typename ctype<R>::type;
 
 template <typename C> FG_HD C cmk(decltype(C::x) a, decltype(C::x) b) {

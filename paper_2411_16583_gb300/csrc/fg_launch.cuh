@@ -169,10 +169,42 @@ SizeOps<R> make_size_ops() {
   return s;
 }
 
+// Float-float launchers: the passes of the FP64 residual transforms only (projection of a
+// nine-component field, the chemistry gradient-flux-divergence chain), reading and writing
+// FP64 real fields.
+template <int N>
+SizeOps<ff> make_size_ops_ff() {
+  SizeOps<ff> s{};
+  s.N = N;
+  if constexpr (N % 2 == 0) {
+    s.xf_copy1 = run_x<XFwd<ff, N, PCopy<ff, 1>>, ff>;
+    s.xf_copy3 = run_x<XFwd<ff, N, PCopy<ff, 3>>, ff>;
+    s.xf_copy9 = run_x<XFwd<ff, N, PCopy<ff, 9>>, ff>;
+    s.xi_norm9 = run_x<XInv<ff, N, ENorm<ff, 9>>, ff>;
+    s.xi_chemflux = run_x<XInv<ff, N, EChemFlux<ff>>, ff>;
+    s.xi_chemrhs = run_x<XInv<ff, N, EChemRhs<ff>>, ff>;
+  }
+  if constexpr (Square<N>::OK) {
+    s.yf = run_y<YPassD<ff, N, false>, ff>;
+    s.yi = run_y<YPassD<ff, N, true>, ff>;
+    s.z_proj = run_z<ZPassD<ff, N, ZProject<ff>>, ff>;
+    s.z_grad = run_z<ZPassD<ff, N, ZGrad<ff>>, ff>;
+    s.z_div = run_z<ZPassD<ff, N, ZDiv<ff>>, ff>;
+  } else {
+    s.yf = run_y<YPass<ff, N, false>, ff>;
+    s.yi = run_y<YPass<ff, N, true>, ff>;
+    s.z_proj = run_z<ZPass<ff, N, ZProject<ff>>, ff>;
+    s.z_grad = run_z<ZPass<ff, N, ZGrad<ff>>, ff>;
+    s.z_div = run_z<ZPass<ff, N, ZDiv<ff>>, ff>;
+  }
+  return s;
+}
+
 // Registry: each instantiation unit registers the sizes it compiles.
 template <typename R>
 const SizeOps<R>* size_ops(int N);
 void register_size_ops_f(const SizeOps<float>& s);
 void register_size_ops_d(const SizeOps<double>& s);
+void register_size_ops_ff(const SizeOps<ff>& s);
 
 }  // namespace fg

@@ -469,4 +469,62 @@ struct EChemRhs {
   }
 };
 
+// ================================================================== float-float epilogues
+// The float-float passes store their results as FP64 (the fields they serve are FP64)
+// and accumulate norms in FP64.
+
+template <int NC>
+struct EStore<ff, NC> {
+  static constexpr int CIN = NC;
+  static constexpr bool RED = false;
+  FG_DEV static void apply(const PassArgs<ff>& a, long long v, const ff* val, Acc<ff>&, const ff*) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a.rout[c * a.V + v] = (double)val[c];
+  }
+};
+
+template <int NC>
+struct ENorm<ff, NC> {
+  static constexpr int CIN = NC;
+  static constexpr bool RED = true;
+  FG_DEV static void apply(const PassArgs<ff>& a, long long v, const ff* val, Acc<ff>& acc, const ff*) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double o = (double)val[c];
+      a.rout[c * a.V + v] = o;
+      acc.add(o * o);
+    }
+  }
+};
+
+// the flux K_c g in FP64 from the float-float gradient; aux0 = K_c (6 FP64 components)
+template <>
+struct EChemFlux<ff> {
+  static constexpr int CIN = 3;
+  static constexpr bool RED = false;
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0, PF_AUX0 = 6, PF_AUX1 = 0;
+  FG_DEV static void apply(const PassArgs<ff>& a, long long v, const ff* gf, Acc<ff>&, const ff*) {
+    const double* K = a.aux[0];
+    const long long V = a.V;
+    const double g[3] = {(double)gf[0], (double)gf[1], (double)gf[2]};
+    const double kxx = K[v], kyy = K[V + v], kzz = K[2 * V + v];
+    const double kxy = K[3 * V + v], kxz = K[4 * V + v], kyz = K[5 * V + v];
+    a.rout[v] = kxx * g[0] + kxy * g[1] + kxz * g[2];
+    a.rout[V + v] = kxy * g[0] + kyy * g[1] + kyz * g[2];
+    a.rout[2 * V + v] = kxz * g[0] + kyz * g[1] + kzz * g[2];
+  }
+};
+
+template <>
+struct EChemRhs<ff> {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0, PF_AUX0 = 1, PF_AUX1 = 0;
+  FG_DEV static void apply(const PassArgs<ff>& a, long long v, const ff* val, Acc<ff>& acc, const ff*) {
+    const double o = -(a.aux[0][v] + (double)a.coef[0] * (double)val[0]);
+    a.rout[v] = o;
+    acc.add(o * o);
+  }
+};
+
 }  // namespace fg

@@ -21,11 +21,12 @@ namespace fg {
 template <typename R>
 struct PassArgs {
   using C = cplx<R>;
+  using IO = io_t<R>;   // storage type of the real-space fields (FP64 for float-float)
   int nx, ny, nz, hx;   // hx = nx/2 + 1
   long long V, VH;      // voxels, half-spectrum points per component
-  const R* rin;         // real input fields (X-fwd prologue)
-  R* rout;              // real output fields (X-inv epilogue)
-  R* rout2;             // second real output (fused Krylov updates)
+  const IO* rin;        // real input fields (X-fwd prologue)
+  IO* rout;             // real output fields (X-inv epilogue)
+  IO* rout2;            // second real output (fused Krylov updates)
   const C* cin;         // complex input
   C* cout;              // complex output
   const C* tw;          // exp(-2 pi i m / N), m < N, for this pass's axis
@@ -34,7 +35,7 @@ struct PassArgs {
   const R* rc[3];       // rotated scheme: cos(pi k / n_j), exactly 0 at Nyquist
   const C* xi[3];       // forward difference: (exp(2 pi i k / n_j) - 1) / h_j
   const R* lap[3];      // 4 sin^2(pi k / n_j) / h_j^2
-  const R* aux[4];      // operator inputs (state, p, H, ...)
+  const IO* aux[4];     // operator inputs (state, p, H, ...)
   R coef[4];            // operator constants
   const double* dscal;  // device scalars read by operators
   double* partials;     // one partial sum per block (reducing epilogues)

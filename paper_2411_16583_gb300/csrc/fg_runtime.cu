@@ -40,6 +40,7 @@ std::atomic<long long>& launch_counter() {
 
 void register_size_ops_f(const SizeOps<float>& s) { registry<float>()[s.N] = s; }
 void register_size_ops_d(const SizeOps<double>& s) { registry<double>()[s.N] = s; }
+void register_size_ops_ff(const SizeOps<ff>& s) { registry<ff>()[s.N] = s; }
 template <typename R>
 const SizeOps<R>* size_ops(int N) {
   auto& m = registry<R>();
@@ -187,14 +188,15 @@ enum { KS_MECH = 0, KS_PFF = 1, KS_CHEM = 2, KS_MISC = 3, KS_HBAR = 4, KS_N = 5 
 template <typename R>
 struct Prec {
   using C = cplx<R>;
+  using IO = io_t<R>;  // real-space fields (FP64 for the float-float set)
   bool on = false;
   C *S1 = nullptr, *S2 = nullptr;
   C *twx = nullptr, *twy = nullptr, *twz = nullptr;
   R *rs[3] = {}, *rc[3] = {}, *lap[3] = {};
   C* xi[3] = {};
-  R *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *z = nullptr;
-  R* xbest = nullptr;  // best-residual CG iterate
-  R *state = nullptr, *kc = nullptr, *w = nullptr, *Hr = nullptr, *tmp3 = nullptr;
+  IO *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *z = nullptr;
+  IO* xbest = nullptr;  // best-residual CG iterate
+  IO *state = nullptr, *kc = nullptr, *w = nullptr, *Hr = nullptr, *tmp3 = nullptr;
   const SizeOps<R>*ox = nullptr, *oy = nullptr, *oz = nullptr;
 };
 
@@ -236,6 +238,8 @@ struct fg_ctx {
   int* flags_host = nullptr;
   fg::Prec<double> pd;
   fg::Prec<float> pf;
+  fg::Prec<fg::ff> pe;  // float-float residual transforms (mixed mode, FP64 fields)
+  bool ffres = false;   // the FP64 residual transforms run in float-float
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_prev[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double last_dt = 0.0;
@@ -354,6 +358,25 @@ static void setup_prec(fg_ctx& c, Prec<R>& P, int krylov_comps) {
   P.Hr = alloc_n<R>(c, c.V);
   P.tmp3 = alloc_n<R>(c, 3 * c.V);
   if (krylov_comps == 9) P.state = alloc_n<R>(c, (long long)state_size(c.law) * c.V);
+}
+
+// The float-float set: its own tables and launchers; the spectra and the FP64 work
+// fields it reads and writes are the FP64 set's (16-byte complex numbers in both).
+static void setup_ff(fg_ctx& c) {
+  Prec<ff>& P = c.pe;
+  P.ox = size_ops<ff>(c.nx);
+  P.oy = size_ops<ff>(c.ny);
+  P.oz = size_ops<ff>(c.nz);
+  if (!P.ox || !P.oy || !P.oz || !P.ox->xf_copy9)
+    fail(FG_ERR_INVALID, "grid size not compiled in for the float-float residuals");
+  static_assert(sizeof(ffc) == sizeof(double2), "float-float and FP64 spectra share buffers");
+  P.S1 = (ffc*)c.pd.S1;
+  P.S2 = (ffc*)c.pd.S2;
+  build_tables(c, P);
+  P.tmp3 = c.pd.tmp3;
+  P.kc = c.pd.kc;
+  P.on = true;
+  c.ffres = true;
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -544,7 +567,7 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
 
 // y = G * x (projection of a tensor field), accumulates |y|^2
 template <typename R>
-static int op_gres(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
+static int op_gres(fg_ctx& c, Prec<R>& P, const io_t<R>* x, io_t<R>* y, const int* done) {
   PassArgs<R> a = pbase(c, P, done);
   a.tw = P.twx;
   a.rin = x;
@@ -599,7 +622,7 @@ static int op_prec(fg_ctx& c, Prec<R>& P, const R* r, R* z, const int* done) {
 
 // L u = grad_f^H (K_c grad_f u) into S1 (1 comp), K_c from P.kc
 template <typename R>
-static void op_chem_L(fg_ctx& c, Prec<R>& P, const R* u, const int* done) {
+static void op_chem_L(fg_ctx& c, Prec<R>& P, const io_t<R>* u, const int* done) {
   PassArgs<R> a = pbase(c, P, done);
   a.tw = P.twx;
   a.rin = u;
@@ -635,17 +658,27 @@ static int op_chem(fg_ctx& c, Prec<R>& P, const R* x, R* y, double dt, const int
   return P.ox->xi_chemop(a, c.st);
 }
 
-// b = -(base + dt L mu) in FP64 ; returns |b|^2 partial count
-static int op_chem_rhs(fg_ctx& c, double* b, double dt) {
-  Prec<double>& P = c.pd;
+// b = -(base + dt L mu) into an FP64 field, transforms in FP64 or float-float ; returns
+// |b|^2 partial count
+template <typename R>
+static int op_chem_rhs_p(fg_ctx& c, Prec<R>& P, double* b, double dt) {
   op_chem_L(c, P, c.mu, nullptr);
-  PassArgs<double> a = pbase(c, P, nullptr);
+  PassArgs<R> a = pbase(c, P, nullptr);
   a.tw = P.twx;
   a.cin = P.S1;
   a.rout = b;
   a.aux[0] = c.base;
-  a.coef[0] = dt;
+  a.coef[0] = (R)dt;
   return P.ox->xi_chemrhs(a, c.st);
+}
+static int op_chem_rhs(fg_ctx& c, double* b, double dt) {
+  return c.ffres ? op_chem_rhs_p(c, c.pe, b, dt) : op_chem_rhs_p(c, c.pd, b, dt);
+}
+
+// y = G * x of FP64 fields with |y|^2 partial sums: the residual projection, in float-float
+// transforms when the context runs them, else in FP64
+static int gres64(fg_ctx& c, const double* x, double* y) {
+  return c.ffres ? op_gres(c, c.pe, x, y, nullptr) : op_gres(c, c.pd, x, y, nullptr);
 }
 
 // ------------------------------------------------------------------ state kernels
@@ -998,7 +1031,7 @@ static double mixed_tol(const fg_ctx& c, double tol) {
 // G keeps the mean of the stress-controlled components M and their prescribed mean
 // stress P-bar* is subtracted
 static double gres_residual(fg_ctx& c) {
-  const int nb = op_gres(c, c.pd, c.P, c.GP, nullptr);
+  const int nb = gres64(c, c.P, c.GP);
   if (!c.smask) {
     fin<FStore>(c, KS_MISC, nb, nullptr);
     read_ks(c);
@@ -1214,7 +1247,7 @@ static void mech_newton(fg_ctx& c, Prec<R>& P, double den, fg_stats& s, double e
       u.in[0] = P.x;
       u.out[0] = c.P;
       launch_vec<KWiden<R>>(u, c.st);
-      op_gres(c, c.pd, c.P, c.dF, nullptr);
+      gres64(c, c.P, c.dF);
       dF = c.dF;
     } else {
       dF = c.pd.x;
@@ -2197,6 +2230,7 @@ void fg_default_opts(fg_opts* o) {
   o->cuda_stream = nullptr;
   o->cg_indefinite = 2;
   o->l2_prefetch = 0;
+  o->residual_ff = 1;
 }
 
 int fg_supported_size(int n) {
@@ -2372,6 +2406,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (o.cg_indefinite < 0 || o.cg_indefinite > 2) fail(FG_ERR_INVALID, "fg_setup: cg_indefinite");
   if (o.chem_full_jacobian != 0 && o.chem_full_jacobian != 1) fail(FG_ERR_INVALID, "fg_setup: chem_full_jacobian");
   if (o.l2_prefetch != 0 && o.l2_prefetch != 1) fail(FG_ERR_INVALID, "fg_setup: l2_prefetch");
+  if (o.residual_ff != 0 && o.residual_ff != 1) fail(FG_ERR_INVALID, "fg_setup: residual_ff");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;
@@ -2488,6 +2523,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     // back to it in the mechanical Newton
     setup_prec<double>(*c, c->pd, 9);
     if (o.precision == FG_MIXED) setup_prec<float>(*c, c->pf, 9);
+    if (o.precision == FG_MIXED && o.residual_ff) setup_ff(*c);
     dsync(c->st);
   } catch (...) {
     fg_destroy(c);
@@ -2582,8 +2618,15 @@ int fg_apply(fg_ctx* c, int op, int prec, const void* x, void* y, double dt, dou
     if (!c->pf.on) fail(FG_ERR_INVALID, "fg_apply: FP32 operators need a mixed-precision context");
     if (op == FG_OP_GRES) fail(FG_ERR_INVALID, "fg_apply: residual projection is FP64 only");
     d = do_apply<float>(*c, c->pf, op, (const float*)x, (float*)y, dt);
+  } else if (prec == 2) {
+    if (!c->pe.on) fail(FG_ERR_INVALID, "fg_apply: float-float transforms need a mixed context with residual_ff");
+    if (op != FG_OP_GRES) fail(FG_ERR_INVALID, "fg_apply: float-float transforms serve FG_OP_GRES only");
+    const int nb = op_gres(*c, c->pe, (const double*)x, (double*)y, nullptr);
+    fin<FStore>(*c, KS_MISC, nb, nullptr);
+    read_ks(*c);
+    d = c->ks_host[KS_MISC].aux;
   } else {
-    fail(FG_ERR_INVALID, "fg_apply: prec must be 0 or 1");
+    fail(FG_ERR_INVALID, "fg_apply: prec must be 0, 1 or 2");
   }
   if (dot) *dot = d;
   FG_API_END
@@ -2981,21 +3024,26 @@ int fg_time_apply(fg_ctx* c, int op, int prec, int n, double* ms) {
   fail(FG_ERR_INVALID, "fg_time_apply: needs the GPU build");
 #else
   const long long nel = (op == FG_OP_MECH || op == FG_OP_GRES) ? 9 * c->V : c->V;
-  const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
+  if (prec == 2 && (op != FG_OP_GRES || !c->pe.on))
+    fail(FG_ERR_INVALID, "fg_time_apply: float-float transforms serve FG_OP_GRES of a mixed context");
+  const size_t es = prec == 1 ? sizeof(float) : sizeof(double);
   void* x = dalloc(nel * es);
   void* y = dalloc(nel * es);
   dzero(x, nel * es, c->st);
   // prepare the operator state once with a first application
-  double dummy;
+  double dummy = 0.0;
   if (prec == 0) dummy = do_apply<double>(*c, c->pd, op, (const double*)x, (double*)y, 1.0);
-  else dummy = do_apply<float>(*c, c->pf, op, (const float*)x, (float*)y, 1.0);
+  else if (prec == 1) dummy = do_apply<float>(*c, c->pf, op, (const float*)x, (float*)y, 1.0);
+  else op_gres(*c, c->pe, (const double*)x, (double*)y, nullptr);
   (void)dummy;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, c->st);
   for (int i = 0; i < n; ++i) {
-    if (prec == 0) {
+    if (prec == 2) {
+      op_gres(*c, c->pe, (const double*)x, (double*)y, nullptr);
+    } else if (prec == 0) {
       Prec<double>& P = c->pd;
       switch (op) {
         case FG_OP_MECH: op_mech(*c, P, (const double*)x, (double*)y, nullptr); break;

@@ -1,4 +1,4 @@
-// Pass kernels of transform length 48, both precisions.
+// Pass kernels of transform length 48: FP32, FP64 and the float-float residual passes.
 #include "fg_launch.cuh"
 
 namespace fg {
@@ -7,6 +7,7 @@ struct RegisterSize48 {
   RegisterSize48() {
     register_size_ops_f(make_size_ops<float, 48>());
     register_size_ops_d(make_size_ops<double, 48>());
+    register_size_ops_ff(make_size_ops_ff<48>());
   }
 } register_size_48;
 }  // namespace

@@ -1,4 +1,4 @@
-// Pass kernels of transform length 64, both precisions.
+// Pass kernels of transform length 64: FP32, FP64 and the float-float residual passes.
 #include "fg_launch.cuh"
 
 namespace fg {
@@ -7,6 +7,7 @@ struct RegisterSize64 {
   RegisterSize64() {
     register_size_ops_f(make_size_ops<float, 64>());
     register_size_ops_d(make_size_ops<double, 64>());
+    register_size_ops_ff(make_size_ops_ff<64>());
   }
 } register_size_64;
 }  // namespace

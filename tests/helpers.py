@@ -7,6 +7,8 @@ from oracle import fg_oracle as O
 # FP64: a few ulps per radix stage.  FP32: about eps32 x (log2 V + pointwise terms).
 TOL_APPLY_FP64 = 1e-12
 TOL_APPLY_FP32 = 1e-5
+# float-float transforms (pairs of FP32, about 48 significant bits) of FP64 fields
+TOL_APPLY_FF = 1e-13
 # FP64 coupled step against the oracle (the GPU FP64 bar)
 TOL_STEP_FP64 = 1e-10
 

@@ -637,3 +637,42 @@ def test_emulated_l2_prefetch_stays_in_bounds_and_changes_nothing(emu, shape):
         out.append(res)
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(8, 12, 16), (1, 100, 100), (12, 8, 8), (8, 8, 256)])
+def test_emulated_float_float_projection_matches_oracle(emu, shape):
+    """The float-float residual projection (FG_OP_GRES, prec 2: FP64 fields, transforms in
+    pairs of FP32) against the oracle's G * x, element by element, to 1e-13 of the largest
+    entry, against 1e-7 for FP32 transforms: it carries the FP64 residual's precision."""
+    pid = S.random_phase_map(shape, 1)
+    sol = B.Solver(shape, H3, S.default_phases(), pid, np.zeros(shape), lib=emu,
+                   precision=B.FG_MIXED)
+    x = S.random_tensor_field(shape, 3) * 1e8
+    y = np.zeros_like(x)
+    sol.apply(B.OP_GRES, x, y, 2)
+    ref = O.apply_G(x.reshape((3, 3) + shape), H3)
+    assert rel_err(y.reshape(ref.shape), ref) < 1e-13
+    y64 = np.zeros_like(x)
+    sol.apply(B.OP_GRES, x, y64, 0)
+    assert rel_err(y, y64) < 1e-13
+    sol.close()
+
+
+
+
+def test_emulated_float_float_residuals_match_fp64_residuals(emu):
+    """Mixed-precision steps of the perturbed-particle recipe (16^3) with the residual
+    transforms in float-float and in FP64: the same converged fields (both stop at the
+    Newton tolerance, so they agree to a few times 1e-10) and the same Krylov counts."""
+    import bench
+    w = bench._workload(16, 0)
+    out = []
+    for rff in (1, 0):
+        sol = B.from_workload(w, precision=B.FG_MIXED, lib=emu, residual_ff=rff)
+        st = [sol.step(w.dt) for _ in range(2)]
+        out.append((sol.get(B.FIELD_F), sol.get(B.FIELD_C), st))
+        sol.close()
+    assert rel_err(out[0][0], out[1][0]) < 1e-9
+    assert rel_err(out[0][1], out[1][1]) < 1e-11
+    for a, b in zip(out[0][2], out[1][2]):
+        assert a["newton_mech"] == b["newton_mech"] and a["newton_chem"] == b["newton_chem"]

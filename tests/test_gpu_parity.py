@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import fg_oracle as O
 from paper_2411_16583_gb300 import binding as B, synth as S
-from tests.helpers import (TOL_APPLY_FP32, TOL_APPLY_FP64, TOL_STEP_FP64,
+from tests.helpers import (TOL_APPLY_FF, TOL_APPLY_FP32, TOL_APPLY_FP64, TOL_STEP_FP64,
                            homogeneous_stretch_damage, oracle_params, rel_err)
 
 pytestmark = pytest.mark.gpu
@@ -81,6 +81,11 @@ def test_operator_parity(lib, shape, law, l2f, prec):
     if prec == 0:
         sol.apply(B.OP_GRES, x9, y9, 0)
         assert rel_err(y9.cpu().numpy().reshape(F.shape), O.apply_G(xn9, H3)) < tol
+    else:  # the residual projection of the mixed mode: FP64 fields, float-float transforms
+        x64 = x9.double()
+        y64 = torch.empty_like(x64)
+        sol.apply(B.OP_GRES, x64, y64, 2)
+        assert rel_err(y64.cpu().numpy().reshape(F.shape), O.apply_G(xn9, H3)) < TOL_APPLY_FF
     # stress of the stored state
     assert rel_err(sol.get(B.FIELD_P), O.stress(F, c, d, prm)) < 1e-13
     sol.close()
@@ -90,7 +95,8 @@ def test_operator_parity(lib, shape, law, l2f, prec):
 def test_operator_parity_full_size(lib, prec):
     """Every operator at the benchmark size (256^3, where the Y and Z passes take their
     register-direct two-stage form), element by element against the oracle: mechanics,
-    phase field and its preconditioner, chemistry, and in FP64 the residual projection."""
+    phase field and its preconditioner, chemistry, and the residual projection (FP64, and
+    float-float in the mixed context)."""
     shape = (256, 256, 256)
     sol, prm, F, c, d, Hh = _solver(lib, shape, B.FG_MIXED if prec else B.FG_FP64, seed=11)
     tdt = torch.float32 if prec else torch.float64
@@ -105,6 +111,13 @@ def test_operator_parity_full_size(lib, prec):
     if prec == 0:
         sol.apply(B.OP_GRES, x, y, 0)
         assert rel_err(y.cpu().numpy().reshape(F.shape), O.apply_G(xn, prm.h)) < tol
+    else:
+        x64 = x.double()
+        del y
+        y = torch.empty_like(x64)
+        sol.apply(B.OP_GRES, x64, y, 2)
+        assert rel_err(y.cpu().numpy().reshape(F.shape), O.apply_G(xn, prm.h)) < TOL_APPLY_FF
+        del x64
     del x, y, xn
     x1 = torch.from_numpy(S.random_tensor_field(shape, 8, ncomp=1)[0]).to("cuda", tdt)
     y1 = torch.empty_like(x1)
@@ -502,3 +515,21 @@ def test_mixed_precision_damage_and_crack_energy(lib):
     g_ref = O.crack_energy(ref.d, prm)
     assert abs(O.crack_energy(d, prm) - g_ref) <= 1e-6 * g_ref
     sol.close()
+
+
+def test_float_float_residuals_match_fp64_residuals(lib):
+    """The mixed form with its residual transforms in float-float and in FP64, three steps
+    of the 64^3 perturbed-particle recipe from the same start: the same Newton iterations
+    and fields that agree to the solver tolerance."""
+    import bench
+    w = bench._workload(64, 0)
+    out = []
+    for rff in (1, 0):
+        sol = B.from_workload(w, precision=B.FG_MIXED, lib=lib, residual_ff=rff)
+        st = [sol.step(w.dt) for _ in range(3)]
+        out.append((sol.get(B.FIELD_F), sol.get(B.FIELD_C), st))
+        sol.close()
+    assert rel_err(out[0][0], out[1][0]) < 1e-9
+    assert rel_err(out[0][1], out[1][1]) < 1e-11
+    for a, b in zip(out[0][2], out[1][2]):
+        assert a["newton_mech"] == b["newton_mech"] and a["newton_chem"] == b["newton_chem"]

@@ -81,5 +81,5 @@ def _compare(case, precision, lib):
 @pytest.mark.parametrize("precision", [B.FG_FP64, B.FG_MIXED])
 def test_plate_trajectory_matches_oracle(lib, precision):
     """The Sec. 4.3 plate (64 x 64 x 1, Saint-Venant-Kirchhoff, Omega = 1.3, a stronger
-    influx at one corner): steps 1-5, the plate cracks in step 3."""
+    influx at one corner): steps 1-4, the plate cracks in step 3."""
     _compare("plate", precision, lib)
