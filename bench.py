@@ -129,6 +129,11 @@ def _args():
                    help="RVEs of the batch timing added to the line (0: skip)")
     p.add_argument("--damage-steps", type=int, default=3,
                    help="damaging steps of the 512^2 Sec. 5.1 disc timed for the line (0: skip)")
+    p.add_argument("--trajectory-error", type=int, default=0,
+                   help="only run this many steps of the workload in the mixed form and then in "
+                        "the FP64 form, and print the per-field error of the mixed trajectory "
+                        "against the FP64 one every quarter of the run (about 0.4 min + 21 s "
+                        "per step at 256^3)")
     p.add_argument("--profile-apply", type=int, default=0,
                    help="only run this many FP32 mechanical operator applications on the "
                         "workload (a small case for ncu captures) and print their time")
@@ -435,6 +440,9 @@ def main():
     if a.profile_apply:
         print(json.dumps(profile_apply(a)))
         return
+    if a.trajectory_error:
+        print(json.dumps(trajectory_error(a)))
+        return
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -664,6 +672,48 @@ def profile_apply(a):
     sol.close()
     return {"mode": "profile-apply", "shape": list(w.shape), "applies": a.profile_apply,
             "ms_per_apply": ms}
+
+
+def trajectory_error(a):
+    """The workload's first n steps in the mixed form, then in the FP64 form (Newton 1e-9,
+    FP64 Krylov 1e-10), both on a side stream; the mixed fields are kept on the device at
+    every quarter of the run and compared with the FP64 fields at the same step: max |dF| /
+    max |F|, the same for c, max |dd| and the fracture energy's relative error (the bars of
+    the mixed form: 1e-7, 1e-7, 1e-6, 1e-6)."""
+    import torch
+    from paper_2411_16583_gb300 import binding as B
+    n = a.trajectory_error
+    marks = sorted({max(1, (n * q) // 4) for q in (1, 2, 3, 4)})
+    w = _workload(a.n, 0, nz=a.nz)
+    stream = torch.cuda.Stream()
+    out = {"mode": "trajectory-error", "workload": f"rough ellipsoid particle {a.n}^3, "
+           f"100-step schedule", "steps": n, "marks": marks, "errors": {}, "ms_per_step": {}}
+    with torch.cuda.stream(stream):
+        kept = {}
+        for prec, name in ((B.FG_MIXED, "mixed"), (B.FG_FP64, "fp64")):
+            sol = B.from_workload(w, precision=prec, stream=stream.cuda_stream)
+            t = 0.0
+            for k in range(1, n + 1):
+                ms, st = _timed_step(sol, w, stream)
+                t += ms
+                if k in marks:
+                    if name == "mixed":
+                        kept[k] = _state(sol)
+                    else:
+                        ref = _state(sol)
+                        mix = kept.pop(k)
+                        rel = lambda x, y: float((x - y).abs().max() / y.abs().max())
+                        gm, gr = crack_energy(mix[B.FIELD_D], w), crack_energy(ref[B.FIELD_D], w)
+                        out["errors"][k] = {
+                            "F_max_rel": rel(mix[B.FIELD_F], ref[B.FIELD_F]),
+                            "c_max_rel": rel(mix[B.FIELD_C], ref[B.FIELD_C]),
+                            "d_max_abs": float((mix[B.FIELD_D] - ref[B.FIELD_D]).abs().max()),
+                            "d_max": float(ref[B.FIELD_D].max()),
+                            "crack_energy_rel": abs(gm - gr) / gr if gr > 0 else None}
+                        del mix, ref
+            out["ms_per_step"][name] = t / n
+            sol.close()
+    return out
 
 
 def damaging_window(steps):

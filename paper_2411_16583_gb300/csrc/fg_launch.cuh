@@ -89,6 +89,8 @@ struct SizeOps {
       xf_copy9;
   PassFn<R> xi_store1, xi_store3, xi_storedot1, xi_storedot9, xi_norm9, xi_pff, xi_chemflux, xi_chemop,
       xi_chemrhs, xi_cgupdate, xi_cgupdate_pc;
+  // the fused chemistry CG: forward X with p = r + beta p, flux round trip, X-inv update
+  PassFn<R> xf_cgchem, xr_chemflux, xi_cgchem;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
   // FP64 only (null in the FP32 table): displacement at the corners and its transpose
@@ -139,6 +141,9 @@ SizeOps<R> make_size_ops() {
     s.xi_chemflux = run_x<XInv<R, N, EChemFlux<R>>, R>;
     s.xi_chemop = run_x<XInv<R, N, EChemOp<R>>, R>;
     s.xi_chemrhs = run_x<XInv<R, N, EChemRhs<R>>, R>;
+    s.xf_cgchem = run_x<XFwd<R, N, PCgChem<R>>, R>;
+    s.xr_chemflux = run_x<XRound<R, N, EChemFluxRound<R>>, R>;
+    s.xi_cgchem = run_x<XInv<R, N, ECgChemUpdate<R>>, R>;
     if constexpr (std::is_same<R, double>::value) s.xi_store9 = run_x<XInv<R, N, EStore<R, 9>>, R>;
   }
   if constexpr (Square<N>::OK) {  // register-direct two-stage passes

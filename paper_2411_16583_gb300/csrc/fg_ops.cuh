@@ -469,6 +469,66 @@ struct EChemRhs {
   }
 };
 
+// ================================================================== fused chemistry CG
+// One iteration of the CG of the chemistry Newton system (y/m + dt L y, Eq. Chemderfc in
+// y = m dc) with its vector updates folded into the operator passes, as in the mechanical
+// CG: <p, A p> = <p, w p> + dt <grad_f p, K_c grad_f p> (w = 1/m) is summed in the forward
+// X pass and in the flux round trip, so the step length is known before the inverse
+// transform, whose epilogue forms q = w p + dt L p and applies the updates.
+
+// p = r + beta p (in place), the transform input p, and the partial sums of w p^2.
+// rin = r, rout = p, aux0 = w, dscal[1] = beta.
+template <typename R>
+struct PCgChem {
+  static constexpr int COUT = 1;
+  static constexpr bool RED = true;
+  static constexpr int PF_RIN = 1, PF_ROUT = 1, PF_ROUT2 = 0, PF_AUX0 = 1, PF_AUX1 = 0;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, R* out, Acc<R>& acc, const R* sc) {
+    const R p = a.rin[v] + sc[1] * a.rout[v];
+    a.rout[v] = p;
+    out[0] = p;
+    acc.add(a.aux[0][v] * p * p);
+  }
+};
+
+// flux K_c g of the gradient g = grad_f p in the X round trip, and the partial sums of
+// dt g . K_c g.  aux0 = K_c (6 components: xx, yy, zz, xy, xz, yz), coef[0] = dt.
+template <typename R>
+struct EChemFluxRound {
+  static constexpr int CIN = 3, COUT = 3;
+  static constexpr bool RED = true;
+  static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0, PF_AUX0 = 6, PF_AUX1 = 0;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* g, R* out, Acc<R>& acc,
+                           const R*) {
+    const R* K = a.aux[0];
+    const long long V = a.V;
+    const R kxx = K[v], kyy = K[V + v], kzz = K[2 * V + v];
+    const R kxy = K[3 * V + v], kxz = K[4 * V + v], kyz = K[5 * V + v];
+    out[0] = kxx * g[0] + kxy * g[1] + kxz * g[2];
+    out[1] = kxy * g[0] + kyy * g[1] + kyz * g[2];
+    out[2] = kxz * g[0] + kyz * g[1] + kzz * g[2];
+    acc.add(a.coef[0] * (g[0] * out[0] + g[1] * out[1] + g[2] * out[2]));
+  }
+};
+
+// q = w p + dt L p from the divergence val, then r -= alpha q, x += alpha p and the partial
+// sums of r^2.  rout = r, rout2 = x, aux0 = p, aux1 = w, coef[0] = dt, dscal[0] = alpha.
+template <typename R>
+struct ECgChemUpdate {
+  static constexpr int CIN = 1;
+  static constexpr bool RED = true;
+  static constexpr int PF_RIN = 0, PF_ROUT = 1, PF_ROUT2 = 1, PF_AUX0 = 1, PF_AUX1 = 1;
+  FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    const R al = sc[0];
+    const R p = a.aux[0][v];
+    const R q = a.aux[1][v] * p + a.coef[0] * val[0];
+    const R rn = a.rout[v] - al * q;
+    a.rout[v] = rn;
+    a.rout2[v] += al * p;
+    acc.add(rn * rn);
+  }
+};
+
 // ================================================================== float-float epilogues
 // The float-float passes store their results as FP64 (the fields they serve are FP64)
 // and accumulate norms in FP64.

@@ -335,6 +335,125 @@ struct XInv {
   }
 };
 
+// ------------------------------------------------------------------ X round trip
+
+// Inverse x-transform, a pointwise map and the forward x-transform in one pass: the
+// spectrum rows (transposed layout, CI components) come in, are turned into real rows
+// (C2R) in shared memory, Op maps the CI real values of each voxel to CO values in place,
+// and the forward R2C of those rows goes back out transposed.  The real-space
+// intermediate never reaches global memory.  Op::apply(a, v, val[CI], out[CO], acc, sc);
+// reducing ops write one partial sum per block.
+template <typename R, int N, class Op>
+struct XRound {
+  using C = cplx<R>;
+  static constexpr int CI = Op::CIN, CO = Op::COUT;
+  static_assert(CI == CO, "the tile holds the same components before and after");
+  static constexpr int ROWS = rows_x(N, CI, sizeof(C));
+  static constexpr int CR = ROWS / 2;
+  static constexpr int NROWS = CI * CR;
+  static constexpr int NT = round32(NROWS * tpr(N));
+  using TFi = TileFFT<R, N, NROWS, NT, true>;
+  using TFf = TileFFT<R, N, NROWS, NT, false>;
+  static constexpr int PITCH = TFi::PITCH;
+  static constexpr int VMAX = TFi::VMAX > TFf::VMAX ? TFi::VMAX : TFf::VMAX;
+  struct Locals {
+    C v[VMAX];
+    Acc<R> acc;
+  };
+  static size_t smem_bytes() { return (size_t)(NROWS * PITCH + N) * sizeof(C) + NT * sizeof(double); }
+  static int grid_x(int ny, int nz) { return (ny * nz + ROWS - 1) / ROWS; }
+
+  template <class Loc>
+  FG_DEV static void body(const PassArgs<R>& a, Dim3 bid, Dim3 grid, char* smem, Loc* Ls) {
+    if (a.done && *a.done) return;
+    C* tile = (C*)smem;
+    C* tw = tile + NROWS * PITCH;
+    double* red = (double*)(tw + N);
+    (void)red;
+    const int nrows = a.ny * a.nz;
+    const int row0 = bid.x * ROWS;
+    const int nr = nrows - row0 < ROWS ? nrows - row0 : ROWS;
+    constexpr int H = N / 2 + 1;
+    FG_PHASE(NT)
+    if (a.l2pf && tid == 0) prefetch_op_rows<Op>(a, (long long)row0 * N, (long long)nr * N, 0);
+    L.acc.zero();
+    for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
+    for (int e = tid; e < CI * CR * H; e += NT) {
+      const int q = e % CR, t = e / CR;
+      const int kx = t % H, c = t / H;
+      const int r0 = 2 * q;
+      C* row = tile + (c * CR + q) * PITCH;
+      if (r0 < nr) {
+        const long long base = c * a.VH + (long long)kx * nrows + row0 + r0;
+        const C A = a.cin[base];
+        const C B = (r0 + 1 < nr) ? a.cin[base + 1] : cmk<C>((R)0, (R)0);
+        if (kx == 0 || 2 * kx == N) {
+          row[pad16(kx)] = cmk<C>(A.x, B.x);
+        } else {
+          row[pad16(kx)] = cmk<C>(A.x - B.y, A.y + B.x);
+          row[pad16(N - kx)] = cmk<C>(A.x + B.y, B.x - A.y);
+        }
+      } else {  // rows past the grid: zeros, so the forward transform sees zero rows
+        row[pad16(kx)] = cmk<C>((R)0, (R)0);
+        if (kx != 0 && 2 * kx != N) row[pad16(N - kx)] = cmk<C>((R)0, (R)0);
+      }
+    }
+    FG_END_PHASE
+    tile_fft<TFi, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    const R sc[2] = {a.dscal ? (R)a.dscal[0] : (R)0, a.dscal ? (R)a.dscal[1] : (R)0};
+    for (int e = tid; e < nr * N; e += NT) {
+      const int r = e / N, x = e - r * N;
+      R val[CI], out[CO];
+#pragma unroll
+      for (int c = 0; c < CI; ++c) {
+        const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+        val[c] = (r & 1) ? z.y : z.x;
+      }
+      Op::apply(a, (long long)(row0 + r) * N + x, val, out, L.acc, sc);
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        C& z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+        if (r & 1) z.y = out[c]; else z.x = out[c];
+      }
+    }
+    // an odd last row's partner (the imaginary half of its complex row) is zero
+    if (nr & 1)
+      for (int e = tid; e < CO * N; e += NT) {
+        const int c = e / N, x = e - c * N;
+        tile[(c * CR + (nr >> 1)) * PITCH + pad16(x)].y = (R)0;
+      }
+    FG_END_PHASE
+    tile_fft<TFf, 0>(Ls, tile, tw, NT);
+    FG_PHASE(NT)
+    for (int e = tid; e < CO * nr * H; e += NT) {
+      const int r = e % nr, t = e / nr;
+      const int kx = t % H, c = t / H;
+      const C* row = tile + (c * CR + (r >> 1)) * PITCH;
+      const C zk = row[pad16(kx)];
+      const C zn = row[pad16((N - kx) % N)];
+      C val;
+      if (!(r & 1)) {
+        val = cmk<C>((zk.x + zn.x) * (R)0.5, (zk.y - zn.y) * (R)0.5);
+      } else {
+        const R dx = zk.x - zn.x, dy = zk.y + zn.y;
+        val = cmk<C>(dy * (R)0.5, -dx * (R)0.5);
+      }
+      a.cout[c * a.VH + (long long)kx * nrows + row0 + r] = val;
+    }
+    FG_END_PHASE
+    if constexpr (Op::RED) {
+      double s = 0.0;
+      FG_BLOCK_REDUCE(NT, red, s)
+#ifdef FG_EMU
+      a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#else
+      if (threadIdx.x == 0) a.partials[block_linear(bid, grid.x, grid.y)] = s;
+#endif
+    }
+  }
+};
+
 // ------------------------------------------------------------------ Y passes
 
 template <typename R, int N, bool INV>

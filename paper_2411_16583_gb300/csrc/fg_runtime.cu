@@ -807,6 +807,86 @@ static int cg_solve(fg_ctx& c, Prec<R>& P, long long n, int slot, double tol, in
   return k.iters;
 }
 
+// Chemistry CG (the linear solve of Alg. 3, operator y/m + dt L y) on P.b from x = 0 with
+// the vector updates fused into the operator passes: the forward X pass forms
+// p = r + beta p and <p, w p>, the flux round trip (inverse X, K_c g, forward X) adds
+// dt <g, K_c g>, so alpha is known before the inverse transform, whose epilogue forms
+// q = w p + dt L p and applies r -= alpha q, x += alpha p with the sums of r^2.  Per
+// iteration: three X passes, two Y-Z-Y chains and two single-block finalisers; q and the
+// real-space flux are never stored.
+template <typename R>
+static int cg_solve_chem(fg_ctx& c, Prec<R>& P, double dt, double tol, int maxit, fg_stats* st) {
+  int* truncated = st ? &st->cg_truncated : nullptr;
+  const long long n = c.V;
+  const int slot = KS_CHEM;
+  KScal* ks = c.ks + slot;
+  VArgs v = vbase(c, n);
+  v.in[0] = P.b;
+  v.out[0] = P.x;
+  v.out[1] = P.r;
+  v.out[2] = P.p;
+  launch_vec<KCgInit<R>>(v, c.st);
+  fin<FCgStart>(c, slot, VEC_BLOCKS, nullptr, tol, (double)maxit, (double)(c.o.cg_indefinite == 1));
+  const int* done = &ks->done;
+  const double* sc = &ks->alpha;  // sc[0] = alpha, sc[1] = beta
+  const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
+  auto iteration = [&]() {
+    PassArgs<R> a = pbase(c, P, done);
+    a.tw = P.twx;
+    a.rin = P.r;
+    a.rout = P.p;
+    a.aux[0] = P.w;
+    a.dscal = sc;
+    a.cout = P.S1;
+    const int nb1 = P.ox->xf_cgchem(a, c.st);
+    yzy(c, P, done, 1, P.oz->z_grad, 3, zc, nullptr);
+    a = pbase(c, P, done);
+    a.tw = P.twx;
+    a.cin = P.S1;
+    a.cout = P.S1;
+    a.aux[0] = P.kc;
+    a.coef[0] = (R)dt;
+    a.partials = c.partials + nb1;  // after the forward pass's partial sums
+    const int nb2 = P.ox->xr_chemflux(a, c.st);
+    fin<FAlpha>(c, slot, nb1 + nb2, done);
+    yzy(c, P, done, 3, P.oz->z_div, 1, zc, nullptr);
+    a = pbase(c, P, done);
+    a.tw = P.twx;
+    a.cin = P.S1;
+    a.rout = P.r;
+    a.rout2 = P.x;
+    a.aux[0] = P.p;
+    a.aux[1] = P.w;
+    a.coef[0] = (R)dt;
+    a.dscal = sc;
+    const int nb = P.ox->xi_cgchem(a, c.st);
+    fin<FBetaCg>(c, slot, nb, done);
+    snap_iterate(c, P, n, ks);
+  };
+  int chunk = 4;
+  while (true) {
+    for (int j = 0; j < chunk; ++j) iteration();
+    read_ks(c);
+    if (c.ks_host[slot].done) break;
+    if (chunk < 16) chunk *= 2;
+  }
+  const KScal& k = c.ks_host[slot];
+  if (st) st->cg_negcurv += k.negc;
+  if (k.status & ST_NUMERIC) fail(FG_ERR_NUMERIC, "Krylov solve produced a non-finite value");
+  if (k.status & ST_INDEFINITE) {
+    if (k.iters == 0) fail(FG_ERR_NUMERIC, "Krylov operator not positive along the residual");
+    keep_best(c, P, n, k);
+    if (truncated) *truncated += 1;
+    return k.iters;
+  }
+  if (k.rr > k.tol2 && k.iters >= maxit) {
+    if (!is_mixed(c) || c.strict) fail(FG_ERR_NOCONV, "Krylov solve hit max_cg");
+    keep_best(c, P, n, k);
+    if (truncated) *truncated += 1;
+  }
+  return k.iters;
+}
+
 // Mechanical CG (Alg. 1) on P.b from x = 0 with the vector updates fused into the
 // operator passes: X-fwd forms p = r + beta p and <p, K p>, X-inv applies r -= alpha q,
 // x += alpha p and sums |r|^2.  Per iteration: 5 passes + 2 single-block finalisers.
@@ -1452,9 +1532,7 @@ static void chem_solve(fg_ctx& c, Prec<R>& P, double dt, fg_stats& s) {
     double* b64 = is_mixed(c) ? c.pd.b : (double*)P.b;
     op_chem_rhs(c, b64, dt);
     if (is_mixed(c)) to_prec<R>(c, b64, P.b, c.V, 1.0);
-    const int n = cg_solve<R>(c, P, c.V, KS_CHEM, mixed_tol(c, c.o.tol_chem_cg), c.o.max_cg,
-                              [&](const R* p, R* q, const int* done) { return op_chem(c, P, p, q, dt, done); },
-                              &s);
+    const int n = cg_solve_chem<R>(c, P, dt, mixed_tol(c, c.o.tol_chem_cg), c.o.max_cg, &s);
     s.cg_chem += n;
     s.newton_chem += 1;
     // c = c_i + lambda y c_i (1 - c_i): halved (at most 10 times) while it leaves (0, 1)
