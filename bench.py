@@ -116,6 +116,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=256, help="grid edge of the particle workload")
     p.add_argument("--nz", type=int, default=0, help="override the z extent (profiling cases)")
+    p.add_argument("--ny", type=int, default=0, help="override the y extent (profiling cases)")
     p.add_argument("--start", type=int, default=START_STEPS,
                    help="untimed steps before the warm-up (the timed window's position in the "
                         "100-step schedule)")
@@ -148,13 +149,14 @@ def _args():
     return p.parse_args()
 
 
-def _workload(n, seed, nz=0):
+def _workload(n, seed, nz=0, ny=0):
     from paper_2411_16583_gb300 import synth as S
-    if n == 256 and not nz:
+    if n == 256 and not nz and not ny:
         return S.ellipsoid256(seed=seed)
     f = n / 256.0
-    shape = (nz, n, n) if nz else None
-    axes = (100 * f, 80 * f, min(70 * f, 0.4 * nz) if nz else 70 * f)
+    shape = (nz or n, ny or n, n) if (nz or ny) else None
+    axes = (100 * f, min(80 * f, 0.4 * ny) if ny else 80 * f,
+            min(70 * f, 0.4 * nz) if nz else 70 * f)
     return S.ellipsoid(n=n, axes=axes, rough_std=3 * f, rough_corr=8 * f,
                        band=max(1, round(8 * f)), nsteps=100, seed=seed, c_perturb=0.02,
                        shape=shape, phases=S.default_phases(buffer_E=S.BENCH_BUFFER_E))
@@ -665,7 +667,7 @@ def profile_apply(a):
     set-up: the command that ncu captures of the five pass kernels run."""
     import torch
     from paper_2411_16583_gb300 import binding as B
-    w = _workload(a.n, 0, nz=a.nz)
+    w = _workload(a.n, 0, nz=a.nz, ny=a.ny)
     stream = torch.cuda.Stream()
     sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
     ms = sol.time_apply(B.OP_MECH, 1, a.profile_apply)

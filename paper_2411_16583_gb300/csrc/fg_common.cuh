@@ -82,7 +82,7 @@ template <> struct Acc<float> {
 // 48 significant bits from FP32 instructions alone (GB300 issues FP64 at a small fraction
 // of its FP32 rate).  Sums use Knuth's error-free TwoSum and products the FMA form of
 // Dekker's TwoProduct, renormalised as in the double-double algorithms of Dekker (1971)
-// and Hida, Li and Bailey (2001); the quotient is one Newton correction of the float
+// and Hida, Li and Bailey (2001); the quotient is one correction step of the float
 // quotient.  The residual transforms of the mixed-precision mode run on it: stored in
 // FP64, transformed in float-float.  FP32 addition and multiplication are IEEE in both
 // builds; only explicit fmaf contracts.
@@ -107,13 +107,13 @@ FG_HD ff ff_quick_two_sum(float a, float b) {  // |a| >= |b| (or a = 0)
   const float s = a + b;
   return ff(s, b - (s - a));
 }
+// The sum of Dekker's add (the "sloppy" addition of the double-double literature): the low
+// parts are added in one float operation, so the error is within a few units of 2^-48 of
+// |a| + |b| (not of |a + b|): the norm-wise accuracy that transforms and projections need,
+// at 11 float operations instead of 20.
 FG_HD ff operator+(ff a, ff b) {
-  ff s = ff_two_sum(a.hi, b.hi);
-  const ff t = ff_two_sum(a.lo, b.lo);
-  s.lo += t.hi;
-  s = ff_quick_two_sum(s.hi, s.lo);
-  s.lo += t.lo;
-  return ff_quick_two_sum(s.hi, s.lo);
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
 FG_HD ff operator-(ff a) { return ff(-a.hi, -a.lo); }
 FG_HD ff operator-(ff a, ff b) { return a + (-b); }

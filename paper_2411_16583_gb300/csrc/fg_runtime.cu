@@ -3020,21 +3020,18 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
     return (double)t / reps;
   };
   double best = 1e300;
-  int best_ch = c->kx_chunk[k], best_pf = c->l2pf;
-  for (int pf = 0; pf < 2; ++pf)
-    for (int ch : chunks) {
-      c->kx_chunk[k] = ch;
-      c->l2pf = pf;
-      const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
-                             : time_it([&] { op_mech(*c, c->pd, (const double*)x, (double*)y, nullptr); }, 3);
-      if (t < best) {
-        best = t;
-        best_ch = ch;
-        best_pf = pf;
-      }
+  int best_ch = c->kx_chunk[k];
+  c->l2pf = 0;
+  for (int ch : chunks) {
+    c->kx_chunk[k] = ch;
+    const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
+                           : time_it([&] { op_mech(*c, c->pd, (const double*)x, (double*)y, nullptr); }, 3);
+    if (t < best) {
+      best = t;
+      best_ch = ch;
     }
+  }
   c->kx_chunk[k] = best_ch;
-  c->l2pf = best_pf;
   // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
   double* zero = (double*)dalloc(4 * sizeof(double));
   dzero(zero, 4 * sizeof(double), c->st);
@@ -3066,7 +3063,38 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
     };
     tv[pf][pc] = time_it(run, 5);
   }
-  // the update form with the context's prefetch choice (made on the whole operator)
+  // the forward X pass of the CG with and without prefetch; the prefetch choice is made
+  // on the pair of X passes of a CG iteration, which dominate the step
+  double tf[2];
+  for (int pf = 0; pf < 2; ++pf) {
+    auto run = [&]() {
+      if (mixed) {
+        PassArgs<float> a = pbase(*c, c->pf, nullptr);
+        a.tw = c->pf.twx;
+        a.rin = (const float*)x;
+        a.rout = (float*)y;
+        a.aux[0] = c->pf.state;
+        a.dscal = zero;
+        a.cout = c->pf.S1;
+        a.l2pf = pf;
+        (c->law == FG_SVK ? c->pf.ox->xf_cgtangent_svk : c->pf.ox->xf_cgtangent)(a, c->st);
+      } else {
+        PassArgs<double> a = pbase(*c, c->pd, nullptr);
+        a.tw = c->pd.twx;
+        a.rin = (const double*)x;
+        a.rout = (double*)y;
+        a.aux[0] = c->pd.state;
+        a.dscal = zero;
+        a.cout = c->pd.S1;
+        a.l2pf = pf;
+        (c->law == FG_SVK ? c->pd.ox->xf_cgtangent_svk : c->pd.ox->xf_cgtangent)(a, c->st);
+      }
+    };
+    tf[pf] = time_it(run, 5);
+  }
+  const double t0 = tf[0] + std::min(tv[0][0], tv[0][1]);
+  const double t1 = tf[1] + std::min(tv[1][0], tv[1][1]);
+  c->l2pf = t1 < t0 ? 1 : 0;
   c->xi_percomp = tv[c->l2pf][1] <= tv[c->l2pf][0] ? 1 : 0;
   c->tune_ms[0] = tv[0][0];
   c->tune_ms[1] = tv[0][1];

@@ -9,7 +9,14 @@ them to ``tests/golden/<case>.npz``.
 FP64 bars: the GPU FP64 path within 1e-10 of the oracle in F and c (relative to the field's
 largest magnitude in the sample) and 1e-8 in d and H, whose damaging solves amplify
 round-off at the crack front.  Mixed FP32/FP64 bars: 1e-7 in F and c, 1e-6 in d, and the
-fracture energy within 1e-6 relative."""
+fracture energy within 1e-6 relative.
+
+Where a voxel is cracked through (d > 0.9 in the oracle's field), its stiffness (1 - d)^2
+is below 1e-2 of the particle's and F and H there are fixed only to the equilibrium
+tolerance divided by that stiffness: any two solutions that meet err_res <= tol_stag may
+differ there by more than the bars.  F and H are compared on the other sampled voxels, and
+the GPU's whole fields must be a valid solution: the oracle's err_res of them (Eq.
+mechresiduum) within twice the staggered tolerance."""
 import os
 
 import numpy as np
@@ -17,8 +24,9 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import fg_oracle as O
 from paper_2411_16583_gb300 import binding as B
-from tests.golden.make_oracle_trajectories import workload
+from tests.golden.make_oracle_trajectories import oracle_params, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +55,7 @@ def _crack_energy(d, w):
 def _compare(case, precision, lib):
     ref = np.load(os.path.join(HERE, f"{case}.npz"))
     w = workload(case)
+    prm = oracle_params(w)
     sol = B.from_workload(w, precision=precision, lib=lib)
     steps = [int(k) for k in ref["steps"]]
     bars = BARS[precision]
@@ -60,17 +69,22 @@ def _compare(case, precision, lib):
         F = sol.get(B.FIELD_F).reshape(9, -1)[:, idx]
         c, d, H = (sol.get(f).ravel()[idx] for f in (B.FIELD_C, B.FIELD_D, B.FIELD_H))
         err = {}
-        for name, got, want in (("F", F, ref[f"F_s{k}"]), ("c", c, ref[f"c_s{k}"])):
-            err[name] = float(np.abs(got - want).max() / np.abs(want).max())
-        for name, got, want in (("d", d, ref[f"d_s{k}"]), ("H", H, ref[f"H_s{k}"])):
-            scale = max(np.abs(want).max(), 1.0 if name == "d" else 1e-30)
-            err[name] = float(np.abs(got - want).max() / scale)
+        sound = ref[f"d_s{k}"] <= 0.9  # voxels not cracked through
+        Fw = ref[f"F_s{k}"]
+        err["F"] = float(np.abs(F - Fw)[:, sound].max() / np.abs(Fw).max())
+        err["c"] = float(np.abs(c - ref[f"c_s{k}"]).max() / np.abs(ref[f"c_s{k}"]).max())
+        err["d"] = float(np.abs(d - ref[f"d_s{k}"]).max())
+        Hw = ref[f"H_s{k}"]
+        err["H"] = float(np.abs(H - Hw)[sound].max() / max(np.abs(Hw[sound]).max(), 1e-30))
         mass, energy, dmax, ndam, _ = ref[f"scal_s{k}"]
         dfull = sol.get(B.FIELD_D)
         e = _crack_energy(dfull, w)
         err["energy"] = abs(e - energy) / energy if energy > 0 else abs(e)
         report[k] = err
         assert abs(sol.get(B.FIELD_C).sum() - mass) <= 1e-11 * mass, (k, "mass")
+        _, err_res = O.mech_residual(sol.get(B.FIELD_F), sol.get(B.FIELD_C), dfull, prm,
+                                     np.eye(3))
+        assert err_res <= 2 * w.tol["tol_stag"], (k, "err_res", err_res)
         assert abs(int((dfull > 1e-3).sum()) - ndam) <= max(2, 0.01 * ndam), (k, "damaged")
         for name, bar in bars.items():
             assert err[name] <= bar, (case, k, name, err)
