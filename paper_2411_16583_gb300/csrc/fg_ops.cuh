@@ -322,14 +322,21 @@ struct ECgUpdate1 {
   static constexpr int PF_RIN = 0, PF_ROUT = 9, PF_ROUT2 = 9,
                        PF_AUX0 = 9, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    apply_ops(a, v, load_ops(a, v), val, acc, sc);
+  }
+  // the operands of one element, loaded ahead of the update (grouped loads in X-inv)
+  struct Ops {
+    R r, x, p;
+  };
+  FG_DEV static Ops load_ops(const PassArgs<R>& a, long long v) {
+    return Ops{a.rout[v], a.rout2[v], a.aux[0][v]};
+  }
+  FG_DEV static void apply_ops(const PassArgs<R>& a, long long v, const Ops& o, const R* val,
+                               Acc<R>& acc, const R* sc) {
     const R al = sc[0];
-    R* __restrict__ r = a.rout;
-    R* __restrict__ x = a.rout2;
-    const R* __restrict__ p = a.aux[0];
-    const R r0 = r[v], x0 = x[v], p0 = p[v];  // loads before stores
-    const R rn = r0 - al * (val[0] + a.coef[1] * p0);
-    r[v] = rn;
-    x[v] = x0 + al * p0;
+    const R rn = o.r - al * (val[0] + a.coef[1] * o.p);
+    a.rout[v] = rn;
+    a.rout2[v] = o.x + al * o.p;
     acc.add(rn * rn);
   }
 };
@@ -378,10 +385,23 @@ struct EStoreDot {
   static constexpr int PF_RIN = 0, PF_ROUT = 0, PF_ROUT2 = 0,
                        PF_AUX0 = NC, PF_AUX1 = 0;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    apply_ops(a, v, load_ops(a, v), val, acc, sc);
+  }
+  struct Ops {
+    R x[NC];
+  };
+  FG_DEV static Ops load_ops(const PassArgs<R>& a, long long v) {
+    Ops o;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) o.x[c] = a.aux[0][c * a.V + v];
+    return o;
+  }
+  FG_DEV static void apply_ops(const PassArgs<R>& a, long long v, const Ops& o, const R* val,
+                               Acc<R>& acc, const R*) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       a.rout[c * a.V + v] = val[c];
-      acc.add(val[c] * a.aux[0][c * a.V + v]);
+      acc.add(val[c] * o.x[c]);
     }
   }
 };
@@ -519,12 +539,21 @@ struct ECgChemUpdate {
   static constexpr bool RED = true;
   static constexpr int PF_RIN = 0, PF_ROUT = 1, PF_ROUT2 = 1, PF_AUX0 = 1, PF_AUX1 = 1;
   FG_DEV static void apply(const PassArgs<R>& a, long long v, const R* val, Acc<R>& acc, const R* sc) {
+    apply_ops(a, v, load_ops(a, v), val, acc, sc);
+  }
+  struct Ops {
+    R p, w, r, x;
+  };
+  FG_DEV static Ops load_ops(const PassArgs<R>& a, long long v) {
+    return Ops{a.aux[0][v], a.aux[1][v], a.rout[v], a.rout2[v]};
+  }
+  FG_DEV static void apply_ops(const PassArgs<R>& a, long long v, const Ops& o, const R* val,
+                               Acc<R>& acc, const R* sc) {
     const R al = sc[0];
-    const R p = a.aux[0][v];
-    const R q = a.aux[1][v] * p + a.coef[0] * val[0];
-    const R rn = a.rout[v] - al * q;
+    const R q = o.w * o.p + a.coef[0] * val[0];
+    const R rn = o.r - al * q;
     a.rout[v] = rn;
-    a.rout2[v] += al * p;
+    a.rout2[v] = o.x + al * o.p;
     acc.add(rn * rn);
   }
 };

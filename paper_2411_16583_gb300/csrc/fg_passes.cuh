@@ -71,6 +71,15 @@ FG_DEV void l2_prefetch(const void* p, long long bytes) {
 #endif
 }
 
+// Epilogues that can load an element's operands apart from its update (Op::Ops,
+// Op::load_ops, Op::apply_ops): X-inv then loads the operands of a group of elements
+// before it updates any of them, so each thread has several loads in flight.
+template <class Op, class = void>
+struct HasOps : std::false_type {};
+template <class Op>
+struct HasOps<Op, std::void_t<typename Op::Ops>> : std::true_type {};
+constexpr int XINV_GROUP = 4;
+
 // Components of each real-space field an X-pass functor reads (0: none); functors that
 // declare none are not prefetched.
 template <class Op, class = void>
@@ -291,20 +300,36 @@ struct XInv {
     L.acc.zero();
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
     constexpr int H = N / 2 + 1;
-    for (int e = tid; e < CI * CR * H; e += NT) {
-      const int q = e % CR, t = e / CR;
-      const int kx = t % H, c = t / H;
-      const int r0 = 2 * q;
-      if (r0 < nr) {
-        const long long base = c * a.VH + (long long)kx * nrows + row0 + r0;
-        const C A = a.cin[base];
-        const C B = (r0 + 1 < nr) ? a.cin[base + 1] : cmk<C>((R)0, (R)0);
-        C* row = tile + (c * CR + q) * PITCH;
-        if (kx == 0 || 2 * kx == N) {
-          row[pad16(kx)] = cmk<C>(A.x, B.x);
-        } else {
-          row[pad16(kx)] = cmk<C>(A.x - B.y, A.y + B.x);
-          row[pad16(N - kx)] = cmk<C>(A.x + B.y, B.x - A.y);
+    constexpr int G = XINV_GROUP;
+    // spectrum pairs of G elements loaded before any is unpacked into the tile
+    for (int e0 = tid; e0 < CI * CR * H; e0 += G * NT) {
+      C A[G], B[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * NT;
+        const int q = e % CR, t = e / CR;
+        const int kx = t % H, c = t / H;
+        const int r0 = 2 * q;
+        if (e < CI * CR * H && r0 < nr) {
+          const long long base = c * a.VH + (long long)kx * nrows + row0 + r0;
+          A[u] = a.cin[base];
+          B[u] = (r0 + 1 < nr) ? a.cin[base + 1] : cmk<C>((R)0, (R)0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * NT;
+        const int q = e % CR, t = e / CR;
+        const int kx = t % H, c = t / H;
+        const int r0 = 2 * q;
+        if (e < CI * CR * H && r0 < nr) {
+          C* row = tile + (c * CR + q) * PITCH;
+          if (kx == 0 || 2 * kx == N) {
+            row[pad16(kx)] = cmk<C>(A[u].x, B[u].x);
+          } else {
+            row[pad16(kx)] = cmk<C>(A[u].x - B[u].y, A[u].y + B[u].x);
+            row[pad16(N - kx)] = cmk<C>(A[u].x + B[u].y, B[u].x - A[u].y);
+          }
         }
       }
     }
@@ -312,15 +337,45 @@ struct XInv {
     tile_fft<TF, 0>(Ls, tile, tw, NT);
     FG_PHASE(NT)
     const R sc[2] = {a.dscal ? (R)a.dscal[0] : (R)0, a.dscal ? (R)a.dscal[1] : (R)0};
-    for (int e = tid; e < nr * N; e += NT) {
-      const int r = e / N, x = e - r * N;
-      R val[CI];
+    if constexpr (HasOps<Op>::value) {
+      // groups of XINV_GROUP elements: every operand load of the group is issued before
+      // the first update (elements are distinct, so no update feeds a load of the group)
+      for (int e0 = tid; e0 < nr * N; e0 += XINV_GROUP * NT) {
+        typename Op::Ops o[XINV_GROUP];
 #pragma unroll
-      for (int c = 0; c < CI; ++c) {
-        const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
-        val[c] = (r & 1) ? z.y : z.x;
+        for (int u = 0; u < XINV_GROUP; ++u) {
+          const int e = e0 + u * NT;
+          if (e < nr * N) {
+            const int r = e / N, x = e - r * N;
+            o[u] = Op::load_ops(a, (long long)(row0 + r) * N + x);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < XINV_GROUP; ++u) {
+          const int e = e0 + u * NT;
+          if (e < nr * N) {
+            const int r = e / N, x = e - r * N;
+            R val[CI];
+#pragma unroll
+            for (int c = 0; c < CI; ++c) {
+              const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+              val[c] = (r & 1) ? z.y : z.x;
+            }
+            Op::apply_ops(a, (long long)(row0 + r) * N + x, o[u], val, L.acc, sc);
+          }
+        }
       }
-      Op::apply(a, (long long)(row0 + r) * N + x, val, L.acc, sc);
+    } else {
+      for (int e = tid; e < nr * N; e += NT) {
+        const int r = e / N, x = e - r * N;
+        R val[CI];
+#pragma unroll
+        for (int c = 0; c < CI; ++c) {
+          const C z = tile[(c * CR + (r >> 1)) * PITCH + pad16(x)];
+          val[c] = (r & 1) ? z.y : z.x;
+        }
+        Op::apply(a, (long long)(row0 + r) * N + x, val, L.acc, sc);
+      }
     }
     FG_END_PHASE
     if constexpr (Op::RED) {
