@@ -121,6 +121,9 @@ typedef struct {
                          arithmetic (pairs of FP32, about 48 significant bits, error-free
                          TwoSum/TwoProduct) on the FP32 pipes; 0: in FP64 arithmetic.  The
                          fields, updates, norms and sums stay FP64 either way */
+  int z_columns;      /* kx-ky columns per block of the FP32 projection pass where the
+                         transform length along z is a square (64, 256): 0 (default) the
+                         built-in tile, 1 or 4; fg_autotune overrides it */
 } fg_opts;
 
 typedef struct {
@@ -242,12 +245,15 @@ int fg_adjoint_mech(fg_ctx* ctx, const double* W, double* grad_logE, int* iters)
  * of the X passes on or off, and a one-component-per-block or nine-component X-inv CG
  * update) and keeps the fastest.  ms_per_iteration (may be NULL) receives the best
  * operator time.  Allocates two temporary 9 V vectors.
- * fg_autotune_report returns the choices in force, choice[3] = {kx planes per chunk of
+ * In a mixed context it also times the FP32 projection pass with 1 and 4 kx-ky columns
+ * per block against its default tile.
+ * fg_autotune_report returns the choices in force, choice[4] = {kx planes per chunk of
  * the Krylov precision, X-inv update one component per block (1) or nine (0), L2 prefetch
- * (1) or not (0)}, and (xinv_ms, may be NULL) the autotuner's X-inv update times
- * [prefetch off, nine; off, one; on, nine; on, one] in ms (zeros before fg_autotune). */
+ * (1) or not (0), columns per block of the FP32 projection pass (0: default)}, and
+ * (xinv_ms, may be NULL) the autotuner's X-inv update times [prefetch off, nine; off, one;
+ * on, nine; on, one] in ms (zeros before fg_autotune). */
 int fg_autotune(fg_ctx* ctx, double* ms_per_iteration);
-int fg_autotune_report(fg_ctx* ctx, int choice[3], double xinv_ms[4]);
+int fg_autotune_report(fg_ctx* ctx, int choice[4], double xinv_ms[4]);
 
 /* Launch-site profiling.  While a site is enabled, every launch at that site is
  * bracketed by two CUDA events on the context stream (at most 32768 launches are recorded

@@ -93,6 +93,9 @@ struct SizeOps {
   PassFn<R> xf_cgchem, xr_chemflux, xi_cgchem;
   PassFn<R> yf, yi;
   PassFn<R> z_proj, z_lap, z_prec, z_grad, z_div;
+  // the projection pass with 1 and 4 rows per block (register-direct sizes; null
+  // elsewhere): tile shapes the autotuner times against the default
+  PassFn<R> z_proj_rows[2];
   // FP64 only (null in the FP32 table): displacement at the corners and its transpose
   PassFn<R> xi_store9, z_disp, z_dispT;
 };
@@ -150,6 +153,10 @@ SizeOps<R> make_size_ops() {
     s.yf = run_y<YPassD<R, N, false>, R>;
     s.yi = run_y<YPassD<R, N, true>, R>;
     s.z_proj = run_z<ZPassD<R, N, ZProject<R>>, R>;
+    if constexpr (std::is_same<R, float>::value && N >= 64) {
+      s.z_proj_rows[0] = run_z<ZPassD<R, N, ZProject<R>, 1>, R>;
+      s.z_proj_rows[1] = run_z<ZPassD<R, N, ZProject<R>, 4>, R>;
+    }
     s.z_lap = run_z<ZPassD<R, N, ZLaplace<R>>, R>;
     s.z_prec = run_z<ZPassD<R, N, ZPrecond<R>>, R>;
     s.z_grad = run_z<ZPassD<R, N, ZGrad<R>>, R>;

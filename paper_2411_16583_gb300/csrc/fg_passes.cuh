@@ -666,7 +666,8 @@ struct YPassD {
   }
 };
 
-template <typename R, int N, class Op>
+// RZ > 0 overrides the rows per block (tile-shape variants the autotuner times)
+template <typename R, int N, class Op, int RZ = 0>
 struct ZPassD {
   using C = cplx<R>;
   using SQ = Square<N>;
@@ -674,7 +675,7 @@ struct ZPassD {
   static constexpr int CI = Op::CIN;
   static constexpr int CO = Op::COUT;
   static constexpr int CM = CI > CO ? CI : CO;
-  static constexpr int ROWS = rows_z(N, CM, sizeof(C));
+  static constexpr int ROWS = RZ > 0 ? RZ : rows_z(N, CM, sizeof(C));
   static constexpr int NT = round32(CM * ROWS * T);
   static constexpr int PITCH = row_pitch(N);
   struct Locals {

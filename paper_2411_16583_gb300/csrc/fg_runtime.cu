@@ -252,6 +252,7 @@ struct fg_ctx {
   int kx_chunk[2] = {1, 1};          // kx planes per Y-Z-Y chunk (FP32, FP64)
   int xi_percomp = 1;                // fused CG update: one component per block
   int l2pf = 0;                      // X passes prefetch their real-space rows into L2
+  int zrows = 0;                     // FP32 projection pass: 0 default tile, 1: 1 row, 2: 4 rows
   double tune_ms[4] = {0, 0, 0, 0};  // autotuner: X-inv update times [prefetch][per comp]
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
@@ -541,6 +542,13 @@ static void yzy(fg_ctx& c, Prec<R>& P, const int* done, int cin, PassFn<R> zop, 
   }
 }
 
+// the projection pass of the context's tile shape (the autotuner's choice, FP32 only)
+template <typename R>
+static PassFn<R> zproj(const fg_ctx& c, const Prec<R>& P) {
+  if (c.zrows > 0 && P.oz->z_proj_rows[c.zrows - 1]) return P.oz->z_proj_rows[c.zrows - 1];
+  return P.oz->z_proj;
+}
+
 // y = G : F^-1[ F[K : x] ] ; accumulates <x, y>; returns partial count
 template <typename R>
 static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
@@ -555,7 +563,7 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
   }
   const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
   static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
-  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
+  yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr, sites);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -574,7 +582,7 @@ static int op_gres(fg_ctx& c, Prec<R>& P, const io_t<R>* x, io_t<R>* y, const in
   a.cout = P.S1;
   P.ox->xf_copy9(a, c.st);
   const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
-  yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr);
+  yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -931,7 +939,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
     fin<FAlpha>(c, slot, nb, done);
     {
       static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
-      yzy(c, P, done, 9, P.oz->z_proj, 9, zc, nullptr, sites);
+      yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr, sites);
     }
     a = pbase(c, P, done);
     a.tw = P.twx;
@@ -2485,6 +2493,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (o.chem_full_jacobian != 0 && o.chem_full_jacobian != 1) fail(FG_ERR_INVALID, "fg_setup: chem_full_jacobian");
   if (o.l2_prefetch != 0 && o.l2_prefetch != 1) fail(FG_ERR_INVALID, "fg_setup: l2_prefetch");
   if (o.residual_ff != 0 && o.residual_ff != 1) fail(FG_ERR_INVALID, "fg_setup: residual_ff");
+  if (o.z_columns != 0 && o.z_columns != 1 && o.z_columns != 4) fail(FG_ERR_INVALID, "fg_setup: z_columns");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;
@@ -2502,6 +2511,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     c->h[2] = g->hz;
     c->o = o;
     c->l2pf = o.l2_prefetch;
+    c->zrows = o.z_columns == 1 ? 1 : (o.z_columns == 4 ? 2 : 0);
     c->st = (cudaStream_t)o.cuda_stream;
     const long long V = c->V;
     // per-voxel material on the host
@@ -3032,6 +3042,19 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
     }
   }
   c->kx_chunk[k] = best_ch;
+  if (mixed) {  // tile shapes of the FP32 projection pass
+    int best_z = 0;
+    for (int zr = 1; zr <= 2; ++zr) {
+      if (!c->pf.oz->z_proj_rows[zr - 1]) continue;
+      c->zrows = zr;
+      const double t = time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5);
+      if (t < best) {
+        best = t;
+        best_z = zr;
+      }
+    }
+    c->zrows = best_z;
+  }
   // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
   double* zero = (double*)dalloc(4 * sizeof(double));
   dzero(zero, 4 * sizeof(double), c->st);
@@ -3112,12 +3135,13 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   FG_API_END
 }
 
-int fg_autotune_report(fg_ctx* c, int choice[3], double xinv_ms[4]) {
+int fg_autotune_report(fg_ctx* c, int choice[4], double xinv_ms[4]) {
   FG_API_BEGIN
   if (!c || !choice) fail(FG_ERR_INVALID, "fg_autotune_report: bad argument");
   choice[0] = c->kx_chunk[is_mixed(*c) ? 0 : 1];
   choice[1] = c->xi_percomp;
   choice[2] = c->l2pf;
+  choice[3] = c->zrows == 1 ? 1 : (c->zrows == 2 ? 4 : 0);
   if (xinv_ms)
     for (int k = 0; k < 4; ++k) xinv_ms[k] = c->tune_ms[k];
   FG_API_END

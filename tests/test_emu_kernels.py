@@ -676,3 +676,25 @@ def test_emulated_float_float_residuals_match_fp64_residuals(emu):
     assert rel_err(out[0][1], out[1][1]) < 1e-10
     for a, b in zip(out[0][2], out[1][2]):
         assert a["newton_mech"] == b["newton_mech"] and a["newton_chem"] == b["newton_chem"]
+
+
+@pytest.mark.parametrize("zc", [1, 4])
+@pytest.mark.parametrize("shape", [(64, 12, 16), (256, 8, 8), (64, 1, 24)])
+def test_emulated_projection_tile_shapes_match_oracle(emu, shape, zc):
+    """The FP32 projection pass with 1 and 4 kx-ky columns per block (the autotuner's tile
+    shapes) gives the oracle's mechanical operator, ragged last blocks included."""
+    pid = S.random_phase_map(shape, 1)
+    phases = S.default_phases()
+    phases[1].E = 2e9
+    sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu, precision=B.FG_MIXED,
+                   z_columns=zc)
+    F, c, d = S.random_state(shape, seed=2)
+    for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d)):
+        sol.set(f, v)
+    x = S.random_tensor_field(shape, 3).astype(np.float32)
+    y = np.zeros_like(x)
+    sol.apply(B.OP_MECH, x, y, 1)
+    prm = oracle_params(phases, pid, H3)
+    ref = O.mech_apply(F.reshape((3, 3) + shape), c, d, prm, x.astype(float).reshape((3, 3) + shape))
+    assert rel_err(y.reshape(ref.shape), ref) < TOL_APPLY_FP32
+    sol.close()
