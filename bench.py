@@ -138,6 +138,10 @@ def _args():
     p.add_argument("--profile-apply", type=int, default=0,
                    help="only run this many FP32 mechanical operator applications on the "
                         "workload (a small case for ncu captures) and print their time")
+    p.add_argument("--l2-prefetch", type=int, default=0,
+                   help="profile-apply: the X passes' L2 prefetch (the autotuner's choice)")
+    p.add_argument("--z-columns", type=int, default=0,
+                   help="profile-apply: columns per block of the projection pass (0, 1, 4)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -669,7 +673,8 @@ def profile_apply(a):
     from paper_2411_16583_gb300 import binding as B
     w = _workload(a.n, 0, nz=a.nz, ny=a.ny)
     stream = torch.cuda.Stream()
-    sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream)
+    sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream,
+                          l2_prefetch=a.l2_prefetch, z_columns=a.z_columns)
     ms = sol.time_apply(B.OP_MECH, 1, a.profile_apply)
     sol.close()
     return {"mode": "profile-apply", "shape": list(w.shape), "applies": a.profile_apply,

@@ -19,7 +19,9 @@ Cases:
                  stiffness and strength, Omega = 1.3, full chemistry Jacobian): its first
                  two steps (the second one damages)
 
-Output ``tests/golden/<case>.npz`` holds, per recorded step s (arrays suffixed _s<k>):
+Recorded steps: the last undamaged step, the first damaging step and the steps after it
+that the case asks for (or the last step when nothing cracks).  Output
+``tests/golden/<case>.npz`` holds, per recorded step s (arrays suffixed _s<k>):
 the flat voxel indices of the sample (a seeded random set plus the voxels of largest d),
 F (9 x n), c, d, H at those voxels, and the scalars mass = sum c, the fracture energy of
 Eq. crack, max d, the number of voxels with d > 1e-3 and the staggered iterations.
@@ -74,15 +76,15 @@ def sample(st, V, seed):
     return np.unique(np.concatenate([idx, top]))
 
 
-def record(out, k, st, prm, stats, V):
+def record(k, st, prm, stats, V):
     idx = sample(st, V, 1000 + k)
-    out[f"idx_s{k}"] = idx
-    out[f"F_s{k}"] = st.F.reshape(9, V)[:, idx]
-    out[f"c_s{k}"] = st.c.ravel()[idx]
-    out[f"d_s{k}"] = st.d.ravel()[idx]
-    out[f"H_s{k}"] = st.H.ravel()[idx]
-    out[f"scal_s{k}"] = np.array([st.c.sum(), O.crack_energy(st.d, prm), st.d.max(),
-                                  float((st.d > 1e-3).sum()), float(stats["stag"])])
+    return {f"idx_s{k}": idx,
+            f"F_s{k}": st.F.reshape(9, V)[:, idx],
+            f"c_s{k}": st.c.ravel()[idx],
+            f"d_s{k}": st.d.ravel()[idx],
+            f"H_s{k}": st.H.ravel()[idx],
+            f"scal_s{k}": np.array([st.c.sum(), O.crack_energy(st.d, prm), st.d.max(),
+                                    float((st.d > 1e-3).sum()), float(stats["stag"])])}
 
 
 def run(case):
@@ -93,6 +95,7 @@ def run(case):
     out = {}
     recorded = []
     first_damage = None
+    prev = None  # the record of the step before (kept until damage appears)
     log = open(os.path.join(HERE, f"{case}.log"), "w")
     for k in range(1, MAX_STEPS[case] + 1):
         t0 = time.time()
@@ -102,11 +105,16 @@ def run(case):
                               "cg_mech": stats.get("cg_mech", 0), "cg_pff": stats.get("cg_pff", 0),
                               "dmax": float(st.d.max()), "damaged": nd}) + "\n")
         log.flush()
+        rec = record(k, st, prm, stats, V)
         if first_damage is None and nd > 0:
             first_damage = k
+            if prev is not None:  # the last undamaged step as well
+                out.update(prev)
+                recorded.append(k - 1)
         if first_damage is not None or k == MAX_STEPS[case]:
-            record(out, k, st, prm, stats, V)
+            out.update(rec)
             recorded.append(k)
+        prev = rec
         if first_damage is not None and k >= first_damage + AFTER_DAMAGE[case]:
             break
     out["steps"] = np.array(recorded)

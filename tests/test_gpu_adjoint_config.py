@@ -49,13 +49,19 @@ def _loss(sol, s):
 
 
 def test_adjoint_128_matches_central_differences(lib):
-    """128^3, one FP64 step at Newton 1e-12 / Krylov 1e-13 (the chaining of steps through
-    checkpoints is checked on the 32^3 sphere of test_gpu_parity.py): the gradient with
-    respect to log E and log D at 32 seeded particle voxels (16 each) against central
-    differences of the forward at h = 1e-6.  The toughness gradient is 0 (no damage; g_c(x)
-    cancels from the phase field as the history carries it)."""
+    """128^3, one step, the hand-written FP64 reverse pass: the gradient with respect to log E
+    and log D at 32 seeded particle voxels (16 each) against central differences of the
+    forward at h = 1e-6, and at 8 of them also at h = 1e-4.  The differenced forwards run in
+    the mixed form at Newton 1e-12 / Krylov 1e-13 (the same converged solution map as the
+    FP64 form; a forward takes about a second instead of ten).  At h = 1e-6 the difference
+    quotient of a loss summed over 2 M voxels carries solver noise of order 1e-4 of the
+    largest gradient entry; at h = 1e-4 that noise is 100 times smaller while the
+    truncation error (h^2) stays far below it, so there the bar is tight.  The toughness
+    gradient is 0 (no damage; g_c(x) cancels from the phase field as the history carries
+    it).  The chaining of steps through checkpoints is checked on the 32^3 sphere of
+    test_gpu_parity.py."""
     w = _particle(128)
-    nsteps, h = 1, 1e-6
+    nsteps = 1
     s = _seeds(w.shape)
     sol = B.from_workload(w, lib=lib, **TIGHT)
     sol.tape(1)
@@ -74,7 +80,7 @@ def test_adjoint_128_matches_central_differences(lib):
         logs[field].flat[v] += dx
         x = B.Solver(w.shape, w.h, w.phases, w.phase_id, w.cdot_B, c_init=w.c_init,
                      log_E=logs["E"], log_D=logs["D"], log_gc=w.log_gc, lib=lib, gc=w.gc,
-                     lc=w.lc, **{**w.tol, **TIGHT})
+                     lc=w.lc, precision=B.FG_MIXED, **{**w.tol, **TIGHT})
         for _ in range(nsteps):
             x.step(w.dt)
         val = _loss(x, s)
@@ -82,16 +88,17 @@ def test_adjoint_128_matches_central_differences(lib):
         return val
 
     scale = {k: np.abs(g[k]).max() for k in ("E", "D")}
-    errs = []
+    errs, errs_wide = [], []
     for field, vox in picks.items():
-        for v in vox:
-            fd = (loss_with(field, v, h) - loss_with(field, v, -h)) / (2 * h)
+        for j, v in enumerate(vox):
+            fd = (loss_with(field, v, 1e-6) - loss_with(field, v, -1e-6)) / 2e-6
             errs.append((field, int(v), abs(fd - g[field].flat[v]) / scale[field]))
-    # The forward solves stop at err_res 1e-12 and the chemistry at 1e-12: at h = 1e-6 the
-    # difference quotient of a loss summed over 2 M voxels carries noise of about 1e-4 of
-    # the largest gradient entry (measured: 1.0e-4 at the worst voxel of two-step runs)
-    assert max(e for _, _, e in errs) <= 3e-4, errs
-    assert np.median([e for _, _, e in errs]) <= 1e-4, errs
+            if j < 4:
+                fd = (loss_with(field, v, 1e-4) - loss_with(field, v, -1e-4)) / 2e-4
+                errs_wide.append((field, int(v), abs(fd - g[field].flat[v]) / scale[field]))
+    assert max(e for _, _, e in errs) <= 5e-4, errs
+    assert np.median([e for _, _, e in errs]) <= 2e-4, errs
+    assert max(e for _, _, e in errs_wide) <= 2e-5, errs_wide
 
 
 def test_adjoint_reduced_3d_matches_oracle(lib):
