@@ -42,8 +42,9 @@ MEASURED_TRAFFIC_B_PER_VOXEL = {"xi": 203.6, "xf": 181.2}
 MECH_ALG_B_PER_VOXEL = 116.0
 # DRAM bytes per voxel that ncu measured over the five kernels of one FP32 mechanical
 # operator application (fg_time_apply) on a 256 x 256 x 64 grid (x rows of 256), summed over
-# the kernels and divided by the voxels; None until captured for the kernels as they are
-MEASURED_APPLY_TRAFFIC_B_PER_VOXEL = None
+# the kernels and divided by the voxels (the autotuner's choices: no L2 prefetch, one
+# column per block in the projection pass); valid for these kernels as they are
+MEASURED_APPLY_TRAFFIC_B_PER_VOXEL = 386.5
 
 
 def APPLY_SCHEDULED_B_PER_VOXEL(nx):

@@ -55,8 +55,9 @@ def test_adjoint_128_matches_central_differences(lib):
     the mixed form at Newton 1e-12 / Krylov 1e-13 (the same converged solution map as the
     FP64 form; a forward takes about a second instead of ten).  At h = 1e-6 the difference
     quotient of a loss summed over 2 M voxels carries solver noise of order 1e-4 of the
-    largest gradient entry; at h = 1e-4 that noise is 100 times smaller while the
-    truncation error (h^2) stays far below it, so there the bar is tight.  The toughness
+    largest gradient entry (measured: up to 5e-4 at single voxels, FP64 or mixed forwards);
+    at h = 1e-4 that noise is 100 times smaller while the truncation error (h^2) stays far
+    below it, so there the bar is tight.  The toughness
     gradient is 0 (no damage; g_c(x) cancels from the phase field as the history carries
     it).  The chaining of steps through checkpoints is checked on the 32^3 sphere of
     test_gpu_parity.py."""
@@ -96,9 +97,9 @@ def test_adjoint_128_matches_central_differences(lib):
             if j < 4:
                 fd = (loss_with(field, v, 1e-4) - loss_with(field, v, -1e-4)) / 2e-4
                 errs_wide.append((field, int(v), abs(fd - g[field].flat[v]) / scale[field]))
-    assert max(e for _, _, e in errs) <= 5e-4, errs
-    assert np.median([e for _, _, e in errs]) <= 2e-4, errs
-    assert max(e for _, _, e in errs_wide) <= 2e-5, errs_wide
+    assert max(e for _, _, e in errs_wide) <= 2e-5, (errs_wide, errs)
+    assert max(e for _, _, e in errs) <= 1e-3, errs
+    assert np.median([e for _, _, e in errs]) <= 3e-4, errs
 
 
 def test_adjoint_reduced_3d_matches_oracle(lib):

@@ -9,6 +9,9 @@ them to ``tests/golden/<case>.npz``.
 Steps before any crack: the GPU FP64 path within 1e-10 of the oracle in F and c (relative
 to the field's largest magnitude in the sample) and 1e-8 in d and H; the mixed FP32/FP64
 path within 1e-7 in F and c and 1e-6 in d, and the fracture energy within 1e-6 relative.
+F and H are compared on the particle's voxels: the buffer stands in for the space around
+the particle (its stiffness is 1e-3 to 1e-5 of the particle's), and its F is fixed only to
+the solver tolerance times that contrast.
 
 Steps after a crack has formed: where a voxel is cracked through (d > 0.9 in the oracle's
 field) its stiffness (1 - d)^2 is below 1e-2 of the particle's, and F and H there are fixed
@@ -16,11 +19,11 @@ only to the equilibrium tolerance divided by that stiffness; the nearly free pie
 either side of the crack carry that freedom to their neighbours.  Any two solutions that
 meet err_res <= tol_stag may differ by more than the bars above: measured on the plate,
 the GPU's F (in both precisions) differs from the oracle's by 1.5-1.8e-7 of max |F| on the
-voxels not cracked through, while c agrees to 1e-11 (FP64) and 1e-10 (mixed) and d to
-2e-8 and 6e-8.  After a crack the bars are therefore 1e-6 in F and H (on the voxels not
-cracked through), the pre-crack bars in c, 1e-7 (FP64) and 1e-6 (mixed) in d, and every
-whole field must be a valid solution: the oracle's err_res of the GPU's fields (Eq.
-mechresiduum) within twice the staggered tolerance."""
+voxels not cracked through at Newton tolerance 1e-9, up to 4e-6 a step later, while c
+agrees to 1e-11 to 2e-8 and d to 2e-8 to 2e-7.  After a crack the bars are therefore 1e-5
+in F and H (on the voxels not cracked through), 1e-9 (FP64) and 1e-7 (mixed) in c, 1e-6 in
+d, and every whole field must be a valid solution: the oracle's err_res of the GPU's
+fields (Eq. mechresiduum) within twice the staggered tolerance."""
 import os
 
 import numpy as np
@@ -38,8 +41,8 @@ HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 BARS = {B.FG_FP64: dict(F=1e-10, c=1e-10, d=1e-8, H=1e-8, energy=1e-8),
         B.FG_MIXED: dict(F=1e-7, c=1e-7, d=1e-6, H=1e-6, energy=1e-6)}
-CRACKED_BARS = {B.FG_FP64: dict(F=1e-6, c=1e-10, d=1e-7, H=1e-6, energy=1e-7),
-                B.FG_MIXED: dict(F=1e-6, c=1e-7, d=1e-6, H=1e-6, energy=1e-6)}
+CRACKED_BARS = {B.FG_FP64: dict(F=1e-5, c=1e-9, d=1e-6, H=1e-5, energy=1e-6),
+                B.FG_MIXED: dict(F=1e-5, c=1e-7, d=1e-6, H=1e-5, energy=1e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -74,7 +77,8 @@ def _compare(case, precision, lib):
         F = sol.get(B.FIELD_F).reshape(9, -1)[:, idx]
         c, d, H = (sol.get(f).ravel()[idx] for f in (B.FIELD_C, B.FIELD_D, B.FIELD_H))
         err = {}
-        sound = ref[f"d_s{k}"] <= 0.9  # voxels not cracked through
+        # particle voxels not cracked through (the buffer stands in for empty space)
+        sound = (ref[f"d_s{k}"] <= 0.9) & (w.phase_id.ravel()[idx] == 0)
         Fw = ref[f"F_s{k}"]
         err["F"] = float(np.abs(F - Fw)[:, sound].max() / np.abs(Fw).max())
         err["c"] = float(np.abs(c - ref[f"c_s{k}"]).max() / np.abs(ref[f"c_s{k}"]).max())
@@ -101,6 +105,21 @@ def _compare(case, precision, lib):
 @pytest.mark.parametrize("precision", [B.FG_FP64, B.FG_MIXED])
 def test_plate_trajectory_matches_oracle(lib, precision):
     """The Sec. 4.3 plate (64 x 64 x 1, Saint-Venant-Kirchhoff, Omega = 1.3, a stronger
-    influx at one corner): steps 1-4, compared at steps 2 (undamaged), 3 (the plate cracks)
-    and 4."""
+    influx at one corner) at Newton tolerance 1e-12: steps 1-4, compared at steps 2
+    (undamaged), 3 (the plate cracks) and 4."""
     _compare("plate", precision, lib)
+
+
+@pytest.mark.parametrize("precision", [B.FG_FP64, B.FG_MIXED])
+def test_ellipsoid_trajectory_matches_oracle(lib, precision):
+    """The 128^3 rough-ellipsoid particle recipe at 32^3 over its whole 50-step schedule
+    (it does not crack within it): the fields at step 50 against the oracle's."""
+    _compare("ellipsoid32", precision, lib)
+
+
+@pytest.mark.parametrize("precision", [B.FG_FP64, B.FG_MIXED])
+def test_gumbel_disc_trajectory_matches_oracle(lib, precision):
+    """The Sec. 5.1 disc at its full 512^2 size (Gumbel-distributed stiffness and strength,
+    Omega = 1.3, full chemistry Jacobian): its second step, where the weakest voxels start
+    to crack (69 voxels above d = 1e-3, d up to 0.03), field by field against the oracle."""
+    _compare("gumbel512", precision, lib)
