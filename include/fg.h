@@ -124,6 +124,12 @@ typedef struct {
   int z_columns;      /* kx-ky columns per block of the FP32 projection pass where the
                          transform length along z is a square (64, 256): 0 (default) the
                          built-in tile, 1 or 4; fg_autotune overrides it */
+  int cluster_pass;   /* 1 (default): where ny = nz is 128 or 256, the FP32 mechanical
+                         operator runs its y transform, projection and inverse y transform as
+                         one pass whose kx planes stay in the distributed shared memory of
+                         16-CTA thread-block clusters (if the device can keep such a cluster
+                         resident); fg_autotune keeps it only where it is faster.  0: the
+                         three separate passes */
 } fg_opts;
 
 typedef struct {
@@ -246,14 +252,16 @@ int fg_adjoint_mech(fg_ctx* ctx, const double* W, double* grad_logE, int* iters)
  * update) and keeps the fastest.  ms_per_iteration (may be NULL) receives the best
  * operator time.  Allocates two temporary 9 V vectors.
  * In a mixed context it also times the FP32 projection pass with 1 and 4 kx-ky columns
- * per block against its default tile.
- * fg_autotune_report returns the choices in force, choice[4] = {kx planes per chunk of
+ * per block against its default tile, and the clustered Y-Z-Y pass (cluster_pass) against
+ * the best separate passes.
+ * fg_autotune_report returns the choices in force, choice[5] = {kx planes per chunk of
  * the Krylov precision, X-inv update one component per block (1) or nine (0), L2 prefetch
- * (1) or not (0), columns per block of the FP32 projection pass (0: default)}, and
+ * (1) or not (0), columns per block of the FP32 projection pass (0: default), the
+ * clustered Y-Z-Y pass (1) or three passes (0)}, and
  * (xinv_ms, may be NULL) the autotuner's X-inv update times [prefetch off, nine; off, one;
  * on, nine; on, one] in ms (zeros before fg_autotune). */
 int fg_autotune(fg_ctx* ctx, double* ms_per_iteration);
-int fg_autotune_report(fg_ctx* ctx, int choice[4], double xinv_ms[4]);
+int fg_autotune_report(fg_ctx* ctx, int choice[5], double xinv_ms[4]);
 
 /* Launch-site profiling.  While a site is enabled, every launch at that site is
  * bracketed by two CUDA events on the context stream (at most 32768 launches are recorded

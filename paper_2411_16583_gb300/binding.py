@@ -49,7 +49,8 @@ class Opts(C.Structure):
                 ("max_newton", C.c_int), ("max_cg", C.c_int), ("max_chem_newton", C.c_int),
                 ("max_stag", C.c_int), ("cuda_stream", C.c_void_p), ("l2_fraction", C.c_double),
                 ("cg_indefinite", C.c_int), ("chem_full_jacobian", C.c_int),
-                ("l2_prefetch", C.c_int), ("residual_ff", C.c_int), ("z_columns", C.c_int)]
+                ("l2_prefetch", C.c_int), ("residual_ff", C.c_int), ("z_columns", C.c_int),
+                ("cluster_pass", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -364,11 +365,11 @@ class Solver:
         """Choices in force (kx planes per chunk, one-component X-inv update, L2 prefetch,
         columns per block of the FP32 projection pass) and the autotuner's X-inv update
         times [prefetch off/on][nine/one component]."""
-        ch = (C.c_int * 4)()
+        ch = (C.c_int * 5)()
         ms = (C.c_double * 4)()
         self._check(self.lib.fg_autotune_report(self.ctx, ch, ms))
         return {"kx_chunk": ch[0], "xinv_per_component": ch[1], "l2_prefetch": ch[2],
-                "z_proj_columns_per_block": ch[3],
+                "z_proj_columns_per_block": ch[3], "cluster_yzy_pass": ch[4],
                 "xinv_ms": {"nine": ms[0], "one": ms[1], "nine_prefetch": ms[2],
                             "one_prefetch": ms[3]}}
 

@@ -28,7 +28,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # transform lengths compiled into the host-emulation library (small test grids)
-EMU_SIZES = (1, 8, 12, 16, 24, 32, 48, 64, 100, 256)
+EMU_SIZES = (1, 8, 12, 16, 24, 32, 48, 64, 100, 128, 256)
 
 
 def _nvcc():

@@ -6,6 +6,7 @@
 #include <vector>
 #include <cstring>
 #include "fg_ops.cuh"
+#include "fg_cluster.cuh"
 
 namespace fg {
 
@@ -96,6 +97,10 @@ struct SizeOps {
   // the projection pass with 1 and 4 rows per block (register-direct sizes; null
   // elsewhere): tile shapes the autotuner times against the default
   PassFn<R> z_proj_rows[2];
+  // Y-fwd, projection and Y-inv in one clustered pass (FP32, ny = nz = N of 128 or 256;
+  // null elsewhere) and whether the device can run its clusters
+  PassFn<R> yzy_proj;
+  bool (*yzy_proj_ok)();
   // FP64 only (null in the FP32 table): displacement at the corners and its transpose
   PassFn<R> xi_store9, z_disp, z_dispT;
 };
@@ -157,6 +162,7 @@ SizeOps<R> make_size_ops() {
       s.z_proj_rows[0] = run_z<ZPassD<R, N, ZProject<R>, 1>, R>;
       s.z_proj_rows[1] = run_z<ZPassD<R, N, ZProject<R>, 4>, R>;
     }
+
     s.z_lap = run_z<ZPassD<R, N, ZLaplace<R>>, R>;
     s.z_prec = run_z<ZPassD<R, N, ZPrecond<R>>, R>;
     s.z_grad = run_z<ZPassD<R, N, ZGrad<R>>, R>;
@@ -177,6 +183,10 @@ SizeOps<R> make_size_ops() {
       s.z_disp = run_z<ZPass<R, N, ZDisp<R>>, R>;
       s.z_dispT = run_z<ZPass<R, N, ZDispT<R>>, R>;
     }
+  }
+  if constexpr (std::is_same<R, float>::value && (N == 128 || N == 256)) {
+    s.yzy_proj = run_yzy_cluster<R, N>;
+    s.yzy_proj_ok = yzy_cluster_ok<R, N>;
   }
   return s;
 }

@@ -253,6 +253,7 @@ struct fg_ctx {
   int xi_percomp = 1;                // fused CG update: one component per block
   int l2pf = 0;                      // X passes prefetch their real-space rows into L2
   int zrows = 0;                     // FP32 projection pass: 0 default tile, 1: 1 row, 2: 4 rows
+  bool yzy_cluster = false;          // FP32 Y-Z-Y projection chain as one clustered pass
   double tune_ms[4] = {0, 0, 0, 0};  // autotuner: X-inv update times [prefetch][per comp]
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
@@ -542,11 +543,33 @@ static void yzy(fg_ctx& c, Prec<R>& P, const int* done, int cin, PassFn<R> zop, 
   }
 }
 
+// Y-fwd, projection and Y-inv of a nine-component spectrum in S1: one clustered pass when
+// the context uses it (FP32, ny = nz of 128 or 256), else the three passes
+template <typename R>
+static void yzy_proj(fg_ctx& c, Prec<R>& P, const int* done, const R* zc, const int* sites);
+
 // the projection pass of the context's tile shape (the autotuner's choice, FP32 only)
 template <typename R>
 static PassFn<R> zproj(const fg_ctx& c, const Prec<R>& P) {
   if (c.zrows > 0 && P.oz->z_proj_rows[c.zrows - 1]) return P.oz->z_proj_rows[c.zrows - 1];
   return P.oz->z_proj;
+}
+
+template <typename R>
+static void yzy_proj(fg_ctx& c, Prec<R>& P, const int* done, const R* zc, const int* sites) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (c.yzy_cluster && P.oz->yzy_proj) {
+      PassArgs<R> a = pbase(c, P, done);
+      a.tw = P.twz;
+      a.cin = P.S1;
+      a.cout = P.S1;
+      for (int k = 0; k < 4; ++k) a.coef[k] = zc[k];
+      ProfScope ps(c, sites ? sites[1] : SITE_N - 1, 1.0);
+      P.oz->yzy_proj(a, c.st);
+      return;
+    }
+  }
+  yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr, sites);
 }
 
 // y = G : F^-1[ F[K : x] ] ; accumulates <x, y>; returns partial count
@@ -563,7 +586,7 @@ static int op_mech(fg_ctx& c, Prec<R>& P, const R* x, R* y, const int* done) {
   }
   const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
   static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
-  yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr, sites);
+  yzy_proj(c, P, done, zc, sites);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -582,7 +605,7 @@ static int op_gres(fg_ctx& c, Prec<R>& P, const io_t<R>* x, io_t<R>* y, const in
   a.cout = P.S1;
   P.ox->xf_copy9(a, c.st);
   const R zc[4] = {(R)(1.0 / (double)c.V), (R)c.smask, 0, 0};
-  yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr);
+  yzy_proj(c, P, done, zc, (const int*)nullptr);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -939,7 +962,7 @@ static int cg_solve_mech(fg_ctx& c, Prec<R>& P, double tol, int maxit, fg_stats*
     fin<FAlpha>(c, slot, nb, done);
     {
       static const int sites[3] = {SITE_YF, SITE_Z, SITE_YI};
-      yzy(c, P, done, 9, zproj(c, P), 9, zc, nullptr, sites);
+      yzy_proj(c, P, done, zc, sites);
     }
     a = pbase(c, P, done);
     a.tw = P.twx;
@@ -2317,6 +2340,7 @@ void fg_default_opts(fg_opts* o) {
   o->cg_indefinite = 2;
   o->l2_prefetch = 0;
   o->residual_ff = 1;
+  o->cluster_pass = 1;
 }
 
 int fg_supported_size(int n) {
@@ -2494,6 +2518,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
   if (o.l2_prefetch != 0 && o.l2_prefetch != 1) fail(FG_ERR_INVALID, "fg_setup: l2_prefetch");
   if (o.residual_ff != 0 && o.residual_ff != 1) fail(FG_ERR_INVALID, "fg_setup: residual_ff");
   if (o.z_columns != 0 && o.z_columns != 1 && o.z_columns != 4) fail(FG_ERR_INVALID, "fg_setup: z_columns");
+  if (o.cluster_pass != 0 && o.cluster_pass != 1) fail(FG_ERR_INVALID, "fg_setup: cluster_pass");
   fg_ctx* c = new fg_ctx();
   try {
     c->law = phases[0].law;
@@ -2612,6 +2637,8 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     setup_prec<double>(*c, c->pd, 9);
     if (o.precision == FG_MIXED) setup_prec<float>(*c, c->pf, 9);
     if (o.precision == FG_MIXED && o.residual_ff) setup_ff(*c);
+    c->yzy_cluster = o.precision == FG_MIXED && o.cluster_pass && c->ny == c->nz &&
+                     c->pf.oz->yzy_proj && c->pf.oz->yzy_proj_ok();
     dsync(c->st);
   } catch (...) {
     fg_destroy(c);
@@ -3032,6 +3059,7 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   double best = 1e300;
   int best_ch = c->kx_chunk[k];
   c->l2pf = 0;
+  c->yzy_cluster = false;
   for (int ch : chunks) {
     c->kx_chunk[k] = ch;
     const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
@@ -3054,6 +3082,14 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
       }
     }
     c->zrows = best_z;
+    const bool can_cluster = c->o.cluster_pass && c->ny == c->nz && c->pf.oz->yzy_proj &&
+                             c->pf.oz->yzy_proj_ok();
+    if (can_cluster) {  // the clustered Y-Z-Y pass against the best separate passes
+      c->yzy_cluster = true;
+      const double t = time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5);
+      c->yzy_cluster = t < best;
+      if (t < best) best = t;
+    }
   }
   // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
   double* zero = (double*)dalloc(4 * sizeof(double));
@@ -3135,13 +3171,14 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   FG_API_END
 }
 
-int fg_autotune_report(fg_ctx* c, int choice[4], double xinv_ms[4]) {
+int fg_autotune_report(fg_ctx* c, int choice[5], double xinv_ms[4]) {
   FG_API_BEGIN
   if (!c || !choice) fail(FG_ERR_INVALID, "fg_autotune_report: bad argument");
   choice[0] = c->kx_chunk[is_mixed(*c) ? 0 : 1];
   choice[1] = c->xi_percomp;
   choice[2] = c->l2pf;
   choice[3] = c->zrows == 1 ? 1 : (c->zrows == 2 ? 4 : 0);
+  choice[4] = c->yzy_cluster ? 1 : 0;
   if (xinv_ms)
     for (int k = 0; k < 4; ++k) xinv_ms[k] = c->tune_ms[k];
   FG_API_END

@@ -698,3 +698,37 @@ def test_emulated_projection_tile_shapes_match_oracle(emu, shape, zc):
     ref = O.mech_apply(F.reshape((3, 3) + shape), c, d, prm, x.astype(float).reshape((3, 3) + shape))
     assert rel_err(y.reshape(ref.shape), ref) < TOL_APPLY_FP32
     sol.close()
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 8), (128, 128, 12)])
+def test_emulated_cluster_yzy_pass_matches_oracle(emu, shape):
+    """The clustered Y-Z-Y projection pass (16 CTAs of a cluster per kx plane and tensor row,
+    their tiles exchanged through distributed shared memory; emulated one stage of all 16
+    CTAs at a time) gives the oracle's mechanical operator, and the three separate passes'
+    result to FP32 round-off; also under mixed stress control (the kept zero mode)."""
+    pid = S.random_phase_map(shape, 1)
+    phases = S.default_phases()
+    phases[1].E = 2e9
+    F, c, d = S.random_state(shape, seed=2)
+    x = S.random_tensor_field(shape, 3).astype(np.float32)
+    prm = oracle_params(phases, pid, H3)
+    out = {}
+    for cp in (1, 0):
+        sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu, precision=B.FG_MIXED,
+                       cluster_pass=cp)
+        for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d)):
+            sol.set(f, v)
+        y = np.zeros_like(x)
+        sol.apply(B.OP_MECH, x, y, 1)
+        mask = np.zeros((3, 3), dtype=bool)
+        mask[1, 2] = mask[0, 0] = True
+        sol.stress_control(mask, np.zeros((3, 3)))
+        ym = np.zeros_like(x)
+        sol.apply(B.OP_MECH, x, ym, 1)
+        out[cp] = (y, ym)
+        sol.close()
+    ref = O.mech_apply(F.reshape((3, 3) + shape), c, d, prm, x.astype(float).reshape((3, 3) + shape))
+    assert rel_err(out[1][0].reshape(ref.shape), ref) < TOL_APPLY_FP32
+    assert rel_err(out[1][0], out[0][0]) < 1e-6
+    assert rel_err(out[1][1], out[0][1]) < 1e-6
+    assert np.abs(out[1][1] - out[1][0]).max() > 0  # the mask changes the result

@@ -21,7 +21,9 @@ SHAPES = [(8, 12, 16), (12, 24, 16), (1, 12, 16), (1, 64, 64), (16, 32, 64), (24
           (32, 32, 32), (1, 100, 100), (100, 96, 80),
           # the transform lengths of the 128^3 particle (two-stage 128 = 16 x 8 in every
           # pass) and of the 512^2 disc (512 = 16 x 16 x 2)
-          (16, 128, 128), (128, 16, 24), (1, 512, 512), (8, 16, 512)]
+          (16, 128, 128), (128, 16, 24), (1, 512, 512), (8, 16, 512),
+          # ny = nz = 128: the mixed context's projection chain is the clustered pass
+          (128, 128, 16)]
 
 
 @pytest.fixture(scope="module")

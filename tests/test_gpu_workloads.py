@@ -55,3 +55,11 @@ def test_adjoint_under_mixed_control_matches_oracle(lib, ckpt):
     """Reverse pass of two damaging steps with F_xx under stress control on the device,
     against the oracle's adjoint (checkpoints every 1 and 2 steps)."""
     TE.test_emulated_adjoint_under_mixed_control_matches_oracle(lib, ckpt)
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 8), (256, 256, 16)])
+def test_cluster_yzy_pass_matches_oracle(lib, shape):
+    """The clustered Y-Z-Y projection pass (16-CTA clusters, tiles exchanged through
+    distributed shared memory) on the device: the oracle's mechanical operator, and the
+    three separate passes' result to FP32 round-off, with and without mixed control."""
+    TE.test_emulated_cluster_yzy_pass_matches_oracle(lib, shape)
