@@ -124,11 +124,12 @@ typedef struct {
   int z_columns;      /* kx-ky columns per block of the FP32 projection pass where the
                          transform length along z is a square (64, 256): 0 (default) the
                          built-in tile, 1 or 4; fg_autotune overrides it */
-  int cluster_pass;   /* 1 (default): where ny = nz is 128 or 256, the FP32 mechanical
-                         operator runs its y transform, projection and inverse y transform as
-                         one pass whose kx planes stay in the distributed shared memory of
+  int cluster_pass;   /* 1 (default): where ny = nz is 128 or 256, the FP32 operators run
+                         their y transform, frequency-space operator and inverse y transform
+                         (the mechanical projection; the chemistry's gradient and divergence)
+                         as one pass whose kx planes stay in the distributed shared memory of
                          16-CTA thread-block clusters (if the device can keep such a cluster
-                         resident); fg_autotune keeps it only where it is faster.  0: the
+                         resident); fg_autotune keeps each only where it is faster.  0: the
                          three separate passes */
 } fg_opts;
 
@@ -256,8 +257,8 @@ int fg_adjoint_mech(fg_ctx* ctx, const double* W, double* grad_logE, int* iters)
  * the best separate passes.
  * fg_autotune_report returns the choices in force, choice[5] = {kx planes per chunk of
  * the Krylov precision, X-inv update one component per block (1) or nine (0), L2 prefetch
- * (1) or not (0), columns per block of the FP32 projection pass (0: default), the
- * clustered Y-Z-Y pass (1) or three passes (0)}, and
+ * (1) or not (0), columns per block of the FP32 projection pass (0: default), clustered
+ * Y-Z-Y passes: bit 0 the projection chain, bit 1 the chemistry's chains}, and
  * (xinv_ms, may be NULL) the autotuner's X-inv update times [prefetch off, nine; off, one;
  * on, nine; on, one] in ms (zeros before fg_autotune). */
 int fg_autotune(fg_ctx* ctx, double* ms_per_iteration);

@@ -369,7 +369,8 @@ class Solver:
         ms = (C.c_double * 4)()
         self._check(self.lib.fg_autotune_report(self.ctx, ch, ms))
         return {"kx_chunk": ch[0], "xinv_per_component": ch[1], "l2_prefetch": ch[2],
-                "z_proj_columns_per_block": ch[3], "cluster_yzy_pass": ch[4],
+                "z_proj_columns_per_block": ch[3], "cluster_yzy_mech": ch[4] & 1,
+                "cluster_yzy_chem": (ch[4] >> 1) & 1,
                 "xinv_ms": {"nine": ms[0], "one": ms[1], "nine_prefetch": ms[2],
                             "one_prefetch": ms[3]}}
 

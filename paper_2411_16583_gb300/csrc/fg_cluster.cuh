@@ -59,14 +59,37 @@ FG_DEV void project_row(const PassArgs<R>& a, int kx, int ky, int kz, int i, cpl
   v[2] = cscale(t, n2);
 }
 
-template <typename R, int N>
+// Frequency-space operators of the clustered pass.  ZRows: the projection, one tensor row
+// (three components) per cluster, GROUPS = 3 clusters per kx plane.  ZWhole<Op>: a Z-pass
+// operator on all its components (the chemistry's 1 -> 3 gradient and 3 -> 1 divergence),
+// one cluster per kx plane.
+template <typename R>
+struct ZRows {
+  static constexpr int CIN = 3, COUT = 3, GROUPS = 3;
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, int g, cplx<R>* v) {
+    project_row(a, kx, ky, kz, g, v);
+  }
+};
+template <class Op>
+struct ZWhole {
+  static constexpr int CIN = Op::CIN, COUT = Op::COUT, GROUPS = 1;
+  template <typename R>
+  FG_DEV static void apply(const PassArgs<R>& a, int kx, int ky, int kz, int, cplx<R>* v) {
+    const R zs = a.dscal ? (R)a.dscal[0] : (R)0;
+    Op::apply(a, kx, ky, kz, v, zs);
+  }
+};
+
+template <typename R, int N, class Z = ZRows<R>>
 struct YZYCluster {
   using C = cplx<R>;
+  static constexpr int CI = Z::CIN, CO = Z::COUT, G = Z::GROUPS;
+  static constexpr int CM = CI > CO ? CI : CO;
   static constexpr int S = N / YZY_CLUSTER;   // z rows (stage 0) or ky rows (stage 1) per CTA
-  static constexpr int ROWS = 3 * S;          // three components
+  static constexpr int ROWS = CM * S;         // rows of the largest component count
   static constexpr int NT = round32(ROWS * tpr(N));
-  using TFf = TileFFT<R, N, ROWS, NT, false>;
-  using TFi = TileFFT<R, N, ROWS, NT, true>;
+  using TFf = TileFFT<R, N, CI * S, NT, false>;  // forward transforms: the CI input rows
+  using TFi = TileFFT<R, N, CO * S, NT, true>;   // inverse transforms: the CO output rows
   static constexpr int PITCH = TFf::PITCH;
   static constexpr int VMAX = TFf::VMAX > TFi::VMAX ? TFf::VMAX : TFi::VMAX;
   struct Locals {
@@ -75,7 +98,7 @@ struct YZYCluster {
   };
   static constexpr size_t TILE = (size_t)ROWS * PITCH * sizeof(C);
   static size_t smem_bytes() { return 2 * TILE + N * sizeof(C); }
-  static int clusters(int hx) { return hx * 3; }
+  static int clusters(int hx) { return hx * G; }
 
   // shared memory of the cluster's CTA q: the distributed shared memory window of that CTA
   // (mapa) on the GPU; the emulation's buffer of that CTA on the host
@@ -94,13 +117,14 @@ struct YZYCluster {
   FG_DEV static C* recv(char* sm) { return (C*)(sm + TILE); }
   FG_DEV static C* twid(char* sm) { return (C*)(sm + 2 * TILE); }
 
-  // Stage s of the CTA of rank `rank` in cluster `cid` (kx = cid / 3, row i = cid % 3).
-  // local is the CTA's own shared memory; sm[q] that of the cluster's CTA q in the
-  // emulation (unused on the GPU, where peer() maps it).
+  // Stage s of the CTA of rank `rank` in cluster `cid` (kx = cid / G, group g = cid % G:
+  // components g CI + cc in, g CO + cc out).  local is the CTA's own shared memory; sm[q]
+  // that of the cluster's CTA q in the emulation (unused on the GPU, where peer() maps it).
+  // Tile rows (cc, r) hold component cc at z (own tile) or ky (recv tile) of the slab.
   template <class Loc>
   FG_DEV static void stage(int s, const PassArgs<R>& a, int cid, int rank, char* local,
                            char* const* sm, Loc* Ls) {
-    const int kx = cid / 3, row = cid % 3;
+    const int kx = cid / G, g = cid % G;
     C* mine = own(local);
     C* rv = recv(local);
     C* tw = twid(local);
@@ -109,19 +133,19 @@ struct YZYCluster {
       FG_PHASE(NT)
       for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
       // S consecutive z-rows of length ny per component: one contiguous block each
-      for (int e = tid; e < ROWS * N; e += NT) {
+      for (int e = tid; e < CI * S * N; e += NT) {
         const int q = e / N, y = e - q * N;
         const int cc = q / S, zz = q - cc * S;
-        const long long g = (long long)(3 * row + cc) * a.VH +
-                            ((long long)kx * nz + rank * S + zz) * ny + y;
-        mine[q * PITCH + pad16(y)] = a.cin[g];
+        const long long gi = (long long)(g * CI + cc) * a.VH +
+                             ((long long)kx * nz + rank * S + zz) * ny + y;
+        mine[q * PITCH + pad16(y)] = a.cin[gi];
       }
       FG_END_PHASE
       tile_fft<TFf, 0>(Ls, mine, tw, NT);
     } else if (s == 1) {
       FG_PHASE(NT)
       // recv row (cc, kyy) holds every z of ky = rank S + kyy: z slab q of it is CTA q's
-      for (int e = tid; e < ROWS * N; e += NT) {
+      for (int e = tid; e < CI * S * N; e += NT) {
         const int qrow = e / N, z = e - qrow * N;
         const int cc = qrow / S, kyy = qrow - cc * S;
         const int src = z / S, zz = z - src * S;
@@ -133,19 +157,19 @@ struct YZYCluster {
       FG_PHASE(NT)
       for (int e = tid; e < S * N; e += NT) {
         const int kyy = e / N, kz = e - kyy * N;
-        C v[3];
+        C v[CM];
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) v[cc] = rv[(cc * S + kyy) * PITCH + pad16(kz)];
-        project_row(a, kx, rank * S + kyy, kz, row, v);
+        for (int cc = 0; cc < CI; ++cc) v[cc] = rv[(cc * S + kyy) * PITCH + pad16(kz)];
+        Z::apply(a, kx, rank * S + kyy, kz, g, v);
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) rv[(cc * S + kyy) * PITCH + pad16(kz)] = v[cc];
+        for (int cc = 0; cc < CO; ++cc) rv[(cc * S + kyy) * PITCH + pad16(kz)] = v[cc];
       }
       FG_END_PHASE
       tile_fft<TFi, 0>(Ls, rv, tw, NT);
     } else if (s == 2) {
       FG_PHASE(NT)
       // own row (cc, zz) gets every ky of z = rank S + zz: ky slab q of it is CTA q's
-      for (int e = tid; e < ROWS * N; e += NT) {
+      for (int e = tid; e < CO * S * N; e += NT) {
         const int q = e / N, ky = e - q * N;
         const int cc = q / S, zz = q - cc * S;
         const int src = ky / S, kyy = ky - src * S;
@@ -156,12 +180,12 @@ struct YZYCluster {
     } else {
       tile_fft<TFi, 0>(Ls, mine, tw, NT);
       FG_PHASE(NT)
-      for (int e = tid; e < ROWS * N; e += NT) {
+      for (int e = tid; e < CO * S * N; e += NT) {
         const int q = e / N, y = e - q * N;
         const int cc = q / S, zz = q - cc * S;
-        const long long g = (long long)(3 * row + cc) * a.VH +
-                            ((long long)kx * nz + rank * S + zz) * ny + y;
-        a.cout[g] = mine[q * PITCH + pad16(y)];
+        const long long gi = (long long)(g * CO + cc) * a.VH +
+                             ((long long)kx * nz + rank * S + zz) * ny + y;
+        a.cout[gi] = mine[q * PITCH + pad16(y)];
       }
       FG_END_PHASE
     }
@@ -259,14 +283,14 @@ int launch_cluster(const A& a, int nclusters, cudaStream_t st) {
   return 0;
 }
 
-template <typename R, int N>
+template <typename R, int N, class Z = ZRows<R>>
 int run_yzy_cluster(const PassArgs<R>& a, cudaStream_t st) {
-  using K = YZYCluster<R, N>;
+  using K = YZYCluster<R, N, Z>;
   return launch_cluster<K>(a, K::clusters(a.hx), st);
 }
-template <typename R, int N>
+template <typename R, int N, class Z = ZRows<R>>
 bool yzy_cluster_ok() {
-  return cluster_pass_available<YZYCluster<R, N>, PassArgs<R>>();
+  return cluster_pass_available<YZYCluster<R, N, Z>, PassArgs<R>>();
 }
 
 }  // namespace fg

@@ -101,6 +101,9 @@ struct SizeOps {
   // null elsewhere) and whether the device can run its clusters
   PassFn<R> yzy_proj;
   bool (*yzy_proj_ok)();
+  // the chemistry's gradient (1 -> 3) and divergence (3 -> 1) chains as clustered passes
+  PassFn<R> yzy_grad, yzy_div;
+  bool (*yzy_chem_ok)();
   // FP64 only (null in the FP32 table): displacement at the corners and its transpose
   PassFn<R> xi_store9, z_disp, z_dispT;
 };
@@ -187,6 +190,11 @@ SizeOps<R> make_size_ops() {
   if constexpr (std::is_same<R, float>::value && (N == 128 || N == 256)) {
     s.yzy_proj = run_yzy_cluster<R, N>;
     s.yzy_proj_ok = yzy_cluster_ok<R, N>;
+    s.yzy_grad = run_yzy_cluster<R, N, ZWhole<ZGrad<R>>>;
+    s.yzy_div = run_yzy_cluster<R, N, ZWhole<ZDiv<R>>>;
+    s.yzy_chem_ok = [] {
+      return yzy_cluster_ok<R, N, ZWhole<ZGrad<R>>>() && yzy_cluster_ok<R, N, ZWhole<ZDiv<R>>>();
+    };
   }
   return s;
 }

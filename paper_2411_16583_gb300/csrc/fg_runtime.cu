@@ -254,6 +254,7 @@ struct fg_ctx {
   int l2pf = 0;                      // X passes prefetch their real-space rows into L2
   int zrows = 0;                     // FP32 projection pass: 0 default tile, 1: 1 row, 2: 4 rows
   bool yzy_cluster = false;          // FP32 Y-Z-Y projection chain as one clustered pass
+  bool yzy_cluster_chem = false;     // FP32 chemistry Y-Z-Y chains as clustered passes
   double tune_ms[4] = {0, 0, 0, 0};  // autotuner: X-inv update times [prefetch][per comp]
   int last_inner_refine = 0;
   bool strict = false;        // an iteration cap is an error in every mode (adjoint solves)
@@ -547,12 +548,33 @@ static void yzy(fg_ctx& c, Prec<R>& P, const int* done, int cin, PassFn<R> zop, 
 // the context uses it (FP32, ny = nz of 128 or 256), else the three passes
 template <typename R>
 static void yzy_proj(fg_ctx& c, Prec<R>& P, const int* done, const R* zc, const int* sites);
+template <typename R>
+static void yzy_chem(fg_ctx& c, Prec<R>& P, const int* done, bool grad, const R* zc);
 
 // the projection pass of the context's tile shape (the autotuner's choice, FP32 only)
 template <typename R>
 static PassFn<R> zproj(const fg_ctx& c, const Prec<R>& P) {
   if (c.zrows > 0 && P.oz->z_proj_rows[c.zrows - 1]) return P.oz->z_proj_rows[c.zrows - 1];
   return P.oz->z_proj;
+}
+
+// the chemistry's Y-Z-Y chains (1 -> 3 gradient, 3 -> 1 divergence on S1): clustered
+// passes when the context uses them, else the three passes
+template <typename R>
+static void yzy_chem(fg_ctx& c, Prec<R>& P, const int* done, bool grad, const R* zc) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (c.yzy_cluster_chem) {
+      PassArgs<R> a = pbase(c, P, done);
+      a.tw = P.twz;
+      a.cin = P.S1;
+      a.cout = P.S1;
+      for (int k = 0; k < 4; ++k) a.coef[k] = zc[k];
+      (grad ? P.oz->yzy_grad : P.oz->yzy_div)(a, c.st);
+      return;
+    }
+  }
+  if (grad) yzy(c, P, done, 1, P.oz->z_grad, 3, zc, nullptr);
+  else yzy(c, P, done, 3, P.oz->z_div, 1, zc, nullptr);
 }
 
 template <typename R>
@@ -660,7 +682,7 @@ static void op_chem_L(fg_ctx& c, Prec<R>& P, const io_t<R>* u, const int* done) 
   a.cout = P.S1;
   P.ox->xf_copy1(a, c.st);
   const R zc[4] = {(R)(1.0 / (double)c.V), 0, 0, 0};
-  yzy(c, P, done, 1, P.oz->z_grad, 3, zc, nullptr);
+  yzy_chem(c, P, done, true, zc);
   a = pbase(c, P, done);
   a.tw = P.twx;
   a.cin = P.S1;
@@ -672,7 +694,7 @@ static void op_chem_L(fg_ctx& c, Prec<R>& P, const io_t<R>* u, const int* done) 
   a.rin = P.tmp3;
   a.cout = P.S1;
   P.ox->xf_copy3(a, c.st);
-  yzy(c, P, done, 3, P.oz->z_div, 1, zc, nullptr);
+  yzy_chem(c, P, done, false, zc);
 }
 
 // y = x c(1-c) + dt L x ; accumulates <x, y>
@@ -870,7 +892,7 @@ static int cg_solve_chem(fg_ctx& c, Prec<R>& P, double dt, double tol, int maxit
     a.dscal = sc;
     a.cout = P.S1;
     const int nb1 = P.ox->xf_cgchem(a, c.st);
-    yzy(c, P, done, 1, P.oz->z_grad, 3, zc, nullptr);
+    yzy_chem(c, P, done, true, zc);
     a = pbase(c, P, done);
     a.tw = P.twx;
     a.cin = P.S1;
@@ -880,7 +902,7 @@ static int cg_solve_chem(fg_ctx& c, Prec<R>& P, double dt, double tol, int maxit
     a.partials = c.partials + nb1;  // after the forward pass's partial sums
     const int nb2 = P.ox->xr_chemflux(a, c.st);
     fin<FAlpha>(c, slot, nb1 + nb2, done);
-    yzy(c, P, done, 3, P.oz->z_div, 1, zc, nullptr);
+    yzy_chem(c, P, done, false, zc);
     a = pbase(c, P, done);
     a.tw = P.twx;
     a.cin = P.S1;
@@ -2639,6 +2661,7 @@ int fg_setup(fg_ctx** out, const fg_grid* g, const fg_phase* phases, int nphases
     if (o.precision == FG_MIXED && o.residual_ff) setup_ff(*c);
     c->yzy_cluster = o.precision == FG_MIXED && o.cluster_pass && c->ny == c->nz &&
                      c->pf.oz->yzy_proj && c->pf.oz->yzy_proj_ok();
+    c->yzy_cluster_chem = c->yzy_cluster && c->pf.oz->yzy_chem_ok();
     dsync(c->st);
   } catch (...) {
     fg_destroy(c);
@@ -3060,6 +3083,7 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
   int best_ch = c->kx_chunk[k];
   c->l2pf = 0;
   c->yzy_cluster = false;
+  c->yzy_cluster_chem = false;
   for (int ch : chunks) {
     c->kx_chunk[k] = ch;
     const double t = mixed ? time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5)
@@ -3089,6 +3113,16 @@ int fg_autotune(fg_ctx* c, double* ms_per_iteration) {
       const double t = time_it([&] { op_mech(*c, c->pf, (const float*)x, (float*)y, nullptr); }, 5);
       c->yzy_cluster = t < best;
       if (t < best) best = t;
+      // the chemistry chains, timed on the chemistry operator's transforms
+      if (c->pf.oz->yzy_chem_ok()) {
+        const float* xf = (const float*)x;
+        double tc[2];
+        for (int on = 0; on < 2; ++on) {
+          c->yzy_cluster_chem = on != 0;
+          tc[on] = time_it([&] { op_chem_L(*c, c->pf, xf, nullptr); }, 5);
+        }
+        c->yzy_cluster_chem = tc[1] < tc[0];
+      }
     }
   }
   // X-inv update variants (alpha read from a zeroed scalar: x and r are unchanged)
@@ -3178,7 +3212,7 @@ int fg_autotune_report(fg_ctx* c, int choice[5], double xinv_ms[4]) {
   choice[1] = c->xi_percomp;
   choice[2] = c->l2pf;
   choice[3] = c->zrows == 1 ? 1 : (c->zrows == 2 ? 4 : 0);
-  choice[4] = c->yzy_cluster ? 1 : 0;
+  choice[4] = (c->yzy_cluster ? 1 : 0) + (c->yzy_cluster_chem ? 2 : 0);
   if (xinv_ms)
     for (int k = 0; k < 4; ++k) xinv_ms[k] = c->tune_ms[k];
   FG_API_END

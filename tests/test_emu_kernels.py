@@ -732,3 +732,32 @@ def test_emulated_cluster_yzy_pass_matches_oracle(emu, shape):
     assert rel_err(out[1][0], out[0][0]) < 1e-6
     assert rel_err(out[1][1], out[0][1]) < 1e-6
     assert np.abs(out[1][1] - out[1][0]).max() > 0  # the mask changes the result
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 8)])
+def test_emulated_cluster_chemistry_passes_match_oracle(emu, shape):
+    """The chemistry's gradient (1 -> 3) and divergence (3 -> 1) chains as clustered passes:
+    the chemistry operator against the oracle's, with the clustered chains and with the
+    three-pass chains."""
+    pid = S.random_phase_map(shape, 1)
+    phases = S.default_phases()
+    phases[1].E = 2e9
+    F, c, d = S.random_state(shape, seed=2)
+    x = S.random_tensor_field(shape, 4, ncomp=1)[0].astype(np.float32)
+    prm = oracle_params(phases, pid, H3)
+    dt = 0.7
+    launches = {}
+    for cp in (1, 0):
+        sol = B.Solver(shape, H3, phases, pid, np.zeros(shape), lib=emu, precision=B.FG_MIXED,
+                       cluster_pass=cp)
+        for f, v in ((B.FIELD_F, F), (B.FIELD_C, c), (B.FIELD_D, d)):
+            sol.set(f, v)
+        y = np.zeros_like(x)
+        l0 = B.kernel_launches(emu)
+        sol.apply(B.OP_CHEM, x, y, 1, dt=dt)
+        launches[cp] = B.kernel_launches(emu) - l0
+        Kc = O.chem_conductivity(F.reshape((3, 3) + shape), c, d, prm)
+        ref = O.chem_apply(x.astype(float), 1.0 / (c * (1 - c)), Kc, dt, prm)
+        assert rel_err(y, ref) < TOL_APPLY_FP32
+        sol.close()
+    assert launches[1] < launches[0]  # the clustered chains replaced three passes each

@@ -63,3 +63,22 @@ def test_cluster_yzy_pass_matches_oracle(lib, shape):
     distributed shared memory) on the device: the oracle's mechanical operator, and the
     three separate passes' result to FP32 round-off, with and without mixed control."""
     TE.test_emulated_cluster_yzy_pass_matches_oracle(lib, shape)
+
+
+def test_cluster_passes_keep_the_coupled_steps(lib):
+    """Two mixed coupled steps of the benchmark particle recipe at 128^3 (ny = nz = 128, so
+    every FP32 Y-Z-Y chain of the mechanics and the chemistry may run clustered) with the
+    clustered passes and with the three-pass chains: the same Newton iterations and fields
+    equal to the solver tolerance."""
+    import bench
+    w = bench._workload(128, 0)
+    out = []
+    for cp in (1, 0):
+        sol = B.from_workload(w, precision=B.FG_MIXED, lib=lib, cluster_pass=cp)
+        st = [sol.step(w.dt) for _ in range(2)]
+        out.append((sol.get(B.FIELD_F), sol.get(B.FIELD_C), st))
+        sol.close()
+    assert rel_err(out[0][0], out[1][0]) < 1e-8
+    assert rel_err(out[0][1], out[1][1]) < 1e-10
+    for a, b in zip(out[0][2], out[1][2]):
+        assert a["newton_mech"] == b["newton_mech"] and a["newton_chem"] == b["newton_chem"]
