@@ -47,12 +47,13 @@ MECH_ALG_B_PER_VOXEL = 116.0
 MEASURED_APPLY_TRAFFIC_B_PER_VOXEL = 386.5
 
 
-def APPLY_SCHEDULED_B_PER_VOXEL(nx):
-    """Bytes per voxel the five passes of one FP32 operator application schedule: X-fwd reads
-    x and the packed 12-real state and writes the half spectrum, Y-fwd, Z and Y-inv read and
-    write it, X-inv reads it and writes y (its <x, y> reads x once more)."""
+def APPLY_SCHEDULED_B_PER_VOXEL(nx, clustered=False):
+    """Bytes per voxel the passes of one FP32 operator application schedule: X-fwd reads x
+    and the packed 12-real state and writes the half spectrum, Y-fwd, Z and Y-inv read and
+    write it (the clustered Y-Z-Y pass once for all three), X-inv reads it and writes y (its
+    <x, y> reads x once more)."""
     spec = 72.0 * (nx // 2 + 1) / nx
-    return (36 + 48 + spec) + 3 * (2 * spec) + (spec + 36 + 36)
+    return (36 + 48 + spec) + (1 if clustered else 3) * (2 * spec) + (spec + 36 + 36)
 
 
 def _apply_traffic(nx, V):
@@ -593,9 +594,13 @@ def run_ours(a, rank, world, local, dist, stream):
     peaks, src = _peaks()
     sb = site_bytes(w.shape[2])
     sites = {}
+    names = dict(SITE_NAMES)
+    if tuning.get("cluster_yzy_mech"):
+        names[2] = ("mech Y-fwd + Z + projection + Y-inv in one clustered pass "
+                    "(cluster_kernel<YZYCluster<float,N,ZRows>>, 16-CTA clusters)")
     for s, (n, t, vol) in prof.items():
         if n:
-            sites[SITE_NAMES[s]] = {"launches": n, "total_ms": t, "volumes": vol,
+            sites[names[s]] = {"launches": n, "total_ms": t, "volumes": vol,
                                     "us_per_volume": t * 1e3 / vol,
                                     "alg_bytes_per_voxel": sb[s],
                                     "gbs": sb[s] * V * vol / (t * 1e-3) / 1e9,
@@ -624,14 +629,20 @@ def run_ours(a, rank, world, local, dist, stream):
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": {"bound": "hbm",
-                     "kernel": "fused FP32 mechanical operator application (five pass kernels: "
-                               "X-fwd tangent + R2C, Y-fwd, Z + projection, Y-inv, C2R X-inv)",
+                     "kernel": ("fused FP32 mechanical operator application (three pass "
+                                "kernels: X-fwd tangent + R2C, clustered Y-Z-Y with the "
+                                "projection, C2R X-inv)" if tuning.get("cluster_yzy_mech") else
+                                "fused FP32 mechanical operator application (five pass "
+                                "kernels: X-fwd tangent + R2C, Y-fwd, Z + projection, Y-inv, "
+                                "C2R X-inv)"),
                      "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": ach / peaks["hbm_gbs"], "peak_source": src,
                      "alg_bytes_per_launch": MECH_ALG_B_PER_VOXEL * V,
                      "avg_launch_us": mech32_ms * 1e3,
-                     "traffic": _apply_traffic(w.shape[2], V),
-                     "scheduled_bytes_per_voxel": APPLY_SCHEDULED_B_PER_VOXEL(w.shape[2])},
+                     "traffic": (None if tuning.get("cluster_yzy_mech") else
+                                 _apply_traffic(w.shape[2], V)),
+                     "scheduled_bytes_per_voxel": APPLY_SCHEDULED_B_PER_VOXEL(
+                         w.shape[2], tuning.get("cluster_yzy_mech"))},
         "window": window,
         "kernels": sites,
         "matvec": matvec,
