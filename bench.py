@@ -144,6 +144,9 @@ def _args():
                    help="profile-apply: the X passes' L2 prefetch (the autotuner's choice)")
     p.add_argument("--z-columns", type=int, default=0,
                    help="profile-apply: columns per block of the projection pass (0, 1, 4)")
+    p.add_argument("--cluster-pass", type=int, default=1,
+                   help="profile-apply: the clustered Y-Z-Y pass where it applies (1) or the "
+                        "three separate passes (0)")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -696,11 +699,12 @@ def profile_apply(a):
     w = _workload(a.n, 0, nz=a.nz, ny=a.ny)
     stream = torch.cuda.Stream()
     sol = B.from_workload(w, precision=B.FG_MIXED, stream=stream.cuda_stream,
-                          l2_prefetch=a.l2_prefetch, z_columns=a.z_columns)
+                          l2_prefetch=a.l2_prefetch, z_columns=a.z_columns,
+                          cluster_pass=a.cluster_pass)
     ms = sol.time_apply(B.OP_MECH, 1, a.profile_apply)
     sol.close()
     return {"mode": "profile-apply", "shape": list(w.shape), "applies": a.profile_apply,
-            "ms_per_apply": ms}
+            "cluster_pass": a.cluster_pass, "ms_per_apply": ms}
 
 
 def trajectory_error(a):

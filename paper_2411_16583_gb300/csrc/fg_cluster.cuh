@@ -1,33 +1,32 @@
 // Y-fwd, Z with the compatibility projection and Y-inv in one pass whose working set lives
-// in the distributed shared memory of a 16-CTA thread-block cluster (FP32, ny = nz = N).
+// in the distributed shared memory of a 16-CTA thread-block cluster (FP32, ny = nz = N,
+// N = R0 R1 a two-stage plan).
 //
 // The projection (Eqs. mapping G, mechanicalsolve) couples the three components of one row
 // i of the tensor only: A'_ij = n_j (A_im n_m) / |n|^2.  So a cluster takes one kx plane of
 // one row (three components, N x N complex numbers: 1.5 MB at N = 256) and keeps it on chip
-// across the three transforms:
+// across the three transforms.  CTA r of the cluster owns the z slab [r S, (r+1) S) in the
+// y stages and the ky slab [r S, (r+1) S) in the z stage (S = N / 16):
 //
-//   stage 0  CTA r loads its slab of S = N/16 z-rows (y contiguous) of the three components
-//            from S1 and transforms them along y                             [own tile]
-//   stage 1  CTA r gathers the ky range [r S, (r+1) S) of every z from all 16 CTAs' own
-//            tiles (distributed shared memory), transforms along z, projects, transforms
-//            back along z                                                   [recv tile]
-//   stage 2  CTA r gathers its z slab back, every ky, from all 16 recv tiles  [own tile]
-//   stage 3  inverse transform along y and store to S1 in place
+//   stage 0  load the S z-rows of each input component from HBM straight into registers
+//            (radix-R0 step), one transpose through the own tile, radix-R1 step; each
+//            thread then stores its ky values into the recv tile of the CTA that owns them
+//            (remote stores to distributed shared memory, 16 lanes writing one 128-byte run)
+//   stage 1  two-stage z-transform of the recv tile, the frequency-space operator (read
+//            across the component rows), two-stage inverse z-transform whose last step
+//            stores its z values into the own tile of the CTA that owns them
+//   stage 2  two-stage inverse y-transform of the own tile, stored to HBM from registers
 //
-// with a cluster barrier between stages (and the last gather ends with one, so that no
-// CTA leaves while a peer still reads its tiles).  The intermediate spectrum of the Y and Z
-// passes never reaches HBM: the pass reads and writes the nine-component spectrum once
-// (72.6 B per voxel at N = 256) where the three passes read and wrote it three times.
-// In the host emulation the stages of all 16 CTAs of a cluster run one stage at a time, so
-// the cluster barriers hold there too.
+// Cluster barriers: one arrive at the start, waited on before the first remote store (every
+// CTA of the cluster has started), and one after each push.  A tile is written remotely
+// only in the stage before the one that reads it, so the two pushes never overlap a read.
+// The pass reads and writes the nine-component spectrum once (72.6 B per voxel at N = 256)
+// where the three passes read and wrote it three times.  In the host emulation the stages
+// of the 16 CTAs run one stage at a time, which is what the barriers guarantee on the GPU.
 #pragma once
 #include <atomic>
 #include <vector>
 #include "fg_ops.cuh"
-
-#ifndef FG_EMU
-#include <cooperative_groups.h>
-#endif
 
 namespace fg {
 
@@ -83,44 +82,82 @@ struct ZWhole {
 template <typename R, int N, class Z = ZRows<R>>
 struct YZYCluster {
   using C = cplx<R>;
+  static constexpr Plan P = make_plan(N);
+  static_assert(P.S == 2, "the clustered pass takes a two-stage plan");
+  static constexpr int R0 = P.r[0], R1 = P.r[1];
+  static constexpr int T0 = N / R0, T1 = N / R1;  // butterflies per row in stage 0 / 1
   static constexpr int CI = Z::CIN, CO = Z::COUT, G = Z::GROUPS;
   static constexpr int CM = CI > CO ? CI : CO;
-  static constexpr int S = N / YZY_CLUSTER;   // z rows (stage 0) or ky rows (stage 1) per CTA
-  static constexpr int ROWS = CM * S;         // rows of the largest component count
-  static constexpr int NT = round32(ROWS * tpr(N));
-  using TFf = TileFFT<R, N, CI * S, NT, false>;  // forward transforms: the CI input rows
-  using TFi = TileFFT<R, N, CO * S, NT, true>;   // inverse transforms: the CO output rows
-  static constexpr int PITCH = TFf::PITCH;
-  static constexpr int VMAX = TFf::VMAX > TFi::VMAX ? TFf::VMAX : TFi::VMAX;
+  static constexpr int S = N / YZY_CLUSTER;  // z rows (y stages) or ky rows (z stage) per CTA
+  static constexpr int ROWS = CM * S;
+  static constexpr int TM = T0 > T1 ? T0 : T1;
+  static constexpr int RM = R0 > R1 ? R0 : R1;
+  static constexpr int NT = round32(ROWS * TM);
+  static constexpr int NSTAGES = 3;
+  static constexpr int PITCH = row_pitch(N);
   struct Locals {
-    C v[VMAX];
+    C v[RM];
     Acc<R> acc;
   };
   static constexpr size_t TILE = (size_t)ROWS * PITCH * sizeof(C);
   static size_t smem_bytes() { return 2 * TILE + N * sizeof(C); }
   static int clusters(int hx) { return hx * G; }
+  // resident CTAs per SM the register budget is sized for
+  static constexpr int MINB = 2 * TILE + N * sizeof(C) <= 110 * 1024 ? 2 : 1;
 
-  // shared memory of the cluster's CTA q: the distributed shared memory window of that CTA
-  // (mapa) on the GPU; the emulation's buffer of that CTA on the host
-  FG_DEV static char* peer(char* local, char* const* sm, int q) {
-#ifdef FG_EMU
-    (void)local;
-    return sm[q];
-#else
-    (void)sm;
-    return cooperative_groups::this_cluster().map_shared_rank(local, q);
-#endif
-  }
-
-  // own tile, recv tile and twiddles of a CTA's shared memory
   FG_DEV static C* own(char* sm) { return (C*)sm; }
   FG_DEV static C* recv(char* sm) { return (C*)(sm + TILE); }
   FG_DEV static C* twid(char* sm) { return (C*)(sm + 2 * TILE); }
 
+  // stores v at element `off` of the tile that starts `base` bytes into the shared memory of
+  // the cluster's CTA q: a remote store to distributed shared memory on the GPU (mapa of the
+  // same offset in the own window), the emulation's buffer of CTA q on the host
+  FG_DEV static void put(char* local, char* const* sm, int q, size_t base, int off, C v) {
+#ifdef FG_EMU
+    (void)local;
+    ((C*)(sm[q] + base))[off] = v;
+#else
+    (void)sm;
+    const unsigned la = (unsigned)__cvta_generic_to_shared(local + base + (size_t)off * sizeof(C));
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(q));
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(ra), "f"(v.x), "f"(v.y)
+                 : "memory");
+#endif
+  }
+
+  // every CTA of the cluster has started: waits on the arrive made at the kernel's start
+  FG_DEV static void wait_started() {
+#ifndef FG_EMU
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+#endif
+  }
+
+  // stage 0 of the plan on registers v = x[b + r T0]: radix-R0 DFT, outputs at b R0 + r
+  template <bool INV>
+  FG_DEV static void step0_store(C* v, C* row, int b) {
+    Dft<R0, INV, C>::run(v);
+#pragma unroll
+    for (int r = 0; r < R0; ++r) row[pad16(b * R0 + r)] = v[r];
+  }
+  // stage 1 (Ns = R0): loads positions b + r T1, twiddles by exp(-+2 pi i r b / N), radix-R1
+  // DFT; v then holds the natural-order outputs b + r T1
+  template <bool INV>
+  FG_DEV static void step1_load(C* v, const C* row, const C* tw, int b) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[r] = row[pad16(b + r * T1)];
+#pragma unroll
+    for (int r = 1; r < R1; ++r) {
+      const C w = tw[r * b];
+      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+    Dft<R1, INV, C>::run(v);
+  }
+
   // Stage s of the CTA of rank `rank` in cluster `cid` (kx = cid / G, group g = cid % G:
   // components g CI + cc in, g CO + cc out).  local is the CTA's own shared memory; sm[q]
-  // that of the cluster's CTA q in the emulation (unused on the GPU, where peer() maps it).
-  // Tile rows (cc, r) hold component cc at z (own tile) or ky (recv tile) of the slab.
+  // that of the cluster's CTA q in the emulation (unused on the GPU).  Tile row cc S + j
+  // holds component cc at z = rank S + j (own tile) or ky = rank S + j (recv tile).
   template <class Loc>
   FG_DEV static void stage(int s, const PassArgs<R>& a, int cid, int rank, char* local,
                            char* const* sm, Loc* Ls) {
@@ -130,62 +167,128 @@ struct YZYCluster {
     C* tw = twid(local);
     const int ny = a.ny, nz = a.nz;
     if (s == 0) {
+      // radix-R0 step straight from HBM (lanes along y: coalesced)
       FG_PHASE(NT)
       for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
-      // S consecutive z-rows of length ny per component: one contiguous block each
-      for (int e = tid; e < CI * S * N; e += NT) {
-        const int q = e / N, y = e - q * N;
-        const int cc = q / S, zz = q - cc * S;
-        const long long gi = (long long)(g * CI + cc) * a.VH +
-                             ((long long)kx * nz + rank * S + zz) * ny + y;
-        mine[q * PITCH + pad16(y)] = a.cin[gi];
+      if (tid < CI * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+        const int cc = rho / S, zz = rho - cc * S;
+        const C* in = a.cin + (long long)(g * CI + cc) * a.VH +
+                      ((long long)kx * nz + rank * S + zz) * ny;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) L.v[r] = in[b + r * T0];
+        step0_store<false>(L.v, mine + rho * PITCH, b);
       }
       FG_END_PHASE
-      tile_fft<TFf, 0>(Ls, mine, tw, NT);
+      // radix-R1 step, then each ky value to the recv tile of the CTA owning that ky (lanes
+      // along z: the 16 lanes of one row of the destination write one contiguous run)
+      FG_PHASE(NT)
+      const bool act = tid < CI * S * T1;
+      const int rho = tid % (CI * S), b = tid / (CI * S);
+      if (act) step1_load<false>(L.v, mine + rho * PITCH, tw, b);
+      wait_started();
+      if (act) {
+        const int cc = rho / S, zz = rho - cc * S;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const int ky = b + r * T1, q = ky / S, kyy = ky - q * S;
+          put(local, sm, q, TILE, (cc * S + kyy) * PITCH + pad16(rank * S + zz), L.v[r]);
+        }
+      }
+      FG_END_PHASE
     } else if (s == 1) {
+      // forward z-transform of the recv tile, radix-R0 step
       FG_PHASE(NT)
-      // recv row (cc, kyy) holds every z of ky = rank S + kyy: z slab q of it is CTA q's
-      for (int e = tid; e < CI * S * N; e += NT) {
-        const int qrow = e / N, z = e - qrow * N;
-        const int cc = qrow / S, kyy = qrow - cc * S;
-        const int src = z / S, zz = z - src * S;
-        const C* pt = own(peer(local, sm, src));
-        rv[qrow * PITCH + pad16(z)] = pt[(cc * S + zz) * PITCH + pad16(rank * S + kyy)];
+      if (tid < CI * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+        const C* row = rv + rho * PITCH;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) L.v[r] = row[pad16(b + r * T0)];
+        Dft<R0, false, C>::run(L.v);
       }
       FG_END_PHASE
-      tile_fft<TFf, 0>(Ls, rv, tw, NT);
       FG_PHASE(NT)
-      for (int e = tid; e < S * N; e += NT) {
-        const int kyy = e / N, kz = e - kyy * N;
-        C v[CM];
+      if (tid < CI * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
 #pragma unroll
-        for (int cc = 0; cc < CI; ++cc) v[cc] = rv[(cc * S + kyy) * PITCH + pad16(kz)];
-        Z::apply(a, kx, rank * S + kyy, kz, g, v);
-#pragma unroll
-        for (int cc = 0; cc < CO; ++cc) rv[(cc * S + kyy) * PITCH + pad16(kz)] = v[cc];
+        for (int r = 0; r < R0; ++r) rv[rho * PITCH + pad16(b * R0 + r)] = L.v[r];
       }
       FG_END_PHASE
-      tile_fft<TFi, 0>(Ls, rv, tw, NT);
-    } else if (s == 2) {
+      // radix-R1 step; each thread writes back the positions it read (natural order)
       FG_PHASE(NT)
-      // own row (cc, zz) gets every ky of z = rank S + zz: ky slab q of it is CTA q's
-      for (int e = tid; e < CO * S * N; e += NT) {
-        const int q = e / N, ky = e - q * N;
-        const int cc = q / S, zz = q - cc * S;
-        const int src = ky / S, kyy = ky - src * S;
-        const C* pt = recv(peer(local, sm, src));
-        mine[q * PITCH + pad16(ky)] = pt[(cc * S + kyy) * PITCH + pad16(rank * S + zz)];
+      if (tid < CI * S * T1) {
+        const int b = tid % T1, rho = tid / T1;
+        C* row = rv + rho * PITCH;
+        step1_load<false>(L.v, row, tw, b);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) row[pad16(b + r * T1)] = L.v[r];
+      }
+      FG_END_PHASE
+      // the operator on the CI components of each frequency, kept for output component co,
+      // and the radix-R0 step of the inverse z-transform
+      FG_PHASE(NT)
+      if (tid < CO * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+        const int co = rho / S, kyy = rho - co * S;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int kz = b + r * T0;
+          C w[CM];
+#pragma unroll
+          for (int ci = 0; ci < CI; ++ci) w[ci] = rv[(ci * S + kyy) * PITCH + pad16(kz)];
+          Z::apply(a, kx, rank * S + kyy, kz, g, w);
+          L.v[r] = w[co];
+        }
+        Dft<R0, true, C>::run(L.v);
+      }
+      FG_END_PHASE
+      FG_PHASE(NT)
+      if (tid < CO * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) rv[rho * PITCH + pad16(b * R0 + r)] = L.v[r];
+      }
+      FG_END_PHASE
+      // radix-R1 step, then each z value to the own tile of the CTA owning that z
+      FG_PHASE(NT)
+      if (tid < CO * S * T1) {
+        const int rho = tid % (CO * S), b = tid / (CO * S);
+        const int co = rho / S, kyy = rho - co * S;
+        step1_load<true>(L.v, rv + rho * PITCH, tw, b);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+          const int z = b + r * T1, q = z / S, zz = z - q * S;
+          put(local, sm, q, 0, (co * S + zz) * PITCH + pad16(rank * S + kyy), L.v[r]);
+        }
       }
       FG_END_PHASE
     } else {
-      tile_fft<TFi, 0>(Ls, mine, tw, NT);
+      // inverse y-transform of the own tile, stored to HBM from registers
       FG_PHASE(NT)
-      for (int e = tid; e < CO * S * N; e += NT) {
-        const int q = e / N, y = e - q * N;
-        const int cc = q / S, zz = q - cc * S;
-        const long long gi = (long long)(g * CO + cc) * a.VH +
-                             ((long long)kx * nz + rank * S + zz) * ny + y;
-        a.cout[gi] = mine[q * PITCH + pad16(y)];
+      if (tid < CO * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+        const C* row = mine + rho * PITCH;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) L.v[r] = row[pad16(b + r * T0)];
+        Dft<R0, true, C>::run(L.v);
+      }
+      FG_END_PHASE
+      FG_PHASE(NT)
+      if (tid < CO * S * T0) {
+        const int b = tid % T0, rho = tid / T0;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) mine[rho * PITCH + pad16(b * R0 + r)] = L.v[r];
+      }
+      FG_END_PHASE
+      FG_PHASE(NT)
+      if (tid < CO * S * T1) {
+        const int b = tid % T1, rho = tid / T1;
+        const int co = rho / S, zz = rho - co * S;
+        step1_load<true>(L.v, mine + rho * PITCH, tw, b);
+        C* out = a.cout + (long long)(g * CO + co) * a.VH +
+                 ((long long)kx * nz + rank * S + zz) * ny;
+#pragma unroll
+        for (int r = 0; r < R1; ++r) out[b + r * T1] = L.v[r];
       }
       FG_END_PHASE
     }
@@ -194,21 +297,21 @@ struct YZYCluster {
 
 #ifndef FG_EMU
 template <class K, class A>
-__global__ void __launch_bounds__(K::NT, 1) cluster_kernel(A a) {
-  namespace cgr = cooperative_groups;
+__global__ void __launch_bounds__(K::NT, K::MINB) cluster_kernel(A a) {
   extern __shared__ __align__(16) char smem[];
   typename K::Locals L;
   if (a.done && *a.done) return;  // the same flag for every CTA of the cluster
-  cgr::cluster_group cluster = cgr::this_cluster();
-  const int rank = (int)cluster.block_rank();
+  unsigned rank;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   const int cid = (int)(blockIdx.x / YZY_CLUSTER);
-  K::stage(0, a, cid, rank, smem, nullptr, &L);
-  cluster.sync();
-  K::stage(1, a, cid, rank, smem, nullptr, &L);
-  cluster.sync();
-  K::stage(2, a, cid, rank, smem, nullptr, &L);
-  cluster.sync();  // no CTA leaves while a peer reads its tiles
-  K::stage(3, a, cid, rank, smem, nullptr, &L);
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  K::stage(0, a, cid, (int)rank, smem, nullptr, &L);  // waits on that arrive before pushing
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+  K::stage(1, a, cid, (int)rank, smem, nullptr, &L);
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+  K::stage(2, a, cid, (int)rank, smem, nullptr, &L);
 }
 #endif
 
@@ -263,7 +366,7 @@ int launch_cluster(const A& a, int nclusters, cudaStream_t st) {
   for (int q = 0; q < YZY_CLUSTER; ++q) ptr[q] = mem[q].data();
   if (a.done && *a.done) return 0;
   for (int cid = 0; cid < nclusters; ++cid)
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < K::NSTAGES; ++s)
       for (int r = 0; r < YZY_CLUSTER; ++r) K::stage(s, a, cid, r, ptr[r], ptr, Ls[r].data());
 #else
   cudaLaunchConfig_t cfg = {};

@@ -14,8 +14,8 @@ Cases:
                  band 2, 50-step influx), run until the first step with damage and two
                  steps beyond it (at most 50 steps)
     plate        the Sec. 4.3 plate (64 x 64 x 1, Saint-Venant-Kirchhoff, Omega = 1.3) at
-                 Newton and staggered tolerance 1e-12, until the first damaging step and
-                 one beyond (at most 20)
+                 Newton and staggered tolerance 1e-12, until the first damaging step (at
+                 most 20; the step after it takes the oracle over an hour at 1e-12)
     gumbel512    the Sec. 5.1 disc (512^2, Saint-Venant-Kirchhoff, Gumbel-distributed
                  stiffness and strength, Omega = 1.3, full chemistry Jacobian): its first
                  two steps (the second one damages)
@@ -67,7 +67,7 @@ def workload(case):
 
 
 MAX_STEPS = {"ellipsoid32": 50, "plate": 20, "gumbel512": 2}
-AFTER_DAMAGE = {"ellipsoid32": 2, "plate": 1, "gumbel512": 0}
+AFTER_DAMAGE = {"ellipsoid32": 2, "plate": 0, "gumbel512": 0}
 
 
 def oracle_params(w):
