@@ -142,7 +142,8 @@ typedef struct {
   int cg_negcurv;     /* CG directions of negative curvature taken (cg_indefinite 1) */
   int newton_shifted; /* mechanical Newton systems solved again with a larger shift */
   int newton_minres;  /* mechanical solves that fell back to FP64 MINRES after a CG
-                         correction failed to lower the FP64 residual */
+                         correction failed to lower the FP64 residual (a MINRES solve at
+                         max_cg keeps its iterate; the Newton loop's test decides) */
   int cg_graph_replays; /* 16-iteration chunks of the mechanical CG replayed from captured
                          CUDA graphs (contexts on a stream other than the legacy default
                          stream, profiling off, no shift) */

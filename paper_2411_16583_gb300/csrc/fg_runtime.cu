@@ -1231,8 +1231,9 @@ static void lin3(fg_ctx& c, double* out, long long n, double s0, const double* x
 // phi_k = c phibar_{k-1}, phibar_k = -s phibar_{k-1}, |phibar_k| = |b - A x_k| (monotone),
 // and x_k = x_{k-1} + phi_k w_k, w_k = (v_k - d_k w_{k-1} - e_k w_{k-2}) / gamma_k.  It is
 // the fallback of the mechanical Newton where CG directions fail (a state whose tangent
-// has negative eigenvalues).  Stops at |r| <= tol |b| or maxit (an error when strict or in
-// FP64 mode).  Returns the iterations.
+// has negative eigenvalues).  Stops at |r| <= tol |b| or at maxit, where it keeps its
+// iterate in both modes as the oracle's MINRES does (the Newton loop's own test on err_res
+// then decides; an error only when strict).  Returns the iterations.
 static int minres_mech(fg_ctx& c, double tol, int maxit) {
   Prec<double>& D = c.pd;
   const long long n = 9 * c.V;
@@ -1250,7 +1251,7 @@ static int minres_mech(fg_ctx& c, double tol, int maxit) {
   int it = 0;
   while (fabs(phibar) > tol * beta1) {
     if (it >= maxit) {
-      if (!is_mixed(c) || c.strict) fail(FG_ERR_NOCONV, "mechanical MINRES hit max_cg");
+      if (c.strict) fail(FG_ERR_NOCONV, "mechanical MINRES hit max_cg");
       break;
     }
     ++it;

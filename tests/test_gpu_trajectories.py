@@ -22,8 +22,14 @@ the GPU's F (in both precisions) differs from the oracle's by 1.5-1.8e-7 of max 
 voxels not cracked through at Newton tolerance 1e-9, up to 4e-6 a step later, while c
 agrees to 1e-11 to 2e-8 and d to 2e-8 to 2e-7.  After a crack the bars are therefore 1e-5
 in F and H (on the voxels not cracked through), 1e-9 (FP64) and 1e-7 (mixed) in c, 1e-6 in
-d, and every whole field must be a valid solution: the oracle's err_res of the GPU's
-fields (Eq. mechresiduum) within twice the staggered tolerance."""
+d.
+
+At every recorded step the GPU's whole fields must also solve the step's equations, by
+the oracle's operators: err_res (Eq. mechresiduum) within twice the staggered tolerance,
+the history field within 1e-10 of max(H_t, psi_c D_f) (Eq. Hist) from the GPU's own
+previous step, and the phase-field system (Eq. PFFA) with residual below 1e-10 of |2H|.
+Where a cracking step has two equilibria (TWO_EQUILIBRIA), the FP64 path is held to these
+checks and to c only."""
 import os
 
 import numpy as np
@@ -43,6 +49,13 @@ BARS = {B.FG_FP64: dict(F=1e-10, c=1e-10, d=1e-8, H=1e-8, energy=1e-8),
         B.FG_MIXED: dict(F=1e-7, c=1e-7, d=1e-6, H=1e-6, energy=1e-6)}
 CRACKED_BARS = {B.FG_FP64: dict(F=1e-5, c=1e-9, d=1e-6, H=1e-5, energy=1e-6),
                 B.FG_MIXED: dict(F=1e-5, c=1e-7, d=1e-6, H=1e-5, energy=1e-6)}
+# Cases whose cracking step has more than one equilibrium reachable by the staggered loop.
+# The Sec. 4.3 plate at Newton 1e-12: the oracle's loop takes 20 staggered iterations and
+# ends with 836 damaged voxels; the GPU's mixed loop takes 19 and matches it within the
+# bars; the GPU's FP64 loop (its exact Newton corrections meet negative curvature and
+# damping more often) takes 47 and ends with 822.  Both end states solve the step's
+# equations to the tolerances, which the comparison checks for every step.
+TWO_EQUILIBRIA = {"plate"}
 
 
 @pytest.fixture(scope="module")
@@ -68,14 +81,18 @@ def _compare(case, precision, lib):
     sol = B.from_workload(w, precision=precision, lib=lib)
     steps = [int(k) for k in ref["steps"]]
     report = {}
+    H_prev = sol.get(B.FIELD_H)
     for k in range(1, max(steps) + 1):
         st = sol.step(w.dt)
         assert st["status"] == 0
+        Hfull = sol.get(B.FIELD_H)
         if k not in steps:
+            H_prev = Hfull
             continue
         idx = ref[f"idx_s{k}"]
-        F = sol.get(B.FIELD_F).reshape(9, -1)[:, idx]
-        c, d, H = (sol.get(f).ravel()[idx] for f in (B.FIELD_C, B.FIELD_D, B.FIELD_H))
+        Ffull, cfull, dfull = (sol.get(f) for f in (B.FIELD_F, B.FIELD_C, B.FIELD_D))
+        F = Ffull.reshape(9, -1)[:, idx]
+        c, d, H = (f.ravel()[idx] for f in (cfull, dfull, Hfull))
         err = {}
         # particle voxels not cracked through (the buffer stands in for empty space)
         sound = (ref[f"d_s{k}"] <= 0.9) & (w.phase_id.ravel()[idx] == 0)
@@ -86,17 +103,32 @@ def _compare(case, precision, lib):
         Hw = ref[f"H_s{k}"]
         err["H"] = float(np.abs(H - Hw)[sound].max() / max(np.abs(Hw[sound]).max(), 1e-30))
         mass, energy, dmax, ndam, _ = ref[f"scal_s{k}"]
-        bars = (CRACKED_BARS if dmax > 0.9 else BARS)[precision]
-        dfull = sol.get(B.FIELD_D)
         e = _crack_energy(dfull, w)
         err["energy"] = abs(e - energy) / energy if energy > 0 else abs(e)
+        err["damaged"] = int((dfull > 1e-3).sum()) - int(ndam)
+        # the GPU's fields solve the step's equations (the oracle's operators): mechanical
+        # equilibrium (Eq. mechresiduum), the history field of Eq. Hist from the previous
+        # step's, and the phase-field system of Eq. PFFA with that history
+        _, err["res_mech"] = O.mech_residual(Ffull, cfull, dfull, prm, np.eye(3))
+        Hh = O.history_update(H_prev, Ffull, cfull, prm)
+        err["res_hist"] = float(np.abs(Hfull - Hh).max() / max(np.abs(Hh).max(), 1e-30))
+        Heff = Hfull / O.gc_ratio(prm)
+        rd = O.pff_apply(dfull, Heff, prm) - 2.0 * Heff
+        err["res_pff"] = float(np.linalg.norm(rd) / max(np.linalg.norm(2.0 * Heff), 1e-300))
         report[k] = err
-        assert abs(sol.get(B.FIELD_C).sum() - mass) <= 1e-11 * mass, (k, "mass")
-        _, err_res = O.mech_residual(sol.get(B.FIELD_F), sol.get(B.FIELD_C), dfull, prm,
-                                     np.eye(3))
-        assert err_res <= 2 * w.tol["tol_stag"], (k, "err_res", err_res)
-        assert abs(int((dfull > 1e-3).sum()) - ndam) <= max(2, 0.01 * ndam), (k, "damaged")
-        for name, bar in bars.items():
+        H_prev = Hfull
+        assert abs(cfull.sum() - mass) <= 1e-11 * mass, (k, "mass")
+        assert err["res_mech"] <= 2 * w.tol["tol_stag"], (case, k, err)
+        assert err["res_hist"] <= 1e-10, (case, k, err)
+        assert err["res_pff"] <= 1e-10, (case, k, err)
+        cracked = dmax > 0.9
+        if cracked and precision == B.FG_FP64 and case in TWO_EQUILIBRIA:
+            # the FP64 staggered loop reaches another equilibrium of this cracking step
+            # (see TWO_EQUILIBRIA): c, found before the loop, is still compared
+            assert err["c"] <= CRACKED_BARS[precision]["c"], (case, k, err)
+            continue
+        assert abs(err["damaged"]) <= max(2, 0.01 * ndam), (case, k, err)
+        for name, bar in (CRACKED_BARS if cracked else BARS)[precision].items():
             assert err[name] <= bar, (case, k, name, err)
     sol.close()
     return report
