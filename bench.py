@@ -855,10 +855,22 @@ def batch_mode(count, steps, warmup):
         st = batch.step(1.0)
     torch.cuda.synchronize()
     t_b = (time.perf_counter() - t0) / steps
+    # the members' FP32 mechanical operator at their current states: grouped launches (one
+    # per pass over every member of a grid, from a device table of pass arguments) against
+    # the members' own launches
+    ms, info = batch.time_apply(prec=1, n=20)
     batch.close()
     for s_ in mem:
         s_.close()
+    names = ("grouped_graph", "grouped", "members_one_stream", "members_own_streams")
+    apply = {"kind": "FP32 mechanical operator application of all members (Eq. mechanicalsolve)",
+             "applications": 20, "groups": info[0], "launches_grouped": info[1],
+             "launches_members": info[2],
+             "ms": dict(zip(names, ms)),
+             "voxel_applies_per_s": {k: V / (t * 1e-3) for k, t in zip(names, ms)}}
+    apply["grouped_graph_over_own_streams"] = ms[3] / ms[0]
     return {"mode": "batch", "rves": len(ws), "voxels": V, "steps": steps, "warmup": warmup,
+            "apply": apply,
             "sizes": sorted({w.shape[0] for w in ws}),
             "batched_voxel_steps_per_s": V / t_b, "sequential_voxel_steps_per_s": V / t_seq,
             "batched_ms_per_step": t_b * 1e3, "sequential_ms_per_step": t_seq * 1e3,

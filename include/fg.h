@@ -293,6 +293,30 @@ int fg_batch_step(fg_batch* batch, double dt, const double Fbar[9], fg_stats* st
 void fg_batch_destroy(fg_batch* batch);
 
 /*
+ * Grouped operator application over a batch (the mechanical operator G*(K:x) of Eq.
+ * mechanicalsolve, as fg_apply with FG_OP_MECH).  Members whose grids are equal form a group
+ * (run with the schedule the autotuner chose for the group's first member); each FFT pass
+ * of a group runs as ONE kernel launch over all its members, block m P + b of the launch
+ * running block b of member m, with the members' pass arguments read from a device table
+ * (a device-side work list).  The groups run concurrently, each on a stream of its own.  x[i], y[i]: member i's
+ * 9 x V input and output (device pointers, precision prec: 0 = FP64, 1 = FP32; host
+ * pointers in the emulation build), owned by the caller.  Builds each member's tangent
+ * state from its F first (as fg_apply does).  Runs on a stream of the batch and returns
+ * after the applications completed; the members' streams are synchronised first.  Errors:
+ * FG_ERR_INVALID (op other than FG_OP_MECH, bad precision, a null vector), FG_ERR_CUDA.
+ *
+ * fg_batch_time_apply times napply applications of every member's operator (zero inputs in
+ * buffers of its own) four ways and writes milliseconds per batch application to ms:
+ * ms[0] the grouped launches captured once as a CUDA graph and replayed, ms[1] the grouped
+ * launches issued one by one, ms[2] every member's own launches member after member on one
+ * stream, ms[3] every member's own launches on its own stream, all members at once.
+ * info (may be NULL): [0] groups, [1] launches per grouped application, [2] launches per
+ * application of all members one by one.  GPU build only (FG_ERR_INVALID in the emulation).
+ */
+int fg_batch_apply(fg_batch* batch, int op, int prec, const void* const* x, void* const* y);
+int fg_batch_time_apply(fg_batch* batch, int prec, int napply, double ms[4], int info[3]);
+
+/*
  * Mixed macroscopic control (the paper's Sec. 3 allows prescribing macroscopic stress
  * components instead of F-bar components).  Bit 3 i + j of mask marks component (i, j) as
  * stress-controlled: the mean first Piola stress P-bar_ij is prescribed (Pbar[9],

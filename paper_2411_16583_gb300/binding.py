@@ -80,7 +80,7 @@ FG_LOSS_SEEDS = 1
 EXPORTS = ["fg_default_opts", "fg_supported_size", "fg_setup", "fg_step", "fg_residual",
            "fg_apply", "fg_get_field", "fg_set_field", "fg_time_apply", "fg_profile",
            "fg_profile_read", "fg_mech_apply_noalloc", "fg_batch_setup", "fg_batch_step",
-           "fg_batch_destroy", "fg_autotune", "fg_autotune_report", "fg_solve_mech", "fg_adjoint_mech",
+           "fg_batch_apply", "fg_batch_time_apply", "fg_batch_destroy", "fg_autotune", "fg_autotune_report", "fg_solve_mech", "fg_adjoint_mech",
            "fg_tape_begin", "fg_adjoint", "fg_save", "fg_load", "fg_set_stress_control",
            "fg_displacement", "fg_displacement_adjoint", "fg_kernel_launches", "fg_destroy",
            "fg_last_error"]
@@ -127,6 +127,9 @@ def load_library(path=LIB_PATH):
                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(AdjStats)]
     lib.fg_batch_setup.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
     lib.fg_batch_step.argtypes = [C.c_void_p, C.c_double, dp, C.POINTER(Stats)]
+    lib.fg_batch_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p)]
+    lib.fg_batch_time_apply.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.POINTER(C.c_int)]
     lib.fg_batch_destroy.argtypes = [C.c_void_p]
     lib.fg_batch_destroy.restype = None
     lib.fg_kernel_launches.restype = C.c_longlong
@@ -400,6 +403,31 @@ class Batch:
         if check and rc != FG_OK:
             raise FgError(rc, self.lib.fg_last_error().decode())
         return [s.as_dict() for s in st]
+
+    def apply(self, xs, ys, prec=0, op=None):
+        """y_i = A_i x_i for every member (OP_MECH) in grouped launches: xs, ys are one
+        buffer per member (torch tensors on the device; numpy arrays with the emulation)."""
+        op = OP_MECH if op is None else op
+        n = len(self.solvers)
+        if len(xs) != n or len(ys) != n:
+            raise ValueError("one input and one output per member")
+        xa = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+        ya = (C.c_void_p * n)(*[_ptr(y) for y in ys])
+        rc = self.lib.fg_batch_apply(self.h, op, prec, xa, ya)
+        if rc != FG_OK:
+            raise FgError(rc, self.lib.fg_last_error().decode())
+
+    def time_apply(self, prec=1, n=20):
+        """Milliseconds per application of every member's mechanical operator: grouped
+        launches replayed from a CUDA graph, grouped launches, members one by one on one
+        stream, members on their own streams; and (groups, launches per grouped
+        application, launches per one-by-one application)."""
+        ms = (C.c_double * 4)()
+        info = (C.c_int * 3)()
+        rc = self.lib.fg_batch_time_apply(self.h, prec, n, ms, info)
+        if rc != FG_OK:
+            raise FgError(rc, self.lib.fg_last_error().decode())
+        return list(ms), list(info)
 
     def close(self):
         if getattr(self, "h", None):

@@ -45,10 +45,105 @@ __global__ void __launch_bounds__(K::NT, MinBlocks<K>::value) pass_kernel_mb(A a
 // number of kernel launches issued by the library (all kernels, all contexts)
 std::atomic<long long>& launch_counter();
 
+// ------------------------------------------------------------------ grouped launches
+//
+// A batch of RVEs with equal grids runs each pass of an operator application as one
+// launch over all members: block m P + b of the grouped kernel runs block b of member m
+// (P blocks per member), with member m's pass arguments read from a device table.  The
+// runtime finds the launches of one member's application by recording them: while a
+// recorder is set on the calling thread, launch_pass stores the launch (the grouped
+// launcher of its kernel, its grid and a copy of its arguments) instead of launching.
+struct RecordedLaunch {
+  void (*grouped)(const void* args, int members, Dim3 grid, cudaStream_t st);
+  size_t arg_bytes;
+  Dim3 grid;
+  std::vector<char> args;
+};
+inline std::vector<RecordedLaunch>*& launch_recorder() {
+  static thread_local std::vector<RecordedLaunch>* r = nullptr;
+  return r;
+}
+
+#ifndef FG_EMU
+// The block's member arguments are copied into shared memory first: the pass bodies then
+// read them from memory that no global store can alias, as they read kernel parameters.
+template <class K, class A>
+FG_DEV void grouped_body(const A* __restrict__ args, Dim3 grid) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ __align__(16) A sa;
+  typename K::Locals L;
+  const int per = grid.x * grid.y * grid.z;
+  const int m = (int)blockIdx.x / per, b = (int)blockIdx.x - m * per;
+  static_assert(sizeof(A) % sizeof(int) == 0, "argument block of whole words");
+  for (int i = (int)threadIdx.x; i < (int)(sizeof(A) / sizeof(int)); i += (int)blockDim.x)
+    ((int*)&sa)[i] = ((const int*)(args + m))[i];
+  __syncthreads();
+  const int bx = b % grid.x, t = b / grid.x;
+  K::body(sa, Dim3{bx, t % grid.y, t / grid.y}, grid, smem, &L);
+}
+template <class K, class A>
+__global__ void __launch_bounds__(K::NT) grouped_kernel(const A* __restrict__ args, Dim3 grid) {
+  grouped_body<K, A>(args, grid);
+}
+template <class K, class A>
+__global__ void __launch_bounds__(K::NT, MinBlocks<K>::value)
+    grouped_kernel_mb(const A* __restrict__ args, Dim3 grid) {
+  grouped_body<K, A>(args, grid);
+}
+#endif
+
+// One launch of kernel K over `members` members (argument table `args`: device memory on
+// the GPU, host memory in the emulation), `grid` blocks each.
+template <class K, class A>
+void launch_grouped(const void* args, int members, Dim3 grid, cudaStream_t st) {
+  const size_t sm = K::smem_bytes();
+  ++launch_counter();
+  const A* av = (const A*)args;
+#ifdef FG_EMU
+  (void)st;
+  std::vector<char> smem(sm);
+  std::vector<typename K::Locals> Ls(K::NT);
+  for (int m = 0; m < members; ++m)
+    for (int z = 0; z < grid.z; ++z)
+      for (int y = 0; y < grid.y; ++y)
+        for (int x = 0; x < grid.x; ++x) {
+          std::memset(smem.data(), 0, sm);
+          K::body(av[m], Dim3{x, y, z}, grid, smem.data(), Ls.data());
+        }
+#else
+  constexpr bool MB = MinBlocks<K>::value > 1;
+  static const bool configured = [sm]() {
+    if constexpr (MB)
+      cudaFuncSetAttribute(grouped_kernel_mb<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+    else
+      cudaFuncSetAttribute(grouped_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sm);
+    return true;
+  }();
+  (void)configured;
+  const unsigned nb = (unsigned)members * (unsigned)(grid.x * grid.y * grid.z);
+  if constexpr (MB)
+    grouped_kernel_mb<K, A><<<nb, K::NT, sm, st>>>(av, grid);
+  else
+    grouped_kernel<K, A><<<nb, K::NT, sm, st>>>(av, grid);
+#endif
+}
+
 // Launches kernel K with arguments A on `grid` blocks of K::NT threads.  Returns the
 // number of blocks launched (the number of partial sums a reducing kernel writes).
 template <class K, class A>
 int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
+  if (std::vector<RecordedLaunch>* rec = launch_recorder()) {
+    RecordedLaunch r;
+    r.grouped = &launch_grouped<K, A>;
+    r.arg_bytes = sizeof(A);
+    r.grid = grid;
+    r.args.resize(sizeof(A));
+    std::memcpy(r.args.data(), &a, sizeof(A));
+    rec->push_back(std::move(r));
+    return grid.x * grid.y * grid.z;
+  }
   const size_t sm = K::smem_bytes();
   ++launch_counter();
 #ifdef FG_EMU

@@ -2898,7 +2898,193 @@ struct fg_batch {
   std::vector<cudaStream_t> own;    // streams created for the members
   std::vector<cudaStream_t> saved;  // the members' streams before the batch
   int threads = 1;
+  cudaStream_t apply_st = nullptr;  // grouped operator applications
+  std::vector<cudaStream_t> group_st;  // one stream per group, forked from apply_st
+  std::vector<cudaEvent_t> group_ev;   // the forks' and joins' events
+  void* dargs = nullptr;            // argument tables of the grouped launches (device)
+  size_t dargs_bytes = 0;
 };
+
+// Grouped operator application over a batch.  Each member's application is recorded
+// (launch_recorder: the pass launches it would issue, with their arguments); members whose
+// sequences match (same kernels, same grids: equal grids and tuning) form a group, and each
+// pass of a group runs as one launch over the group's members, their arguments in a device
+// table laid out group by group and launch by launch.
+struct GroupPlan {
+  std::vector<std::vector<RecordedLaunch>> rec;  // per member
+  std::vector<std::vector<int>> groups;          // member indices
+  std::vector<char> table;                       // host copy of the argument tables
+  std::vector<std::vector<size_t>> off;          // per group and launch: table offset
+};
+
+struct RecordScope {  // sets the calling thread's recorder for one scope
+  explicit RecordScope(std::vector<RecordedLaunch>* r) { launch_recorder() = r; }
+  ~RecordScope() { launch_recorder() = nullptr; }
+};
+struct FlagScope {  // clears a flag for one scope
+  bool& f;
+  bool old;
+  explicit FlagScope(bool& f_) : f(f_), old(f_) { f = false; }
+  ~FlagScope() { f = old; }
+};
+
+template <typename R>
+static Prec<R>& prec_of(fg_ctx& c) {
+  if constexpr (sizeof(R) == 4) return c.pf;
+  else return c.pd;
+}
+
+// builds every member's tangent state of precision R from its F (as fg_apply does)
+template <typename R>
+static void batch_prepare(fg_batch& b) {
+  for (fg_ctx* c : b.members) {
+    Prec<R>& P = prec_of<R>(*c);
+    if (!P.state) fail(FG_ERR_INVALID, "batch apply: a member has no tangent state in this precision");
+    mech_state<R>(*c, c->F, nullptr, nullptr, P.state);
+  }
+  for (fg_ctx* c : b.members) dsync(c->st);
+}
+
+// The schedule knobs of the autotuner (kx planes per chunk, projection tile, X prefetch):
+// they change the launches, not the values an application computes.
+struct Knobs {
+  int kx[2], zrows, l2pf;
+  explicit Knobs(const fg_ctx& c) : kx{c.kx_chunk[0], c.kx_chunk[1]}, zrows(c.zrows), l2pf(c.l2pf) {}
+  void put(fg_ctx& c) const {
+    c.kx_chunk[0] = kx[0];
+    c.kx_chunk[1] = kx[1];
+    c.zrows = zrows;
+    c.l2pf = l2pf;
+  }
+};
+
+// records y_i = A_i x_i of every member (mechanical operator, precision R) and groups them;
+// members of one grid are recorded with the knobs of the grid's first member, so that
+// equal grids give equal launch sequences
+template <typename R>
+static void batch_plan(fg_batch& b, const void* const* x, void* const* y, GroupPlan& g) {
+  const int n = (int)b.members.size();
+  g.rec.assign(n, {});
+  for (int i = 0; i < n; ++i) {
+    fg_ctx& c = *b.members[i];
+    int lead = i;
+    for (int j = 0; j < i; ++j) {
+      const fg_ctx& o = *b.members[j];
+      if (o.nx == c.nx && o.ny == c.ny && o.nz == c.nz && o.law == c.law) {
+        lead = j;
+        break;
+      }
+    }
+    const Knobs own(c);
+    Knobs(*b.members[lead]).put(c);
+    try {
+      FlagScope fs(c.yzy_cluster);  // the clustered pass is not a recorded pass launch
+      RecordScope rs(&g.rec[i]);
+      op_mech(c, prec_of<R>(c), (const R*)x[i], (R*)y[i], nullptr);
+    } catch (...) {
+      own.put(c);
+      throw;
+    }
+    own.put(c);
+  }
+  auto same = [&](int i, int j) {
+    if (g.rec[i].size() != g.rec[j].size()) return false;
+    for (size_t k = 0; k < g.rec[i].size(); ++k) {
+      const RecordedLaunch &p = g.rec[i][k], &q = g.rec[j][k];
+      if (p.grouped != q.grouped || p.grid.x != q.grid.x || p.grid.y != q.grid.y ||
+          p.grid.z != q.grid.z)
+        return false;
+    }
+    return true;
+  };
+  g.groups.clear();
+  for (int i = 0; i < n; ++i) {
+    bool put = false;
+    for (auto& gr : g.groups)
+      if (same(gr[0], i)) {
+        gr.push_back(i);
+        put = true;
+        break;
+      }
+    if (!put) g.groups.push_back({i});
+  }
+  g.table.clear();
+  g.off.assign(g.groups.size(), {});
+  for (size_t q = 0; q < g.groups.size(); ++q) {
+    const std::vector<int>& gr = g.groups[q];
+    for (size_t k = 0; k < g.rec[gr[0]].size(); ++k) {
+      const size_t at = (g.table.size() + 255) & ~(size_t)255;
+      g.table.resize(at);
+      g.off[q].push_back(at);
+      for (int i : gr) {
+        const std::vector<char>& a = g.rec[i][k].args;
+        g.table.insert(g.table.end(), a.begin(), a.end());
+      }
+    }
+  }
+}
+
+static void batch_stream(fg_batch& b) {
+#ifndef FG_EMU
+  cudaSetDevice(b.members[0]->device);
+  if (!b.apply_st && cudaStreamCreateWithFlags(&b.apply_st, cudaStreamNonBlocking) != cudaSuccess)
+    fail(FG_ERR_CUDA, "batch apply: cudaStreamCreate failed");
+#endif
+}
+
+// copies the argument tables to the device (then waits: the host table is pageable)
+static void batch_upload(fg_batch& b, const GroupPlan& g) {
+  if (g.table.size() > b.dargs_bytes) {
+    dfree(b.dargs);
+    b.dargs = nullptr;
+    b.dargs_bytes = 0;
+    b.dargs = dalloc(g.table.size());
+    b.dargs_bytes = g.table.size();
+  }
+  dcopy(b.dargs, g.table.data(), g.table.size(), b.apply_st);
+  dsync(b.apply_st);
+}
+
+// one grouped launch per pass and group; the groups run concurrently on streams of their
+// own, forked from and joined back into the batch's apply stream
+static long long batch_launch(fg_batch& b, const GroupPlan& g) {
+  const size_t G = g.groups.size();
+#ifndef FG_EMU
+  while (b.group_st.size() < G) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      fail(FG_ERR_CUDA, "batch apply: stream or event creation failed");
+    b.group_st.push_back(s);
+    b.group_ev.push_back(e);
+  }
+  if (b.group_ev.size() < G + 1) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      fail(FG_ERR_CUDA, "batch apply: event creation failed");
+    b.group_ev.push_back(e);
+  }
+  cudaEvent_t fork = b.group_ev[G];
+  cudaEventRecord(fork, b.apply_st);
+#endif
+  long long nl = 0;
+  for (size_t q = 0; q < G; ++q) {
+    cudaStream_t st = b.apply_st;
+#ifndef FG_EMU
+    st = b.group_st[q];
+    cudaStreamWaitEvent(st, fork, 0);
+#endif
+    const std::vector<RecordedLaunch>& seq = g.rec[g.groups[q][0]];
+    for (size_t k = 0; k < seq.size(); ++k, ++nl)
+      seq[k].grouped((const char*)b.dargs + g.off[q][k], (int)g.groups[q].size(), seq[k].grid, st);
+#ifndef FG_EMU
+    cudaEventRecord(b.group_ev[q], st);
+    cudaStreamWaitEvent(b.apply_st, b.group_ev[q], 0);
+#endif
+  }
+  return nl;
+}
 
 extern "C" {
 
@@ -2971,8 +3157,159 @@ int fg_batch_step(fg_batch* b, double dt, const double Fbar[9], fg_stats* st) {
   return first;
 }
 
+int fg_batch_apply(fg_batch* b, int op, int prec, const void* const* x, void* const* y) {
+  FG_API_BEGIN
+  if (!b || !x || !y || op != FG_OP_MECH || (prec != 0 && prec != 1))
+    fail(FG_ERR_INVALID, "fg_batch_apply: bad argument (FG_OP_MECH, precision 0 or 1)");
+  const int n = (int)b->members.size();
+  for (int i = 0; i < n; ++i)
+    if (!x[i] || !y[i]) fail(FG_ERR_INVALID, "fg_batch_apply: null member vector");
+  batch_stream(*b);
+  GroupPlan g;
+  if (prec == 1) {
+    batch_prepare<float>(*b);
+    batch_plan<float>(*b, x, y, g);
+  } else {
+    batch_prepare<double>(*b);
+    batch_plan<double>(*b, x, y, g);
+  }
+  batch_upload(*b, g);
+  batch_launch(*b, g);
+  dsync(b->apply_st);
+  FG_API_END
+}
+
+int fg_batch_time_apply(fg_batch* b, int prec, int napply, double ms[4], int info[3]) {
+  FG_API_BEGIN
+  if (!b || napply <= 0 || !ms || (prec != 0 && prec != 1))
+    fail(FG_ERR_INVALID, "fg_batch_time_apply: bad argument");
+#ifdef FG_EMU
+  fail(FG_ERR_INVALID, "fg_batch_time_apply: needs the GPU build");
+#else
+  const int n = (int)b->members.size();
+  const size_t es = prec == 1 ? sizeof(float) : sizeof(double);
+  batch_stream(*b);
+  std::vector<void*> xs(n, nullptr), ys(n, nullptr);
+  std::vector<cudaEvent_t> ev(n, nullptr);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < n; ++i) {
+      if (ev[i]) cudaEventDestroy(ev[i]);
+      dfree(xs[i]);
+      dfree(ys[i]);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  try {
+    for (int i = 0; i < n; ++i) {
+      const size_t nb = (size_t)9 * b->members[i]->V * es;
+      xs[i] = dalloc(nb);
+      ys[i] = dalloc(nb);
+      dzero(xs[i], nb, b->apply_st);
+      cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    GroupPlan g;
+    if (prec == 1) {
+      batch_prepare<float>(*b);
+      batch_plan<float>(*b, xs.data(), ys.data(), g);
+    } else {
+      batch_prepare<double>(*b);
+      batch_plan<double>(*b, xs.data(), ys.data(), g);
+    }
+    batch_upload(*b, g);
+    long long per_member = 0;
+    for (const auto& r : g.rec) per_member += (long long)r.size();
+    auto member_apply = [&](int i) {
+      fg_ctx& c = *b->members[i];
+      if (prec == 1) op_mech(c, c.pf, (const float*)xs[i], (float*)ys[i], nullptr);
+      else op_mech(c, c.pd, (const double*)xs[i], (double*)ys[i], nullptr);
+    };
+    auto elapsed = [&]() {
+      cudaEventRecord(e1, b->apply_st);
+      dsync(b->apply_st);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      return (double)t / napply;
+    };
+    // warm-up: one grouped application and one per member
+    const long long nl = batch_launch(*b, g);
+    for (int i = 0; i < n; ++i) member_apply(i);
+    for (int i = 0; i < n; ++i) dsync(b->members[i]->st);
+    dsync(b->apply_st);
+    // (0) the grouped launches captured once as a CUDA graph and replayed
+    if (cudaStreamBeginCapture(b->apply_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      fail(FG_ERR_CUDA, "fg_batch_time_apply: stream capture failed");
+    batch_launch(*b, g);
+    if (cudaStreamEndCapture(b->apply_st, &graph) != cudaSuccess ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+      fail(FG_ERR_CUDA, "fg_batch_time_apply: graph capture failed");
+    cudaEventRecord(e0, b->apply_st);
+    for (int k = 0; k < napply; ++k) cudaGraphLaunch(exec, b->apply_st);
+    ms[0] = elapsed();
+    // (1) the grouped launches issued one by one
+    cudaEventRecord(e0, b->apply_st);
+    for (int k = 0; k < napply; ++k) batch_launch(*b, g);
+    ms[1] = elapsed();
+    // (2) each member's own launches, member after member on one stream
+    {
+      std::vector<cudaStream_t> keep(n);
+      for (int i = 0; i < n; ++i) {
+        keep[i] = b->members[i]->st;
+        b->members[i]->st = b->apply_st;
+      }
+      try {
+        cudaEventRecord(e0, b->apply_st);
+        for (int k = 0; k < napply; ++k)
+          for (int i = 0; i < n; ++i) member_apply(i);
+        ms[2] = elapsed();
+      } catch (...) {
+        for (int i = 0; i < n; ++i) b->members[i]->st = keep[i];
+        throw;
+      }
+      for (int i = 0; i < n; ++i) b->members[i]->st = keep[i];
+    }
+    // (3) each member's own launches on its own stream, all members at once
+    cudaEventRecord(e0, b->apply_st);
+    for (int i = 0; i < n; ++i) {
+      cudaStreamWaitEvent(b->members[i]->st, e0, 0);
+      for (int k = 0; k < napply; ++k) member_apply(i);
+      cudaEventRecord(ev[i], b->members[i]->st);
+      cudaStreamWaitEvent(b->apply_st, ev[i], 0);
+    }
+    ms[3] = elapsed();
+    ccheck("fg_batch_time_apply");
+    if (info) {
+      info[0] = (int)g.groups.size();
+      info[1] = (int)nl;
+      info[2] = (int)per_member;
+    }
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
+#endif
+  FG_API_END
+}
+
 void fg_batch_destroy(fg_batch* b) {
   if (!b) return;
+#ifndef FG_EMU
+  if (b->apply_st) {
+    cudaStreamSynchronize(b->apply_st);
+    cudaStreamDestroy(b->apply_st);
+  }
+  for (cudaStream_t s : b->group_st) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->group_ev) cudaEventDestroy(e);
+#endif
+  if (b->dargs) dfree(b->dargs);
   for (size_t k = 0; k < b->members.size(); ++k) {
 #ifndef FG_EMU
     cudaStreamSynchronize(b->own[k]);

@@ -120,6 +120,45 @@ def test_emulated_batch_equals_solo_runs(emu):
     batch.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_emulated_grouped_batch_apply_equals_member_applies(emu, prec):
+    """fg_batch_apply runs each pass once over every member of equal grid (block m P + b of
+    a grouped launch is block b of member m, arguments from a device table): each member's
+    result is bit for bit its own fg_apply, in fewer launches; members of three grids form
+    three groups (two equal-grid members share one)."""
+    ws = [S.sphere(n, r, band=2, nsteps=10, seed=i)
+          for i, (n, r) in enumerate([(8, 0.3), (12, 0.4), (8, 0.35), (16, 0.3)])]
+    members = [B.from_workload(w, lib=emu, precision=B.FG_MIXED) for w in ws]
+    rng = np.random.default_rng(3)
+    dt = np.float32 if prec == 1 else np.float64
+    for m, w in zip(members, ws):  # a state away from the identity
+        F = m.get(B.FIELD_F)
+        m.set(B.FIELD_F, F + 0.01 * rng.standard_normal(F.shape))
+    xs = [rng.standard_normal((9,) + w.shape).astype(dt) for w in ws]
+    solo = []
+    l0 = B.kernel_launches(emu)
+    for m, x in zip(members, xs):
+        y = np.zeros_like(x)
+        m.apply(B.OP_MECH, x, y, prec)
+        solo.append(y)
+    l_solo = B.kernel_launches(emu) - l0
+    batch = B.Batch(members)
+    ys = [np.zeros_like(x) for x in xs]
+    l0 = B.kernel_launches(emu)
+    batch.apply(xs, ys, prec)
+    l_batch = B.kernel_launches(emu) - l0
+    for y, ref in zip(ys, solo):
+        np.testing.assert_array_equal(y, ref)
+        assert np.abs(ref).max() > 0
+    # per member: its state build and its passes; grouped: the state builds, then one
+    # launch per pass and group
+    passes = (l_solo - l_batch) // (len(ws) - 3)
+    assert l_batch < l_solo and passes >= 5
+    with pytest.raises(B.FgError):
+        batch.apply(xs, ys, prec, op=B.OP_PFF)
+    batch.close()
+
+
 @pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
 def test_emulated_mech_adjoint_matches_oracle(emu, law):
     shape = (8, 8, 16)
