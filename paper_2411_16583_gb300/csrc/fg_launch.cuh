@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(K::NT, MinBlocks<K>::value)
 // the GPU, host memory in the emulation), `grid` blocks each.
 template <class K, class A>
 void launch_grouped(const void* args, int members, Dim3 grid, cudaStream_t st) {
+  static_assert(K::NT <= 1024, "a block holds at most 1024 threads");
   const size_t sm = K::smem_bytes();
   ++launch_counter();
   const A* av = (const A*)args;
@@ -134,6 +135,7 @@ void launch_grouped(const void* args, int members, Dim3 grid, cudaStream_t st) {
 // number of blocks launched (the number of partial sums a reducing kernel writes).
 template <class K, class A>
 int launch_pass(const A& a, Dim3 grid, cudaStream_t st) {
+  static_assert(K::NT <= 1024, "a block holds at most 1024 threads");
   if (std::vector<RecordedLaunch>* rec = launch_recorder()) {
     RecordedLaunch r;
     r.grouped = &launch_grouped<K, A>;

@@ -567,23 +567,25 @@ struct YPass {
 };
 
 // ------------------------------------------------------------------ register-direct passes
-// For N = RAD^2 (two equal radix stages, e.g. 64 = 8 x 8, 256 = 16 x 16) the first stage
-// reads its butterfly inputs straight from global memory into registers and the last
+// For a two-stage plan N = R0 R1 (64 = 8 x 8, 256 = 16 x 16, 128 = 16 x 8, 48 = 16 x 3,
+// 80 = 16 x 5, ...) the first stage reads its butterfly inputs straight from global memory
+// into registers (T0 = N / R0 butterflies per row) and the last
 // stage writes its outputs straight to global memory: every element crosses shared
 // memory once between the stages.  Thread-to-row maps are chosen per stage so that the
 // global side of each stage is coalesced (row-fastest for transposed layouts).
 
 template <int N>
-struct Square {
+struct Square {  // two-stage plans N = R0 R1: register-direct Y and Z passes
   static constexpr Plan P = make_plan(N);
-  static constexpr bool OK = P.S == 2 && P.r[0] == P.r[1];
-  static constexpr int RAD = P.r[0];
-  static constexpr int T = N / RAD;  // butterflies per row and stage
+  static constexpr bool OK = P.S == 2;
+  static constexpr int R0 = P.r[0], R1 = P.r[1];
+  static constexpr int T0 = N / R0, T1 = N / R1;  // butterflies per row in stage 0 and 1
+  static constexpr int RM = R0 > R1 ? R0 : R1, TM = T0 > T1 ? T0 : T1;
 };
 
-// stage 0 (Ns = 1): v holds x[b + r T]; outputs go to positions b RAD + r
-// stage 1 (Ns = RAD): v holds positions b + r T, twiddle exp(-+ 2 pi i r b / N); outputs
-// land in natural order at b + r T
+// stage 0 (Ns = 1): v holds x[b + r T0], r < R0; outputs go to positions b R0 + r
+// stage 1 (Ns = R0): v holds positions b + r T1, r < R1 (T1 = N / R1 = R0), twiddle
+// exp(-+ 2 pi i r b / N); outputs land in natural order at b + r T1
 template <typename C, int RAD, bool INV>
 FG_DEV void square_stage1_twiddle(C* v, const C* tw, int b) {
 #pragma unroll
@@ -597,12 +599,14 @@ template <typename R, int N, bool INV>
 struct YPassD {
   using C = cplx<R>;
   using SQ = Square<N>;
-  static constexpr int RAD = SQ::RAD, T = SQ::T;
-  static constexpr int ROWS = rows_y(N, sizeof(C));
-  static constexpr int NT = round32(ROWS * T);
+  static constexpr int R0 = SQ::R0, R1 = SQ::R1, T0 = SQ::T0, T1 = SQ::T1;
+  // rows per block: the shared-memory budget of rows_y, at most 512 threads
+  static constexpr int ROWS_M = rows_y(N, sizeof(C));
+  static constexpr int ROWS = ROWS_M * SQ::TM <= 512 ? ROWS_M : (512 / SQ::TM > 0 ? 512 / SQ::TM : 1);
+  static constexpr int NT = round32(ROWS * SQ::TM);
   static constexpr int PITCH = row_pitch(N);
   struct Locals {
-    C v[RAD];
+    C v[SQ::RM];
     Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(ROWS * PITCH + N) * sizeof(C); }
@@ -626,38 +630,38 @@ struct YPassD {
     const bool rfast = a.nz >= 4;
     FG_PHASE(NT)
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
-    if (tid < ROWS * T) {
+    if (tid < ROWS * T0) {
       int rho, b;  // inputs: transposed layout row-fastest, contiguous rows butterfly-fastest
       if (INV && rfast) { rho = tid % ROWS; b = tid / ROWS; }
-      else { b = tid % T; rho = tid / T; }
+      else { b = tid % T0; rho = tid / T0; }
       if (rho < nr) {
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-          const int n = b + r * T;
+        for (int r = 0; r < R0; ++r) {
+          const int n = b + r * T0;
           L.v[r] = in[INV ? tpos(row0 + rho, n, a.nz) : (long long)(row0 + rho) * N + n];
         }
       } else {
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) L.v[r] = cmk<C>((R)0, (R)0);
+        for (int r = 0; r < R0; ++r) L.v[r] = cmk<C>((R)0, (R)0);
       }
-      Dft<RAD, INV, C>::run(L.v);
+      Dft<R0, INV, C>::run(L.v);
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) tile[rho * PITCH + pad16(b * RAD + r)] = L.v[r];
+      for (int r = 0; r < R0; ++r) tile[rho * PITCH + pad16(b * R0 + r)] = L.v[r];
     }
     FG_END_PHASE
     FG_PHASE(NT)
-    if (tid < ROWS * T) {
+    if (tid < ROWS * T1) {
       int rho, b;  // outputs: transposed layout row-fastest
       if (!INV && rfast) { rho = tid % ROWS; b = tid / ROWS; }
-      else { b = tid % T; rho = tid / T; }
+      else { b = tid % T1; rho = tid / T1; }
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) L.v[r] = tile[rho * PITCH + pad16(b + r * T)];
-      square_stage1_twiddle<C, RAD, INV>(L.v, tw, b);
-      Dft<RAD, INV, C>::run(L.v);
+      for (int r = 0; r < R1; ++r) L.v[r] = tile[rho * PITCH + pad16(b + r * T1)];
+      square_stage1_twiddle<C, R1, INV>(L.v, tw, b);
+      Dft<R1, INV, C>::run(L.v);
       if (rho < nr) {
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-          const int n = b + r * T;
+        for (int r = 0; r < R1; ++r) {
+          const int n = b + r * T1;
           out[INV ? (long long)(row0 + rho) * N + n : tpos(row0 + rho, n, a.nz)] = L.v[r];
         }
       }
@@ -671,15 +675,18 @@ template <typename R, int N, class Op, int RZ = 0>
 struct ZPassD {
   using C = cplx<R>;
   using SQ = Square<N>;
-  static constexpr int RAD = SQ::RAD, T = SQ::T;
+  static constexpr int R0 = SQ::R0, R1 = SQ::R1, T0 = SQ::T0, T1 = SQ::T1;
   static constexpr int CI = Op::CIN;
   static constexpr int CO = Op::COUT;
   static constexpr int CM = CI > CO ? CI : CO;
-  static constexpr int ROWS = RZ > 0 ? RZ : rows_z(N, CM, sizeof(C));
-  static constexpr int NT = round32(CM * ROWS * T);
+  // rows per block: the shared-memory budget of rows_z, at most 1024 threads
+  static constexpr int ROWS_M = rows_z(N, CM, sizeof(C));
+  static constexpr int ROWS_T = 1024 / (CM * SQ::TM) > 0 ? 1024 / (CM * SQ::TM) : 1;
+  static constexpr int ROWS = RZ > 0 ? RZ : (ROWS_M < ROWS_T ? ROWS_M : ROWS_T);
+  static constexpr int NT = round32(CM * ROWS * SQ::TM);
   static constexpr int PITCH = row_pitch(N);
   struct Locals {
-    C v[RAD];
+    C v[SQ::RM];
     Acc<R> acc;
   };
   static size_t smem_bytes() { return (size_t)(CM * ROWS * PITCH + N) * sizeof(C); }
@@ -695,34 +702,34 @@ struct ZPassD {
     // forward stage 0 from global
     FG_PHASE(NT)
     for (int m = tid; m < N; m += NT) tw[m] = a.tw[m];
-    if (tid < CI * ROWS * T) {
-      const int b = tid % T, q = tid / T;  // q = c ROWS + rho
+    if (tid < CI * ROWS * T0) {
+      const int b = tid % T0, q = tid / T0;  // q = c ROWS + rho
       const int rho = q % ROWS, c = q / ROWS;
       if (rho < nr) {
         const C* in = a.cin + c * a.VH + (long long)(row0 + rho) * N;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) L.v[r] = in[b + r * T];
+        for (int r = 0; r < R0; ++r) L.v[r] = in[b + r * T0];
       } else {
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) L.v[r] = cmk<C>((R)0, (R)0);
+        for (int r = 0; r < R0; ++r) L.v[r] = cmk<C>((R)0, (R)0);
       }
-      Dft<RAD, false, C>::run(L.v);
+      Dft<R0, false, C>::run(L.v);
       C* t = tile + q * PITCH;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) t[pad16(b * RAD + r)] = L.v[r];
+      for (int r = 0; r < R0; ++r) t[pad16(b * R0 + r)] = L.v[r];
     }
     FG_END_PHASE
     // forward stage 1 in place (each thread reads and writes the same positions)
     FG_PHASE(NT)
-    if (tid < CI * ROWS * T) {
-      const int b = tid % T, q = tid / T;
+    if (tid < CI * ROWS * T1) {
+      const int b = tid % T1, q = tid / T1;
       C* t = tile + q * PITCH;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
-      square_stage1_twiddle<C, RAD, false>(L.v, tw, b);
-      Dft<RAD, false, C>::run(L.v);
+      for (int r = 0; r < R1; ++r) L.v[r] = t[pad16(b + r * T1)];
+      square_stage1_twiddle<C, R1, false>(L.v, tw, b);
+      Dft<R1, false, C>::run(L.v);
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) t[pad16(b + r * T)] = L.v[r];
+      for (int r = 0; r < R1; ++r) t[pad16(b + r * T1)] = L.v[r];
     }
     FG_END_PHASE
     // frequency-space operator on all components of each (row, kz)
@@ -742,36 +749,36 @@ struct ZPassD {
     FG_END_PHASE
     // inverse stage 0: read, then write after the barrier
     FG_PHASE(NT)
-    if (tid < CO * ROWS * T) {
-      const int b = tid % T, q = tid / T;
+    if (tid < CO * ROWS * T0) {
+      const int b = tid % T0, q = tid / T0;
       const C* t = tile + q * PITCH;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
-      Dft<RAD, true, C>::run(L.v);
+      for (int r = 0; r < R0; ++r) L.v[r] = t[pad16(b + r * T0)];
+      Dft<R0, true, C>::run(L.v);
     }
     FG_END_PHASE
     FG_PHASE(NT)
-    if (tid < CO * ROWS * T) {
-      const int b = tid % T, q = tid / T;
+    if (tid < CO * ROWS * T0) {
+      const int b = tid % T0, q = tid / T0;
       C* t = tile + q * PITCH;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) t[pad16(b * RAD + r)] = L.v[r];
+      for (int r = 0; r < R0; ++r) t[pad16(b * R0 + r)] = L.v[r];
     }
     FG_END_PHASE
     // inverse stage 1 straight to global
     FG_PHASE(NT)
-    if (tid < CO * ROWS * T) {
-      const int b = tid % T, q = tid / T;
+    if (tid < CO * ROWS * T1) {
+      const int b = tid % T1, q = tid / T1;
       const int rho = q % ROWS, c = q / ROWS;
       const C* t = tile + q * PITCH;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) L.v[r] = t[pad16(b + r * T)];
-      square_stage1_twiddle<C, RAD, true>(L.v, tw, b);
-      Dft<RAD, true, C>::run(L.v);
+      for (int r = 0; r < R1; ++r) L.v[r] = t[pad16(b + r * T1)];
+      square_stage1_twiddle<C, R1, true>(L.v, tw, b);
+      Dft<R1, true, C>::run(L.v);
       if (rho < nr) {
         C* o = a.cout + c * a.VH + (long long)(row0 + rho) * N;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) o[b + r * T] = L.v[r];
+        for (int r = 0; r < R1; ++r) o[b + r * T1] = L.v[r];
       }
     }
     FG_END_PHASE

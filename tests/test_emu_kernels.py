@@ -22,11 +22,13 @@ def emu():
 
 
 # (64, 16, 16), (256, 8, 8), (8, 256, 8): the register-direct Y and Z passes (64 = 8 x 8,
-# 256 = 16 x 16), including ragged row tiles; (1, 8, 256): the X passes at the benchmark's
-# row length
+# 256 = 16 x 16), including ragged row tiles; (8, 12, 16), (12, 8, 8), (48, 24, 8),
+# (32, 48, 8): the same passes for two-stage plans of unequal radices (12 = 4 x 3,
+# 24 = 8 x 3, 32 = 8 x 4, 48 = 16 x 3); (1, 8, 256): the X passes at the benchmark's row
+# length
 @pytest.mark.parametrize("shape", [(8, 12, 16), (1, 16, 24), (12, 8, 8), (64, 16, 16),
                                    (256, 8, 8), (8, 256, 8), (1, 64, 16), (1, 100, 100),
-                                   (1, 8, 256)])
+                                   (1, 8, 256), (48, 24, 8), (32, 48, 8)])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
 def test_emulated_operators_match_oracle(emu, shape, prec, law):
