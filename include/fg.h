@@ -435,8 +435,8 @@ void fg_destroy(fg_ctx* ctx);
  * Limits: nx even, every edge <= 64 (so V <= 262,144) and a compiled transform length;
  * larger grids return FG_ERR_INVALID without touching the GPU.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current, so make the first call on a device before any stream capture.  Every call
- * reuses the same array and leaves the last call's contents in it; calls that overlap on
+ * current.  Every call copies its inputs from host memory and waits for its work.  Every
+ * call reuses the same array and leaves the last call's contents in it; calls that overlap on
  * the GPU (other streams, other host threads) race on it.  No cudaMalloc, cudaFree or
  * other allocating routine is called.  Errors: FG_ERR_INVALID, FG_ERR_DOMAIN
  * (det F <= 0 or J_c <= 0), FG_ERR_CUDA; message in fg_last_error().
