@@ -303,7 +303,8 @@ void fg_batch_destroy(fg_batch* batch);
  * pointers in the emulation build), owned by the caller.  Builds each member's tangent
  * state from its F first (as fg_apply does).  Runs on a stream of the batch and returns
  * after the applications completed; the members' streams are synchronised first.  Errors:
- * FG_ERR_INVALID (op other than FG_OP_MECH, bad precision, a null vector), FG_ERR_CUDA.
+ * FG_ERR_INVALID (op other than FG_OP_MECH, bad precision, a null vector, members on
+ * different devices), FG_ERR_CUDA.
  *
  * fg_batch_time_apply times napply applications of every member's operator (zero inputs in
  * buffers of its own) four ways and writes milliseconds per batch application to ms:

@@ -3025,6 +3025,9 @@ static void batch_plan(fg_batch& b, const void* const* x, void* const* y, GroupP
 }
 
 static void batch_stream(fg_batch& b) {
+  for (const fg_ctx* c : b.members)
+    if (c->device != b.members[0]->device)
+      fail(FG_ERR_INVALID, "batch apply: the members live on different devices");
 #ifndef FG_EMU
   cudaSetDevice(b.members[0]->device);
   if (!b.apply_st && cudaStreamCreateWithFlags(&b.apply_st, cudaStreamNonBlocking) != cudaSuccess)
