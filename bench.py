@@ -37,7 +37,7 @@ UNIT = "voxel-steps/s"
 MEASURED_TRAFFIC_B_PER_VOXEL = {"xi": 203.6, "xf": 181.2}
 
 
-# SURVEY's algorithmic minimum of one FP32 mechanical operator application, per voxel:
+# algorithmic minimum of one FP32 mechanical operator application, per voxel:
 # read x (9 x 4 B) and the state (F 9 x 4 B, c, d, phase), write y (9 x 4 B)
 MECH_ALG_B_PER_VOXEL = 116.0
 # DRAM bytes per voxel that ncu measured over the five kernels of one FP32 mechanical
@@ -558,7 +558,7 @@ def run_ours(a, rank, world, local, dist, stream):
                "h2d_bytes_per_step": 12 * V * 8,
                "d2h_bytes_per_step": 11 * V * 8}
 
-    # fused matvec rates (SURVEY's measurement: 50 applies after 5 warm-ups, CUDA events):
+    # fused matvec rates (50 applications after 5 warm-ups, CUDA events):
     # the FP32 operators of the mixed context, and the cuFFT comparator of the mechanical one
     sol.time_apply(B.OP_MECH, 1, 5)
     mech32_ms = sol.time_apply(B.OP_MECH, 1, 50)
@@ -608,7 +608,7 @@ def run_ours(a, rank, world, local, dist, stream):
                                     "alg_bytes_per_voxel": sb[s],
                                     "gbs": sb[s] * V * vol / (t * 1e-3) / 1e9,
                                     "frac_of_peak": sb[s] * V * vol / (t * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-    # the roofline of SURVEY's measurement: one fused mechanical operator application (five
+    # the roofline: one fused mechanical operator application (five
     # pass kernels) moves at least 116 B per voxel (read x and the state, write y)
     ach = MECH_ALG_B_PER_VOXEL * V / (mech32_ms * 1e-3) / 1e9
     line = {
