@@ -31,10 +31,12 @@ Readings of points the paper leaves open:
 * toughness and strength may vary per voxel, g_c(x) = g_c exp(log_gc) and
   sigma_max(x) = sigma_max exp(log_smax) (Sec. 5.1 draws the strength per voxel).
 
-Parity status: every function below is pinned by ``tests/test_oracle_*.py``
-except the composition of a whole coupled step (Alg. 4), which is pinned only
-through its parts and its invariants (mass balance, monotone history, converged
-residual) -- "parity unpinned" for the coupled step as a whole.
+Parity status: every function below is pinned by ``tests/test_oracle_*.py``.  The
+composition of a whole coupled step (Alg. 4) is an iteration; it is pinned by the
+equations its result must solve (the Fick residual with F and d frozen at the step's
+start, mechanical equilibrium, the history field, the phase-field system, each through
+the separately pinned functions), by a homogeneous case in closed form and by invariants
+(mass balance, monotone history).
 """
 from __future__ import annotations
 

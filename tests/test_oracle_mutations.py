@@ -214,3 +214,36 @@ def test_crack_energy_without_voxel_volume_is_caught(monkeypatch):
                         lambda d, prm, gc_field=None: good(d, prm, gc_field) / prm.h[2] * prm.h[0])
     with pytest.raises(AssertionError):
         TS.test_crack_energy_closed_form()
+
+
+def test_phase_field_with_half_driving_term_is_caught(monkeypatch):
+    from tests import test_oracle_solvers as TSO
+    good = O.pff_solve
+
+    def bad(H, d0, prm, tol, maxit, stats=None):  # solves A d = H instead of 2H
+        return good(0.5 * H, d0, prm, tol, maxit, stats)
+    monkeypatch.setattr(O, "pff_solve", bad)
+    with pytest.raises(AssertionError):
+        TSO.test_coupled_step_output_solves_the_step_equations()
+
+
+def test_chemistry_with_half_time_step_is_caught(monkeypatch):
+    from tests import test_oracle_solvers as TSO
+    good = O.chem_solve
+
+    def bad(c_t, F, d_t, dt, *args, **kw):  # the Fick step advanced by dt / 2
+        return good(c_t, F, d_t, 0.5 * dt, *args, **kw)
+    monkeypatch.setattr(O, "chem_solve", bad)
+    with pytest.raises(AssertionError):
+        TSO.test_coupled_step_output_solves_the_step_equations()
+
+
+def test_chemistry_with_final_damage_is_caught(monkeypatch):
+    from tests import test_oracle_solvers as TSO
+    good = O.chem_solve
+
+    def bad(c_t, F, d_t, dt, *args, **kw):  # the mobility from a damage field not d_t
+        return good(c_t, F, np.clip(d_t + 0.5, 0.0, 0.9), dt, *args, **kw)
+    monkeypatch.setattr(O, "chem_solve", bad)
+    with pytest.raises(AssertionError):
+        TSO.test_coupled_step_output_solves_the_step_equations()

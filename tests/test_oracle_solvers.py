@@ -395,6 +395,57 @@ def test_coupled_steps_invariants():
     assert st.H.max() > 0.0  # the band's swelling mismatch reaches the damage threshold
 
 
+def _cracking_disc():
+    shape = (1, 16, 16)
+    y, x = np.meshgrid(np.arange(16) - 7.5, np.arange(16) - 7.5, indexing="ij")
+    part = (x * x + y * y <= 36.0)[None]
+    pid = np.where(part, 0, 1)
+    phases = [O.Phase(E=10e9, Omega=0.1 / 0.99, D=1e-14, sigma_max=25e6),
+              O.Phase(E=10e6, Omega=0.0, D=1e-19, sigma_max=25e6)]
+    prm = O.make_params(phases, pid, H, gc=1.0, lc=2e-7)
+    src = np.where(part & ~((x * x + y * y) <= 9.0)[None], 0.05, 0.0)
+    return prm, O.CoupledState(prm, np.full(shape, 0.01), src), src
+
+
+def step_equation_residuals(prm, src, dt, before, after):
+    """Residuals of the equations that define one step of Alg. 4, at the state it returned:
+    the Fick residual (Eq. Chemresidualfc, relative to |c_t|) with F and d frozen at the
+    step's start (Alg. 3; F-bar unchanged, so F at the start is F_t) and K_c from
+    (F_t, c_t, d_t); err_res (Eq. mechresiduum) of the final (F, c, d); the history field
+    against max(H_t, psi_c D_f(F, c)) (Eq. Hist); the phase-field system of Eq. PFFA with
+    that history (relative to |2H|)."""
+    F_t, c_t, d_t, H_t = before
+    F, c, d, Hf = after
+    Kc = O.chem_conductivity(F_t, c_t, d_t, prm)
+    f = O.chem_residual(c, c_t, F_t, d_t, Kc, dt, src, prm)
+    _, err = O.mech_residual(F, c, d, prm, np.eye(3))
+    Hh = O.history_update(H_t, F, c, prm)
+    Heff = Hf / O.gc_ratio(prm)
+    rd = O.pff_apply(d, Heff, prm) - 2.0 * Heff
+    return (np.linalg.norm(f) / np.linalg.norm(c_t), err,
+            np.abs(Hf - Hh).max() / max(np.abs(Hh).max(), 1e-300),
+            np.linalg.norm(rd) / max(np.linalg.norm(2.0 * Heff), 1e-300))
+
+
+def test_coupled_step_output_solves_the_step_equations():
+    """The state a coupled step returns is the fixed point Alg. 4 defines (the iteration is
+    judged by the equations it solves, not by its own stopping tests): three steps of the
+    cracking disc, the last with damage, each within the solver tolerances of every
+    equation of the step (default tolerances: Newton 1e-9, Krylov 1e-10; the Fick Newton
+    stops on |dc| / |c_t| < 1e-9, which leaves a residual below that)."""
+    prm, st, src = _cracking_disc()
+    for k in range(3):
+        before = (st.F.copy(), st.c.copy(), st.d.copy(), st.H.copy())
+        st.step(1.0, np.eye(3))
+        r_chem, r_mech, r_hist, r_pff = step_equation_residuals(
+            prm, src, 1.0, before, (st.F, st.c, st.d, st.H))
+        assert r_chem <= 1e-9, (k, r_chem)
+        assert r_mech <= 1e-9, (k, r_mech)
+        assert r_hist <= 1e-13, (k, r_hist)
+        assert r_pff <= 1e-10, (k, r_pff)
+    assert st.d.max() > 1e-3  # the last step was checked with damage
+
+
 def test_cg_truncates_at_nonpositive_curvature():
     """On an indefinite operator CG returns the iterate before the first search direction
     of non-positive curvature: here diag(3, 1, -2) with b = (1, 1, 1), worked by hand.
