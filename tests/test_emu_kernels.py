@@ -161,6 +161,39 @@ def test_emulated_grouped_batch_apply_equals_member_applies(emu, prec):
     batch.close()
 
 
+def test_emulated_grouped_batch_apply_keeps_member_settings(emu):
+    """Members of one grid that differ in law (Saint-Venant-Kirchhoff against Neo-Hookean)
+    run in separate groups, and a member under mixed stress control keeps its projection
+    (the kept zero modes): every result is still bit for bit the member's own fg_apply."""
+    ws = [S.sphere(8, 0.3, band=2, nsteps=10, seed=0),
+          S.sphere(8, 0.35, band=2, nsteps=10, seed=1, phases=S.default_phases(law=S.LAW_SVK)),
+          S.sphere(8, 0.4, band=2, nsteps=10, seed=2)]
+    members = [B.from_workload(w, lib=emu, precision=B.FG_MIXED) for w in ws]
+    mask = np.zeros((3, 3), dtype=bool)
+    mask[1, 1] = mask[0, 2] = True
+    members[2].stress_control(mask, np.zeros((3, 3)))
+    rng = np.random.default_rng(4)
+    xs = [rng.standard_normal((9,) + w.shape).astype(np.float32) for w in ws]
+    solo = []
+    for m, x in zip(members, xs):
+        y = np.zeros_like(x)
+        m.apply(B.OP_MECH, x, y, 1)
+        solo.append(y)
+    batch = B.Batch(members)
+    ys = [np.zeros_like(x) for x in xs]
+    l0 = B.kernel_launches(emu)
+    batch.apply(xs, ys, 1)
+    l_batch = B.kernel_launches(emu) - l0
+    for y, ref in zip(ys, solo):
+        np.testing.assert_array_equal(y, ref)
+    members[2].stress_control(None)
+    y_free = np.zeros_like(xs[2])
+    members[2].apply(B.OP_MECH, xs[2], y_free, 1)
+    assert np.abs(y_free - ys[2]).max() > 0  # the mask changed that member's result
+    batch.close()
+    assert l_batch > 0
+
+
 @pytest.mark.parametrize("law", [S.LAW_NEOHOOKE, S.LAW_SVK])
 def test_emulated_mech_adjoint_matches_oracle(emu, law):
     shape = (8, 8, 16)
